@@ -1,0 +1,37 @@
+"""Build the FP64 CPU oracle (test infrastructure only).
+
+Compiles ``fdtd_oracle.c`` with gcc, ``-O2 -ffp-contract=off`` (no fused
+multiply-add: every operation rounds on its own, as written) and OpenMP when
+available, into ``oracle/_build/liboracle.so``.  Only the tests, the smoke check
+and the benchmark's CPU-baseline leg use it.
+"""
+from __future__ import annotations
+
+import os
+import subprocess
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+SRC = os.path.join(HERE, "fdtd_oracle.c")
+OUT_DIR = os.path.join(HERE, "_build")
+LIB = os.path.join(OUT_DIR, "liboracle.so")
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle if it is missing or older than its source; return the path."""
+    os.makedirs(OUT_DIR, exist_ok=True)
+    if (not force and os.path.exists(LIB)
+            and os.path.getmtime(LIB) >= os.path.getmtime(SRC)):
+        return LIB
+    base = ["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
+            "-std=c11", "-D_GNU_SOURCE", SRC, "-o", LIB + ".tmp", "-lm"]
+    try:
+        subprocess.run(base[:1] + ["-fopenmp"] + base[1:], check=True,
+                       capture_output=True, text=True)
+    except subprocess.CalledProcessError:
+        subprocess.run(base, check=True, capture_output=True, text=True)
+    os.replace(LIB + ".tmp", LIB)
+    return LIB
+
+
+if __name__ == "__main__":
+    print(build(force=True))

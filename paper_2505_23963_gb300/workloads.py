@@ -1,0 +1,187 @@
+"""Seeded synthetic inputs for the FDTD-Bath path.
+
+This module only builds problem descriptions -- grid sizes, planar material
+layers with their Lorentz / Drude / Lorentz-Bath parameters, Gaussian-pulse
+sources, DFT monitors and random initial states -- as plain dicts and numpy
+arrays.  It performs none of the method's arithmetic (no field, polarization,
+bath, absorber or DFT update) and imports nothing else from this package, so
+both the CUDA library's binding and the CPU oracle can consume its output.
+
+Conventions: c = eps0 = mu0 = 1; lengths in units of a with dx = 1/resolution
+and dt = courant * dx; every frequency-like parameter (frequency, gamma, sigma
+is dimensionless, bath frequencies/dampings/couplings, pulse centre and width,
+DFT frequencies) is in nu-units (nu = omega / 2 pi), the unit MEEP and the paper
+use.  Grids are [nz][ny][nx] with x fastest, periodic in x and y, with the
+absorber and all layers stacked along z.
+
+Problem dict keys:
+    n=(nx, ny, nz), resolution, courant, pml (cells at each z end),
+    materials=[{kind, z=(lo, hi), eps_inf, frequency, gamma, sigma,
+                bath_frequencies, bath_gammas, bath_couplings}],
+    sources=[{component, z, center, fwidth, amplitude, t0, phase (ny, nx) or None}],
+    monitors=[{z, freqs}], energy_box=(lo, hi), steps, name.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+
+def ohmic_bath(num_bath: int, freqs: np.ndarray, frequency: float, dephasing: float,
+               width: float, bath_gamma: float):
+    """Bath arrays for the 'Ohmic-like' weighted coupling used by the cavity workloads.
+
+    Frequencies are given; dampings are all ``bath_gamma``; couplings are
+    k_j = k_b sqrt(w_j) with the weight w_j = (f_j/f0) exp(1 - f_j/f0) and the
+    uniform-bath scale k_b = sqrt(2 df / pi * dephasing), df = width / (N - 1).
+    """
+    freqs = np.asarray(freqs, dtype=np.float64)
+    df = width / (num_bath - 1)
+    kb = math.sqrt(2.0 * df / math.pi * dephasing)
+    wgt = (freqs / frequency) * np.exp(1.0 - freqs / frequency)
+    return freqs, np.full(num_bath, float(bath_gamma)), kb * np.sqrt(wgt)
+
+
+def pulse_t0(fwidth: float) -> float:
+    """Pulse delay: five Gaussian widths, tau = 1/(2 pi fwidth)."""
+    return 5.0 / (2.0 * math.pi * fwidth)
+
+
+def slab_cavity(nx: int, ny: int, layout, resolution: float, *, num_bath: int, sigma: float,
+                bath_seed: int | None = None, phase_seed: int | None = 0,
+                src_z: int | None = None, mon_z: int | None = None, nfreq: int = 256,
+                steps: int = 100, name: str = "slab", drude_sigma: float = 25.0,
+                drude_gamma: float = 0.01, gamma0: float = 0.01, bath_gamma: float = 0.005,
+                dephasing: float = 0.01, courant: float = 0.5, source_component: int = 0,
+                phase_scale: float = math.pi / 8.0) -> dict:
+    """Planar Fabry-Perot cavity: CPML | vacuum | Drude | Lorentz-Bath | Drude | vacuum | CPML.
+
+    ``layout`` = (pml, vac_left, mirror, layer, mirror, vac_right) in cells along z.
+    Bath frequencies are linspace(0.9, 1.1) or, with ``bath_seed``, uniform in
+    [0.9, 1.1] from numpy.random.default_rng(bath_seed).  The source is an Ex
+    plane in the left vacuum with a per-(x,y) phase (pi/8) U[-1, 1] drawn from
+    default_rng(phase_seed) (None: zero phase).
+    """
+    pml, vl, mir, lay, mir2, vr = (int(v) for v in layout)
+    nz = pml + vl + mir + lay + mir2 + vr + pml
+    z_m1 = pml + vl
+    z_lb = z_m1 + mir
+    z_m2 = z_lb + lay
+    z_end = z_m2 + mir2
+    if num_bath > 0:
+        if bath_seed is None:
+            bf = np.linspace(0.9, 1.1, num_bath)
+        else:
+            bf = np.random.default_rng(bath_seed).uniform(0.9, 1.1, num_bath)
+        bf, bg, bk = ohmic_bath(num_bath, bf, 1.0, dephasing, 0.2, bath_gamma)
+        layer = dict(kind="lorentz_bath", z=(z_lb, z_m2), eps_inf=1.0, frequency=1.0,
+                     gamma=gamma0, sigma=sigma, bath_frequencies=bf, bath_gammas=bg,
+                     bath_couplings=bk)
+    else:
+        layer = dict(kind="lorentz", z=(z_lb, z_m2), eps_inf=1.0, frequency=1.0, gamma=gamma0,
+                     sigma=sigma)
+    mats = []
+    if mir > 0:
+        mats.append(dict(kind="drude", z=(z_m1, z_lb), eps_inf=1.0, frequency=1.0,
+                         gamma=drude_gamma, sigma=drude_sigma))
+    if lay > 0:
+        mats.append(layer)
+    if mir2 > 0:
+        mats.append(dict(kind="drude", z=(z_m2, z_end), eps_inf=1.0, frequency=1.0,
+                         gamma=drude_gamma, sigma=drude_sigma))
+    if src_z is None:
+        src_z = pml + max(1, vl // 3)
+    if mon_z is None:
+        mon_z = nz - pml - max(1, vr // 3)
+    phase = None
+    if phase_seed is not None and nx * ny > 1:
+        rng = np.random.default_rng(phase_seed)
+        phase = phase_scale * rng.uniform(-1.0, 1.0, size=(ny, nx))
+    fwidth = 0.5
+    return dict(
+        name=name, n=(nx, ny, nz), resolution=float(resolution), courant=float(courant), pml=pml,
+        materials=mats,
+        sources=[dict(component=source_component, z=src_z, center=1.0, fwidth=fwidth,
+                      amplitude=1.0, t0=pulse_t0(fwidth), phase=phase)],
+        monitors=[dict(z=mon_z, freqs=np.linspace(0.5, 1.5, nfreq))],
+        energy_box=(z_lb, z_m2), steps=int(steps))
+
+
+# ----------------------------------------------------------------- named workloads
+def cavity_1d(steps: int = 20000) -> dict:
+    """1D Fabry-Perot, plain method: Nz = 2000 at resolution 100, Courant 0.5, two 20-cell
+    Drude mirrors around an 800-cell Lorentz-Bath layer (f0 = 1, gamma0 = 0.01, sigma =
+    0.05^2 for a Rabi splitting of 0.05 f0), N_b = 16 bath modes with frequencies from
+    default_rng(0) uniform in [0.9, 1.1], bath damping 0.005, Ohmic-like couplings;
+    16-cell CPML, pulse centred at 1.0 with width 0.5, 500 DFT frequencies."""
+    p = slab_cavity(1, 1, (16, 564, 20, 800, 20, 564), 100.0, num_bath=16, sigma=0.05 ** 2,
+                    bath_seed=0, phase_seed=None, src_z=40, mon_z=1960, nfreq=500, steps=steps,
+                    name="cavity1d_nz2000_nb16")
+    return p
+
+
+def slab_3d(steps: int = 4000) -> dict:
+    """3D slab cavity: 256^3 at resolution 32, periodic x/y, 16-cell CPML in z, 8-cell Drude
+    mirrors around a 64-cell (1/4 of z) Lorentz-Bath layer with N_b = 8 (frequencies
+    linspace(0.9, 1.1)), sigma = 0.05^2; Ex plane source at z = 24 with a seeded random
+    transverse phase; 256 DFT frequencies at z = 232."""
+    return slab_cavity(256, 256, (16, 72, 8, 64, 8, 72), 32.0, num_bath=8, sigma=0.05 ** 2,
+                       phase_seed=0, src_z=24, mon_z=232, nfreq=256, steps=steps,
+                       name="slab3d_256cubed_nb8")
+
+
+def precision_3d(steps: int = 3000) -> dict:
+    """Precision form: 512 x 512 x 384 at resolution 48, N_b = 16, sigma = 0.1^2 (Rabi 0.1)."""
+    return slab_cavity(512, 512, (16, 120, 8, 96, 8, 120), 48.0, num_bath=16, sigma=0.1 ** 2,
+                       phase_seed=0, src_z=40, mon_z=344, nfreq=256, steps=steps,
+                       name="precision3d_512x512x384_nb16")
+
+
+def precision_crop(steps: int = 400) -> dict:
+    """64^3 crop of the precision form at resolution 8 (layer 16, mirrors 2, CPML 16)."""
+    return slab_cavity(64, 64, (16, 6, 2, 16, 2, 6), 8.0, num_bath=16, sigma=0.1 ** 2,
+                       phase_seed=0, src_z=18, mon_z=46, nfreq=256, steps=steps,
+                       name="crop64_nb16")
+
+
+def small_3d(nx=40, ny=12, layout=(6, 5, 3, 10, 3, 5), nb=8, steps=60, seed=0) -> dict:
+    """Small 3D case with ragged x/y tiles for element-wise parity against the oracle."""
+    return slab_cavity(nx, ny, layout, 10.0, num_bath=nb, sigma=0.05 ** 2, bath_seed=seed,
+                       phase_seed=seed, nfreq=16, steps=steps, name=f"small3d_{nx}x{ny}_nb{nb}")
+
+
+# ----------------------------------------------------------------- random states
+def random_state(prob: dict, seed: int, scale: float = 1e-2, with_bath: bool = True) -> dict:
+    """Seeded random E, H, P (two levels) and Y (two levels) for every material cell.
+
+    Returns {("E", c): arr, ("H", c): arr, ("P", c): arr, ("Pm", c): arr,
+    ("Y", c, j, level): arr}; material-only quantities are zero outside their
+    layers.  Arrays are float64 with shape (nz, ny, nx)."""
+    nx, ny, nz = prob["n"]
+    rng = np.random.default_rng(seed)
+    shp = (nz, ny, nx)
+    st = {}
+    for c in range(3):
+        st[("E", c)] = scale * rng.standard_normal(shp)
+        st[("H", c)] = scale * rng.standard_normal(shp)
+    mask = np.zeros(shp, dtype=bool)
+    for m in prob["materials"]:
+        mask[m["z"][0]:m["z"][1]] = True
+    for c in range(3):
+        st[("P", c)] = np.where(mask, 0.1 * scale * rng.standard_normal(shp), 0.0)
+        st[("Pm", c)] = np.where(mask, 0.1 * scale * rng.standard_normal(shp), 0.0)
+    if with_bath:
+        for m in prob["materials"]:
+            if m["kind"] != "lorentz_bath":
+                continue
+            lo, hi = m["z"]
+            for c in range(3):
+                for j in range(len(m["bath_frequencies"])):
+                    for lvl in (0, 1):
+                        a = st.get(("Y", c, j, lvl))
+                        if a is None:
+                            a = np.zeros(shp)
+                            st[("Y", c, j, lvl)] = a
+                        a[lo:hi] = 0.1 * scale * rng.standard_normal((hi - lo, ny, nx))
+    return st
