@@ -1,0 +1,1000 @@
+// api.cpp -- host planner and C ABI of the FDTD-Bath library (see include/fdtdbath.h).
+//
+// The planner validates a problem, expands the per-material coefficients of the explicit
+// ADE updates (Eq. Pz_1D_Lorentz, Pz_update-LB, Yzj_finite_difference), builds the CPML
+// profiles, sizes and allocates the device state, plans the z-chunks of the fused step
+// kernel and drives it: one launch per step, the H half-step of step n folded into the
+// launch of step n+1 (an "H pending" flag carries it across calls), and a fixed-order
+// reduction of the monitor / energy partial sums every few hundred steps.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/fdtdbath.h"
+#include "internal.h"
+
+using namespace fdtdbath;
+
+namespace {
+
+thread_local std::string g_create_error;
+
+struct HostMat {
+  int kind, nb;
+  int64_t zlo, zhi, ncell, base, ybase;
+  double eps, w0, g0, sigma;
+  std::vector<double> wj, gj, kj;
+  // derived (double)
+  double cE, c1m, W, c2, A, rho, w0r2;
+  std::vector<double> rowsLit, rowsInc;  // [nb][kCoefStride]
+};
+
+struct HostSrc {
+  int comp;
+  int64_t z;
+  double nu, fwidth, amp, t0;
+  bool has_phase;
+  void *dcos, *dsin;
+};
+
+struct HostMon {
+  int64_t z;
+  int nfreq;
+  void* dfreq;
+  void* dacc;
+};
+
+}  // namespace
+
+struct fdtdbath_sim {
+  int prec = 64;
+  size_t esz = 8;
+  int64_t nx = 0, ny = 0, nz = 0, plane = 0, ncell = 0;
+  double res = 0, courant = 0, dx = 0, dt = 0;
+  int npml = 0;
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  void* (*ualloc)(size_t, void*) = nullptr;
+  void (*ufree)(void*, void*) = nullptr;
+  void* uctx = nullptr;
+  std::vector<void*> allocs;
+  size_t bytes_held = 0;
+  // state
+  void* E[2] = {nullptr, nullptr};
+  void* H[2] = {nullptr, nullptr};
+  int ecur = 0, hcur = 0;
+  void* psiE = nullptr;
+  void* psiH[2] = {nullptr, nullptr};
+  int psicur = 0;
+  void* pmlE = nullptr;
+  void* pmlH = nullptr;
+  void* D = nullptr;
+  void* Pslot[2] = {nullptr, nullptr};
+  void* Yslot[2] = {nullptr, nullptr};
+  int pcur = 0;  // literal form: slot holding P^{n+1/2}
+  void* coef = nullptr;
+  int64_t nmatcell = 0, nybath = 0;
+  std::vector<HostMat> mats;
+  std::vector<HostSrc> srcs;
+  std::vector<HostMon> mons;
+  int64_t e_lo = 0, e_hi = 0, e_cap = 0;
+  int e_every = 1;
+  bool energy_on = false;
+  void* trace = nullptr;
+  // partial sums
+  int ring_cap = 256;
+  int64_t ring_stride = 0, monE_off = 0, monH_off = 0, enE_off = 0, enH_off = 0;
+  void* partial = nullptr;
+  void* series = nullptr;
+  // progress
+  int64_t n = 0;           // completed E half-steps (= completed steps)
+  bool h_pending = false;  // H^n not yet computed
+  int64_t reduced = 0;     // steps whose partials are folded into DFT / trace
+  int64_t launches = 0;
+  // launch plan
+  int ty = 8, nbx = 1, nby = 1, nchunks = 1, nbmax = 0;
+  void* zstart = nullptr;
+  std::string err;
+};
+
+namespace {
+
+int fail(fdtdbath_sim* s, int code, const std::string& msg) {
+  if (s) s->err = msg;
+  else g_create_error = msg;
+  return code;
+}
+
+int cuda_fail(fdtdbath_sim* s, cudaError_t e, const char* what) {
+  std::string m = std::string(what) + ": " + cudaGetErrorString(e);
+  return fail(s, FDTDBATH_ERR_CUDA, m);
+}
+
+void* dalloc(fdtdbath_sim* s, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  bytes = (bytes + 255) & ~size_t(255);
+  void* p = nullptr;
+  if (s->ualloc) {
+    p = s->ualloc(bytes, s->uctx);
+  } else {
+    if (cudaMalloc(&p, bytes) != cudaSuccess) p = nullptr;
+  }
+  if (p) {
+    s->allocs.push_back(p);
+    s->bytes_held += bytes;
+    cudaMemsetAsync(p, 0, bytes, s->stream);
+  }
+  return p;
+}
+
+template <typename T>
+std::vector<T> cast_vec(const std::vector<double>& v) {
+  std::vector<T> o(v.size());
+  for (size_t i = 0; i < v.size(); ++i) o[i] = (T)v[i];
+  return o;
+}
+
+int h2d(fdtdbath_sim* s, void* dst, const void* src, size_t bytes) {
+  cudaError_t e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, s->stream);
+  if (e != cudaSuccess) return cuda_fail(s, e, "cudaMemcpyAsync H2D");
+  e = cudaStreamSynchronize(s->stream);
+  if (e != cudaSuccess) return cuda_fail(s, e, "cudaStreamSynchronize");
+  return 0;
+}
+
+int d2h(fdtdbath_sim* s, void* dst, const void* src, size_t bytes) {
+  cudaError_t e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, s->stream);
+  if (e != cudaSuccess) return cuda_fail(s, e, "cudaMemcpyAsync D2H");
+  e = cudaStreamSynchronize(s->stream);
+  if (e != cudaSuccess) return cuda_fail(s, e, "cudaStreamSynchronize");
+  return 0;
+}
+
+// CPML profile (Roden-Gedney, kappa = 1) at a z position in cells.  The left absorber
+// interface sits at z = npml, the right one at z = nz-1-npml; depth d is clamped to npml;
+// sigma = 0.8 (m+1)/dx (d/npml)^m with m = 3; alpha = 2 pi 0.05 (1 - d/npml);
+// b = exp(-(sigma + alpha) dt), c = sigma/(sigma + alpha) (b - 1).
+void cpml_bc(const fdtdbath_sim* s, double zpos, double* b, double* c) {
+  *b = 1.0;
+  *c = 0.0;
+  if (s->npml <= 0) return;
+  const double zl = (double)s->npml, zr = (double)(s->nz - 1 - s->npml);
+  double d = 0.0;
+  if (zpos < zl) d = zl - zpos;
+  else if (zpos > zr) d = zpos - zr;
+  if (d > (double)s->npml) d = (double)s->npml;
+  if (d <= 0.0) return;
+  const double r = d / (double)s->npml;
+  const double sig = 0.8 * 4.0 / s->dx * r * r * r;
+  const double alpha = 2.0 * M_PI * 0.05 * (1.0 - r);
+  *b = std::exp(-(sig + alpha) * s->dt);
+  *c = sig / (sig + alpha) * (*b - 1.0);
+}
+
+// Coefficients of the explicit updates of one material (double precision).
+void expand_material(HostMat& m, double dt) {
+  const double dt2 = dt * dt;
+  double S = 0.0;
+  m.rowsLit.assign((size_t)m.nb * kCoefStride, 0.0);
+  m.rowsInc.assign((size_t)m.nb * kCoefStride, 0.0);
+  for (int j = 0; j < m.nb; ++j) {
+    const double wj = m.wj[j], gj = m.gj[j], kj = m.kj[j];
+    const double den = 1.0 + 0.5 * gj * dt;
+    const double a = (2.0 - wj * wj * dt * dt) / den;   // a_j
+    const double b = -2.0 / den;                        // b_j
+    const double c = kj * dt / (2.0 * den);             // c_j
+    S += kj * c;
+    const double apb = -(wj * wj * dt2) / den;          // a_j + b_j without cancellation
+    const double mbp1 = (1.0 - 0.5 * gj * dt) / den;    // -(b_j + 1)
+    double* L = &m.rowsLit[(size_t)j * kCoefStride];
+    L[0] = kj;
+    L[1] = a;
+    L[2] = b;
+    L[3] = b + 1.0;
+    L[4] = c;
+    L[5] = wj * wj;
+    double* I = &m.rowsInc[(size_t)j * kCoefStride];
+    I[0] = kj * apb;
+    I[1] = -kj * b;
+    I[2] = apb;
+    I[3] = mbp1;
+    I[4] = c;
+    I[5] = wj * wj;
+  }
+  const double w0 = m.w0, g0 = m.g0;
+  m.cE = w0 * w0 * dt * dt * m.sigma;
+  if (m.kind == FDTDBATH_DRUDE) {
+    m.c1m = 0.0 * dt * dt - 2.0;
+    m.W = 0.0;
+    m.w0r2 = 0.0;
+  } else {
+    m.c1m = w0 * w0 * dt * dt - 2.0;
+    m.W = w0 * w0 * dt * dt;
+    m.w0r2 = w0 * w0;
+  }
+  if (m.kind == FDTDBATH_LORENTZ_BATH) {
+    m.c2 = 1.0 - 0.5 * g0 * dt - 0.5 * dt * S;
+    m.A = 1.0 + 0.5 * g0 * dt + 0.5 * dt * S;
+  } else {
+    m.c2 = 1.0 - 0.5 * g0 * dt;
+    m.A = 1.0 + 0.5 * g0 * dt;
+  }
+  m.rho = (m.sigma > 0.0 && w0 > 0.0) ? 1.0 / (m.sigma * w0 * w0) : 0.0;
+  if (m.kind == FDTDBATH_VACUUM) {
+    m.cE = m.c1m = m.W = m.c2 = 0.0;
+    m.A = 1.0;
+    m.rho = 0.0;
+  }
+}
+
+template <typename T>
+MatK<T> mat_k(const HostMat& m, int coef_off) {
+  MatK<T> k{};
+  k.zlo = (int)m.zlo;
+  k.zhi = (int)m.zhi;
+  k.kind = m.kind;
+  k.nb = m.nb;
+  k.base = m.base;
+  k.ybase = m.ybase;
+  k.ncell = m.ncell;
+  k.coef_off = coef_off;
+  k.eps = (T)m.eps;
+  k.cE = (T)m.cE;
+  k.c1m = (T)m.c1m;
+  k.W = (T)m.W;
+  k.c2 = (T)m.c2;
+  k.A = (T)m.A;
+  k.rho = (T)m.rho;
+  k.w0r2 = (T)m.w0r2;
+  return k;
+}
+
+int plan_chunks(fdtdbath_sim* s, int zc, std::vector<int>& starts) {
+  starts.clear();
+  int64_t z = 0;
+  starts.push_back(0);
+  const int64_t lo_ok = s->npml + 1, hi_ok = s->nz - 1 - s->npml;
+  while (z < s->nz) {
+    int64_t nx = z + zc;
+    if (nx < lo_ok) nx = lo_ok;
+    if (nx > hi_ok) nx = s->nz;
+    if (nx > s->nz) nx = s->nz;
+    starts.push_back((int)nx);
+    z = nx;
+  }
+  return (int)starts.size() - 1;
+}
+
+// Source amplitude at t_n: A exp(-u^2/(2 tau^2)) sin(2 pi nu u), u = t_n - t0 (no phase), or
+// the pair (A g sin(theta), A g cos(theta)) combined with cos/sin of the phase table.
+void source_amp(const HostSrc& q, double t, double* a, double* b) {
+  const double tau = 1.0 / (2.0 * M_PI * q.fwidth);
+  const double u = t - q.t0;
+  if (!q.has_phase) {
+    *a = q.amp * std::exp(-u * u / (2.0 * tau * tau)) * std::sin(2.0 * M_PI * q.nu * u + 0.0);
+    *b = 0.0;
+  } else {
+    const double g = q.amp * std::exp(-u * u / (2.0 * tau * tau));
+    const double th = 2.0 * M_PI * q.nu * u;
+    *a = g * std::sin(th);
+    *b = g * std::cos(th);
+  }
+}
+
+template <typename T>
+Step3DParams<T> make_params(fdtdbath_sim* s, int doH, int doE) {
+  Step3DParams<T> p{};
+  p.nx = (int)s->nx;
+  p.ny = (int)s->ny;
+  p.nz = (int)s->nz;
+  p.plane = s->plane;
+  p.ncell = s->ncell;
+  p.dx = (T)s->dx;
+  p.dt = (T)s->dt;
+  p.inv_dx = (T)(1.0 / s->dx);
+  p.Ein = (const T*)s->E[s->ecur];
+  p.Eout = (T*)s->E[1 - s->ecur];
+  p.Hin = (const T*)s->H[s->hcur];
+  p.Hout = (T*)s->H[1 - s->hcur];
+  p.doH = doH;
+  p.doE = doE;
+  p.npml = s->npml;
+  p.pmlE = (const T*)s->pmlE;
+  p.pmlH = (const T*)s->pmlH;
+  p.psiE = (T*)s->psiE;
+  p.psiHin = (const T*)s->psiH[s->psicur];
+  p.psiHout = (T*)s->psiH[1 - s->psicur];
+  p.nmat = (int)s->mats.size();
+  int off = 0;
+  for (size_t m = 0; m < s->mats.size(); ++m) {
+    p.mat[m] = mat_k<T>(s->mats[m], off);
+    off += s->mats[m].nb;
+  }
+  p.coef = (const T*)s->coef;
+  p.D = (T*)s->D;
+  p.nmatcell = s->nmatcell;
+  if (s->prec == 64) {
+    p.Pa = (T*)s->Pslot[s->pcur];
+    p.Pb = (T*)s->Pslot[1 - s->pcur];
+    p.Ya = (T*)s->Yslot[s->pcur];
+    p.Yb = (T*)s->Yslot[1 - s->pcur];
+  } else {
+    p.Pa = (T*)s->Pslot[0];
+    p.Pb = (T*)s->Pslot[1];
+    p.Ya = (T*)s->Yslot[0];
+    p.Yb = (T*)s->Yslot[1];
+  }
+  p.nsrc = (int)s->srcs.size();
+  const double t = (double)s->n * s->dt;
+  for (size_t q = 0; q < s->srcs.size(); ++q) {
+    double a, b;
+    source_amp(s->srcs[q], t, &a, &b);
+    p.src_comp[q] = s->srcs[q].comp;
+    p.src_z[q] = (int)s->srcs[q].z;
+    p.src_a[q] = (T)a;
+    p.src_b[q] = (T)b;
+    p.src_cos[q] = (const T*)s->srcs[q].dcos;
+    p.src_sin[q] = (const T*)s->srcs[q].dsin;
+  }
+  p.nmon = (int)s->mons.size();
+  for (size_t m = 0; m < s->mons.size(); ++m) p.mon_z[m] = (int)s->mons[m].z;
+  double* part = (double*)s->partial;
+  const int64_t eslot = s->n % s->ring_cap;
+  const int64_t hslot = (s->n - 1 + s->ring_cap) % s->ring_cap;
+  p.mon_partial_E = doE ? part + eslot * s->ring_stride + s->monE_off : nullptr;
+  p.mon_partial_H = doH ? part + hslot * s->ring_stride + s->monH_off : nullptr;
+  p.eE_on = (doE && s->energy_on && (s->n % s->e_every) == 0) ? 1 : 0;
+  p.eH_on = (doH && s->energy_on && ((s->n - 1) % s->e_every) == 0) ? 1 : 0;
+  p.ebox_lo = (int)s->e_lo;
+  p.ebox_hi = (int)s->e_hi;
+  p.en_partial_E = part + eslot * s->ring_stride + s->enE_off;
+  p.en_partial_H = part + hslot * s->ring_stride + s->enH_off;
+  p.ew = s->dx / (double)s->plane;
+  p.zstart = (const int*)s->zstart;
+  return p;
+}
+
+int launch_step(fdtdbath_sim* s, int doH, int doE) {
+  int rc;
+  if (s->prec == 64) {
+    Step3DParams<double> p = make_params<double>(s, doH, doE);
+    rc = launch_step3d_f64(p, s->nbmax, s->ty, s->nbx, s->nby, s->nchunks, s->stream);
+  } else {
+    Step3DParams<float> p = make_params<float>(s, doH, doE);
+    rc = launch_step3d_f32(p, s->nbmax, s->ty, s->nbx, s->nby, s->nchunks, s->stream);
+  }
+  s->launches++;
+  if (rc) return cuda_fail(s, (cudaError_t)rc, "step kernel launch");
+  if (doE) s->ecur = 1 - s->ecur;
+  if (doH) {
+    s->hcur = 1 - s->hcur;
+    s->psicur = 1 - s->psicur;
+  }
+  return 0;
+}
+
+// Fold the partial sums of complete steps [reduced, upto) into the DFT accumulators / trace.
+int reduce_upto(fdtdbath_sim* s, int64_t upto) {
+  if (upto <= s->reduced) return 0;
+  if (s->mons.empty() && !s->energy_on) {
+    s->reduced = upto;
+    return 0;
+  }
+  const int nbxy = s->nbx * s->nby, nblocks = nbxy * s->nchunks;
+  ReduceParams r{};
+  r.partial = (const double*)s->partial;
+  r.ring_stride = s->ring_stride;
+  r.ring_cap = s->ring_cap;
+  r.nmon = (int)s->mons.size();
+  r.nbxy = nbxy;
+  r.nblocks = nblocks;
+  r.mon_E_off = s->monE_off;
+  r.mon_H_off = s->monH_off;
+  r.en_E_off = s->enE_off;
+  r.en_H_off = s->enH_off;
+  r.energy_on = s->energy_on ? 1 : 0;
+  r.step_lo = s->reduced;
+  r.step_hi = upto;
+  r.every = s->e_every;
+  r.series = (double*)s->series;
+  int rc = launch_reduce_series(r, s->stream);
+  s->launches++;
+  if (rc) return cuda_fail(s, (cudaError_t)rc, "reduce kernel launch");
+  DftParams d{};
+  d.series = (const double*)s->series;
+  d.ring_cap = s->ring_cap;
+  d.series_stride = 6 * (int)s->mons.size() + 4;
+  d.nmon = (int)s->mons.size();
+  d.step_lo = s->reduced;
+  d.step_hi = upto;
+  d.dt = s->dt;
+  for (size_t m = 0; m < s->mons.size(); ++m) {
+    d.freqs[m] = (const double*)s->mons[m].dfreq;
+    d.nfreq[m] = s->mons[m].nfreq;
+    d.acc[m] = (double*)s->mons[m].dacc;
+  }
+  d.energy_on = s->energy_on ? 1 : 0;
+  d.every = s->e_every;
+  d.trace = (double*)s->trace;
+  d.trace_cap = s->e_cap;
+  d.inv_plane = 1.0 / (double)s->plane;
+  d.ew = s->dx / (double)s->plane;
+  rc = launch_dft_accumulate(d, s->stream);
+  s->launches++;
+  if (rc) return cuda_fail(s, (cudaError_t)rc, "dft kernel launch");
+  s->reduced = upto;
+  return 0;
+}
+
+int flush_h(fdtdbath_sim* s) {
+  if (!s->h_pending) return 0;
+  int rc = launch_step(s, 1, 0);
+  if (rc) return rc;
+  s->h_pending = false;
+  return 0;
+}
+
+int flush_all(fdtdbath_sim* s) {
+  int rc = flush_h(s);
+  if (rc) return rc;
+  return reduce_upto(s, s->n);
+}
+
+// ---- field access ------------------------------------------------------------------
+struct FieldRef {
+  int kind;  // 0 full grid, 1 material P / PM, 2 bath mode
+  int comp, mode, level;
+};
+
+bool parse_field(int32_t f, FieldRef* r) {
+  if (f >= 0 && f < 6) {
+    *r = {0, f, 0, 0};
+    return true;
+  }
+  if (f >= 6 && f < 12) {
+    *r = {1, (f - 6) % 3, 0, f >= 9 ? 1 : 0};
+    return true;
+  }
+  if (f >= 1024 && f < 1024 + 6 * 256) {
+    const int q = f - 1024;
+    const int cl = q / 256;
+    *r = {2, cl / 2, q % 256, cl % 2};
+    return r->mode < kMaxBath;
+  }
+  return false;
+}
+
+// Host copies of canonical state pieces as double.
+int fetch(fdtdbath_sim* s, const void* dptr, int64_t count, std::vector<double>& out) {
+  out.assign((size_t)count, 0.0);
+  if (s->prec == 64) return d2h(s, out.data(), dptr, (size_t)count * 8);
+  std::vector<float> tmp((size_t)count);
+  int rc = d2h(s, tmp.data(), dptr, (size_t)count * 4);
+  for (int64_t i = 0; i < count; ++i) out[(size_t)i] = tmp[(size_t)i];
+  return rc;
+}
+
+int store(fdtdbath_sim* s, void* dptr, const std::vector<double>& in) {
+  if (s->prec == 64) return h2d(s, dptr, in.data(), in.size() * 8);
+  std::vector<float> tmp(in.size());
+  for (size_t i = 0; i < in.size(); ++i) tmp[i] = (float)in[i];
+  return h2d(s, dptr, tmp.data(), tmp.size() * 4);
+}
+
+char* elem_ptr(void* base, int64_t idx, size_t esz) { return (char*)base + idx * (int64_t)esz; }
+
+}  // namespace
+
+// ======================================================================================
+extern "C" {
+
+int fdtdbath_create(const fdtdbath_grid* grid, double resolution, double courant,
+                    const fdtdbath_material* materials, int32_t nmat,
+                    const fdtdbath_source* sources, int32_t nsrc,
+                    const fdtdbath_monitor* monitors, int32_t nmon,
+                    const fdtdbath_options* opt, fdtdbath_sim** out) {
+  if (!out) return fail(nullptr, FDTDBATH_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (!grid || !opt) return fail(nullptr, FDTDBATH_ERR_ARG, "grid/options is NULL");
+  if (grid->n[0] < 1 || grid->n[1] < 1 || grid->n[2] < 4)
+    return fail(nullptr, FDTDBATH_ERR_ARG, "grid needs nx, ny >= 1 and nz >= 4");
+  if (grid->n[0] > (1 << 20) || grid->n[1] > (1 << 20) || grid->n[2] > (1 << 20))
+    return fail(nullptr, FDTDBATH_ERR_ARG, "grid dimension too large");
+  if (!(resolution > 0) || !(courant > 0))
+    return fail(nullptr, FDTDBATH_ERR_ARG, "resolution and courant must be positive");
+  if (opt->precision != 32 && opt->precision != 64)
+    return fail(nullptr, FDTDBATH_ERR_ARG, "precision must be 32 or 64");
+  if (opt->bath_storage != 0)
+    return fail(nullptr, FDTDBATH_ERR_UNSUPPORTED, "bf16 bath storage is not built yet");
+  if (nmat < 0 || nmat > kMaxMat || (nmat && !materials))
+    return fail(nullptr, FDTDBATH_ERR_ARG, "0 <= nmat <= 8");
+  if (nsrc < 0 || nsrc > kMaxSrc || (nsrc && !sources))
+    return fail(nullptr, FDTDBATH_ERR_ARG, "0 <= nsrc <= 4");
+  if (nmon < 0 || nmon > kMaxMon || (nmon && !monitors))
+    return fail(nullptr, FDTDBATH_ERR_ARG, "0 <= nmon <= 4");
+  const int64_t nx = grid->n[0], ny = grid->n[1], nz = grid->n[2];
+  if (grid->pml_cells < 0 || 2 * (int64_t)grid->pml_cells + 2 > nz)
+    return fail(nullptr, FDTDBATH_ERR_ARG, "pml_cells out of range");
+  int dims = (nx > 1) + (ny > 1) + (nz > 1);
+  if (courant > 1.0 / std::sqrt((double)dims) + 1e-12)
+    return fail(nullptr, FDTDBATH_ERR_CFL, "Courant number above 1/sqrt(dims)");
+
+  fdtdbath_sim* s = new fdtdbath_sim();
+  s->prec = opt->precision;
+  s->esz = s->prec == 64 ? 8 : 4;
+  s->nx = nx;
+  s->ny = ny;
+  s->nz = nz;
+  s->plane = nx * ny;
+  s->ncell = nx * ny * nz;
+  s->res = resolution;
+  s->courant = courant;
+  s->dx = 1.0 / resolution;
+  s->dt = courant * s->dx;
+  s->npml = grid->pml_cells;
+  s->stream = (cudaStream_t)opt->cuda_stream;
+  s->device = opt->device;
+  s->ualloc = opt->alloc;
+  s->ufree = opt->free;
+  s->uctx = opt->alloc_ctx;
+  auto bail = [&](int code, const std::string& msg) {
+    g_create_error = msg;
+    fdtdbath_destroy(s);
+    return code;
+  };
+  if ((s->ualloc == nullptr) != (s->ufree == nullptr))
+    return bail(FDTDBATH_ERR_ARG, "alloc and free must both be set or both NULL");
+  // ---- materials ----
+  std::vector<int> order(nmat);
+  for (int m = 0; m < nmat; ++m) order[m] = m;
+  std::sort(order.begin(), order.end(), [&](int a, int b) { return materials[a].z_lo < materials[b].z_lo; });
+  int64_t prev_hi = 0;
+  for (int oi = 0; oi < nmat; ++oi) {
+    const fdtdbath_material& M = materials[order[oi]];
+    if (M.kind < 0 || M.kind > 3) return bail(FDTDBATH_ERR_ARG, "unknown material kind");
+    if (M.z_lo < 0 || M.z_hi > nz || M.z_lo >= M.z_hi) return bail(FDTDBATH_ERR_ARG, "material z-range outside the grid");
+    if (M.z_lo < prev_hi) return bail(FDTDBATH_ERR_ARG, "material layers overlap");
+    prev_hi = M.z_hi;
+    if (!(M.eps_inf > 0)) return bail(FDTDBATH_ERR_ARG, "eps_inf must be positive");
+    if (M.sigma < 0 || M.gamma < 0 || M.frequency < 0) return bail(FDTDBATH_ERR_ARG, "negative material parameter");
+    HostMat h{};
+    h.kind = M.kind;
+    h.zlo = M.z_lo;
+    h.zhi = M.z_hi;
+    h.ncell = (M.z_hi - M.z_lo) * s->plane;
+    h.eps = M.eps_inf;
+    h.w0 = 2.0 * M_PI * M.frequency;
+    h.g0 = 2.0 * M_PI * M.gamma;
+    h.sigma = M.sigma;
+    h.nb = 0;
+    if (M.kind == FDTDBATH_LORENTZ_BATH) {
+      if (M.num_bath < 0 || M.num_bath > kMaxBath) return bail(FDTDBATH_ERR_ARG, "num_bath must be in [0, 32]");
+      if (M.num_bath && (!M.bath_frequencies || !M.bath_gammas || !M.bath_couplings))
+        return bail(FDTDBATH_ERR_ARG, "bath arrays missing");
+      h.nb = M.num_bath;
+      for (int j = 0; j < h.nb; ++j) {
+        if (M.bath_frequencies[j] < 0 || M.bath_gammas[j] < 0) return bail(FDTDBATH_ERR_ARG, "negative bath parameter");
+        h.wj.push_back(2.0 * M_PI * M.bath_frequencies[j]);
+        h.gj.push_back(2.0 * M_PI * M.bath_gammas[j]);
+        h.kj.push_back(2.0 * M_PI * M.bath_couplings[j]);
+      }
+    }
+    // explicit oscillator updates are stable only for w dt < 2
+    if (M.kind != FDTDBATH_DRUDE && M.kind != FDTDBATH_VACUUM && h.w0 * s->dt >= 2.0)
+      return bail(FDTDBATH_ERR_CFL, "w0 dt >= 2: oscillator update unstable");
+    for (double w : h.wj)
+      if (w * s->dt >= 2.0) return bail(FDTDBATH_ERR_CFL, "w_j dt >= 2: bath update unstable");
+    // coupled field + oscillator stability: a plane wave of the scheme obeys
+    // Omega^2 (eps_inf + chi_d) = K^2 with Omega = 2 sin(w dt/2)/dt and K^2 <= 4 dims/dx^2, and
+    // its largest Omega^2 is below w_max^2 + K^2/eps_inf (w_max^2 = w0^2 (1 + sigma) + sum k_j^2,
+    // or w0^2 sigma for Drude); every root stays on the unit circle while that is <= 4/dt^2.
+    {
+      double wmax2 = 0.0;
+      if (M.kind == FDTDBATH_DRUDE) wmax2 = h.w0 * h.w0 * h.sigma;
+      else if (M.kind != FDTDBATH_VACUUM) wmax2 = h.w0 * h.w0 * (1.0 + h.sigma);
+      for (double k : h.kj) wmax2 += k * k;
+      const double lhs = wmax2 * s->dt * s->dt + 4.0 * courant * courant * dims / h.eps;
+      if (lhs > 4.0 * (1.0 + 1e-12))
+        return bail(FDTDBATH_ERR_CFL, "field-oscillator update unstable: w_max^2 dt^2 + 4 S^2 dims/eps_inf > 4");
+    }
+    expand_material(h, s->dt);
+    s->mats.push_back(h);
+  }
+  int64_t base = 0, ybase = 0;
+  for (auto& m : s->mats) {
+    m.base = base;
+    base += m.ncell;
+    m.ybase = ybase;
+    ybase += (int64_t)3 * m.nb * m.ncell;
+    s->nbmax = std::max(s->nbmax, m.nb);
+  }
+  s->nmatcell = base;
+  s->nybath = ybase;
+  if (s->nbmax > 0) s->nbmax = s->nbmax <= 4 ? 4 : s->nbmax <= 8 ? 8 : s->nbmax <= 16 ? 16 : 32;
+
+  // ---- sources / monitors / energy box ----
+  for (int q = 0; q < nsrc; ++q) {
+    const fdtdbath_source& S = sources[q];
+    if (S.component < 0 || S.component > 2 || S.z < 0 || S.z >= nz)
+      return bail(FDTDBATH_ERR_ARG, "source component or plane out of range");
+    if (!(S.fwidth > 0)) return bail(FDTDBATH_ERR_ARG, "source fwidth must be positive");
+    HostSrc h{S.component, S.z, S.center, S.fwidth, S.amplitude, S.t0, S.phase != nullptr, nullptr, nullptr};
+    s->srcs.push_back(h);
+  }
+  for (int q = 0; q < nmon; ++q) {
+    const fdtdbath_monitor& M = monitors[q];
+    if (M.z < 1 || M.z >= nz || M.nfreq < 1 || !M.freqs) return bail(FDTDBATH_ERR_ARG, "monitor out of range");
+    s->mons.push_back(HostMon{M.z, M.nfreq, nullptr, nullptr});
+  }
+  s->energy_on = opt->energy_hi > opt->energy_lo;
+  if (s->energy_on) {
+    if (opt->energy_lo < 0 || opt->energy_hi > nz) return bail(FDTDBATH_ERR_ARG, "energy box outside the grid");
+    s->e_lo = opt->energy_lo;
+    s->e_hi = opt->energy_hi;
+    s->e_cap = opt->energy_capacity > 0 ? opt->energy_capacity : 65536;
+    s->e_every = 1;
+  }
+
+  // ---- launch plan ----
+  int ty_max = 8;
+  if (const char* e = std::getenv("FDTDBATH_TY")) ty_max = std::min(8, std::max(1, std::atoi(e)));
+  s->ty = (int)std::min<int64_t>(ty_max, ny);
+  s->nbx = (int)((nx + kTX - 1) / kTX);
+  s->nby = (int)((ny + s->ty - 1) / s->ty);
+  int zc = 32;
+  if (const char* e = std::getenv("FDTDBATH_ZCHUNK")) zc = std::max(1, std::atoi(e));
+  std::vector<int> starts;
+  s->nchunks = plan_chunks(s, zc, starts);
+  if ((int64_t)s->nbx * s->nby > 65535 * 64) return bail(FDTDBATH_ERR_ARG, "grid too large for the launch plan");
+
+  cudaError_t ce = cudaSetDevice(s->device);
+  if (ce != cudaSuccess) return bail(FDTDBATH_ERR_CUDA, std::string("cudaSetDevice: ") + cudaGetErrorString(ce));
+
+  // ---- device state ----
+  const size_t esz = s->esz;
+  for (int b = 0; b < 2; ++b) {
+    s->E[b] = dalloc(s, 3 * s->ncell * esz);
+    s->H[b] = dalloc(s, 3 * s->ncell * esz);
+    s->psiH[b] = dalloc(s, 2 * (size_t)(2 * s->npml + 1) * s->plane * esz);
+    s->Pslot[b] = dalloc(s, 3 * (size_t)s->nmatcell * esz);
+    s->Yslot[b] = dalloc(s, (size_t)s->nybath * esz);
+    if (!s->E[b] || !s->H[b] || !s->psiH[b] || !s->Pslot[b] || !s->Yslot[b])
+      return bail(FDTDBATH_ERR_OOM, "device allocation failed");
+  }
+  s->psiE = dalloc(s, 2 * (size_t)(2 * s->npml) * s->plane * esz);
+  s->pmlE = dalloc(s, 2 * (size_t)nz * esz);
+  s->pmlH = dalloc(s, 2 * (size_t)nz * esz);
+  s->D = dalloc(s, s->prec == 64 ? 3 * (size_t)s->nmatcell * esz : 16);
+  int nmodes = 0;
+  for (auto& m : s->mats) nmodes += m.nb;
+  s->coef = dalloc(s, (size_t)std::max(1, nmodes) * kCoefStride * esz);
+  s->zstart = dalloc(s, starts.size() * sizeof(int));
+  if (!s->psiE || !s->pmlE || !s->pmlH || !s->D || !s->coef || !s->zstart)
+    return bail(FDTDBATH_ERR_OOM, "device allocation failed");
+  // partial-sum ring
+  const int64_t nbxy = (int64_t)s->nbx * s->nby, nblocks = nbxy * s->nchunks;
+  s->monE_off = 0;
+  s->monH_off = 2 * (int64_t)s->mons.size() * nbxy;
+  s->enE_off = s->monH_off + 4 * (int64_t)s->mons.size() * nbxy;
+  s->enH_off = s->enE_off + 3 * nblocks;
+  s->ring_stride = s->enH_off + nblocks;
+  s->partial = dalloc(s, (size_t)s->ring_cap * s->ring_stride * 8);
+  s->series = dalloc(s, (size_t)s->ring_cap * (6 * s->mons.size() + 4) * 8);
+  if (!s->partial || !s->series) return bail(FDTDBATH_ERR_OOM, "device allocation failed");
+  if (s->energy_on) {
+    s->trace = dalloc(s, (size_t)s->e_cap * 4 * 8);
+    if (!s->trace) return bail(FDTDBATH_ERR_OOM, "device allocation failed");
+  }
+
+  // ---- tables ----
+  std::vector<double> pe(2 * nz), ph(2 * nz);
+  for (int64_t k = 0; k < nz; ++k) {
+    cpml_bc(s, (double)k, &pe[2 * k], &pe[2 * k + 1]);
+    cpml_bc(s, (double)k + 0.5, &ph[2 * k], &ph[2 * k + 1]);
+  }
+  std::vector<double> rows;
+  for (auto& m : s->mats) {
+    const auto& src = (s->prec == 64) ? m.rowsLit : m.rowsInc;
+    rows.insert(rows.end(), src.begin(), src.end());
+  }
+  if (rows.empty()) rows.assign(kCoefStride, 0.0);
+  int rc = 0;
+  if (s->prec == 64) {
+    rc = rc ? rc : h2d(s, s->pmlE, pe.data(), pe.size() * 8);
+    rc = rc ? rc : h2d(s, s->pmlH, ph.data(), ph.size() * 8);
+    rc = rc ? rc : h2d(s, s->coef, rows.data(), rows.size() * 8);
+  } else {
+    auto pef = cast_vec<float>(pe), phf = cast_vec<float>(ph), rf = cast_vec<float>(rows);
+    rc = rc ? rc : h2d(s, s->pmlE, pef.data(), pef.size() * 4);
+    rc = rc ? rc : h2d(s, s->pmlH, phf.data(), phf.size() * 4);
+    rc = rc ? rc : h2d(s, s->coef, rf.data(), rf.size() * 4);
+  }
+  rc = rc ? rc : h2d(s, s->zstart, starts.data(), starts.size() * sizeof(int));
+  if (rc) return bail(rc, s->err);
+  for (int q = 0; q < nsrc; ++q) {
+    if (!sources[q].phase) continue;
+    std::vector<double> c((size_t)s->plane), sn((size_t)s->plane);
+    for (int64_t p = 0; p < s->plane; ++p) {
+      c[(size_t)p] = std::cos(sources[q].phase[p]);
+      sn[(size_t)p] = std::sin(sources[q].phase[p]);
+    }
+    s->srcs[q].dcos = dalloc(s, (size_t)s->plane * esz);
+    s->srcs[q].dsin = dalloc(s, (size_t)s->plane * esz);
+    if (!s->srcs[q].dcos || !s->srcs[q].dsin) return bail(FDTDBATH_ERR_OOM, "device allocation failed");
+    rc = store(s, s->srcs[q].dcos, c);
+    rc = rc ? rc : store(s, s->srcs[q].dsin, sn);
+    if (rc) return bail(rc, s->err);
+  }
+  for (int q = 0; q < nmon; ++q) {
+    s->mons[q].dfreq = dalloc(s, (size_t)monitors[q].nfreq * 8);
+    s->mons[q].dacc = dalloc(s, (size_t)monitors[q].nfreq * 8 * 8);
+    if (!s->mons[q].dfreq || !s->mons[q].dacc) return bail(FDTDBATH_ERR_OOM, "device allocation failed");
+    rc = h2d(s, s->mons[q].dfreq, monitors[q].freqs, (size_t)monitors[q].nfreq * 8);
+    if (rc) return bail(rc, s->err);
+  }
+  ce = cudaStreamSynchronize(s->stream);
+  if (ce != cudaSuccess) return bail(FDTDBATH_ERR_CUDA, std::string("create: ") + cudaGetErrorString(ce));
+  *out = s;
+  return FDTDBATH_OK;
+}
+
+int fdtdbath_step(fdtdbath_sim* s, int64_t nsteps) {
+  if (!s || nsteps < 0) return fail(s, FDTDBATH_ERR_ARG, "bad arguments to fdtdbath_step");
+  cudaSetDevice(s->device);
+  for (int64_t it = 0; it < nsteps; ++it) {
+    // keep the ring from overwriting partials not yet reduced
+    if (s->n + 1 - s->reduced > s->ring_cap) {
+      const int64_t complete = s->h_pending ? s->n - 1 : s->n;
+      int rc = reduce_upto(s, complete);
+      if (rc) return rc;
+    }
+    int rc = launch_step(s, s->h_pending ? 1 : 0, 1);
+    if (rc) return rc;
+    if (s->prec == 64) s->pcur = 1 - s->pcur;
+    s->n += 1;
+    s->h_pending = true;
+  }
+  return FDTDBATH_OK;
+}
+
+int fdtdbath_sync(fdtdbath_sim* s) {
+  if (!s) return fail(s, FDTDBATH_ERR_ARG, "sim is NULL");
+  cudaSetDevice(s->device);
+  cudaError_t e = cudaStreamSynchronize(s->stream);
+  if (e != cudaSuccess) return cuda_fail(s, e, "stream");
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(s, e, "deferred");
+  return FDTDBATH_OK;
+}
+
+int fdtdbath_read_fields(fdtdbath_sim* s, int32_t field, void* dst, size_t dst_bytes, int32_t dst_on_device) {
+  if (!s || !dst) return fail(s, FDTDBATH_ERR_ARG, "NULL argument");
+  FieldRef f;
+  if (!parse_field(field, &f)) return fail(s, FDTDBATH_ERR_ARG, "unknown field id");
+  if (dst_bytes < (size_t)s->ncell * s->esz) return fail(s, FDTDBATH_ERR_ARG, "destination too small");
+  cudaSetDevice(s->device);
+  int rc = flush_all(s);
+  if (rc) return rc;
+  std::vector<double> full((size_t)s->ncell, 0.0);
+  if (f.kind == 0) {
+    const void* src = f.comp < 3 ? elem_ptr(s->E[s->ecur], f.comp * s->ncell, s->esz)
+                                 : elem_ptr(s->H[s->hcur], (f.comp - 3) * s->ncell, s->esz);
+    rc = fetch(s, src, s->ncell, full);
+    if (rc) return rc;
+  } else {
+    for (auto& m : s->mats) {
+      std::vector<double> a, b;
+      const void* pa;
+      const void* pb = nullptr;
+      if (f.kind == 1) {
+        if (m.kind == FDTDBATH_VACUUM) continue;
+        const int64_t off = f.comp * s->nmatcell + m.base;
+        if (s->prec == 64) {
+          pa = elem_ptr(s->Pslot[f.level == 0 ? s->pcur : 1 - s->pcur], off, s->esz);
+        } else {
+          pa = elem_ptr(s->Pslot[0], off, s->esz);
+          if (f.level == 1) pb = elem_ptr(s->Pslot[1], off, s->esz);
+        }
+      } else {
+        if (f.mode >= m.nb) continue;
+        const int64_t off = m.ybase + ((int64_t)f.comp * m.nb + f.mode) * m.ncell;
+        if (s->prec == 64) {
+          pa = elem_ptr(s->Yslot[f.level == 0 ? s->pcur : 1 - s->pcur], off, s->esz);
+        } else {
+          pa = elem_ptr(s->Yslot[0], off, s->esz);
+          if (f.level == 1) pb = elem_ptr(s->Yslot[1], off, s->esz);
+        }
+      }
+      rc = fetch(s, pa, m.ncell, a);
+      if (!rc && pb) rc = fetch(s, pb, m.ncell, b);
+      if (rc) return rc;
+      for (int64_t r = 0; r < m.ncell; ++r)
+        full[(size_t)(m.zlo * s->plane + r)] = pb ? a[(size_t)r] - b[(size_t)r] : a[(size_t)r];
+    }
+  }
+  // convert to the element type and deliver
+  if (s->prec == 64) {
+    if (dst_on_device) return h2d(s, dst, full.data(), full.size() * 8);
+    std::memcpy(dst, full.data(), full.size() * 8);
+  } else {
+    std::vector<float> tmp(full.size());
+    for (size_t i = 0; i < full.size(); ++i) tmp[i] = (float)full[i];
+    if (dst_on_device) return h2d(s, dst, tmp.data(), tmp.size() * 4);
+    std::memcpy(dst, tmp.data(), tmp.size() * 4);
+  }
+  return FDTDBATH_OK;
+}
+
+int fdtdbath_write_fields(fdtdbath_sim* s, int32_t field, const void* src, size_t src_bytes, int32_t src_on_device) {
+  if (!s || !src) return fail(s, FDTDBATH_ERR_ARG, "NULL argument");
+  FieldRef f;
+  if (!parse_field(field, &f)) return fail(s, FDTDBATH_ERR_ARG, "unknown field id");
+  if (src_bytes < (size_t)s->ncell * s->esz) return fail(s, FDTDBATH_ERR_ARG, "source too small");
+  cudaSetDevice(s->device);
+  int rc = flush_all(s);
+  if (rc) return rc;
+  std::vector<double> in((size_t)s->ncell);
+  {
+    std::vector<unsigned char> raw((size_t)s->ncell * s->esz);
+    if (src_on_device) {
+      rc = d2h(s, raw.data(), src, raw.size());
+      if (rc) return rc;
+    } else {
+      std::memcpy(raw.data(), src, raw.size());
+    }
+    for (int64_t i = 0; i < s->ncell; ++i)
+      in[(size_t)i] = s->prec == 64 ? ((const double*)raw.data())[i] : (double)((const float*)raw.data())[i];
+  }
+  auto refresh_D = [&](void) -> int {
+    // FP64 path: D = eps_inf E + P^{n-1/2} in material cells (the relation E = (D - P)/eps_inf
+    // holds between D^{n-1/2}, E^{n-1/2} and P^{n-1/2})
+    if (s->prec != 64) return 0;
+    for (auto& m : s->mats) {
+      for (int c = 0; c < 3; ++c) {
+        std::vector<double> e, pm;
+        int r = fetch(s, elem_ptr(s->E[s->ecur], c * s->ncell + m.zlo * s->plane, 8), m.ncell, e);
+        if (!r) r = fetch(s, elem_ptr(s->Pslot[1 - s->pcur], c * s->nmatcell + m.base, 8), m.ncell, pm);
+        if (r) return r;
+        std::vector<double> d((size_t)m.ncell);
+        for (int64_t q = 0; q < m.ncell; ++q) d[(size_t)q] = m.eps * e[(size_t)q] + pm[(size_t)q];
+        r = store(s, elem_ptr(s->D, c * s->nmatcell + m.base, 8), d);
+        if (r) return r;
+      }
+    }
+    return 0;
+  };
+  if (f.kind == 0) {
+    void* dstp = f.comp < 3 ? elem_ptr(s->E[s->ecur], f.comp * s->ncell, s->esz)
+                            : elem_ptr(s->H[s->hcur], (f.comp - 3) * s->ncell, s->esz);
+    rc = store(s, dstp, in);
+    if (!rc && f.comp < 3) rc = refresh_D();
+    return rc;
+  }
+  for (auto& m : s->mats) {
+    void *pa, *pb = nullptr;
+    if (f.kind == 1) {
+      if (m.kind == FDTDBATH_VACUUM) continue;
+      const int64_t off = f.comp * s->nmatcell + m.base;
+      if (s->prec == 64) {
+        pa = elem_ptr(s->Pslot[f.level == 0 ? s->pcur : 1 - s->pcur], off, s->esz);
+      } else {
+        pa = elem_ptr(s->Pslot[0], off, s->esz);
+        pb = elem_ptr(s->Pslot[1], off, s->esz);
+      }
+    } else {
+      if (f.mode >= m.nb) continue;
+      const int64_t off = m.ybase + ((int64_t)f.comp * m.nb + f.mode) * m.ncell;
+      if (s->prec == 64) {
+        pa = elem_ptr(s->Yslot[f.level == 0 ? s->pcur : 1 - s->pcur], off, s->esz);
+      } else {
+        pa = elem_ptr(s->Yslot[0], off, s->esz);
+        pb = elem_ptr(s->Yslot[1], off, s->esz);
+      }
+    }
+    std::vector<double> v(in.begin() + m.zlo * s->plane, in.begin() + m.zlo * s->plane + m.ncell);
+    if (!pb) {
+      rc = store(s, pa, v);
+    } else {
+      // increment storage (value X, increment V = X - X'): writing X keeps X', writing X' keeps X
+      std::vector<double> a, b;
+      rc = fetch(s, pa, m.ncell, a);
+      if (!rc) rc = fetch(s, pb, m.ncell, b);
+      if (rc) return rc;
+      std::vector<double> vnew((size_t)m.ncell);
+      if (f.level == 0) {
+        for (int64_t q = 0; q < m.ncell; ++q) vnew[(size_t)q] = v[(size_t)q] - (a[(size_t)q] - b[(size_t)q]);
+        rc = store(s, pa, v);
+        if (!rc) rc = store(s, pb, vnew);
+      } else {
+        for (int64_t q = 0; q < m.ncell; ++q) vnew[(size_t)q] = a[(size_t)q] - v[(size_t)q];
+        rc = store(s, pb, vnew);
+      }
+    }
+    if (rc) return rc;
+  }
+  if (f.kind == 1 && f.level == 1) rc = refresh_D();
+  return rc;
+}
+
+int fdtdbath_dft(fdtdbath_sim* s, int32_t monitor, double* out) {
+  if (!s || !out || monitor < 0 || monitor >= (int)s->mons.size()) return fail(s, FDTDBATH_ERR_ARG, "bad monitor");
+  cudaSetDevice(s->device);
+  int rc = flush_all(s);
+  if (rc) return rc;
+  return d2h(s, out, s->mons[monitor].dacc, (size_t)s->mons[monitor].nfreq * 8 * 8);
+}
+
+int fdtdbath_energy(fdtdbath_sim* s, double* trace, int64_t maxlen, int64_t* len) {
+  if (!s || !len || (maxlen > 0 && !trace)) return fail(s, FDTDBATH_ERR_ARG, "bad arguments");
+  *len = 0;
+  if (!s->energy_on) return FDTDBATH_OK;
+  cudaSetDevice(s->device);
+  int rc = flush_all(s);
+  if (rc) return rc;
+  int64_t n = (s->n + s->e_every - 1) / s->e_every;
+  if (n > s->e_cap) n = s->e_cap;
+  if (n > maxlen) n = maxlen;
+  if (n > 0) rc = d2h(s, trace, s->trace, (size_t)n * 4 * 8);
+  *len = n;
+  return rc;
+}
+
+int64_t fdtdbath_steps_done(const fdtdbath_sim* s) { return s ? s->n : -1; }
+
+const char* fdtdbath_last_error(const fdtdbath_sim* s) {
+  return s ? s->err.c_str() : g_create_error.c_str();
+}
+
+void fdtdbath_destroy(fdtdbath_sim* s) {
+  if (!s) return;
+  if (!s->allocs.empty()) {
+    cudaSetDevice(s->device);
+    cudaStreamSynchronize(s->stream);
+  }
+  for (void* p : s->allocs) {
+    if (s->ufree) s->ufree(p, s->uctx);
+    else cudaFree(p);
+  }
+  delete s;
+}
+
+int fdtdbath_bath_form(int32_t shape, double frequency, double gamma, int32_t num_bath, double width,
+                       double bath_gamma, double dephasing, double* frequencies, double* gammas,
+                       double* couplings) {
+  if (num_bath < 2 || !frequencies || !gammas || !couplings || !(width > 0) || dephasing < 0)
+    return fail(nullptr, FDTDBATH_ERR_ARG, "bath_form needs num_bath >= 2, width > 0, dephasing >= 0");
+  if (shape < 0 || shape > 2) return fail(nullptr, FDTDBATH_ERR_ARG, "unknown bath shape");
+  const double dw = width / (double)(num_bath - 1);
+  const double kb = std::sqrt(2.0 * dw / M_PI * dephasing);
+  const double G = gamma + dephasing;
+  for (int j = 0; j < num_bath; ++j) {
+    const double f = (frequency - 0.5 * width) + dw * (double)j;
+    frequencies[j] = f;
+    gammas[j] = bath_gamma;
+    const double d = f - frequency;
+    if (shape == FDTDBATH_BATH_UNIFORM) couplings[j] = kb;
+    else if (shape == FDTDBATH_BATH_LORENTZIAN) couplings[j] = kb * std::sqrt(G * G / (G * G + d * d));
+    else couplings[j] = kb * std::exp(-d * d / (4.0 * G * G));
+  }
+  return FDTDBATH_OK;
+}
+
+int64_t fdtdbath_query(const fdtdbath_sim* s, int32_t key) {
+  if (!s) return -1;
+  switch (key) {
+    case 0: return (int64_t)s->esz;
+    case 1: return s->launches;
+    case 2: return (int64_t)s->bytes_held;
+    case 3: return (int64_t)s->nbx * s->nby * s->nchunks;
+    case 4: return s->nchunks;
+    default: return -1;
+  }
+}
+
+}  // extern "C"

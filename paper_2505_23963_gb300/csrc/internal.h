@@ -1,0 +1,140 @@
+// internal.h -- data structures shared by the host planner (api.cpp) and the kernels.
+//
+// State layout in HBM (one simulation):
+//   E, H        : two buffers each (ping-pong), [3][nz][ny][nx]; one launch reads the
+//                 "in" buffer (halo neighbours included) and writes the "out" buffer.
+//   psiE        : CPML memories of the E update, [2][2*npml][ny][nx], updated in place.
+//   psiH        : CPML memories of the H update, two buffers, [2][2*npml+1][ny][nx].
+//   D           : FP64 path only, [3][material cells] (material planes only).
+//   Pa / Pb     : FP64 path: P^{n+1/2} and P^{n-1/2} slots, the new P^{n+3/2} overwrites
+//                 the older slot and the host swaps the two pointers each step.
+//                 FP32 path (increment form): Pa = P^{n+1/2}, Pb = V = P^{n+1/2} - P^{n-1/2}.
+//   Ya / Yb     : the same two slots for every bath mode, [3][nb][cells] per
+//                 Lorentz-Bath material (material-only storage).
+//   partial     : per-block FP64 partial sums of the monitor planes and of the energy box,
+//                 reduced in a fixed order by reduce.cu.
+#pragma once
+
+#include <cstdint>
+
+namespace fdtdbath {
+
+constexpr int kMaxMat = 8;
+constexpr int kMaxSrc = 4;
+constexpr int kMaxMon = 4;
+constexpr int kMaxBath = 32;
+constexpr int kTX = 32;
+constexpr int kCoefStride = 8;  // coefficient row per bath mode
+
+enum Kind { kVacuum = 0, kLorentz = 1, kDrude = 2, kLorentzBath = 3 };
+
+template <typename T>
+struct MatK {
+  int zlo, zhi, kind, nb;
+  int64_t base;   // first cell of this material in the pooled material arrays
+  int64_t ybase;  // first element of this material's bath block in Ya / Yb
+  int64_t ncell;  // cells of this material
+  int coef_off;   // first row of this material's modes in coef[]
+  T eps;          // eps_inf
+  T cE;           // eps0 w0^2 dt^2 sigma
+  T c1m;          // w0^2 dt^2 - 2 (Drude: -2)         [FP64 path]
+  T W;            // w0^2 dt^2 (Drude: 0)                [FP32 increment path]
+  T c2;           // 1 - gamma0 dt/2 - dt/2 sum_j k_j c_j
+  T A;            // 1 + gamma0 dt/2 + dt/2 sum_j k_j c_j
+  T rho;          // 1/(sigma w0^2) for the energy density (0 when sigma = 0)
+  T w0r2;         // w0^2 in the potential term (Drude: 0)
+};
+
+// Per bath mode j (coefficient row of kCoefStride values):
+//   FP64 path : {k_j, a_j, b_j, b_j + 1, c_j, w_j^2}
+//   FP32 path : {k_j (a_j + b_j), -k_j b_j, a_j + b_j, -(b_j + 1), c_j, w_j^2}
+
+template <typename T>
+struct Step3DParams {
+  int nx, ny, nz;
+  int64_t plane, ncell;
+  T dx, dt, inv_dx;
+  const T* Ein;
+  T* Eout;
+  const T* Hin;
+  T* Hout;
+  int doH, doE;
+  // CPML
+  int npml;
+  const T* pmlE;  // [nz][2] = (b, c) at integer z
+  const T* pmlH;  // [nz][2] = (b, c) at z + 1/2
+  T* psiE;        // [2][2*npml][plane]
+  const T* psiHin;
+  T* psiHout;     // [2][2*npml+1][plane]
+  // materials
+  int nmat;
+  MatK<T> mat[kMaxMat];
+  const T* coef;
+  T* D;
+  T* Pa;
+  T* Pb;
+  T* Ya;
+  T* Yb;
+  int64_t nmatcell;
+  // sources: J(x, y) = src_a * cos(phase) + src_b * sin(phase)   (src_b unused without phase)
+  int nsrc;
+  int src_comp[kMaxSrc];
+  int src_z[kMaxSrc];
+  T src_a[kMaxSrc];
+  T src_b[kMaxSrc];
+  const T* src_cos[kMaxSrc];
+  const T* src_sin[kMaxSrc];
+  // monitors and energy partial sums
+  int nmon;
+  int mon_z[kMaxMon];
+  double* mon_partial_E;  // [2*nmon][nbxy] for this launch's E step (or null)
+  double* mon_partial_H;  // [4*nmon][nbxy] for this launch's H step (or null)
+  int eE_on, eH_on;       // energy of E / H parts recorded in this launch
+  int ebox_lo, ebox_hi;
+  double* en_partial_E;   // [3][nblocks]
+  double* en_partial_H;   // [1][nblocks]
+  double ew;              // dx / (nx ny)
+  // z chunks
+  const int* zstart;      // [nchunks + 1]
+};
+
+// Launchers (defined in step3d_f32.cu / step3d_f64.cu).
+int launch_step3d_f32(const Step3DParams<float>& p, int nbmax, int ty, int nbx, int nby,
+                      int nchunks, void* stream);
+int launch_step3d_f64(const Step3DParams<double>& p, int nbmax, int ty, int nbx, int nby,
+                      int nchunks, void* stream);
+
+// reduce.cu: fixed-order reduction of the per-block partials into per-step series,
+// running DFT accumulation and energy traces.
+struct ReduceParams {
+  const double* partial;  // ring of per-step partial blocks
+  int64_t ring_stride;    // doubles per ring step
+  int ring_cap;           // steps in the ring
+  int nmon;
+  int nbxy, nblocks;
+  int64_t mon_E_off, mon_H_off, en_E_off, en_H_off;  // offsets inside one ring step
+  int energy_on;
+  int64_t step_lo, step_hi;  // global steps to reduce: [lo, hi)
+  int every;                 // energy recorded on steps with step % every == 0
+  double* series;            // [ring_cap][6*nmon + 4]
+};
+int launch_reduce_series(const ReduceParams& r, void* stream);
+
+struct DftParams {
+  const double* series;
+  int ring_cap, series_stride;
+  int nmon;
+  int64_t step_lo, step_hi;
+  double dt;
+  const double* freqs[kMaxMon];
+  int nfreq[kMaxMon];
+  double* acc[kMaxMon];   // [nfreq][8]
+  int energy_on, every;
+  double* trace;          // [cap][4]
+  int64_t trace_cap;
+  double inv_plane;       // 1/(nx ny)
+  double ew;              // dx/(nx ny)
+};
+int launch_dft_accumulate(const DftParams& d, void* stream);
+
+}  // namespace fdtdbath

@@ -1,0 +1,514 @@
+// step3d.cuh -- fused Yee + CPML + source + Lorentz/Drude/Lorentz-Bath step, one launch per step.
+//
+// One launch performs, for every cell, the H half-step of the previous step (H^n from
+// E^{n-1/2}, Eq. 1b) followed by this step's D/E half-step (Eq. 1a, D = E + P), the
+// polarization update ("evaluate P^{n+3/2}" of Eq. FDTD-1D with Eq. Pz_1D_Lorentz or
+// Eq. Pz_update-LB) and the bath-mode update (Eq. Yzj_finite_difference), with one
+// independent bath set per P component (Sec. II.C, 3D extension).
+//
+// Decomposition: a CTA owns a 32 x TY column tile in (x, y) and marches along a chunk of
+// z planes.  Per plane it stages E^{n-1/2} of plane k+1 (tile + 1-cell frame) in shared
+// memory, recomputes H^n on the tile plus the -x / -y halo (H is read by neighbours'
+// E updates), writes H^n of its own cells, then updates E, P and the bath modes of its own
+// cells with H^n of planes k (shared) and k-1 (registers).  E, H and the H-side CPML
+// memories are double-buffered so neighbouring CTAs never see a half-updated plane;
+// P, Y, D and the E-side CPML memories are cell-local and updated in place.  Every state
+// word is read once and written once per step; halo re-reads hit L1/L2.
+//
+// Two arithmetic forms:
+//   INC = false (FP64): the literal form -- D stored in material cells, E = (D - P)/eps,
+//     two time levels of P and Y with the new level overwriting the oldest; every
+//     expression is evaluated in the order the equations print it.
+//   INC = true (FP32): the increment form -- E updated D-free
+//     (E += (dt curl H + dt J - (P^{n+1/2} - P^{n-1/2}))/eps), P and every Y_j carried as
+//     (value, increment).  Algebraically identical to Eq. Pz_update-LB / Yzj_finite_difference
+//     but without the 2 - w^2 dt^2 cancellation that costs FP32 its phase accuracy.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "internal.h"
+
+namespace fdtdbath {
+
+template <typename T>
+__device__ __forceinline__ T ddiff(T a, T b, T dx, T inv_dx);
+template <>
+__device__ __forceinline__ double ddiff<double>(double a, double b, double dx, double) {
+  return (a - b) / dx;
+}
+template <>
+__device__ __forceinline__ float ddiff<float>(float a, float b, float, float inv_dx) {
+  return (a - b) * inv_dx;
+}
+
+__device__ __forceinline__ int wrapi(int v, int n) {
+  v %= n;
+  return v < 0 ? v + n : v;
+}
+
+__device__ __forceinline__ int psiE_plane(int k, int nz, int npml) {
+  if (k < npml) return k;
+  if (k >= nz - npml) return npml + (k - (nz - npml));
+  return -1;
+}
+__device__ __forceinline__ int psiH_plane(int k, int nz, int npml) {
+  if (npml <= 0) return -1;
+  if (k < npml) return k;
+  if (k >= nz - npml - 1) return npml + (k - (nz - npml - 1));
+  return -1;
+}
+
+// Fixed-order block reduction of a double; the result is valid in thread 0.
+__device__ __forceinline__ double block_sum(double v, double* scratch) {
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+  const int nw = (blockDim.x * blockDim.y) >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  __syncthreads();
+  if ((tid & 31) == 0) scratch[tid >> 5] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (tid == 0)
+    for (int w = 0; w < nw; ++w) s += scratch[w];
+  return s;
+}
+
+// H update of one cell (Eq. 1b, mu0 = 1) from the 9 E values it needs:
+//   Hx -= dt (dEz/dy - (dEy/dz + psi_x)),  Hy -= dt ((dEx/dz + psi_y) - dEz/dx),
+//   Hz -= dt (dEy/dx - dEx/dy);  psi <- b psi + c dE/dz inside the CPML.
+template <typename T>
+struct HIn {
+  T ex0, ex_k1, ex_j1;  // Ex(i,j,k), Ex(i,j,k+1), Ex(i,j+1,k)
+  T ey0, ey_k1, ey_i1;  // Ey(i,j,k), Ey(i,j,k+1), Ey(i+1,j,k)
+  T ez0, ez_j1, ez_i1;  // Ez(i,j,k), Ez(i,j+1,k), Ez(i+1,j,k)
+};
+
+template <typename T>
+__device__ __forceinline__ void h_update(const HIn<T>& e, T& hx, T& hy, T& hz, T* psix, T* psiy,
+                                         T b, T c, bool pml, T dx, T dt, T inv_dx) {
+  T dyEz = ddiff<T>(e.ez_j1, e.ez0, dx, inv_dx);
+  T dzEy = ddiff<T>(e.ey_k1, e.ey0, dx, inv_dx);
+  T dzEx = ddiff<T>(e.ex_k1, e.ex0, dx, inv_dx);
+  T dxEz = ddiff<T>(e.ez_i1, e.ez0, dx, inv_dx);
+  T dxEy = ddiff<T>(e.ey_i1, e.ey0, dx, inv_dx);
+  T dyEx = ddiff<T>(e.ex_j1, e.ex0, dx, inv_dx);
+  if (pml) {
+    *psix = b * (*psix) + c * dzEy;
+    *psiy = b * (*psiy) + c * dzEx;
+    hx = hx - dt * (dyEz - (dzEy + *psix));
+    hy = hy - dt * ((dzEx + *psiy) - dxEz);
+  } else {
+    hx = hx - dt * (dyEz - dzEy);
+    hy = hy - dt * (dzEx - dxEz);
+  }
+  hz = hz - dt * (dxEy - dyEx);
+}
+
+// cp.async (LDGSTS) of one element into shared memory, and its group bookkeeping
+template <typename T>
+__device__ __forceinline__ void cp_async_elem(T* sdst, const T* gsrc) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(sdst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(sa), "l"(gsrc), "n"(sizeof(T)));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+__device__ __forceinline__ void cp_async_wait_1() { asm volatile("cp.async.wait_group 1;\n" ::); }
+
+template <typename T, bool INC, int NBMAX>
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) step3d_kernel(const Step3DParams<T> p) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int TY = blockDim.y;
+  constexpr int TX = kTX;
+  constexpr int FX = TX + 2;
+  const int FY = TY + 2;
+  constexpr int HX = TX + 1;
+  const int HY = TY + 1;
+  // bath modes preloaded for all three components with the rest of the plane's state
+  constexpr int NBP = NBMAX <= 8 ? NBMAX : 0;
+  constexpr int NBA = NBMAX > 0 ? NBMAX : 1;
+  // E_in frames, ring of 4 planes [4][3][FY][FX]: planes k, k+1 feed H^n(k), plane k also the
+  // E update of k (after the second barrier), plane k+2 is in flight; the slot refilled at the
+  // top of step k+1 (plane k+3) held plane k-1, last read before this step's first barrier.
+  T* sE = reinterpret_cast<T*>(smem_raw);
+  T* sHin = sE + 12 * FY * FX;                   // H_in frames, ring of 2 planes: [2][3][HY][HX]
+  T* sH = sHin + 6 * HY * HX;                    // H^n of the current plane:     [3][HY][HX]
+  double* sred = reinterpret_cast<double*>(
+      (reinterpret_cast<uintptr_t>(sH + 3 * HY * HX) + 15) & ~uintptr_t(15));
+
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int tid = ty * TX + tx;
+  const int nthr = TX * TY;
+  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+  const int i = x0 + tx, j = y0 + ty;
+  const bool own = (i < p.nx) && (j < p.ny);
+  const int zb = p.zstart[blockIdx.z], ze = p.zstart[blockIdx.z + 1];
+  const int64_t plane = p.plane, ncell = p.ncell;
+  const int64_t qxy = own ? (int64_t)j * p.nx + i : 0;
+  const T dx = p.dx, dt = p.dt, inv_dx = p.inv_dx;
+  const int nbxy = gridDim.x * gridDim.y;
+  const int bxy = blockIdx.y * gridDim.x + blockIdx.x;
+  const int blin = blockIdx.z * nbxy + bxy;
+  const T* __restrict__ Ein = p.Ein;
+  const T* __restrict__ Hin = p.Hin;
+
+  auto sEi = [&](int k, int c, int yy, int xx) -> T& {
+    return sE[(((k & 3) * 3 + c) * FY + yy) * FX + xx];
+  };
+  auto sHini = [&](int k, int c, int yy, int xx) -> T& {
+    return sHin[(((k & 1) * 3 + c) * HY + yy) * HX + xx];
+  };
+  auto sHi = [&](int c, int yy, int xx) -> T& { return sH[(c * HY + yy) * HX + xx]; };
+
+  // asynchronous staging of the E_in frame of plane k (tile + 1 cell, periodic in x, y)
+  auto issueE = [&](int k) {
+    for (int idx = tid; idx < FY * FX; idx += nthr) {
+      const int yy = idx / FX, xx = idx - yy * FX;
+      const int gx = wrapi(x0 - 1 + xx, p.nx), gy = wrapi(y0 - 1 + yy, p.ny);
+      const int64_t q = (int64_t)k * plane + (int64_t)gy * p.nx + gx;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        if (k < p.nz) cp_async_elem(&sEi(k, c, yy, xx), Ein + c * ncell + q);
+        else sEi(k, c, yy, xx) = T(0);
+      }
+    }
+  };
+  // asynchronous staging of the H_in frame of plane k (tile + the -x / -y halo)
+  auto issueH = [&](int k) {
+    for (int idx = tid; idx < HY * HX; idx += nthr) {
+      const int yy = idx / HX, xx = idx - yy * HX;
+      const int gx = wrapi(x0 - 1 + xx, p.nx), gy = wrapi(y0 - 1 + yy, p.ny);
+      const int64_t q = (int64_t)k * plane + (int64_t)gy * p.nx + gx;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) cp_async_elem(&sHini(k, c, yy, xx), Hin + c * ncell + q);
+    }
+  };
+
+  // H^n of one frame position (hy, hx) at plane k (frame origin at (x0-1, y0-1))
+  auto computeH = [&](int hy, int hx, int k, bool write_out) {
+    T hx_ = sHini(k, 0, hy, hx), hy_ = sHini(k, 1, hy, hx), hz_ = sHini(k, 2, hy, hx);
+    if (p.doH) {
+      HIn<T> e;
+      e.ex0 = sEi(k, 0, hy, hx);
+      e.ex_k1 = sEi(k + 1, 0, hy, hx);
+      e.ex_j1 = sEi(k, 0, hy + 1, hx);
+      e.ey0 = sEi(k, 1, hy, hx);
+      e.ey_k1 = sEi(k + 1, 1, hy, hx);
+      e.ey_i1 = sEi(k, 1, hy, hx + 1);
+      e.ez0 = sEi(k, 2, hy, hx);
+      e.ez_j1 = sEi(k, 2, hy + 1, hx);
+      e.ez_i1 = sEi(k, 2, hy, hx + 1);
+      const int ip = psiH_plane(k, p.nz, p.npml);
+      T psx = T(0), psy = T(0), b = T(1), c = T(0);
+      const int gx = wrapi(x0 - 1 + hx, p.nx), gy = wrapi(y0 - 1 + hy, p.ny);
+      const int64_t pq = (int64_t)ip * plane + (int64_t)gy * p.nx + gx;
+      const int64_t pstride = (int64_t)(2 * p.npml + 1) * plane;
+      if (ip >= 0) {
+        b = p.pmlH[2 * k];
+        c = p.pmlH[2 * k + 1];
+        psx = p.psiHin[pq];
+        psy = p.psiHin[pstride + pq];
+      }
+      h_update<T>(e, hx_, hy_, hz_, &psx, &psy, b, c, ip >= 0, dx, dt, inv_dx);
+      if (write_out) {
+        const int64_t q = (int64_t)k * plane + (int64_t)gy * p.nx + gx;
+        p.Hout[q] = hx_;
+        p.Hout[ncell + q] = hy_;
+        p.Hout[2 * ncell + q] = hz_;
+        if (ip >= 0) {
+          p.psiHout[pq] = psx;
+          p.psiHout[pstride + pq] = psy;
+        }
+      }
+    }
+    sHi(0, hy, hx) = hx_;
+    sHi(1, hy, hx) = hy_;
+    sHi(2, hy, hx) = hz_;
+  };
+
+  // ---- prologue: H^n of plane zb-1 at the own cell (for d/dz of the E update at zb) ----
+  T hxm = T(0), hym = T(0);
+  if (p.doE && zb > 0 && own) {
+    const int64_t q = (int64_t)(zb - 1) * plane + qxy;
+    hxm = Hin[q];
+    hym = Hin[ncell + q];
+    if (p.doH) {
+      // zb-1 is never inside the CPML (chunk starts are planned that way)
+      const int ip1 = (i + 1) % p.nx, jp1 = (j + 1) % p.ny;
+      const int64_t qj1 = (int64_t)(zb - 1) * plane + (int64_t)jp1 * p.nx + i;
+      const int64_t qi1 = (int64_t)(zb - 1) * plane + (int64_t)j * p.nx + ip1;
+      HIn<T> e;
+      e.ex0 = Ein[q];
+      e.ex_k1 = Ein[q + plane];
+      e.ex_j1 = Ein[qj1];
+      e.ey0 = Ein[ncell + q];
+      e.ey_k1 = Ein[ncell + q + plane];
+      e.ey_i1 = Ein[ncell + qi1];
+      e.ez0 = Ein[2 * ncell + q];
+      e.ez_j1 = Ein[2 * ncell + qj1];
+      e.ez_i1 = Ein[2 * ncell + qi1];
+      T hz_dummy = T(0), psx = T(0), psy = T(0);
+      h_update<T>(e, hxm, hym, hz_dummy, &psx, &psy, T(1), T(0), false, dx, dt, inv_dx);
+    }
+  }
+
+  // per-thread energy accumulators (state precision; reduced in FP64 per block)
+  T uE = T(0), uP = T(0), uB = T(0), uH = T(0);
+
+  issueE(zb);
+  issueE(zb + 1);
+  issueH(zb);
+  cp_async_commit();
+  for (int k = zb; k < ze; ++k) {
+    // ---------------- material state of plane k: loads issued before the stencil ----------
+    int mi = -1;
+    for (int m = 0; m < p.nmat; ++m)
+      if (k >= p.mat[m].zlo && k < p.mat[m].zhi) mi = m;
+    const bool mat_here = p.doE && own && mi >= 0 && p.mat[mi].kind != kVacuum;
+    T rPa[3], rPb[3], rD[3];
+    T rY[3][NBP > 0 ? NBP : 1], rV[3][NBP > 0 ? NBP : 1];
+    int64_t r = 0, rl = 0;
+    if (p.doE && own && mi >= 0) {
+      const MatK<T>& M = p.mat[mi];
+      r = M.base + (int64_t)(k - M.zlo) * plane + qxy;
+      rl = (int64_t)(k - M.zlo) * plane + qxy;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        rPa[c] = p.Pa[c * p.nmatcell + r];
+        rPb[c] = p.Pb[c * p.nmatcell + r];
+        if (!INC) rD[c] = p.D[c * p.nmatcell + r];
+      }
+      if (NBP > 0 && M.kind == kLorentzBath) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          const int64_t yoff = M.ybase + (int64_t)c * M.nb * M.ncell + rl;
+#pragma unroll
+          for (int jj = 0; jj < (NBP > 0 ? NBP : 1); ++jj) {
+            if (jj < M.nb) {
+              rY[c][jj] = p.Ya[yoff + (int64_t)jj * M.ncell];
+              rV[c][jj] = p.Yb[yoff + (int64_t)jj * M.ncell];
+            }
+          }
+        }
+      }
+    }
+    // ---------------- prefetch the next planes' frames ----------------
+    if (k + 1 < ze) {
+      issueE(k + 2);
+      issueH(k + 1);
+    }
+    cp_async_commit();
+    cp_async_wait_1();
+    __syncthreads();
+    // ---------------- H^n of plane k (own cells + -x/-y halo) ----------------
+    // own cell (threads past the grid edge compute wrapped values that are never stored)
+    computeH(ty + 1, tx + 1, k, own);
+    // halo: row y0-1 (TX cells) and column x0-1 (TY cells), recomputed, never stored
+    for (int t = tid; t < TX + TY; t += nthr) {
+      if (t < TX) computeH(0, t + 1, k, false);
+      else computeH(t - TX + 1, 0, k, false);
+    }
+    __syncthreads();
+
+    // H-side monitor and energy partials
+    if (p.doH) {
+      for (int m = 0; m < p.nmon; ++m) {
+        const int zm = p.mon_z[m];
+        if (k == zm - 1 || k == zm) {
+          const int off = (k == zm) ? 1 : 0;
+          T vx = own ? sHi(0, ty + 1, tx + 1) : T(0);
+          T vy = own ? sHi(1, ty + 1, tx + 1) : T(0);
+          double sx = block_sum((double)vx, sred);
+          double sy = block_sum((double)vy, sred);
+          if (tid == 0 && p.mon_partial_H) {
+            p.mon_partial_H[(int64_t)(4 * m + off) * nbxy + bxy] = sx;
+            p.mon_partial_H[(int64_t)(4 * m + 2 + off) * nbxy + bxy] = sy;
+          }
+        }
+      }
+      if (p.eH_on && own && k >= p.ebox_lo && k < p.ebox_hi) {
+        T a = sHi(0, ty + 1, tx + 1), b = sHi(1, ty + 1, tx + 1), c = sHi(2, ty + 1, tx + 1);
+        uH += a * a + b * b + c * c;
+      }
+    }
+
+    // ---------------- D/E, P, Y of plane k (own cells) ----------------
+    if (p.doE) {
+      T Ev[3] = {T(0), T(0), T(0)};
+      if (own) {
+        const int64_t q = (int64_t)k * plane + qxy;
+        const int hy = ty + 1, hx = tx + 1;
+        const T Hx = sHi(0, hy, hx), Hy = sHi(1, hy, hx), Hz = sHi(2, hy, hx);
+        const T dyHz = ddiff<T>(Hz, sHi(2, hy - 1, hx), dx, inv_dx);
+        const T dzHy = ddiff<T>(Hy, hym, dx, inv_dx);
+        const T dzHx = ddiff<T>(Hx, hxm, dx, inv_dx);
+        const T dxHz = ddiff<T>(Hz, sHi(2, hy, hx - 1), dx, inv_dx);
+        const T dxHy = ddiff<T>(Hy, sHi(1, hy, hx - 1), dx, inv_dx);
+        const T dyHx = ddiff<T>(Hx, sHi(0, hy - 1, hx), dx, inv_dx);
+        T curl[3];
+        const int ip = psiE_plane(k, p.nz, p.npml);
+        if (ip >= 0) {
+          const T b = p.pmlE[2 * k], c = p.pmlE[2 * k + 1];
+          const int64_t pq = (int64_t)ip * plane + qxy;
+          const int64_t pstride = (int64_t)(2 * p.npml) * plane;
+          T px = b * p.psiE[pq] + c * dzHy;
+          T py = b * p.psiE[pstride + pq] + c * dzHx;
+          p.psiE[pq] = px;
+          p.psiE[pstride + pq] = py;
+          curl[0] = dyHz - (dzHy + px);
+          curl[1] = (dzHx + py) - dxHz;
+        } else {
+          curl[0] = dyHz - dzHy;
+          curl[1] = dzHx - dxHz;
+        }
+        curl[2] = dxHy - dyHx;
+        // soft source current on this plane
+        T J[3] = {T(0), T(0), T(0)};
+        bool hasJ[3] = {false, false, false};
+        for (int s = 0; s < p.nsrc; ++s) {
+          if (p.src_z[s] == k) {
+            T v = p.src_a[s];
+            if (p.src_cos[s]) v = p.src_a[s] * p.src_cos[s][qxy] + p.src_b[s] * p.src_sin[s][qxy];
+            J[p.src_comp[s]] += v;
+            hasJ[p.src_comp[s]] = true;
+          }
+        }
+        if (mi < 0) {
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            T e = sEi(k, c, hy, hx) + dt * curl[c];
+            if (hasJ[c]) e = e + dt * J[c];
+            Ev[c] = e;
+            p.Eout[c * ncell + q] = e;
+          }
+        } else {
+          const MatK<T>& M = p.mat[mi];
+          const bool bath = (M.kind == kLorentzBath) && (NBMAX > 0);
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            T E;
+            const T Pa = rPa[c];
+            const T Pb = rPb[c];
+            if (!INC) {
+              // D^{n+1/2} = D^{n-1/2} + dt curl H^n (+ dt J);  E = (D - P^{n+1/2}) / eps_inf
+              T D = rD[c] + dt * curl[c];
+              if (hasJ[c]) D = D + dt * J[c];
+              p.D[c * p.nmatcell + r] = D;
+              E = (D - Pa) / M.eps;
+            } else {
+              // D-free: E += (dt curl H + dt J - (P^{n+1/2} - P^{n-1/2})) / eps_inf
+              T inc = dt * curl[c];
+              if (hasJ[c]) inc = inc + dt * J[c];
+              E = sEi(k, c, hy, hx) + (inc - Pb) / M.eps;
+            }
+            Ev[c] = E;
+            p.Eout[c * ncell + q] = E;
+            if (!mat_here) continue;
+            // ---- polarization (and bath) update ----
+            T Yl[NBA], Vl[NBA];
+            const int nb = bath ? M.nb : 0;
+            const int64_t yoff = M.ybase + (int64_t)c * M.nb * M.ncell + rl;
+            T bsum = T(0);
+#pragma unroll
+            for (int jj = 0; jj < NBA; ++jj) {
+              if (jj < nb) {
+                if (NBP > 0) {
+                  Yl[jj] = rY[c][jj < NBP ? jj : 0];
+                  Vl[jj] = rV[c][jj < NBP ? jj : 0];
+                } else {
+                  Yl[jj] = p.Ya[yoff + (int64_t)jj * M.ncell];
+                  Vl[jj] = p.Yb[yoff + (int64_t)jj * M.ncell];
+                }
+                const T* cf = p.coef + (M.coef_off + jj) * kCoefStride;
+                if (!INC) bsum = bsum + cf[0] * (cf[1] * Yl[jj] + cf[2] * Vl[jj]);   // k_j (a_j Y^n + b_j Y^{n-1})
+                else bsum = bsum + (cf[0] * Yl[jj] + cf[1] * Vl[jj]);               // k_j ((a_j+b_j) Y - b_j V)
+              }
+            }
+            T Pn, Vn;
+            if (!INC) {
+              // Eq. Pz_update-LB (Eq. Pz_1D_Lorentz when there is no bath):
+              // P^{n+1} = [cE E - (w0^2 dt^2 - 2) P^n - c2 P^{n-1} - dt/2 sum_j k_j(a_j Y^n + b_j Y^{n-1})] / A
+              T num = M.cE * E - M.c1m * Pa - M.c2 * Pb;
+              if (bath) num = num - T(0.5) * dt * bsum;
+              Pn = num / M.A;
+              p.Pb[c * p.nmatcell + r] = Pn;   // overwrites P^{n-1}
+              Vn = Pn - Pa;
+            } else {
+              // increment form: V^{n+1} = [cE E - w0^2 dt^2 P^n + c2 V^n - dt/2 sum(...)] / A
+              T num = M.cE * E - M.W * Pa + M.c2 * Pb;
+              if (bath) num = num - T(0.5) * dt * bsum;
+              Vn = num / M.A;
+              Pn = Pa + Vn;
+              p.Pa[c * p.nmatcell + r] = Pn;
+              p.Pb[c * p.nmatcell + r] = Vn;
+            }
+            T ub = T(0);
+#pragma unroll
+            for (int jj = 0; jj < NBA; ++jj) {
+              if (jj < nb) {
+                const T* cf = p.coef + (M.coef_off + jj) * kCoefStride;
+                T Ynew, Vy;
+                if (!INC) {
+                  // Eq. Yzj_finite_difference: Y^{n+1} = a Y^n + (b+1) Y^{n-1} + c (P^{n+1} - P^{n-1})
+                  Ynew = cf[1] * Yl[jj] + cf[3] * Vl[jj] + cf[4] * (Pn - Pb);
+                  p.Yb[yoff + (int64_t)jj * M.ncell] = Ynew;
+                  Vy = Ynew - Yl[jj];
+                } else {
+                  // V_Y^{n+1} = (a+b) Y^n - (b+1) V_Y^n + c (V_P^{n+1} + V_P^n);  Y^{n+1} = Y^n + V_Y^{n+1}
+                  Vy = cf[2] * Yl[jj] + cf[3] * Vl[jj] + cf[4] * (Vn + Pb);
+                  Ynew = Yl[jj] + Vy;
+                  p.Ya[yoff + (int64_t)jj * M.ncell] = Ynew;
+                  p.Yb[yoff + (int64_t)jj * M.ncell] = Vy;
+                }
+                if (p.eE_on) ub += M.rho * ((Vy / dt) * (Vy / dt) + cf[5] * Ynew * Ynew);
+              }
+            }
+            if (p.eE_on && k >= p.ebox_lo && k < p.ebox_hi) {
+              uP += M.rho * ((Vn / dt) * (Vn / dt) + M.w0r2 * Pn * Pn);
+              uB += ub;
+            }
+          }
+        }
+        if (p.eE_on && k >= p.ebox_lo && k < p.ebox_hi) {
+          T eps = T(1);
+          if (mi >= 0) eps = p.mat[mi].eps;
+          uE += eps * (Ev[0] * Ev[0] + Ev[1] * Ev[1] + Ev[2] * Ev[2]);
+        }
+      }
+      // E-side monitor partials
+      for (int m = 0; m < p.nmon; ++m) {
+        if (k == p.mon_z[m]) {
+          double sx = block_sum(own ? (double)Ev[0] : 0.0, sred);
+          double sy = block_sum(own ? (double)Ev[1] : 0.0, sred);
+          if (tid == 0 && p.mon_partial_E) {
+            p.mon_partial_E[(int64_t)(2 * m) * nbxy + bxy] = sx;
+            p.mon_partial_E[(int64_t)(2 * m + 1) * nbxy + bxy] = sy;
+          }
+        }
+      }
+      hxm = sHi(0, ty + 1, tx + 1);
+      hym = sHi(1, ty + 1, tx + 1);
+    }
+  }
+  // energy partials of this block (every block writes, zero when outside the box)
+  if (p.eE_on) {
+    double a = block_sum((double)uE, sred);
+    double b = block_sum((double)uP, sred);
+    double c = block_sum((double)uB, sred);
+    if (tid == 0) {
+      p.en_partial_E[blin] = a;
+      p.en_partial_E[(int64_t)gridDim.x * gridDim.y * gridDim.z + blin] = b;
+      p.en_partial_E[(int64_t)2 * gridDim.x * gridDim.y * gridDim.z + blin] = c;
+    }
+  }
+  if (p.eH_on) {
+    double a = block_sum((double)uH, sred);
+    if (tid == 0) p.en_partial_H[blin] = a;
+  }
+}
+
+inline size_t step3d_smem_bytes(int ty, size_t elem) {
+  const size_t n = (size_t)12 * (ty + 2) * (kTX + 2) + (size_t)9 * (ty + 1) * (kTX + 1);
+  return n * elem + 16 + 8 * sizeof(double);
+}
+
+}  // namespace fdtdbath

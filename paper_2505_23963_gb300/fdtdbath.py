@@ -1,0 +1,326 @@
+"""Python binding of the C ABI in ``include/fdtdbath.h`` (argument marshalling only).
+
+The functions below carry the C names without the ``fdtdbath_`` prefix and do
+nothing but convert arguments: every step of the method runs in the CUDA
+library.  Loading fails loudly when the library is missing or no CUDA device is
+present -- there is no CPU fallback.
+
+PyTorch supplies device memory and streams: by default a simulation allocates
+through ``torch.cuda.caching_allocator_alloc`` and queues work on the current
+torch stream.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+OK = 0
+ERR_ARG, ERR_CFL, ERR_OOM, ERR_CUDA, ERR_NONFINITE, ERR_TIMEOUT, ERR_UNSUPPORTED = range(-1, -8, -1)
+KINDS = {"vacuum": 0, "lorentz": 1, "drude": 2, "lorentz_bath": 3}
+BATH_SHAPES = {"uniform": 0, "lorentzian": 1, "gaussian": 2}
+
+EXPORTED = ["fdtdbath_create", "fdtdbath_step", "fdtdbath_sync", "fdtdbath_read_fields",
+            "fdtdbath_write_fields", "fdtdbath_dft", "fdtdbath_energy", "fdtdbath_steps_done",
+            "fdtdbath_last_error", "fdtdbath_destroy", "fdtdbath_bath_form", "fdtdbath_query"]
+
+
+def field_E(c): return 0 + c
+def field_H(c): return 3 + c
+def field_P(c): return 6 + c
+def field_PM(c): return 9 + c
+def field_Y(c, j, level): return 1024 + (c * 2 + level) * 256 + j
+
+
+class Grid(C.Structure):
+    _fields_ = [("n", C.c_int64 * 3), ("pml_cells", C.c_int32)]
+
+
+class Material(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("z_lo", C.c_int64), ("z_hi", C.c_int64),
+                ("eps_inf", C.c_double), ("frequency", C.c_double), ("gamma", C.c_double),
+                ("sigma", C.c_double), ("num_bath", C.c_int32),
+                ("bath_frequencies", C.POINTER(C.c_double)),
+                ("bath_gammas", C.POINTER(C.c_double)),
+                ("bath_couplings", C.POINTER(C.c_double))]
+
+
+class Source(C.Structure):
+    _fields_ = [("component", C.c_int32), ("z", C.c_int64), ("center", C.c_double),
+                ("fwidth", C.c_double), ("amplitude", C.c_double), ("t0", C.c_double),
+                ("phase", C.POINTER(C.c_double))]
+
+
+class Monitor(C.Structure):
+    _fields_ = [("z", C.c_int64), ("nfreq", C.c_int32), ("freqs", C.POINTER(C.c_double))]
+
+
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
+
+
+class Options(C.Structure):
+    _fields_ = [("precision", C.c_int32), ("bath_storage", C.c_int32),
+                ("cuda_stream", C.c_void_p), ("alloc", ALLOC_FN), ("free", FREE_FN),
+                ("alloc_ctx", C.c_void_p), ("energy_lo", C.c_int64), ("energy_hi", C.c_int64),
+                ("energy_capacity", C.c_int64), ("device", C.c_int32)]
+
+
+_lib = None
+
+
+def lib(build_if_missing: bool = True):
+    """Load (building first if needed) the CUDA library; raise if it cannot be loaded."""
+    global _lib
+    if _lib is None:
+        path = _build.LIB
+        if build_if_missing:
+            path = _build.build()
+        if not os.path.exists(path):
+            raise RuntimeError(f"CUDA library not built: {path}")
+        L = C.CDLL(path)
+        vp, i32, i64, dp = C.c_void_p, C.c_int32, C.c_int64, C.POINTER(C.c_double)
+        L.fdtdbath_create.restype = i32
+        L.fdtdbath_create.argtypes = [C.POINTER(Grid), C.c_double, C.c_double,
+                                      C.POINTER(Material), i32, C.POINTER(Source), i32,
+                                      C.POINTER(Monitor), i32, C.POINTER(Options), C.POINTER(vp)]
+        L.fdtdbath_step.restype = i32
+        L.fdtdbath_step.argtypes = [vp, i64]
+        L.fdtdbath_sync.restype = i32
+        L.fdtdbath_sync.argtypes = [vp]
+        L.fdtdbath_read_fields.restype = i32
+        L.fdtdbath_read_fields.argtypes = [vp, i32, vp, C.c_size_t, i32]
+        L.fdtdbath_write_fields.restype = i32
+        L.fdtdbath_write_fields.argtypes = [vp, i32, vp, C.c_size_t, i32]
+        L.fdtdbath_dft.restype = i32
+        L.fdtdbath_dft.argtypes = [vp, i32, dp]
+        L.fdtdbath_energy.restype = i32
+        L.fdtdbath_energy.argtypes = [vp, dp, i64, C.POINTER(i64)]
+        L.fdtdbath_steps_done.restype = i64
+        L.fdtdbath_steps_done.argtypes = [vp]
+        L.fdtdbath_last_error.restype = C.c_char_p
+        L.fdtdbath_last_error.argtypes = [vp]
+        L.fdtdbath_destroy.restype = None
+        L.fdtdbath_destroy.argtypes = [vp]
+        L.fdtdbath_bath_form.restype = i32
+        L.fdtdbath_bath_form.argtypes = [i32, C.c_double, C.c_double, i32, C.c_double,
+                                         C.c_double, C.c_double, dp, dp, dp]
+        L.fdtdbath_query.restype = i64
+        L.fdtdbath_query.argtypes = [vp, i32]
+        _lib = L
+    return _lib
+
+
+class FdtdBathError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"fdtdbath error {code}: {msg}")
+        self.code = code
+
+
+def _check(rc: int, handle=None):
+    if rc != OK:
+        msg = lib().fdtdbath_last_error(handle)
+        raise FdtdBathError(rc, msg.decode() if msg else "")
+
+
+def _dptr(a: np.ndarray):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def _f64(a) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+
+
+# ------------------------------------------------------------------ C-named wrappers
+def bath_form(shape: str, frequency: float, gamma: float, num_bath: int, width: float,
+              bath_gamma: float, dephasing: float):
+    """Table I expansion (fdtdbath_bath_form): returns (frequencies, gammas, couplings)."""
+    f, g, k = (np.empty(num_bath) for _ in range(3))
+    _check(lib().fdtdbath_bath_form(BATH_SHAPES[shape], frequency, gamma, num_bath, width,
+                                    bath_gamma, dephasing, _dptr(f), _dptr(g), _dptr(k)))
+    return f, g, k
+
+
+class _TorchAllocator:
+    """Device allocator callbacks backed by torch's caching allocator."""
+
+    def __init__(self, device: int, stream: int):
+        import torch
+        self._torch = torch
+        self.device, self.stream = device, stream
+
+        def _alloc(size, _ctx):
+            try:
+                return int(torch.cuda.caching_allocator_alloc(int(size), self.device,
+                                                              self.stream or None))
+            except Exception:
+                return None
+
+        def _free(ptr, _ctx):
+            torch.cuda.caching_allocator_delete(int(ptr))
+
+        self.alloc = ALLOC_FN(_alloc)
+        self.free = FREE_FN(_free)
+
+
+def create(prob: dict, precision: int = 64, stream=None, use_torch_allocator: bool = True,
+           energy: bool = True, energy_capacity: int = 0, device: int = 0, bath_storage: int = 0):
+    """fdtdbath_create from a problem dict; returns (handle, keepalive)."""
+    L = lib()
+    nx, ny, nz = (int(v) for v in prob["n"])
+    grid = Grid((C.c_int64 * 3)(nx, ny, nz), int(prob.get("pml", 0)))
+    keep = []
+    mats = prob.get("materials", [])
+    marr = (Material * max(1, len(mats)))()
+    for i, m in enumerate(mats):
+        nb = len(m.get("bath_frequencies", [])) if m["kind"] == "lorentz_bath" else 0
+        arrs = [_f64(m.get(k, np.zeros(1)) if nb else np.zeros(1))
+                for k in ("bath_frequencies", "bath_gammas", "bath_couplings")]
+        keep += arrs
+        marr[i] = Material(KINDS[m["kind"]], int(m["z"][0]), int(m["z"][1]),
+                           float(m.get("eps_inf", 1.0)), float(m.get("frequency", 0.0)),
+                           float(m.get("gamma", 0.0)), float(m.get("sigma", 0.0)), nb,
+                           _dptr(arrs[0]), _dptr(arrs[1]), _dptr(arrs[2]))
+    srcs = prob.get("sources", [])
+    sarr = (Source * max(1, len(srcs)))()
+    for i, s in enumerate(srcs):
+        ph = s.get("phase")
+        php = None
+        if ph is not None:
+            ph = _f64(ph).reshape(-1)
+            keep.append(ph)
+            php = _dptr(ph)
+        sarr[i] = Source(int(s["component"]), int(s["z"]), float(s["center"]), float(s["fwidth"]),
+                         float(s.get("amplitude", 1.0)), float(s["t0"]), php)
+    mons = prob.get("monitors", [])
+    monarr = (Monitor * max(1, len(mons)))()
+    for i, mo in enumerate(mons):
+        fr = _f64(mo["freqs"])
+        keep.append(fr)
+        monarr[i] = Monitor(int(mo["z"]), int(fr.size), _dptr(fr))
+    opt = Options()
+    opt.precision = int(precision)
+    opt.bath_storage = int(bath_storage)
+    opt.device = int(device)
+    sptr = 0
+    if stream is not None:
+        sptr = int(getattr(stream, "cuda_stream", stream))
+    opt.cuda_stream = sptr or None
+    if use_torch_allocator:
+        alloc = _TorchAllocator(device, sptr)
+        keep.append(alloc)
+        opt.alloc, opt.free = alloc.alloc, alloc.free
+    lo, hi = prob.get("energy_box", (0, 0)) if energy else (0, 0)
+    opt.energy_lo, opt.energy_hi = int(lo), int(hi)
+    opt.energy_capacity = int(energy_capacity or max(1, int(prob.get("steps", 1024))) + 16)
+    h = C.c_void_p()
+    rc = L.fdtdbath_create(C.byref(grid), float(prob["resolution"]), float(prob["courant"]),
+                           marr, len(mats), sarr, len(srcs), monarr, len(mons), C.byref(opt),
+                           C.byref(h))
+    _check(rc, None)
+    return h, keep
+
+
+def step(h, n: int):
+    _check(lib().fdtdbath_step(h, int(n)), h)
+
+
+def sync(h):
+    _check(lib().fdtdbath_sync(h), h)
+
+
+def read_fields(h, field: int, shape, dtype) -> np.ndarray:
+    out = np.empty(shape, dtype=dtype)
+    _check(lib().fdtdbath_read_fields(h, int(field), out.ctypes.data, out.nbytes, 0), h)
+    return out
+
+
+def write_fields(h, field: int, arr: np.ndarray):
+    a = np.ascontiguousarray(arr)
+    _check(lib().fdtdbath_write_fields(h, int(field), a.ctypes.data, a.nbytes, 0), h)
+
+
+def dft(h, monitor: int, nfreq: int) -> np.ndarray:
+    out = np.empty((nfreq, 8), dtype=np.float64)
+    _check(lib().fdtdbath_dft(h, int(monitor), _dptr(out)), h)
+    return out[:, 0::2] + 1j * out[:, 1::2]
+
+
+def energy(h, maxlen: int) -> np.ndarray:
+    out = np.empty((max(1, maxlen), 4), dtype=np.float64)
+    n = C.c_int64(0)
+    _check(lib().fdtdbath_energy(h, _dptr(out), int(maxlen), C.byref(n)), h)
+    return out[:n.value].copy()
+
+
+def steps_done(h) -> int:
+    return int(lib().fdtdbath_steps_done(h))
+
+
+def query(h, key: int) -> int:
+    return int(lib().fdtdbath_query(h, int(key)))
+
+
+def destroy(h):
+    lib().fdtdbath_destroy(h)
+
+
+# ------------------------------------------------------------------ convenience class
+class Simulation:
+    """A simulation built from a problem dict (see ``workloads``), owning its handle."""
+
+    def __init__(self, prob: dict, precision: int = 64, stream=None, energy: bool = True,
+                 use_torch_allocator: bool = True, energy_capacity: int = 0,
+                 bath_storage: int = 0):
+        self.prob = prob
+        self.precision = precision
+        nx, ny, nz = (int(v) for v in prob["n"])
+        self.shape = (nz, ny, nx)
+        self.dtype = np.float64 if precision == 64 else np.float32
+        self.nfreq = [len(m["freqs"]) for m in prob.get("monitors", [])]
+        self.h, self._keep = create(prob, precision, stream=stream, energy=energy,
+                                    use_torch_allocator=use_torch_allocator,
+                                    energy_capacity=energy_capacity, bath_storage=bath_storage)
+
+    def step(self, n: int):
+        step(self.h, n)
+
+    def sync(self):
+        sync(self.h)
+
+    @property
+    def steps_done(self) -> int:
+        return steps_done(self.h)
+
+    def get(self, name: str, comp: int = 0, mode: int = 0, level: int = 0) -> np.ndarray:
+        fid = {"E": field_E, "H": field_H, "P": field_P, "Pm": field_PM}.get(name)
+        f = fid(comp) if fid else field_Y(comp, mode, level)
+        return read_fields(self.h, f, self.shape, self.dtype)
+
+    def set(self, name: str, arr, comp: int = 0, mode: int = 0, level: int = 0):
+        fid = {"E": field_E, "H": field_H, "P": field_P, "Pm": field_PM}.get(name)
+        f = fid(comp) if fid else field_Y(comp, mode, level)
+        write_fields(self.h, f, np.asarray(arr, dtype=self.dtype).reshape(self.shape))
+
+    def dft(self, mon: int = 0) -> np.ndarray:
+        return dft(self.h, mon, self.nfreq[mon])
+
+    def trace(self, maxlen: int | None = None) -> np.ndarray:
+        return energy(self.h, maxlen or self.steps_done + 1)
+
+    def launches(self) -> int:
+        return query(self.h, 1)
+
+    def close(self):
+        if getattr(self, "h", None):
+            destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -146,8 +146,9 @@ def precision_crop(steps: int = 400) -> dict:
 
 
 def small_3d(nx=40, ny=12, layout=(6, 5, 3, 10, 3, 5), nb=8, steps=60, seed=0) -> dict:
-    """Small 3D case with ragged x/y tiles for element-wise parity against the oracle."""
-    return slab_cavity(nx, ny, layout, 10.0, num_bath=nb, sigma=0.05 ** 2, bath_seed=seed,
+    """Small 3D case with ragged x/y tiles for element-wise parity against the oracle
+    (resolution 20 keeps the Drude mirrors inside the coupled stability limit)."""
+    return slab_cavity(nx, ny, layout, 20.0, num_bath=nb, sigma=0.05 ** 2, bath_seed=seed,
                        phase_seed=seed, nfreq=16, steps=steps, name=f"small3d_{nx}x{ny}_nb{nb}")
 
 
