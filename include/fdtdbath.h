@@ -186,6 +186,20 @@ int fdtdbath_bath_form(int32_t shape, double frequency, double gamma, int32_t nu
  * so far, 2 bytes of device memory held, 3 blocks of the 3D step kernel, 4 z-chunks. */
 int64_t fdtdbath_query(const fdtdbath_sim *sim, int32_t key);
 
+/* Energy (U_EM, U_P, U_bath) of planes z_lo <= k < z_hi of the current state -- the same
+ * quantities and weights as one fdtdbath_energy() entry -- computed WITHOUT allocating memory.
+ * The paper has no counterpart: this entry point exists for callers that cannot allocate device
+ * memory when they need the result (code running inside a stream capture, a real-time loop that
+ * forbids allocation, a host framework that owns the whole memory pool).  Its scratch space is a
+ * static device array of this library holding one partial sum per plane: boxes deeper than 4096
+ * planes are rejected with FDTDBATH_ERR_ARG.  out receives 3 doubles, in device memory when
+ * out_on_device is nonzero, else in host memory; the call waits for the simulation's stream.
+ * The first call on a device looks the array's address up (a host-side runtime call), so make
+ * it before any stream capture on that device.  All calls on a device share the array: calls
+ * that overlap on the GPU (e.g. from two streams) race and must be serialized by the caller. */
+int fdtdbath_box_energy_noalloc(fdtdbath_sim *sim, int64_t z_lo, int64_t z_hi, double *out,
+                                int32_t out_on_device);
+
 #ifdef __cplusplus
 }
 #endif

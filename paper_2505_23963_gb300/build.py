@@ -27,6 +27,7 @@ UNITS = [
     ("step3d_f32.cu", []),
     ("step3d_f64.cu", ["--fmad=false"]),
     ("reduce.cu", ["--fmad=false"]),
+    ("noalloc.cu", ["--fmad=false"]),
 ]
 
 

@@ -491,6 +491,58 @@ char* elem_ptr(void* base, int64_t idx, size_t esz) { return (char*)base + idx *
 
 }  // namespace
 
+int fdtdbath_internal_view(fdtdbath_sim* s, SimView* v) {
+  if (!s || !v) return FDTDBATH_ERR_ARG;
+  cudaSetDevice(s->device);
+  int rc = flush_h(s);
+  if (rc) return rc;
+  *v = SimView{};
+  v->prec = s->prec;
+  v->inc = s->prec == 32 ? 1 : 0;
+  v->nx = s->nx;
+  v->ny = s->ny;
+  v->nz = s->nz;
+  v->plane = s->plane;
+  v->ncell = s->ncell;
+  v->nmatcell = s->nmatcell;
+  v->dx = s->dx;
+  v->dt = s->dt;
+  v->E = s->E[s->ecur];
+  v->H = s->H[s->hcur];
+  if (s->prec == 64) {
+    v->Pa = s->Pslot[s->pcur];
+    v->Pb = s->Pslot[1 - s->pcur];
+    v->Ya = s->Yslot[s->pcur];
+    v->Yb = s->Yslot[1 - s->pcur];
+  } else {
+    v->Pa = s->Pslot[0];
+    v->Pb = s->Pslot[1];
+    v->Ya = s->Yslot[0];
+    v->Yb = s->Yslot[1];
+  }
+  v->nmat = (int)s->mats.size();
+  for (size_t m = 0; m < s->mats.size(); ++m) {
+    const HostMat& h = s->mats[m];
+    SimViewMat& o = v->mat[m];
+    o.kind = h.kind;
+    o.nb = h.nb;
+    o.zlo = h.zlo;
+    o.zhi = h.zhi;
+    o.ncell = h.ncell;
+    o.base = h.base;
+    o.ybase = h.ybase;
+    o.eps = h.eps;
+    o.rho = h.rho;
+    o.w0r2 = h.w0r2;
+    for (int j = 0; j < h.nb; ++j) o.wj2[j] = h.wj[j] * h.wj[j];
+  }
+  v->stream = s->stream;
+  v->device = s->device;
+  return 0;
+}
+
+int fdtdbath_internal_fail(fdtdbath_sim* s, int code, const char* msg) { return fail(s, code, msg); }
+
 // ======================================================================================
 extern "C" {
 

@@ -137,4 +137,34 @@ struct DftParams {
 };
 int launch_dft_accumulate(const DftParams& d, void* stream);
 
+// Read-only view of a simulation's current device state (after its pending H half-step has
+// been flushed), for entry points defined outside api.cpp.
+struct SimViewMat {
+  int kind, nb;
+  int64_t zlo, zhi, ncell, base, ybase;
+  double eps, rho, w0r2;
+  double wj2[kMaxBath];
+};
+struct SimView {
+  int prec;                 // 32 or 64
+  int inc;                  // 1: (value, increment) storage of P and Y; 0: two time levels
+  int64_t nx, ny, nz, plane, ncell, nmatcell;
+  double dx, dt;
+  const void* E;            // [3][ncell], E^{n-1/2}
+  const void* H;            // [3][ncell], H^n
+  const void* Pa;           // P^{n+1/2}
+  const void* Pb;           // P^{n-1/2} (two levels) or P^{n+1/2} - P^{n-1/2} (increment)
+  const void* Ya;
+  const void* Yb;
+  int nmat;
+  SimViewMat mat[kMaxMat];
+  void* stream;
+  int device;
+};
+
 }  // namespace fdtdbath
+
+struct fdtdbath_sim;
+// Implemented in api.cpp: flush the pending H half-step and describe the state; record errors.
+int fdtdbath_internal_view(fdtdbath_sim* s, fdtdbath::SimView* v);
+int fdtdbath_internal_fail(fdtdbath_sim* s, int code, const char* msg);

@@ -25,7 +25,8 @@ BATH_SHAPES = {"uniform": 0, "lorentzian": 1, "gaussian": 2}
 
 EXPORTED = ["fdtdbath_create", "fdtdbath_step", "fdtdbath_sync", "fdtdbath_read_fields",
             "fdtdbath_write_fields", "fdtdbath_dft", "fdtdbath_energy", "fdtdbath_steps_done",
-            "fdtdbath_last_error", "fdtdbath_destroy", "fdtdbath_bath_form", "fdtdbath_query"]
+            "fdtdbath_last_error", "fdtdbath_destroy", "fdtdbath_bath_form", "fdtdbath_query",
+            "fdtdbath_box_energy_noalloc"]
 
 
 def field_E(c): return 0 + c
@@ -110,6 +111,8 @@ def lib(build_if_missing: bool = True):
                                          C.c_double, C.c_double, dp, dp, dp]
         L.fdtdbath_query.restype = i64
         L.fdtdbath_query.argtypes = [vp, i32]
+        L.fdtdbath_box_energy_noalloc.restype = i32
+        L.fdtdbath_box_energy_noalloc.argtypes = [vp, i64, i64, vp, i32]
         _lib = L
     return _lib
 
@@ -266,6 +269,18 @@ def query(h, key: int) -> int:
 
 def destroy(h):
     lib().fdtdbath_destroy(h)
+
+
+def box_energy_noalloc(h, z_lo: int, z_hi: int, out_ptr: int | None = None) -> np.ndarray | None:
+    """fdtdbath_box_energy_noalloc: (U_EM, U_P, U_bath) of planes [z_lo, z_hi) of the current
+    state, computed by the library without allocating memory.  With out_ptr (a device address
+    of 3 doubles) the result stays on the device and None is returned."""
+    if out_ptr is not None:
+        _check(lib().fdtdbath_box_energy_noalloc(h, int(z_lo), int(z_hi), int(out_ptr), 1), h)
+        return None
+    out = np.zeros(3, dtype=np.float64)
+    _check(lib().fdtdbath_box_energy_noalloc(h, int(z_lo), int(z_hi), out.ctypes.data, 0), h)
+    return out
 
 
 # ------------------------------------------------------------------ convenience class
