@@ -198,14 +198,14 @@ void expand_material(HostMat& m, double dt) {
     L[2] = b;
     L[3] = b + 1.0;
     L[4] = c;
-    L[5] = wj * wj;
+    L[5] = wj * wj * dt2;
     double* I = &m.rowsInc[(size_t)j * kCoefStride];
     I[0] = kj * apb;
     I[1] = -kj * b;
     I[2] = apb;
     I[3] = mbp1;
     I[4] = c;
-    I[5] = wj * wj;
+    I[5] = wj * wj * dt2;
   }
   const double w0 = m.w0, g0 = m.g0;
   m.cE = w0 * w0 * dt * dt * m.sigma;
@@ -234,7 +234,7 @@ void expand_material(HostMat& m, double dt) {
 }
 
 template <typename T>
-MatK<T> mat_k(const HostMat& m, int coef_off) {
+MatK<T> mat_k(const HostMat& m, int coef_off, double dt) {
   MatK<T> k{};
   k.zlo = (int)m.zlo;
   k.zhi = (int)m.zhi;
@@ -250,8 +250,10 @@ MatK<T> mat_k(const HostMat& m, int coef_off) {
   k.W = (T)m.W;
   k.c2 = (T)m.c2;
   k.A = (T)m.A;
-  k.rho = (T)m.rho;
-  k.w0r2 = (T)m.w0r2;
+  k.inv_A = (T)(1.0 / m.A);
+  k.inv_eps = (T)(1.0 / m.eps);
+  k.rho_idt2 = (T)(m.rho / (dt * dt));
+  k.w0r2dt2 = (T)(m.w0r2 * dt * dt);
   return k;
 }
 
@@ -313,23 +315,17 @@ Step3DParams<T> make_params(fdtdbath_sim* s, int doH, int doE) {
   p.nmat = (int)s->mats.size();
   int off = 0;
   for (size_t m = 0; m < s->mats.size(); ++m) {
-    p.mat[m] = mat_k<T>(s->mats[m], off);
+    p.mat[m] = mat_k<T>(s->mats[m], off, s->dt);
     off += s->mats[m].nb;
   }
   p.coef = (const T*)s->coef;
+  p.nmodes = off;
   p.D = (T*)s->D;
   p.nmatcell = s->nmatcell;
-  if (s->prec == 64) {
-    p.Pa = (T*)s->Pslot[s->pcur];
-    p.Pb = (T*)s->Pslot[1 - s->pcur];
-    p.Ya = (T*)s->Yslot[s->pcur];
-    p.Yb = (T*)s->Yslot[1 - s->pcur];
-  } else {
-    p.Pa = (T*)s->Pslot[0];
-    p.Pb = (T*)s->Pslot[1];
-    p.Ya = (T*)s->Yslot[0];
-    p.Yb = (T*)s->Yslot[1];
-  }
+  p.Pa = (T*)s->Pslot[s->pcur];
+  p.Pb = (T*)s->Pslot[1 - s->pcur];
+  p.Ya = (T*)s->Yslot[s->pcur];
+  p.Yb = (T*)s->Yslot[1 - s->pcur];
   p.nsrc = (int)s->srcs.size();
   const double t = (double)s->n * s->dt;
   for (size_t q = 0; q < s->srcs.size(); ++q) {
@@ -498,7 +494,7 @@ int fdtdbath_internal_view(fdtdbath_sim* s, SimView* v) {
   if (rc) return rc;
   *v = SimView{};
   v->prec = s->prec;
-  v->inc = s->prec == 32 ? 1 : 0;
+  v->inc = 0;
   v->nx = s->nx;
   v->ny = s->ny;
   v->nz = s->nz;
@@ -509,17 +505,10 @@ int fdtdbath_internal_view(fdtdbath_sim* s, SimView* v) {
   v->dt = s->dt;
   v->E = s->E[s->ecur];
   v->H = s->H[s->hcur];
-  if (s->prec == 64) {
-    v->Pa = s->Pslot[s->pcur];
-    v->Pb = s->Pslot[1 - s->pcur];
-    v->Ya = s->Yslot[s->pcur];
-    v->Yb = s->Yslot[1 - s->pcur];
-  } else {
-    v->Pa = s->Pslot[0];
-    v->Pb = s->Pslot[1];
-    v->Ya = s->Yslot[0];
-    v->Yb = s->Yslot[1];
-  }
+  v->Pa = s->Pslot[s->pcur];
+  v->Pb = s->Pslot[1 - s->pcur];
+  v->Ya = s->Yslot[s->pcur];
+  v->Yb = s->Yslot[1 - s->pcur];
   v->nmat = (int)s->mats.size();
   for (size_t m = 0; m < s->mats.size(); ++m) {
     const HostMat& h = s->mats[m];
@@ -668,6 +657,11 @@ int fdtdbath_create(const fdtdbath_grid* grid, double resolution, double courant
   }
   s->nmatcell = base;
   s->nybath = ybase;
+  // the kernels index every array with 32-bit offsets
+  const int64_t lim = ((int64_t)1 << 31) - 1;
+  if (3 * s->ncell > lim || 3 * s->nmatcell > lim || s->nybath > lim ||
+      2 * (2 * (int64_t)s->npml + 1) * s->plane > lim)
+    return bail(FDTDBATH_ERR_ARG, "state arrays above 2^31 elements are not supported");
   if (s->nbmax > 0) s->nbmax = s->nbmax <= 4 ? 4 : s->nbmax <= 8 ? 8 : s->nbmax <= 16 ? 16 : 32;
 
   // ---- sources / monitors / energy box ----
@@ -694,9 +688,8 @@ int fdtdbath_create(const fdtdbath_grid* grid, double resolution, double courant
   }
 
   // ---- launch plan ----
-  int ty_max = 8;
-  if (const char* e = std::getenv("FDTDBATH_TY")) ty_max = std::min(8, std::max(1, std::atoi(e)));
-  s->ty = (int)std::min<int64_t>(ty_max, ny);
+  // tile height: 8 rows, or single-row tiles for grids with fewer than 8 rows
+  s->ty = ny >= 8 ? 8 : 1;
   s->nbx = (int)((nx + kTX - 1) / kTX);
   s->nby = (int)((ny + s->ty - 1) / s->ty);
   int zc = 32;
@@ -808,7 +801,7 @@ int fdtdbath_step(fdtdbath_sim* s, int64_t nsteps) {
     }
     int rc = launch_step(s, s->h_pending ? 1 : 0, 1);
     if (rc) return rc;
-    if (s->prec == 64) s->pcur = 1 - s->pcur;
+    s->pcur = 1 - s->pcur;
     s->n += 1;
     s->h_pending = true;
   }
@@ -841,33 +834,20 @@ int fdtdbath_read_fields(fdtdbath_sim* s, int32_t field, void* dst, size_t dst_b
     if (rc) return rc;
   } else {
     for (auto& m : s->mats) {
-      std::vector<double> a, b;
+      std::vector<double> a;
       const void* pa;
-      const void* pb = nullptr;
       if (f.kind == 1) {
         if (m.kind == FDTDBATH_VACUUM) continue;
         const int64_t off = f.comp * s->nmatcell + m.base;
-        if (s->prec == 64) {
-          pa = elem_ptr(s->Pslot[f.level == 0 ? s->pcur : 1 - s->pcur], off, s->esz);
-        } else {
-          pa = elem_ptr(s->Pslot[0], off, s->esz);
-          if (f.level == 1) pb = elem_ptr(s->Pslot[1], off, s->esz);
-        }
+        pa = elem_ptr(s->Pslot[f.level == 0 ? s->pcur : 1 - s->pcur], off, s->esz);
       } else {
         if (f.mode >= m.nb) continue;
         const int64_t off = m.ybase + ((int64_t)f.comp * m.nb + f.mode) * m.ncell;
-        if (s->prec == 64) {
-          pa = elem_ptr(s->Yslot[f.level == 0 ? s->pcur : 1 - s->pcur], off, s->esz);
-        } else {
-          pa = elem_ptr(s->Yslot[0], off, s->esz);
-          if (f.level == 1) pb = elem_ptr(s->Yslot[1], off, s->esz);
-        }
+        pa = elem_ptr(s->Yslot[f.level == 0 ? s->pcur : 1 - s->pcur], off, s->esz);
       }
       rc = fetch(s, pa, m.ncell, a);
-      if (!rc && pb) rc = fetch(s, pb, m.ncell, b);
       if (rc) return rc;
-      for (int64_t r = 0; r < m.ncell; ++r)
-        full[(size_t)(m.zlo * s->plane + r)] = pb ? a[(size_t)r] - b[(size_t)r] : a[(size_t)r];
+      for (int64_t r = 0; r < m.ncell; ++r) full[(size_t)(m.zlo * s->plane + r)] = a[(size_t)r];
     }
   }
   // convert to the element type and deliver
@@ -929,45 +909,18 @@ int fdtdbath_write_fields(fdtdbath_sim* s, int32_t field, const void* src, size_
     return rc;
   }
   for (auto& m : s->mats) {
-    void *pa, *pb = nullptr;
+    void* pa;
     if (f.kind == 1) {
       if (m.kind == FDTDBATH_VACUUM) continue;
       const int64_t off = f.comp * s->nmatcell + m.base;
-      if (s->prec == 64) {
-        pa = elem_ptr(s->Pslot[f.level == 0 ? s->pcur : 1 - s->pcur], off, s->esz);
-      } else {
-        pa = elem_ptr(s->Pslot[0], off, s->esz);
-        pb = elem_ptr(s->Pslot[1], off, s->esz);
-      }
+      pa = elem_ptr(s->Pslot[f.level == 0 ? s->pcur : 1 - s->pcur], off, s->esz);
     } else {
       if (f.mode >= m.nb) continue;
       const int64_t off = m.ybase + ((int64_t)f.comp * m.nb + f.mode) * m.ncell;
-      if (s->prec == 64) {
-        pa = elem_ptr(s->Yslot[f.level == 0 ? s->pcur : 1 - s->pcur], off, s->esz);
-      } else {
-        pa = elem_ptr(s->Yslot[0], off, s->esz);
-        pb = elem_ptr(s->Yslot[1], off, s->esz);
-      }
+      pa = elem_ptr(s->Yslot[f.level == 0 ? s->pcur : 1 - s->pcur], off, s->esz);
     }
     std::vector<double> v(in.begin() + m.zlo * s->plane, in.begin() + m.zlo * s->plane + m.ncell);
-    if (!pb) {
-      rc = store(s, pa, v);
-    } else {
-      // increment storage (value X, increment V = X - X'): writing X keeps X', writing X' keeps X
-      std::vector<double> a, b;
-      rc = fetch(s, pa, m.ncell, a);
-      if (!rc) rc = fetch(s, pb, m.ncell, b);
-      if (rc) return rc;
-      std::vector<double> vnew((size_t)m.ncell);
-      if (f.level == 0) {
-        for (int64_t q = 0; q < m.ncell; ++q) vnew[(size_t)q] = v[(size_t)q] - (a[(size_t)q] - b[(size_t)q]);
-        rc = store(s, pa, v);
-        if (!rc) rc = store(s, pb, vnew);
-      } else {
-        for (int64_t q = 0; q < m.ncell; ++q) vnew[(size_t)q] = a[(size_t)q] - v[(size_t)q];
-        rc = store(s, pb, vnew);
-      }
-    }
+    rc = store(s, pa, v);
     if (rc) return rc;
   }
   if (f.kind == 1 && f.level == 1) rc = refresh_D();

@@ -6,9 +6,8 @@
 //   psiE        : CPML memories of the E update, [2][2*npml][ny][nx], updated in place.
 //   psiH        : CPML memories of the H update, two buffers, [2][2*npml+1][ny][nx].
 //   D           : FP64 path only, [3][material cells] (material planes only).
-//   Pa / Pb     : FP64 path: P^{n+1/2} and P^{n-1/2} slots, the new P^{n+3/2} overwrites
-//                 the older slot and the host swaps the two pointers each step.
-//                 FP32 path (increment form): Pa = P^{n+1/2}, Pb = V = P^{n+1/2} - P^{n-1/2}.
+//   Pa / Pb     : P^{n+1/2} and P^{n-1/2} slots; the new P^{n+3/2} overwrites the older
+//                 slot and the host swaps the two pointers each step (both precisions).
 //   Ya / Yb     : the same two slots for every bath mode, [3][nb][cells] per
 //                 Lorentz-Bath material (material-only storage).
 //   partial     : per-block FP64 partial sums of the monitor planes and of the energy box,
@@ -41,13 +40,15 @@ struct MatK {
   T W;            // w0^2 dt^2 (Drude: 0)                [FP32 increment path]
   T c2;           // 1 - gamma0 dt/2 - dt/2 sum_j k_j c_j
   T A;            // 1 + gamma0 dt/2 + dt/2 sum_j k_j c_j
-  T rho;          // 1/(sigma w0^2) for the energy density (0 when sigma = 0)
-  T w0r2;         // w0^2 in the potential term (Drude: 0)
+  T inv_A;        // 1/A                                 [FP32 increment path]
+  T inv_eps;      // 1/eps_inf                           [FP32 increment path]
+  T rho_idt2;     // rho/dt^2, rho = 1/(sigma w0^2) (0 when sigma = 0), energy density
+  T w0r2dt2;      // (w0 dt)^2 in the potential term (Drude: 0)
 };
 
 // Per bath mode j (coefficient row of kCoefStride values):
-//   FP64 path : {k_j, a_j, b_j, b_j + 1, c_j, w_j^2}
-//   FP32 path : {k_j (a_j + b_j), -k_j b_j, a_j + b_j, -(b_j + 1), c_j, w_j^2}
+//   FP64 path : {k_j, a_j, b_j, b_j + 1, c_j, (w_j dt)^2}
+//   FP32 path : {k_j (a_j + b_j), -k_j b_j, a_j + b_j, -(b_j + 1), c_j, (w_j dt)^2}  (increment arithmetic)
 
 template <typename T>
 struct Step3DParams {
@@ -69,7 +70,8 @@ struct Step3DParams {
   // materials
   int nmat;
   MatK<T> mat[kMaxMat];
-  const T* coef;
+  const T* coef;   // [nmodes][kCoefStride], staged into shared memory by every CTA
+  int nmodes;
   T* D;
   T* Pa;
   T* Pb;
@@ -147,13 +149,13 @@ struct SimViewMat {
 };
 struct SimView {
   int prec;                 // 32 or 64
-  int inc;                  // 1: (value, increment) storage of P and Y; 0: two time levels
+  int inc;                  // 1: Pb/Yb hold increments X^{n+1/2} - X^{n-1/2}; 0: the older level
   int64_t nx, ny, nz, plane, ncell, nmatcell;
   double dx, dt;
   const void* E;            // [3][ncell], E^{n-1/2}
   const void* H;            // [3][ncell], H^n
   const void* Pa;           // P^{n+1/2}
-  const void* Pb;           // P^{n-1/2} (two levels) or P^{n+1/2} - P^{n-1/2} (increment)
+  const void* Pb;           // P^{n-1/2}
   const void* Ya;
   const void* Yb;
   int nmat;

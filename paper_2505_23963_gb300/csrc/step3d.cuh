@@ -19,10 +19,11 @@
 //   INC = false (FP64): the literal form -- D stored in material cells, E = (D - P)/eps,
 //     two time levels of P and Y with the new level overwriting the oldest; every
 //     expression is evaluated in the order the equations print it.
-//   INC = true (FP32): the increment form -- E updated D-free
-//     (E += (dt curl H + dt J - (P^{n+1/2} - P^{n-1/2}))/eps), P and every Y_j carried as
-//     (value, increment).  Algebraically identical to Eq. Pz_update-LB / Yzj_finite_difference
-//     but without the 2 - w^2 dt^2 cancellation that costs FP32 its phase accuracy.
+//   INC = true (FP32): increment arithmetic on the same two stored levels -- E updated D-free
+//     (E += (dt curl H + dt J - V)/eps with V = P^{n+1/2} - P^{n-1/2}), and P and every Y_j
+//     advanced through their increment, X^{n+1} = X^n + V^{n+1}, written over X^{n-1}.
+//     Algebraically identical to Eq. Pz_update-LB / Yzj_finite_difference but without
+//     representing 2 - w^2 dt^2, whose FP32 rounding would shift every oscillator frequency.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -114,36 +115,50 @@ __device__ __forceinline__ void cp_async_elem(T* sdst, const T* gsrc) {
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
 __device__ __forceinline__ void cp_async_wait_1() { asm volatile("cp.async.wait_group 1;\n" ::); }
 
-template <typename T, bool INC, int NBMAX>
-__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) step3d_kernel(const Step3DParams<T> p) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int TY = blockDim.y;
-  constexpr int TX = kTX;
-  constexpr int FX = TX + 2;
-  const int FY = TY + 2;
-  constexpr int HX = TX + 1;
-  const int HY = TY + 1;
+template <int TY>
+struct Tile {
+  static constexpr int TX = kTX, FX = kTX + 2, FY = TY + 2, HX = kTX + 1, HY = TY + 1;
+  static constexpr int NTHR = kTX * TY;
+  static constexpr int FE = FY * FX;                 // E frame cells (tile + 1 on every side)
+  static constexpr int FH = HY * HX;                 // H frame cells (tile + -x / -y halo)
+  static constexpr int RE = (FE + NTHR - 1) / NTHR;  // E frame cells staged per thread
+  static constexpr int RH = (FH + NTHR - 1) / NTHR;
+};
+
+template <typename T, int NBMAX, int TY>
+struct StepBounds {
+  static constexpr int threads = kTX * TY;
+  static constexpr int min_blocks = TY == 8 ? ((sizeof(T) == 8 && NBMAX >= 16) ? 1 : 2) : 8;
+};
+
+template <typename T, bool INC, int NBMAX, int TY>
+__global__ void __launch_bounds__(StepBounds<T, NBMAX, TY>::threads, StepBounds<T, NBMAX, TY>::min_blocks)
+step3d_kernel(const Step3DParams<T> p) {
+  using G = Tile<TY>;
+  constexpr int TX = G::TX, FX = G::FX, HX = G::HX, NTHR = G::NTHR, FE = G::FE, FH = G::FH;
   // bath modes preloaded for all three components with the rest of the plane's state
-  constexpr int NBP = NBMAX <= 8 ? NBMAX : 0;
+  constexpr int NBP = NBMAX <= (sizeof(T) == 4 ? 8 : 4) ? NBMAX : 0;
   constexpr int NBA = NBMAX > 0 ? NBMAX : 1;
-  // E_in frames, ring of 4 planes [4][3][FY][FX]: planes k, k+1 feed H^n(k), plane k also the
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  // E_in frames, ring of 4 planes [4][3][FE]: planes k, k+1 feed H^n(k), plane k also the
   // E update of k (after the second barrier), plane k+2 is in flight; the slot refilled at the
   // top of step k+1 (plane k+3) held plane k-1, last read before this step's first barrier.
   T* sE = reinterpret_cast<T*>(smem_raw);
-  T* sHin = sE + 12 * FY * FX;                   // H_in frames, ring of 2 planes: [2][3][HY][HX]
-  T* sH = sHin + 6 * HY * HX;                    // H^n of the current plane:     [3][HY][HX]
+  T* sHin = sE + 12 * FE;                        // H_in frames, ring of 2 planes: [2][3][FH]
+  T* sH = sHin + 6 * FH;                         // H^n of the current plane:     [3][FH]
+  T* sCoef = sH + 3 * FH;                        // bath coefficients:            [modes][8]
   double* sred = reinterpret_cast<double*>(
-      (reinterpret_cast<uintptr_t>(sH + 3 * HY * HX) + 15) & ~uintptr_t(15));
+      (reinterpret_cast<uintptr_t>(sCoef + kCoefStride * p.nmodes) + 15) & ~uintptr_t(15));
 
   const int tx = threadIdx.x, ty = threadIdx.y;
   const int tid = ty * TX + tx;
-  const int nthr = TX * TY;
   const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
   const int i = x0 + tx, j = y0 + ty;
   const bool own = (i < p.nx) && (j < p.ny);
   const int zb = p.zstart[blockIdx.z], ze = p.zstart[blockIdx.z + 1];
-  const int64_t plane = p.plane, ncell = p.ncell;
-  const int64_t qxy = own ? (int64_t)j * p.nx + i : 0;
+  // every array index fits in 32 bits (checked when the simulation is created)
+  const int plane = (int)p.plane, ncell = (int)p.ncell;
+  const int qxy = own ? j * p.nx + i : 0;
   const T dx = p.dx, dt = p.dt, inv_dx = p.inv_dx;
   const int nbxy = gridDim.x * gridDim.y;
   const int bxy = blockIdx.y * gridDim.x + blockIdx.x;
@@ -151,57 +166,99 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) step3d_kernel(con
   const T* __restrict__ Ein = p.Ein;
   const T* __restrict__ Hin = p.Hin;
 
-  auto sEi = [&](int k, int c, int yy, int xx) -> T& {
-    return sE[(((k & 3) * 3 + c) * FY + yy) * FX + xx];
-  };
-  auto sHini = [&](int k, int c, int yy, int xx) -> T& {
-    return sHin[(((k & 1) * 3 + c) * HY + yy) * HX + xx];
-  };
-  auto sHi = [&](int c, int yy, int xx) -> T& { return sH[(c * HY + yy) * HX + xx]; };
+  for (int q = tid; q < kCoefStride * p.nmodes; q += NTHR) sCoef[q] = p.coef[q];
+
+  // Frame cells this thread stages every plane: shared-memory offset and periodic (x, y) offset
+  int es[G::RE], eg[G::RE], hs[G::RH], hg[G::RH];
+#pragma unroll
+  for (int r = 0; r < G::RE; ++r) {
+    const int idx = tid + r * NTHR;
+    es[r] = -1;
+    eg[r] = 0;
+    if (idx < FE) {
+      const int yy = idx / FX, xx = idx - yy * FX;
+      es[r] = idx;
+      eg[r] = wrapi(y0 - 1 + yy, p.ny) * p.nx + wrapi(x0 - 1 + xx, p.nx);
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < G::RH; ++r) {
+    const int idx = tid + r * NTHR;
+    hs[r] = -1;
+    hg[r] = 0;
+    if (idx < FH) {
+      const int yy = idx / HX, xx = idx - yy * HX;
+      hs[r] = idx;
+      hg[r] = wrapi(y0 - 1 + yy, p.ny) * p.nx + wrapi(x0 - 1 + xx, p.nx);
+    }
+  }
+  // H tasks of this thread: its own cell, and up to two cells of the -y row / -x column halo
+  const int own_fe = (ty + 1) * FX + (tx + 1), own_fh = (ty + 1) * HX + (tx + 1);
+  constexpr int NHT = (TX + TY + NTHR - 1) / NTHR;
+  int ht_fe[NHT], ht_fh[NHT], ht_g[NHT];
+#pragma unroll
+  for (int r = 0; r < NHT; ++r) {
+    const int t = tid + r * NTHR;
+    ht_fe[r] = -1;
+    ht_fh[r] = 0;
+    ht_g[r] = 0;
+    if (t < TX + TY) {
+      const int hy = t < TX ? 0 : t - TX + 1, hx = t < TX ? t + 1 : 0;
+      ht_fe[r] = hy * FX + hx;
+      ht_fh[r] = hy * HX + hx;
+      ht_g[r] = wrapi(y0 - 1 + hy, p.ny) * p.nx + wrapi(x0 - 1 + hx, p.nx);
+    }
+  }
+  auto slotE = [&](int k) -> T* { return sE + (k & 3) * 3 * FE; };
+  auto slotH = [&](int k) -> T* { return sHin + (k & 1) * 3 * FH; };
 
   // asynchronous staging of the E_in frame of plane k (tile + 1 cell, periodic in x, y)
   auto issueE = [&](int k) {
-    for (int idx = tid; idx < FY * FX; idx += nthr) {
-      const int yy = idx / FX, xx = idx - yy * FX;
-      const int gx = wrapi(x0 - 1 + xx, p.nx), gy = wrapi(y0 - 1 + yy, p.ny);
-      const int64_t q = (int64_t)k * plane + (int64_t)gy * p.nx + gx;
+    T* dst = slotE(k);
+    const bool in = k < p.nz;
+    const T* src = Ein + k * plane;
+#pragma unroll
+    for (int r = 0; r < G::RE; ++r) {
+      if (es[r] < 0) continue;
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
-        if (k < p.nz) cp_async_elem(&sEi(k, c, yy, xx), Ein + c * ncell + q);
-        else sEi(k, c, yy, xx) = T(0);
+        if (in) cp_async_elem(dst + c * FE + es[r], src + c * ncell + eg[r]);
+        else dst[c * FE + es[r]] = T(0);
       }
     }
   };
   // asynchronous staging of the H_in frame of plane k (tile + the -x / -y halo)
   auto issueH = [&](int k) {
-    for (int idx = tid; idx < HY * HX; idx += nthr) {
-      const int yy = idx / HX, xx = idx - yy * HX;
-      const int gx = wrapi(x0 - 1 + xx, p.nx), gy = wrapi(y0 - 1 + yy, p.ny);
-      const int64_t q = (int64_t)k * plane + (int64_t)gy * p.nx + gx;
+    T* dst = slotH(k);
+    const T* src = Hin + k * plane;
 #pragma unroll
-      for (int c = 0; c < 3; ++c) cp_async_elem(&sHini(k, c, yy, xx), Hin + c * ncell + q);
+    for (int r = 0; r < G::RH; ++r) {
+      if (hs[r] < 0) continue;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) cp_async_elem(dst + c * FH + hs[r], src + c * ncell + hg[r]);
     }
   };
 
-  // H^n of one frame position (hy, hx) at plane k (frame origin at (x0-1, y0-1))
-  auto computeH = [&](int hy, int hx, int k, bool write_out) {
-    T hx_ = sHini(k, 0, hy, hx), hy_ = sHini(k, 1, hy, hx), hz_ = sHini(k, 2, hy, hx);
+  // H^n at E-frame cell fe / H-frame cell fh / grid column gxy of plane k; e0/e1 = E frames of
+  // planes k and k+1 (the E frame's origin is the H frame's, (x0-1, y0-1), one cell wider)
+  auto computeH = [&](int fe, int fh, int gxy, int k, bool write_out, const T* e0, const T* e1,
+                      const T* hin) {
+    T hx_ = hin[fh], hy_ = hin[FH + fh], hz_ = hin[2 * FH + fh];
     if (p.doH) {
       HIn<T> e;
-      e.ex0 = sEi(k, 0, hy, hx);
-      e.ex_k1 = sEi(k + 1, 0, hy, hx);
-      e.ex_j1 = sEi(k, 0, hy + 1, hx);
-      e.ey0 = sEi(k, 1, hy, hx);
-      e.ey_k1 = sEi(k + 1, 1, hy, hx);
-      e.ey_i1 = sEi(k, 1, hy, hx + 1);
-      e.ez0 = sEi(k, 2, hy, hx);
-      e.ez_j1 = sEi(k, 2, hy + 1, hx);
-      e.ez_i1 = sEi(k, 2, hy, hx + 1);
+      e.ex0 = e0[fe];
+      e.ex_k1 = e1[fe];
+      e.ex_j1 = e0[fe + FX];
+      e.ey0 = e0[FE + fe];
+      e.ey_k1 = e1[FE + fe];
+      e.ey_i1 = e0[FE + fe + 1];
+      e.ez0 = e0[2 * FE + fe];
+      e.ez_j1 = e0[2 * FE + fe + FX];
+      e.ez_i1 = e0[2 * FE + fe + 1];
       const int ip = psiH_plane(k, p.nz, p.npml);
       T psx = T(0), psy = T(0), b = T(1), c = T(0);
-      const int gx = wrapi(x0 - 1 + hx, p.nx), gy = wrapi(y0 - 1 + hy, p.ny);
-      const int64_t pq = (int64_t)ip * plane + (int64_t)gy * p.nx + gx;
-      const int64_t pstride = (int64_t)(2 * p.npml + 1) * plane;
+      const int pstride = (2 * p.npml + 1) * plane;
+      const int pq = ip * plane + gxy;
       if (ip >= 0) {
         b = p.pmlH[2 * k];
         c = p.pmlH[2 * k + 1];
@@ -210,7 +267,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) step3d_kernel(con
       }
       h_update<T>(e, hx_, hy_, hz_, &psx, &psy, b, c, ip >= 0, dx, dt, inv_dx);
       if (write_out) {
-        const int64_t q = (int64_t)k * plane + (int64_t)gy * p.nx + gx;
+        const int q = k * plane + gxy;
         p.Hout[q] = hx_;
         p.Hout[ncell + q] = hy_;
         p.Hout[2 * ncell + q] = hz_;
@@ -220,22 +277,22 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) step3d_kernel(con
         }
       }
     }
-    sHi(0, hy, hx) = hx_;
-    sHi(1, hy, hx) = hy_;
-    sHi(2, hy, hx) = hz_;
+    sH[fh] = hx_;
+    sH[FH + fh] = hy_;
+    sH[2 * FH + fh] = hz_;
   };
 
   // ---- prologue: H^n of plane zb-1 at the own cell (for d/dz of the E update at zb) ----
   T hxm = T(0), hym = T(0);
   if (p.doE && zb > 0 && own) {
-    const int64_t q = (int64_t)(zb - 1) * plane + qxy;
+    const int q = (zb - 1) * plane + qxy;
     hxm = Hin[q];
     hym = Hin[ncell + q];
     if (p.doH) {
       // zb-1 is never inside the CPML (chunk starts are planned that way)
       const int ip1 = (i + 1) % p.nx, jp1 = (j + 1) % p.ny;
-      const int64_t qj1 = (int64_t)(zb - 1) * plane + (int64_t)jp1 * p.nx + i;
-      const int64_t qi1 = (int64_t)(zb - 1) * plane + (int64_t)j * p.nx + ip1;
+      const int qj1 = (zb - 1) * plane + jp1 * p.nx + i;
+      const int qi1 = (zb - 1) * plane + j * p.nx + ip1;
       HIn<T> e;
       e.ex0 = Ein[q];
       e.ex_k1 = Ein[q + plane];
@@ -266,26 +323,30 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) step3d_kernel(con
     const bool mat_here = p.doE && own && mi >= 0 && p.mat[mi].kind != kVacuum;
     T rPa[3], rPb[3], rD[3];
     T rY[3][NBP > 0 ? NBP : 1], rV[3][NBP > 0 ? NBP : 1];
-    int64_t r = 0, rl = 0;
+    int r = 0, rl = 0, mstride = 0, yb0 = 0;
+    const int nmc = (int)p.nmatcell;
     if (p.doE && own && mi >= 0) {
       const MatK<T>& M = p.mat[mi];
-      r = M.base + (int64_t)(k - M.zlo) * plane + qxy;
-      rl = (int64_t)(k - M.zlo) * plane + qxy;
+      rl = (k - M.zlo) * plane + qxy;
+      r = (int)M.base + rl;
+      mstride = (int)M.ncell;
+      yb0 = (int)M.ybase + rl;
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
-        rPa[c] = p.Pa[c * p.nmatcell + r];
-        rPb[c] = p.Pb[c * p.nmatcell + r];
-        if (!INC) rD[c] = p.D[c * p.nmatcell + r];
+        rPa[c] = p.Pa[c * nmc + r];
+        rPb[c] = p.Pb[c * nmc + r];
+        if (!INC) rD[c] = p.D[c * nmc + r];
       }
       if (NBP > 0 && M.kind == kLorentzBath) {
+        const T* ya = p.Ya + yb0;
+        const T* yb = p.Yb + yb0;
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-          const int64_t yoff = M.ybase + (int64_t)c * M.nb * M.ncell + rl;
 #pragma unroll
           for (int jj = 0; jj < (NBP > 0 ? NBP : 1); ++jj) {
             if (jj < M.nb) {
-              rY[c][jj] = p.Ya[yoff + (int64_t)jj * M.ncell];
-              rV[c][jj] = p.Yb[yoff + (int64_t)jj * M.ncell];
+              rY[c][jj] = ya[(c * M.nb + jj) * mstride];
+              rV[c][jj] = yb[(c * M.nb + jj) * mstride];
             }
           }
         }
@@ -300,12 +361,16 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) step3d_kernel(con
     cp_async_wait_1();
     __syncthreads();
     // ---------------- H^n of plane k (own cells + -x/-y halo) ----------------
-    // own cell (threads past the grid edge compute wrapped values that are never stored)
-    computeH(ty + 1, tx + 1, k, own);
-    // halo: row y0-1 (TX cells) and column x0-1 (TY cells), recomputed, never stored
-    for (int t = tid; t < TX + TY; t += nthr) {
-      if (t < TX) computeH(0, t + 1, k, false);
-      else computeH(t - TX + 1, 0, k, false);
+    {
+      const T* e0 = slotE(k);
+      const T* e1 = slotE(k + 1);
+      const T* hin = slotH(k);
+      // own cell (threads past the grid edge compute wrapped values that are never stored)
+      computeH(own_fe, own_fh, qxy, k, own, e0, e1, hin);
+      // halo: row y0-1 (TX cells) and column x0-1 (TY cells), recomputed, never stored
+#pragma unroll
+      for (int t = 0; t < NHT; ++t)
+        if (ht_fe[t] >= 0) computeH(ht_fe[t], ht_fh[t], ht_g[t], k, false, e0, e1, hin);
     }
     __syncthreads();
 
@@ -315,8 +380,8 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) step3d_kernel(con
         const int zm = p.mon_z[m];
         if (k == zm - 1 || k == zm) {
           const int off = (k == zm) ? 1 : 0;
-          T vx = own ? sHi(0, ty + 1, tx + 1) : T(0);
-          T vy = own ? sHi(1, ty + 1, tx + 1) : T(0);
+          T vx = own ? sH[own_fh] : T(0);
+          T vy = own ? sH[FH + own_fh] : T(0);
           double sx = block_sum((double)vx, sred);
           double sy = block_sum((double)vy, sred);
           if (tid == 0 && p.mon_partial_H) {
@@ -326,7 +391,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) step3d_kernel(con
         }
       }
       if (p.eH_on && own && k >= p.ebox_lo && k < p.ebox_hi) {
-        T a = sHi(0, ty + 1, tx + 1), b = sHi(1, ty + 1, tx + 1), c = sHi(2, ty + 1, tx + 1);
+        T a = sH[own_fh], b = sH[FH + own_fh], c = sH[2 * FH + own_fh];
         uH += a * a + b * b + c * c;
       }
     }
@@ -335,21 +400,22 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) step3d_kernel(con
     if (p.doE) {
       T Ev[3] = {T(0), T(0), T(0)};
       if (own) {
-        const int64_t q = (int64_t)k * plane + qxy;
-        const int hy = ty + 1, hx = tx + 1;
-        const T Hx = sHi(0, hy, hx), Hy = sHi(1, hy, hx), Hz = sHi(2, hy, hx);
-        const T dyHz = ddiff<T>(Hz, sHi(2, hy - 1, hx), dx, inv_dx);
+        const int q = k * plane + qxy;
+        const T* e0 = slotE(k);
+        const int fh = own_fh;
+        const T Hx = sH[fh], Hy = sH[FH + fh], Hz = sH[2 * FH + fh];
+        const T dyHz = ddiff<T>(Hz, sH[2 * FH + fh - HX], dx, inv_dx);
         const T dzHy = ddiff<T>(Hy, hym, dx, inv_dx);
         const T dzHx = ddiff<T>(Hx, hxm, dx, inv_dx);
-        const T dxHz = ddiff<T>(Hz, sHi(2, hy, hx - 1), dx, inv_dx);
-        const T dxHy = ddiff<T>(Hy, sHi(1, hy, hx - 1), dx, inv_dx);
-        const T dyHx = ddiff<T>(Hx, sHi(0, hy - 1, hx), dx, inv_dx);
+        const T dxHz = ddiff<T>(Hz, sH[2 * FH + fh - 1], dx, inv_dx);
+        const T dxHy = ddiff<T>(Hy, sH[FH + fh - 1], dx, inv_dx);
+        const T dyHx = ddiff<T>(Hx, sH[fh - HX], dx, inv_dx);
         T curl[3];
         const int ip = psiE_plane(k, p.nz, p.npml);
         if (ip >= 0) {
           const T b = p.pmlE[2 * k], c = p.pmlE[2 * k + 1];
-          const int64_t pq = (int64_t)ip * plane + qxy;
-          const int64_t pstride = (int64_t)(2 * p.npml) * plane;
+          const int pq = ip * plane + qxy;
+          const int pstride = 2 * p.npml * plane;
           T px = b * p.psiE[pq] + c * dzHy;
           T py = b * p.psiE[pstride + pq] + c * dzHx;
           p.psiE[pq] = px;
@@ -361,21 +427,25 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) step3d_kernel(con
           curl[1] = dzHx - dxHz;
         }
         curl[2] = dxHy - dyHx;
-        // soft source current on this plane
-        T J[3] = {T(0), T(0), T(0)};
-        bool hasJ[3] = {false, false, false};
+        // soft source current on this plane (per component, kept in scalars)
+        T J0 = T(0), J1 = T(0), J2 = T(0);
+        bool h0 = false, h1 = false, h2 = false;
         for (int s = 0; s < p.nsrc; ++s) {
           if (p.src_z[s] == k) {
             T v = p.src_a[s];
             if (p.src_cos[s]) v = p.src_a[s] * p.src_cos[s][qxy] + p.src_b[s] * p.src_sin[s][qxy];
-            J[p.src_comp[s]] += v;
-            hasJ[p.src_comp[s]] = true;
+            const int sc = p.src_comp[s];
+            if (sc == 0) { J0 += v; h0 = true; }
+            else if (sc == 1) { J1 += v; h1 = true; }
+            else { J2 += v; h2 = true; }
           }
         }
+        const T J[3] = {J0, J1, J2};
+        const bool hasJ[3] = {h0, h1, h2};
         if (mi < 0) {
 #pragma unroll
           for (int c = 0; c < 3; ++c) {
-            T e = sEi(k, c, hy, hx) + dt * curl[c];
+            T e = e0[c * FE + own_fe] + dt * curl[c];
             if (hasJ[c]) e = e + dt * J[c];
             Ev[c] = e;
             p.Eout[c * ncell + q] = e;
@@ -383,6 +453,9 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) step3d_kernel(con
         } else {
           const MatK<T>& M = p.mat[mi];
           const bool bath = (M.kind == kLorentzBath) && (NBMAX > 0);
+          const T* cfm = sCoef + M.coef_off * kCoefStride;
+          T* const ya = p.Ya + yb0;
+          T* const yb = p.Yb + yb0;
 #pragma unroll
           for (int c = 0; c < 3; ++c) {
             T E;
@@ -392,13 +465,13 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) step3d_kernel(con
               // D^{n+1/2} = D^{n-1/2} + dt curl H^n (+ dt J);  E = (D - P^{n+1/2}) / eps_inf
               T D = rD[c] + dt * curl[c];
               if (hasJ[c]) D = D + dt * J[c];
-              p.D[c * p.nmatcell + r] = D;
+              p.D[c * nmc + r] = D;
               E = (D - Pa) / M.eps;
             } else {
               // D-free: E += (dt curl H + dt J - (P^{n+1/2} - P^{n-1/2})) / eps_inf
               T inc = dt * curl[c];
               if (hasJ[c]) inc = inc + dt * J[c];
-              E = sEi(k, c, hy, hx) + (inc - Pb) / M.eps;
+              E = e0[c * FE + own_fe] + (inc - (Pa - Pb)) * M.inv_eps;
             }
             Ev[c] = E;
             p.Eout[c * ncell + q] = E;
@@ -406,7 +479,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) step3d_kernel(con
             // ---- polarization (and bath) update ----
             T Yl[NBA], Vl[NBA];
             const int nb = bath ? M.nb : 0;
-            const int64_t yoff = M.ybase + (int64_t)c * M.nb * M.ncell + rl;
+            const int yc = c * M.nb * mstride;
             T bsum = T(0);
 #pragma unroll
             for (int jj = 0; jj < NBA; ++jj) {
@@ -415,56 +488,61 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) step3d_kernel(con
                   Yl[jj] = rY[c][jj < NBP ? jj : 0];
                   Vl[jj] = rV[c][jj < NBP ? jj : 0];
                 } else {
-                  Yl[jj] = p.Ya[yoff + (int64_t)jj * M.ncell];
-                  Vl[jj] = p.Yb[yoff + (int64_t)jj * M.ncell];
+                  Yl[jj] = ya[yc + jj * mstride];
+                  Vl[jj] = yb[yc + jj * mstride];
                 }
-                const T* cf = p.coef + (M.coef_off + jj) * kCoefStride;
-                if (!INC) bsum = bsum + cf[0] * (cf[1] * Yl[jj] + cf[2] * Vl[jj]);   // k_j (a_j Y^n + b_j Y^{n-1})
-                else bsum = bsum + (cf[0] * Yl[jj] + cf[1] * Vl[jj]);               // k_j ((a_j+b_j) Y - b_j V)
+                const T* cf = cfm + jj * kCoefStride;
+                if (!INC) {
+                  bsum = bsum + cf[0] * (cf[1] * Yl[jj] + cf[2] * Vl[jj]);   // k_j (a_j Y^n + b_j Y^{n-1})
+                } else {
+                  Vl[jj] = Yl[jj] - Vl[jj];                                  // V_j = Y^n - Y^{n-1}
+                  bsum = bsum + (cf[0] * Yl[jj] + cf[1] * Vl[jj]);           // k_j ((a_j+b_j) Y - b_j V)
+                }
               }
             }
-            T Pn, Vn;
+            T Pn, Vn, V0;
             if (!INC) {
               // Eq. Pz_update-LB (Eq. Pz_1D_Lorentz when there is no bath):
               // P^{n+1} = [cE E - (w0^2 dt^2 - 2) P^n - c2 P^{n-1} - dt/2 sum_j k_j(a_j Y^n + b_j Y^{n-1})] / A
               T num = M.cE * E - M.c1m * Pa - M.c2 * Pb;
               if (bath) num = num - T(0.5) * dt * bsum;
               Pn = num / M.A;
-              p.Pb[c * p.nmatcell + r] = Pn;   // overwrites P^{n-1}
+              p.Pb[c * nmc + r] = Pn;   // overwrites P^{n-1}
               Vn = Pn - Pa;
+              V0 = Pa - Pb;
             } else {
               // increment form: V^{n+1} = [cE E - w0^2 dt^2 P^n + c2 V^n - dt/2 sum(...)] / A
-              T num = M.cE * E - M.W * Pa + M.c2 * Pb;
+              V0 = Pa - Pb;
+              T num = M.cE * E - M.W * Pa + M.c2 * V0;
               if (bath) num = num - T(0.5) * dt * bsum;
-              Vn = num / M.A;
+              Vn = num * M.inv_A;
               Pn = Pa + Vn;
-              p.Pa[c * p.nmatcell + r] = Pn;
-              p.Pb[c * p.nmatcell + r] = Vn;
+              p.Pb[c * nmc + r] = Pn;   // overwrites P^{n-1}
             }
             T ub = T(0);
+            const T dP = Vn + V0;   // P^{n+1} - P^{n-1}
 #pragma unroll
             for (int jj = 0; jj < NBA; ++jj) {
               if (jj < nb) {
-                const T* cf = p.coef + (M.coef_off + jj) * kCoefStride;
+                const T* cf = cfm + jj * kCoefStride;
                 T Ynew, Vy;
                 if (!INC) {
                   // Eq. Yzj_finite_difference: Y^{n+1} = a Y^n + (b+1) Y^{n-1} + c (P^{n+1} - P^{n-1})
                   Ynew = cf[1] * Yl[jj] + cf[3] * Vl[jj] + cf[4] * (Pn - Pb);
-                  p.Yb[yoff + (int64_t)jj * M.ncell] = Ynew;
                   Vy = Ynew - Yl[jj];
                 } else {
                   // V_Y^{n+1} = (a+b) Y^n - (b+1) V_Y^n + c (V_P^{n+1} + V_P^n);  Y^{n+1} = Y^n + V_Y^{n+1}
-                  Vy = cf[2] * Yl[jj] + cf[3] * Vl[jj] + cf[4] * (Vn + Pb);
+                  Vy = cf[2] * Yl[jj] + cf[3] * Vl[jj] + cf[4] * dP;
                   Ynew = Yl[jj] + Vy;
-                  p.Ya[yoff + (int64_t)jj * M.ncell] = Ynew;
-                  p.Yb[yoff + (int64_t)jj * M.ncell] = Vy;
                 }
-                if (p.eE_on) ub += M.rho * ((Vy / dt) * (Vy / dt) + cf[5] * Ynew * Ynew);
+                yb[yc + jj * mstride] = Ynew;   // overwrites Y^{n-1}
+                if (p.eE_on) ub += Vy * Vy + cf[5] * Ynew * Ynew;   // (w_j dt)^2 Y^2
               }
             }
             if (p.eE_on && k >= p.ebox_lo && k < p.ebox_hi) {
-              uP += M.rho * ((Vn / dt) * (Vn / dt) + M.w0r2 * Pn * Pn);
-              uB += ub;
+              // rho/dt^2 (V^2 + (w0 dt)^2 P^2) = rho (V/dt)^2 + rho w0^2 P^2, likewise per mode
+              uP += M.rho_idt2 * (Vn * Vn + M.w0r2dt2 * Pn * Pn);
+              uB += M.rho_idt2 * ub;
             }
           }
         }
@@ -485,8 +563,8 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) step3d_kernel(con
           }
         }
       }
-      hxm = sHi(0, ty + 1, tx + 1);
-      hym = sHi(1, ty + 1, tx + 1);
+      hxm = sH[own_fh];
+      hym = sH[FH + own_fh];
     }
   }
   // energy partials of this block (every block writes, zero when outside the box)
@@ -506,8 +584,9 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) step3d_kernel(con
   }
 }
 
-inline size_t step3d_smem_bytes(int ty, size_t elem) {
-  const size_t n = (size_t)12 * (ty + 2) * (kTX + 2) + (size_t)9 * (ty + 1) * (kTX + 1);
+inline size_t step3d_smem_bytes(int ty, int nmodes, size_t elem) {
+  const size_t n = (size_t)12 * (ty + 2) * (kTX + 2) + (size_t)9 * (ty + 1) * (kTX + 1) +
+                   (size_t)kCoefStride * nmodes;
   return n * elem + 16 + 8 * sizeof(double);
 }
 

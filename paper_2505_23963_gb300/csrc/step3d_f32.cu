@@ -5,31 +5,38 @@
 
 namespace fdtdbath {
 
-template <int NB>
-static int launch_nb(const Step3DParams<float>& p, int ty, int nbx, int nby, int nchunks, void* stream) {
-  auto kern = step3d_kernel<float, true, NB>;
-  const size_t smem = step3d_smem_bytes(ty, sizeof(float));
+template <int NB, int TY>
+static int launch_nb(const Step3DParams<float>& p, int nbx, int nby, int nchunks, void* stream) {
+  auto kern = step3d_kernel<float, true, NB, TY>;
+  const size_t smem = step3d_smem_bytes(TY, p.nmodes, sizeof(float));
   static size_t smem_set = 0;   // opt in once per instantiation for more than 48 KB
   if (smem > smem_set) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return (int)e;
     smem_set = smem;
   }
-  dim3 grid(nbx, nby, nchunks), block(kTX, ty);
+  dim3 grid(nbx, nby, nchunks), block(kTX, TY);
   kern<<<grid, block, smem, (cudaStream_t)stream>>>(p);
   return (int)cudaGetLastError();
 }
 
-int launch_step3d_f32(const Step3DParams<float>& p, int nbmax, int ty, int nbx, int nby, int nchunks,
-                       void* stream) {
+template <int TY>
+static int launch_ty(const Step3DParams<float>& p, int nbmax, int nbx, int nby, int nchunks, void* stream) {
   switch (nbmax) {
-    case 0: return launch_nb<0>(p, ty, nbx, nby, nchunks, stream);
-    case 4: return launch_nb<4>(p, ty, nbx, nby, nchunks, stream);
-    case 8: return launch_nb<8>(p, ty, nbx, nby, nchunks, stream);
-    case 16: return launch_nb<16>(p, ty, nbx, nby, nchunks, stream);
-    case 32: return launch_nb<32>(p, ty, nbx, nby, nchunks, stream);
+    case 0: return launch_nb<0, TY>(p, nbx, nby, nchunks, stream);
+    case 4: return launch_nb<4, TY>(p, nbx, nby, nchunks, stream);
+    case 8: return launch_nb<8, TY>(p, nbx, nby, nchunks, stream);
+    case 16: return launch_nb<16, TY>(p, nbx, nby, nchunks, stream);
+    case 32: return launch_nb<32, TY>(p, nbx, nby, nchunks, stream);
     default: return (int)cudaErrorInvalidValue;
   }
+}
+
+int launch_step3d_f32(const Step3DParams<float>& p, int nbmax, int ty, int nbx, int nby, int nchunks,
+                       void* stream) {
+  if (ty == 8) return launch_ty<8>(p, nbmax, nbx, nby, nchunks, stream);
+  if (ty == 1) return launch_ty<1>(p, nbmax, nbx, nby, nchunks, stream);
+  return (int)cudaErrorInvalidValue;
 }
 
 }  // namespace fdtdbath
