@@ -20,7 +20,9 @@
  *     mode update Eq. (Yzj_finite_difference) with a_j, b_j, c_j.  P first, then
  *     every Y_j with the new P.  One independent bath set per P component.
  *   - A convolutional PML (Roden-Gedney CPML, kappa = 1) on the two z ends; the
- *     paper's absorber is MEEP's PML and is not specified further.
+ *     paper's absorber is MEEP's PML and is not specified further.  Its memory is kept
+ *     in units of a field difference (dx times the usual psi), so that every curl term
+ *     enters as (dt/dx) times a difference, the form Eq. (FDTD-1D) prints.
  *   - A soft Gaussian-pulse source, running-DFT monitors of the plane-mean fields,
  *     EM/oscillator/bath energy traces and the exact discrete energy invariant
  *     (derived from the Hamiltonian density, Eq. H_full).
@@ -260,14 +262,14 @@ static double orc_wave(const osrc *q, double t, double phase) {
  *                                  - (1 - gamma dt/2) P^{n-1}] / (1 + gamma dt/2).        */
 double orc_lorentz_update(double E, double P, double Pm, double w0, double g, double sigma, double dt) {
   double num = w0 * w0 * dt * dt * sigma * E - (w0 * w0 * dt * dt - 2.0) * P - (1.0 - 0.5 * g * dt) * Pm;
-  return num / (1.0 + 0.5 * g * dt);
+  return (1.0 / (1.0 + 0.5 * g * dt)) * num;
 }
 
 /* Drude limit (text after Eq. chi_L): w0^2 := 0 in the restoring term only;
  * the driving term keeps w0^2 sigma (the squared plasma frequency).             */
 double orc_drude_update(double E, double P, double Pm, double w0, double g, double sigma, double dt) {
   double num = w0 * w0 * dt * dt * sigma * E - (0.0 * dt * dt - 2.0) * P - (1.0 - 0.5 * g * dt) * Pm;
-  return num / (1.0 + 0.5 * g * dt);
+  return (1.0 / (1.0 + 0.5 * g * dt)) * num;
 }
 
 /* Eq. (Yzj_finite_difference) coefficients. */
@@ -293,7 +295,7 @@ double orc_lorentz_bath_update(double E, double P, double Pm, double w0, double 
   double A = 1.0 + 0.5 * g0 * dt + 0.5 * dt * S;
   double num = w0 * w0 * dt * dt * sigma * E - (w0 * w0 * dt * dt - 2.0) * P -
                (1.0 - 0.5 * g0 * dt - 0.5 * dt * S) * Pm - 0.5 * dt * bath;
-  double Pn = num / A;
+  double Pn = (1.0 / A) * num;
   for (int j = 0; j < nb; ++j) {
     double a, b, c;
     orc_bath_abc(wj[j], gj[j], kj[j], dt, &a, &b, &c);
@@ -307,27 +309,27 @@ double orc_lorentz_bath_update(double E, double P, double Pm, double w0, double 
 /* ---- one full time step ------------------------------------------------------------ */
 
 static void orc_update_D(osim *s) {
-  const double dx = s->dx, dt = s->dt;
+  const double dt = s->dt, S = s->dt / s->dx;
   const double tn = (double)s->n * dt; /* D^{n-1/2} -> D^{n+1/2} is centred on t_n */
 #pragma omp parallel for schedule(static)
   for (int64_t k = 0; k < s->nz; ++k) {
     for (int64_t j = 0; j < s->ny; ++j) {
       for (int64_t i = 0; i < s->nx; ++i) {
         int64_t q = IDX(s, i, j, k);
-        /* (curl H)_x = dHz/dy - dHy/dz */
-        double dyHz = (F(s, s->H[2], i, j, k) - F(s, s->H[2], i, j - 1, k)) / dx;
-        double dzHy = (F(s, s->H[1], i, j, k) - F(s, s->H[1], i, j, k - 1)) / dx;
+        /* dt (curl H)_x = dt/dx [dHz along y - dHy along z], the latter with the CPML memory */
+        double dyHz = F(s, s->H[2], i, j, k) - F(s, s->H[2], i, j - 1, k);
+        double dzHy = F(s, s->H[1], i, j, k) - F(s, s->H[1], i, j, k - 1);
         s->psiE[0][q] = s->bE[k] * s->psiE[0][q] + s->cE[k] * dzHy;
-        s->D[0][q] += dt * (dyHz - (dzHy + s->psiE[0][q]));
-        /* (curl H)_y = dHx/dz - dHz/dx */
-        double dzHx = (F(s, s->H[0], i, j, k) - F(s, s->H[0], i, j, k - 1)) / dx;
-        double dxHz = (F(s, s->H[2], i, j, k) - F(s, s->H[2], i - 1, j, k)) / dx;
+        s->D[0][q] += S * (dyHz - (dzHy + s->psiE[0][q]));
+        /* dt (curl H)_y = dt/dx [dHx along z - dHz along x] */
+        double dzHx = F(s, s->H[0], i, j, k) - F(s, s->H[0], i, j, k - 1);
+        double dxHz = F(s, s->H[2], i, j, k) - F(s, s->H[2], i - 1, j, k);
         s->psiE[1][q] = s->bE[k] * s->psiE[1][q] + s->cE[k] * dzHx;
-        s->D[1][q] += dt * ((dzHx + s->psiE[1][q]) - dxHz);
-        /* (curl H)_z = dHy/dx - dHx/dy */
-        double dxHy = (F(s, s->H[1], i, j, k) - F(s, s->H[1], i - 1, j, k)) / dx;
-        double dyHx = (F(s, s->H[0], i, j, k) - F(s, s->H[0], i, j - 1, k)) / dx;
-        s->D[2][q] += dt * (dxHy - dyHx);
+        s->D[1][q] += S * ((dzHx + s->psiE[1][q]) - dxHz);
+        /* dt (curl H)_z = dt/dx [dHy along x - dHx along y] */
+        double dxHy = F(s, s->H[1], i, j, k) - F(s, s->H[1], i - 1, j, k);
+        double dyHx = F(s, s->H[0], i, j, k) - F(s, s->H[0], i, j - 1, k);
+        s->D[2][q] += S * (dxHy - dyHx);
       }
     }
   }
@@ -342,7 +344,7 @@ static void orc_update_D(osim *s) {
   }
 }
 
-/* E^{n+1/2} = (D^{n+1/2} - P^{n+1/2}) / eps_inf  (eps0 = 1). */
+/* E^{n+1/2} = (1/eps_inf) (D^{n+1/2} - P^{n+1/2})  (eps0 = 1). */
 static void orc_update_E(osim *s) {
   const int64_t plane = s->nx * s->ny;
 #pragma omp parallel for schedule(static)
@@ -352,11 +354,11 @@ static void orc_update_E(osim *s) {
       int64_t q = k * plane + p;
       for (int c = 0; c < 3; ++c) {
         if (mi < 0) {
-          s->E[c][q] = (s->D[c][q] - 0.0) / 1.0;
+          s->E[c][q] = 1.0 * (s->D[c][q] - 0.0);
         } else {
           const omat *m = &s->mat[mi];
           int64_t r = (k - m->zlo) * plane + p;
-          s->E[c][q] = (s->D[c][q] - m->P[c][r]) / m->eps_inf;
+          s->E[c][q] = (1.0 / m->eps_inf) * (s->D[c][q] - m->P[c][r]);
         }
       }
     }
@@ -401,7 +403,7 @@ static void orc_update_P(osim *s) {
 /* H^{n+1} = H^n - dt (curl E^{n+1/2})  (mu0 = 1), with CPML on the d/dz terms.
  * If hdot != NULL it receives sum over cells of H^n . H^{n+1}. */
 static void orc_update_H(osim *s, double *hdot) {
-  const double dx = s->dx, dt = s->dt;
+  const double S = s->dt / s->dx;
   double acc = 0.0;
 #pragma omp parallel for schedule(static) reduction(+ : acc)
   for (int64_t k = 0; k < s->nz; ++k) {
@@ -409,20 +411,20 @@ static void orc_update_H(osim *s, double *hdot) {
       for (int64_t i = 0; i < s->nx; ++i) {
         int64_t q = IDX(s, i, j, k);
         double h0[3] = {s->H[0][q], s->H[1][q], s->H[2][q]};
-        /* (curl E)_x = dEz/dy - dEy/dz */
-        double dyEz = (F(s, s->E[2], i, j + 1, k) - F(s, s->E[2], i, j, k)) / dx;
-        double dzEy = (F(s, s->E[1], i, j, k + 1) - F(s, s->E[1], i, j, k)) / dx;
+        /* dt (curl E)_x = dt/dx [dEz along y - dEy along z], the latter with the CPML memory */
+        double dyEz = F(s, s->E[2], i, j + 1, k) - F(s, s->E[2], i, j, k);
+        double dzEy = F(s, s->E[1], i, j, k + 1) - F(s, s->E[1], i, j, k);
         s->psiH[0][q] = s->bH[k] * s->psiH[0][q] + s->cH[k] * dzEy;
-        s->H[0][q] -= dt * (dyEz - (dzEy + s->psiH[0][q]));
-        /* (curl E)_y = dEx/dz - dEz/dx */
-        double dzEx = (F(s, s->E[0], i, j, k + 1) - F(s, s->E[0], i, j, k)) / dx;
-        double dxEz = (F(s, s->E[2], i + 1, j, k) - F(s, s->E[2], i, j, k)) / dx;
+        s->H[0][q] -= S * (dyEz - (dzEy + s->psiH[0][q]));
+        /* dt (curl E)_y = dt/dx [dEx along z - dEz along x] */
+        double dzEx = F(s, s->E[0], i, j, k + 1) - F(s, s->E[0], i, j, k);
+        double dxEz = F(s, s->E[2], i + 1, j, k) - F(s, s->E[2], i, j, k);
         s->psiH[1][q] = s->bH[k] * s->psiH[1][q] + s->cH[k] * dzEx;
-        s->H[1][q] -= dt * ((dzEx + s->psiH[1][q]) - dxEz);
-        /* (curl E)_z = dEy/dx - dEx/dy */
-        double dxEy = (F(s, s->E[1], i + 1, j, k) - F(s, s->E[1], i, j, k)) / dx;
-        double dyEx = (F(s, s->E[0], i, j + 1, k) - F(s, s->E[0], i, j, k)) / dx;
-        s->H[2][q] -= dt * (dxEy - dyEx);
+        s->H[1][q] -= S * ((dzEx + s->psiH[1][q]) - dxEz);
+        /* dt (curl E)_z = dt/dx [dEy along x - dEx along y] */
+        double dxEy = F(s, s->E[1], i + 1, j, k) - F(s, s->E[1], i, j, k);
+        double dyEx = F(s, s->E[0], i, j + 1, k) - F(s, s->E[0], i, j, k);
+        s->H[2][q] -= S * (dxEy - dyEx);
         acc += h0[0] * s->H[0][q] + h0[1] * s->H[1][q] + h0[2] * s->H[2][q];
       }
     }
