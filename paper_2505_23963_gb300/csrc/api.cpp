@@ -100,6 +100,12 @@ struct fdtdbath_sim {
   // launch plan
   int ty = 8, nbx = 1, nby = 1, nchunks = 1, nbmax = 0;
   void* zstart = nullptr;
+  // chunk ids on the device: [all chunks..., chunks without bath planes..., chunks with them...]
+  void* chunk_ids = nullptr;
+  int nplain = 0, nbath = 0;
+  // a bath-free kernel for the plain chunks runs beside the bath kernel on a forked stream
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   std::string err;
 };
 
@@ -257,13 +263,25 @@ MatK<T> mat_k(const HostMat& m, int coef_off, double dt) {
   return k;
 }
 
+// z-chunks of about zc planes.  Chunk starts avoid the CPML planes (the chunk-start H
+// recompute needs no CPML memory) and fall on every Lorentz-Bath layer boundary inside the
+// allowed range, so that a chunk holds either no bath plane or only bath planes (plus
+// whatever the boundary rule forces in).
 int plan_chunks(fdtdbath_sim* s, int zc, std::vector<int>& starts) {
   starts.clear();
   int64_t z = 0;
   starts.push_back(0);
   const int64_t lo_ok = s->npml + 1, hi_ok = s->nz - 1 - s->npml;
+  std::vector<int64_t> cuts;
+  for (auto& m : s->mats)
+    if (m.kind == FDTDBATH_LORENTZ_BATH) {
+      if (m.zlo >= lo_ok && m.zlo <= hi_ok) cuts.push_back(m.zlo);
+      if (m.zhi >= lo_ok && m.zhi <= hi_ok) cuts.push_back(m.zhi);
+    }
   while (z < s->nz) {
     int64_t nx = z + zc;
+    for (int64_t c : cuts)
+      if (c > z && c < nx) nx = c;
     if (nx < lo_ok) nx = lo_ok;
     if (nx > hi_ok) nx = s->nz;
     if (nx > s->nz) nx = s->nz;
@@ -297,9 +315,8 @@ Step3DParams<T> make_params(fdtdbath_sim* s, int doH, int doE) {
   p.nz = (int)s->nz;
   p.plane = s->plane;
   p.ncell = s->ncell;
-  p.dx = (T)s->dx;
   p.dt = (T)s->dt;
-  p.inv_dx = (T)(1.0 / s->dx);
+  p.S = (T)(s->dt / s->dx);
   p.Ein = (const T*)s->E[s->ecur];
   p.Eout = (T*)s->E[1 - s->ecur];
   p.Hin = (const T*)s->H[s->hcur];
@@ -353,19 +370,50 @@ Step3DParams<T> make_params(fdtdbath_sim* s, int doH, int doE) {
   p.en_partial_H = part + hslot * s->ring_stride + s->enH_off;
   p.ew = s->dx / (double)s->plane;
   p.zstart = (const int*)s->zstart;
+  p.chunk_ids = (const int*)s->chunk_ids;
+  p.nchunks_total = s->nchunks;
+  p.vec16 = (s->nx % (int64_t)(16 / sizeof(T)) == 0) ? 1 : 0;
   return p;
 }
 
-int launch_step(fdtdbath_sim* s, int doH, int doE) {
-  int rc;
-  if (s->prec == 64) {
-    Step3DParams<double> p = make_params<double>(s, doH, doE);
-    rc = launch_step3d_f64(p, s->nbmax, s->ty, s->nbx, s->nby, s->nchunks, s->stream);
-  } else {
-    Step3DParams<float> p = make_params<float>(s, doH, doE);
-    rc = launch_step3d_f32(p, s->nbmax, s->ty, s->nbx, s->nby, s->nchunks, s->stream);
-  }
+int launch_typed(const Step3DParams<float>& p, int nbmax, int ty, int nbx, int nby, int n, cudaStream_t st) {
+  return launch_step3d_f32(p, nbmax, ty, nbx, nby, n, st);
+}
+int launch_typed(const Step3DParams<double>& p, int nbmax, int ty, int nbx, int nby, int n, cudaStream_t st) {
+  return launch_step3d_f64(p, nbmax, ty, nbx, nby, n, st);
+}
+
+template <typename T>
+int launch_chunks(fdtdbath_sim* s, Step3DParams<T> p, int nbmax, int id_off, int n, cudaStream_t st) {
+  p.chunk_ids = (const int*)s->chunk_ids + id_off;
   s->launches++;
+  return launch_typed(p, nbmax, s->ty, s->nbx, s->nby, n, st);
+}
+
+// One step's launches: without a pending E half-step, or without bath chunks, one launch over
+// all chunks (the bath-free kernel when no bath update runs); otherwise the bath-free kernel
+// over the plain chunks on the side stream, concurrently with the bath kernel over the bath
+// chunks on the simulation's stream, joined before anything that follows.
+template <typename T>
+int launch_all(fdtdbath_sim* s, int doH, int doE) {
+  Step3DParams<T> p = make_params<T>(s, doH, doE);
+  if (!doE || s->nbmax == 0 || s->nbath == 0)
+    return launch_chunks<T>(s, p, doE ? s->nbmax : 0, 0, s->nchunks, s->stream);
+  if (s->nplain == 0) return launch_chunks<T>(s, p, s->nbmax, s->nchunks, s->nbath, s->stream);
+  cudaError_t e = cudaEventRecord(s->ev_fork, s->stream);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(s->side, s->ev_fork, 0);
+  if (e != cudaSuccess) return (int)e;
+  int rc = launch_chunks<T>(s, p, 0, s->nchunks, s->nplain, s->side);
+  if (rc) return rc;
+  rc = launch_chunks<T>(s, p, s->nbmax, s->nchunks + s->nplain, s->nbath, s->stream);
+  if (rc) return rc;
+  e = cudaEventRecord(s->ev_join, s->side);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(s->stream, s->ev_join, 0);
+  return (int)e;
+}
+
+int launch_step(fdtdbath_sim* s, int doH, int doE) {
+  const int rc = s->prec == 64 ? launch_all<double>(s, doH, doE) : launch_all<float>(s, doH, doE);
   if (rc) return cuda_fail(s, (cudaError_t)rc, "step kernel launch");
   if (doE) s->ecur = 1 - s->ecur;
   if (doH) {
@@ -693,9 +741,11 @@ int fdtdbath_create(const fdtdbath_grid* grid, double resolution, double courant
   s->nbx = (int)((nx + kTX - 1) / kTX);
   s->nby = (int)((ny + s->ty - 1) / s->ty);
   int zc = 32;
-  if (const char* e = std::getenv("FDTDBATH_ZCHUNK")) zc = std::max(1, std::atoi(e));
+  if (const char* e = std::getenv("FDTDBATH_ZCHUNK")) zc = std::min(64, std::max(1, std::atoi(e)));
   std::vector<int> starts;
   s->nchunks = plan_chunks(s, zc, starts);
+  for (size_t c = 0; c + 1 < starts.size(); ++c)
+    if (starts[c + 1] - starts[c] > 128) return bail(FDTDBATH_ERR_ARG, "z-chunk longer than 128 planes");
   if ((int64_t)s->nbx * s->nby > 65535 * 64) return bail(FDTDBATH_ERR_ARG, "grid too large for the launch plan");
 
   cudaError_t ce = cudaSetDevice(s->device);
@@ -720,8 +770,26 @@ int fdtdbath_create(const fdtdbath_grid* grid, double resolution, double courant
   for (auto& m : s->mats) nmodes += m.nb;
   s->coef = dalloc(s, (size_t)std::max(1, nmodes) * kCoefStride * esz);
   s->zstart = dalloc(s, starts.size() * sizeof(int));
-  if (!s->psiE || !s->pmlE || !s->pmlH || !s->D || !s->coef || !s->zstart)
+  s->chunk_ids = dalloc(s, 2 * (size_t)s->nchunks * sizeof(int));
+  if (!s->psiE || !s->pmlE || !s->pmlH || !s->D || !s->coef || !s->zstart || !s->chunk_ids)
     return bail(FDTDBATH_ERR_OOM, "device allocation failed");
+  std::vector<int> ids;
+  for (int c = 0; c < s->nchunks; ++c) ids.push_back(c);
+  std::vector<int> plain, bathc;
+  for (int c = 0; c < s->nchunks; ++c) {
+    bool has_bath = false;
+    for (auto& m : s->mats)
+      if (m.kind == FDTDBATH_LORENTZ_BATH && m.nb > 0 && m.zlo < starts[c + 1] && m.zhi > starts[c]) has_bath = true;
+    (has_bath ? bathc : plain).push_back(c);
+  }
+  s->nplain = (int)plain.size();
+  s->nbath = (int)bathc.size();
+  ids.insert(ids.end(), plain.begin(), plain.end());
+  ids.insert(ids.end(), bathc.begin(), bathc.end());
+  if (cudaStreamCreateWithFlags(&s->side, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&s->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&s->ev_join, cudaEventDisableTiming) != cudaSuccess)
+    return bail(FDTDBATH_ERR_CUDA, "stream/event creation failed");
   // partial-sum ring
   const int64_t nbxy = (int64_t)s->nbx * s->nby, nblocks = nbxy * s->nchunks;
   s->monE_off = 0;
@@ -761,6 +829,7 @@ int fdtdbath_create(const fdtdbath_grid* grid, double resolution, double courant
     rc = rc ? rc : h2d(s, s->coef, rf.data(), rf.size() * 4);
   }
   rc = rc ? rc : h2d(s, s->zstart, starts.data(), starts.size() * sizeof(int));
+  rc = rc ? rc : h2d(s, s->chunk_ids, ids.data(), ids.size() * sizeof(int));
   if (rc) return bail(rc, s->err);
   for (int q = 0; q < nsrc; ++q) {
     if (!sources[q].phase) continue;
@@ -966,6 +1035,9 @@ void fdtdbath_destroy(fdtdbath_sim* s) {
     if (s->ufree) s->ufree(p, s->uctx);
     else cudaFree(p);
   }
+  if (s->ev_fork) cudaEventDestroy(s->ev_fork);
+  if (s->ev_join) cudaEventDestroy(s->ev_join);
+  if (s->side) cudaStreamDestroy(s->side);
   delete s;
 }
 

@@ -40,8 +40,8 @@ struct MatK {
   T W;            // w0^2 dt^2 (Drude: 0)                [FP32 increment path]
   T c2;           // 1 - gamma0 dt/2 - dt/2 sum_j k_j c_j
   T A;            // 1 + gamma0 dt/2 + dt/2 sum_j k_j c_j
-  T inv_A;        // 1/A                                 [FP32 increment path]
-  T inv_eps;      // 1/eps_inf                           [FP32 increment path]
+  T inv_A;        // 1/A (1/(1 + gamma dt/2) without a bath)
+  T inv_eps;      // 1/eps_inf
   T rho_idt2;     // rho/dt^2, rho = 1/(sigma w0^2) (0 when sigma = 0), energy density
   T w0r2dt2;      // (w0 dt)^2 in the potential term (Drude: 0)
 };
@@ -54,7 +54,7 @@ template <typename T>
 struct Step3DParams {
   int nx, ny, nz;
   int64_t plane, ncell;
-  T dx, dt, inv_dx;
+  T dt, S;   // time step and Courant factor S = dt/dx
   const T* Ein;
   T* Eout;
   const T* Hin;
@@ -96,8 +96,11 @@ struct Step3DParams {
   double* en_partial_E;   // [3][nblocks]
   double* en_partial_H;   // [1][nblocks]
   double ew;              // dx / (nx ny)
-  // z chunks
-  const int* zstart;      // [nchunks + 1]
+  // z chunks (at most 128 planes each); block z of this launch works on chunk chunk_ids[z]
+  const int* zstart;      // [nchunks_total + 1]
+  const int* chunk_ids;
+  int nchunks_total;
+  int vec16;              // nx is a multiple of 16 bytes' worth of elements: 16-byte staging
 };
 
 // Launchers (defined in step3d_f32.cu / step3d_f64.cu).

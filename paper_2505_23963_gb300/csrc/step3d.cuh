@@ -32,17 +32,6 @@
 
 namespace fdtdbath {
 
-template <typename T>
-__device__ __forceinline__ T ddiff(T a, T b, T dx, T inv_dx);
-template <>
-__device__ __forceinline__ double ddiff<double>(double a, double b, double dx, double) {
-  return (a - b) / dx;
-}
-template <>
-__device__ __forceinline__ float ddiff<float>(float a, float b, float, float inv_dx) {
-  return (a - b) * inv_dx;
-}
-
 __device__ __forceinline__ int wrapi(int v, int n) {
   v %= n;
   return v < 0 ? v + n : v;
@@ -75,9 +64,10 @@ __device__ __forceinline__ double block_sum(double v, double* scratch) {
   return s;
 }
 
-// H update of one cell (Eq. 1b, mu0 = 1) from the 9 E values it needs:
-//   Hx -= dt (dEz/dy - (dEy/dz + psi_x)),  Hy -= dt ((dEx/dz + psi_y) - dEz/dx),
-//   Hz -= dt (dEy/dx - dEx/dy);  psi <- b psi + c dE/dz inside the CPML.
+// H update of one cell (Eq. 1b, mu0 = 1) from the 9 E values it needs, in the form of
+// Eq. FDTD-1D (S = dt/dx times differences of neighbours):
+//   Hx -= S (dEz|y - (dEy|z + psi_x)),  Hy -= S ((dEx|z + psi_y) - dEz|x),  Hz -= S (dEy|x - dEx|y);
+// psi <- b psi + c dE|z inside the CPML (memory in units of a field difference).
 template <typename T>
 struct HIn {
   T ex0, ex_k1, ex_j1;  // Ex(i,j,k), Ex(i,j,k+1), Ex(i,j+1,k)
@@ -87,23 +77,23 @@ struct HIn {
 
 template <typename T>
 __device__ __forceinline__ void h_update(const HIn<T>& e, T& hx, T& hy, T& hz, T* psix, T* psiy,
-                                         T b, T c, bool pml, T dx, T dt, T inv_dx) {
-  T dyEz = ddiff<T>(e.ez_j1, e.ez0, dx, inv_dx);
-  T dzEy = ddiff<T>(e.ey_k1, e.ey0, dx, inv_dx);
-  T dzEx = ddiff<T>(e.ex_k1, e.ex0, dx, inv_dx);
-  T dxEz = ddiff<T>(e.ez_i1, e.ez0, dx, inv_dx);
-  T dxEy = ddiff<T>(e.ey_i1, e.ey0, dx, inv_dx);
-  T dyEx = ddiff<T>(e.ex_j1, e.ex0, dx, inv_dx);
+                                         T b, T c, bool pml, T S) {
+  const T dyEz = e.ez_j1 - e.ez0;
+  const T dzEy = e.ey_k1 - e.ey0;
+  const T dzEx = e.ex_k1 - e.ex0;
+  const T dxEz = e.ez_i1 - e.ez0;
+  const T dxEy = e.ey_i1 - e.ey0;
+  const T dyEx = e.ex_j1 - e.ex0;
   if (pml) {
     *psix = b * (*psix) + c * dzEy;
     *psiy = b * (*psiy) + c * dzEx;
-    hx = hx - dt * (dyEz - (dzEy + *psix));
-    hy = hy - dt * ((dzEx + *psiy) - dxEz);
+    hx = hx - S * (dyEz - (dzEy + *psix));
+    hy = hy - S * ((dzEx + *psiy) - dxEz);
   } else {
-    hx = hx - dt * (dyEz - dzEy);
-    hy = hy - dt * (dzEx - dxEz);
+    hx = hx - S * (dyEz - dzEy);
+    hy = hy - S * (dzEx - dxEz);
   }
-  hz = hz - dt * (dxEy - dyEx);
+  hz = hz - S * (dxEy - dyEx);
 }
 
 // cp.async (LDGSTS) of one element into shared memory, and its group bookkeeping
@@ -113,22 +103,56 @@ __device__ __forceinline__ void cp_async_elem(T* sdst, const T* gsrc) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(sa), "l"(gsrc), "n"(sizeof(T)));
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
-__device__ __forceinline__ void cp_async_wait_1() { asm volatile("cp.async.wait_group 1;\n" ::); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
 
+// Depth of the plane pipeline: the E_in frame of plane k+kAheadE and the H_in frame of plane
+// k+kAheadE-1 are requested while plane k is computed; kAheadE-1 commit groups stay in flight.
+constexpr int kAheadE = 4;
+constexpr int kRingE = 6;   // E frames: k-1 (still read by the E update of k-1), k .. k+kAheadE
+constexpr int kRingH = 4;   // H frames: k .. k+kAheadE-1
+constexpr int kMaxChunk = 128;   // planes per z-chunk (the per-plane table in shared memory)
+
+// plane-info bits of the per-chunk table
+enum : int { kPlaneMat = 0xF, kPlaneEbox = 0x10, kPlaneMonE = 0x20, kPlaneMonH = 0x40, kPlaneSrc = 0x80 };
+
+template <typename T>
+__device__ __forceinline__ void cp_async16(T* sdst, const T* gsrc) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(sdst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gsrc));
+}
+
+// the six coefficients of a bath-mode row, read with vector shared-memory loads
+__device__ __forceinline__ void load_coef6(const float* cf, float* o) {
+  const float4 a = *reinterpret_cast<const float4*>(cf);
+  const float2 b = *reinterpret_cast<const float2*>(cf + 4);
+  o[0] = a.x; o[1] = a.y; o[2] = a.z; o[3] = a.w; o[4] = b.x; o[5] = b.y;
+}
+__device__ __forceinline__ void load_coef6(const double* cf, double* o) {
+  const double2 a = *reinterpret_cast<const double2*>(cf);
+  const double2 b = *reinterpret_cast<const double2*>(cf + 2);
+  const double2 c = *reinterpret_cast<const double2*>(cf + 4);
+  o[0] = a.x; o[1] = a.y; o[2] = b.x; o[3] = b.y; o[4] = c.x; o[5] = c.y;
+}
+
+// Shared-memory frames of one plane.  Rows start 16-byte aligned at x0-4 so that whole rows
+// can be staged with 16-byte copies: the E frame spans x0-4 .. x0+35 (the tile, one halo cell
+// on each side, padding) and rows y0-1 .. y0+TY; the H frame spans x0-4 .. x0+31 and rows
+// y0-1 .. y0+TY-1 (the tile and its -x / -y halo).  Frame column = x - (x0 - 4), so the
+// halo-relative column hx (x = x0-1+hx) sits at hx + kXO.
+constexpr int kXO = 3;
 template <int TY>
 struct Tile {
-  static constexpr int TX = kTX, FX = kTX + 2, FY = TY + 2, HX = kTX + 1, HY = TY + 1;
+  static constexpr int TX = kTX, FX = kTX + 8, FY = TY + 2, HX = kTX + 4, HY = TY + 1;
   static constexpr int NTHR = kTX * TY;
-  static constexpr int FE = FY * FX;                 // E frame cells (tile + 1 on every side)
-  static constexpr int FH = HY * HX;                 // H frame cells (tile + -x / -y halo)
-  static constexpr int RE = (FE + NTHR - 1) / NTHR;  // E frame cells staged per thread
-  static constexpr int RH = (FH + NTHR - 1) / NTHR;
+  static constexpr int FE = FY * FX;                 // E frame elements per component
+  static constexpr int FH = HY * HX;                 // H frame elements per component
 };
 
 template <typename T, int NBMAX, int TY>
 struct StepBounds {
   static constexpr int threads = kTX * TY;
-  static constexpr int min_blocks = TY == 8 ? ((sizeof(T) == 8 && NBMAX >= 16) ? 1 : 2) : 8;
+  static constexpr int min_blocks = TY == 8 ? (NBMAX == 0 ? (sizeof(T) == 4 ? 4 : 2) : ((sizeof(T) == 8 && NBMAX >= 16) ? 1 : 2)) : 8;
 };
 
 template <typename T, bool INC, int NBMAX, int TY>
@@ -136,64 +160,91 @@ __global__ void __launch_bounds__(StepBounds<T, NBMAX, TY>::threads, StepBounds<
 step3d_kernel(const Step3DParams<T> p) {
   using G = Tile<TY>;
   constexpr int TX = G::TX, FX = G::FX, HX = G::HX, NTHR = G::NTHR, FE = G::FE, FH = G::FH;
+  constexpr int FY = G::FY, HY = G::HY;
+  constexpr int VE = 16 / (int)sizeof(T);      // elements per 16-byte copy
+  constexpr int NCE = FY * (FX / VE), NCH = HY * (HX / VE);   // 16-byte chunks per frame component
+  constexpr int CE = (NCE + NTHR - 1) / NTHR, CH = (NCH + NTHR - 1) / NTHR;
   // bath modes preloaded for all three components with the rest of the plane's state
   constexpr int NBP = NBMAX <= (sizeof(T) == 4 ? 8 : 4) ? NBMAX : 0;
   constexpr int NBA = NBMAX > 0 ? NBMAX : 1;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  // E_in frames, ring of 4 planes [4][3][FE]: planes k, k+1 feed H^n(k), plane k also the
-  // E update of k (after the second barrier), plane k+2 is in flight; the slot refilled at the
-  // top of step k+1 (plane k+3) held plane k-1, last read before this step's first barrier.
+  // E_in frames, ring of kRingE planes [kRingE][3][FE]: planes k, k+1 feed H^n(k), plane k
+  // also the E update of k (after the second barrier), planes up to k+kAheadE are in flight;
+  // the slot refilled at the top of step k+1 held plane k+1+kAheadE-kRingE <= k-1, last read
+  // before this step's first barrier.  H_in frames likewise, ring of kRingH planes.
   T* sE = reinterpret_cast<T*>(smem_raw);
-  T* sHin = sE + 12 * FE;                        // H_in frames, ring of 2 planes: [2][3][FH]
-  T* sH = sHin + 6 * FH;                         // H^n of the current plane:     [3][FH]
+  T* sHin = sE + kRingE * 3 * FE;                // H_in frames: [kRingH][3][FH]
+  T* sH = sHin + kRingH * 3 * FH;                // H^n of the current plane: [3][FH]
   T* sCoef = sH + 3 * FH;                        // bath coefficients:            [modes][8]
+  int* sInfo = reinterpret_cast<int*>(sCoef + kCoefStride * p.nmodes);   // [kMaxChunk]
   double* sred = reinterpret_cast<double*>(
-      (reinterpret_cast<uintptr_t>(sCoef + kCoefStride * p.nmodes) + 15) & ~uintptr_t(15));
+      (reinterpret_cast<uintptr_t>(sInfo + kMaxChunk) + 15) & ~uintptr_t(15));
 
   const int tx = threadIdx.x, ty = threadIdx.y;
   const int tid = ty * TX + tx;
   const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
   const int i = x0 + tx, j = y0 + ty;
   const bool own = (i < p.nx) && (j < p.ny);
-  const int zb = p.zstart[blockIdx.z], ze = p.zstart[blockIdx.z + 1];
+  const int chunk = p.chunk_ids[blockIdx.z];
+  const int zb = p.zstart[chunk], ze = p.zstart[chunk + 1];
   // every array index fits in 32 bits (checked when the simulation is created)
   const int plane = (int)p.plane, ncell = (int)p.ncell;
   const int qxy = own ? j * p.nx + i : 0;
-  const T dx = p.dx, dt = p.dt, inv_dx = p.inv_dx;
+  const T dt = p.dt, S = p.S;
   const int nbxy = gridDim.x * gridDim.y;
   const int bxy = blockIdx.y * gridDim.x + blockIdx.x;
-  const int blin = blockIdx.z * nbxy + bxy;
+  const int blin = chunk * nbxy + bxy;   // unique over the launches of one step
   const T* __restrict__ Ein = p.Ein;
   const T* __restrict__ Hin = p.Hin;
 
   for (int q = tid; q < kCoefStride * p.nmodes; q += NTHR) sCoef[q] = p.coef[q];
 
-  // Frame cells this thread stages every plane: shared-memory offset and periodic (x, y) offset
-  int es[G::RE], eg[G::RE], hs[G::RH], hg[G::RH];
+  // per-plane facts of this chunk: material index + 1, energy box, monitor and source planes
+  for (int t = tid; t < ze - zb; t += NTHR) {
+    const int k = zb + t;
+    int info = 0;
+    for (int m = 0; m < p.nmat; ++m)
+      if (k >= p.mat[m].zlo && k < p.mat[m].zhi) info = m + 1;
+    if (k >= p.ebox_lo && k < p.ebox_hi) info |= kPlaneEbox;
+    for (int m = 0; m < p.nmon; ++m) {
+      if (k == p.mon_z[m]) info |= kPlaneMonE;
+      if (k == p.mon_z[m] || k == p.mon_z[m] - 1) info |= kPlaneMonH;
+    }
+    for (int q = 0; q < p.nsrc; ++q)
+      if (k == p.src_z[q]) info |= kPlaneSrc;
+    sInfo[t] = info;
+  }
+
+  // 16-byte chunks this thread stages every plane (when nx is a multiple of VE): frame offset
+  // and periodic (x, y) offset of the chunk's first element; E chunks from the low threads up,
+  // H chunks from the high threads down
+  int ce_s[CE], ce_g[CE], ch_s[CH], ch_g[CH];
+  constexpr int cpr_e = FX / VE, cpr_h = HX / VE;
 #pragma unroll
-  for (int r = 0; r < G::RE; ++r) {
+  for (int r = 0; r < CE; ++r) {
     const int idx = tid + r * NTHR;
-    es[r] = -1;
-    eg[r] = 0;
-    if (idx < FE) {
-      const int yy = idx / FX, xx = idx - yy * FX;
-      es[r] = idx;
-      eg[r] = wrapi(y0 - 1 + yy, p.ny) * p.nx + wrapi(x0 - 1 + xx, p.nx);
+    ce_s[r] = -1;
+    ce_g[r] = 0;
+    if (idx < NCE && p.vec16) {
+      const int yy = idx / cpr_e, cx = idx - yy * cpr_e;
+      ce_s[r] = yy * FX + cx * VE;
+      ce_g[r] = wrapi(y0 - 1 + yy, p.ny) * p.nx + wrapi(x0 - 4 + cx * VE, p.nx);
     }
   }
 #pragma unroll
-  for (int r = 0; r < G::RH; ++r) {
-    const int idx = tid + r * NTHR;
-    hs[r] = -1;
-    hg[r] = 0;
-    if (idx < FH) {
-      const int yy = idx / HX, xx = idx - yy * HX;
-      hs[r] = idx;
-      hg[r] = wrapi(y0 - 1 + yy, p.ny) * p.nx + wrapi(x0 - 1 + xx, p.nx);
+  for (int r = 0; r < CH; ++r) {
+    const int idx = (NTHR - 1 - tid) + r * NTHR;
+    ch_s[r] = -1;
+    ch_g[r] = 0;
+    if (idx < NCH && p.vec16) {
+      const int yy = idx / cpr_h, cx = idx - yy * cpr_h;
+      ch_s[r] = yy * HX + cx * VE;
+      ch_g[r] = wrapi(y0 - 1 + yy, p.ny) * p.nx + wrapi(x0 - 4 + cx * VE, p.nx);
     }
   }
+
   // H tasks of this thread: its own cell, and up to two cells of the -y row / -x column halo
-  const int own_fe = (ty + 1) * FX + (tx + 1), own_fh = (ty + 1) * HX + (tx + 1);
+  const int own_fe = (ty + 1) * FX + (tx + 1 + kXO), own_fh = (ty + 1) * HX + (tx + 1 + kXO);
   constexpr int NHT = (TX + TY + NTHR - 1) / NTHR;
   int ht_fe[NHT], ht_fh[NHT], ht_g[NHT];
 #pragma unroll
@@ -204,26 +255,43 @@ step3d_kernel(const Step3DParams<T> p) {
     ht_g[r] = 0;
     if (t < TX + TY) {
       const int hy = t < TX ? 0 : t - TX + 1, hx = t < TX ? t + 1 : 0;
-      ht_fe[r] = hy * FX + hx;
-      ht_fh[r] = hy * HX + hx;
+      ht_fe[r] = hy * FX + hx + kXO;
+      ht_fh[r] = hy * HX + hx + kXO;
       ht_g[r] = wrapi(y0 - 1 + hy, p.ny) * p.nx + wrapi(x0 - 1 + hx, p.nx);
     }
   }
-  auto slotE = [&](int k) -> T* { return sE + (k & 3) * 3 * FE; };
-  auto slotH = [&](int k) -> T* { return sHin + (k & 1) * 3 * FH; };
+  auto slotE = [&](int k) -> T* { return sE + (k % kRingE) * 3 * FE; };
+  auto slotH = [&](int k) -> T* { return sHin + (k & (kRingH - 1)) * 3 * FH; };
 
   // asynchronous staging of the E_in frame of plane k (tile + 1 cell, periodic in x, y)
   auto issueE = [&](int k) {
     T* dst = slotE(k);
     const bool in = k < p.nz;
     const T* src = Ein + k * plane;
+    if (p.vec16) {
 #pragma unroll
-    for (int r = 0; r < G::RE; ++r) {
-      if (es[r] < 0) continue;
+      for (int r = 0; r < CE; ++r) {
+        if (ce_s[r] < 0) continue;
 #pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        if (in) cp_async_elem(dst + c * FE + es[r], src + c * ncell + eg[r]);
-        else dst[c * FE + es[r]] = T(0);
+        for (int c = 0; c < 3; ++c) {
+          if (in) {
+            cp_async16(dst + c * FE + ce_s[r], src + c * ncell + ce_g[r]);
+          } else {
+#pragma unroll
+            for (int v = 0; v < VE; ++v) dst[c * FE + ce_s[r] + v] = T(0);
+          }
+        }
+      }
+    } else {
+      for (int idx = tid; idx < FY * (kTX + 2); idx += NTHR) {
+        const int yy = idx / (kTX + 2), hx = idx - yy * (kTX + 2);
+        const int g = wrapi(y0 - 1 + yy, p.ny) * p.nx + wrapi(x0 - 1 + hx, p.nx);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          T* d = dst + c * FE + yy * FX + hx + kXO;
+          if (in) cp_async_elem(d, src + c * ncell + g);
+          else *d = T(0);
+        }
       }
     }
   };
@@ -231,11 +299,20 @@ step3d_kernel(const Step3DParams<T> p) {
   auto issueH = [&](int k) {
     T* dst = slotH(k);
     const T* src = Hin + k * plane;
+    if (p.vec16) {
 #pragma unroll
-    for (int r = 0; r < G::RH; ++r) {
-      if (hs[r] < 0) continue;
+      for (int r = 0; r < CH; ++r) {
+        if (ch_s[r] < 0) continue;
 #pragma unroll
-      for (int c = 0; c < 3; ++c) cp_async_elem(dst + c * FH + hs[r], src + c * ncell + hg[r]);
+        for (int c = 0; c < 3; ++c) cp_async16(dst + c * FH + ch_s[r], src + c * ncell + ch_g[r]);
+      }
+    } else {
+      for (int idx = tid; idx < HY * (kTX + 1); idx += NTHR) {
+        const int yy = idx / (kTX + 1), hx = idx - yy * (kTX + 1);
+        const int g = wrapi(y0 - 1 + yy, p.ny) * p.nx + wrapi(x0 - 1 + hx, p.nx);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) cp_async_elem(dst + c * FH + yy * HX + hx + kXO, src + c * ncell + g);
+      }
     }
   };
 
@@ -265,7 +342,7 @@ step3d_kernel(const Step3DParams<T> p) {
         psx = p.psiHin[pq];
         psy = p.psiHin[pstride + pq];
       }
-      h_update<T>(e, hx_, hy_, hz_, &psx, &psy, b, c, ip >= 0, dx, dt, inv_dx);
+      h_update<T>(e, hx_, hy_, hz_, &psx, &psy, b, c, ip >= 0, S);
       if (write_out) {
         const int q = k * plane + gxy;
         p.Hout[q] = hx_;
@@ -304,22 +381,33 @@ step3d_kernel(const Step3DParams<T> p) {
       e.ez_j1 = Ein[2 * ncell + qj1];
       e.ez_i1 = Ein[2 * ncell + qi1];
       T hz_dummy = T(0), psx = T(0), psy = T(0);
-      h_update<T>(e, hxm, hym, hz_dummy, &psx, &psy, T(1), T(0), false, dx, dt, inv_dx);
+      h_update<T>(e, hxm, hym, hz_dummy, &psx, &psy, T(1), T(0), false, S);
     }
   }
 
   // per-thread energy accumulators (state precision; reduced in FP64 per block)
   T uE = T(0), uP = T(0), uB = T(0), uH = T(0);
+  __syncthreads();   // coefficient and plane tables ready
 
+  // prologue: E frames zb .. zb+kAheadE-1 and H frames zb .. zb+kAheadE-2, one commit group
+  // per plane so that group g carries E(zb+1+g) and H(zb+g)
   issueE(zb);
   issueE(zb + 1);
   issueH(zb);
   cp_async_commit();
+#pragma unroll
+  for (int a = 1; a < kAheadE - 1; ++a) {
+    if (zb + a < ze) {
+      issueE(zb + 1 + a);
+      issueH(zb + a);
+    }
+    cp_async_commit();
+  }
   for (int k = zb; k < ze; ++k) {
     // ---------------- material state of plane k: loads issued before the stencil ----------
-    int mi = -1;
-    for (int m = 0; m < p.nmat; ++m)
-      if (k >= p.mat[m].zlo && k < p.mat[m].zhi) mi = m;
+    const int info = sInfo[k - zb];
+    const int mi = (info & kPlaneMat) - 1;
+    const bool in_box = (info & kPlaneEbox) != 0;
     const bool mat_here = p.doE && own && mi >= 0 && p.mat[mi].kind != kVacuum;
     T rPa[3], rPb[3], rD[3];
     T rY[3][NBP > 0 ? NBP : 1], rV[3][NBP > 0 ? NBP : 1];
@@ -352,13 +440,15 @@ step3d_kernel(const Step3DParams<T> p) {
         }
       }
     }
-    // ---------------- prefetch the next planes' frames ----------------
-    if (k + 1 < ze) {
-      issueE(k + 2);
-      issueH(k + 1);
+    // ---------------- prefetch the frames kAheadE-1 planes ahead ----------------
+    if (k + kAheadE - 1 < ze) {
+      issueE(k + kAheadE);
+      issueH(k + kAheadE - 1);
     }
     cp_async_commit();
-    cp_async_wait_1();
+    // groups g0..g(t+3) are committed (t = k - zb; group g carries E(zb+1+g), H(zb+g));
+    // leaving the three newest in flight guarantees g(t): E(k+1) and H(k) have landed
+    cp_async_wait<kAheadE - 1>();
     __syncthreads();
     // ---------------- H^n of plane k (own cells + -x/-y halo) ----------------
     {
@@ -376,6 +466,7 @@ step3d_kernel(const Step3DParams<T> p) {
 
     // H-side monitor and energy partials
     if (p.doH) {
+      if (info & kPlaneMonH)
       for (int m = 0; m < p.nmon; ++m) {
         const int zm = p.mon_z[m];
         if (k == zm - 1 || k == zm) {
@@ -390,7 +481,7 @@ step3d_kernel(const Step3DParams<T> p) {
           }
         }
       }
-      if (p.eH_on && own && k >= p.ebox_lo && k < p.ebox_hi) {
+      if (p.eH_on && own && in_box) {
         T a = sH[own_fh], b = sH[FH + own_fh], c = sH[2 * FH + own_fh];
         uH += a * a + b * b + c * c;
       }
@@ -404,12 +495,13 @@ step3d_kernel(const Step3DParams<T> p) {
         const T* e0 = slotE(k);
         const int fh = own_fh;
         const T Hx = sH[fh], Hy = sH[FH + fh], Hz = sH[2 * FH + fh];
-        const T dyHz = ddiff<T>(Hz, sH[2 * FH + fh - HX], dx, inv_dx);
-        const T dzHy = ddiff<T>(Hy, hym, dx, inv_dx);
-        const T dzHx = ddiff<T>(Hx, hxm, dx, inv_dx);
-        const T dxHz = ddiff<T>(Hz, sH[2 * FH + fh - 1], dx, inv_dx);
-        const T dxHy = ddiff<T>(Hy, sH[FH + fh - 1], dx, inv_dx);
-        const T dyHx = ddiff<T>(Hx, sH[fh - HX], dx, inv_dx);
+        // differences of H^n for dt curl H^n = S [...] (Eq. FDTD-1D form)
+        const T dyHz = Hz - sH[2 * FH + fh - HX];
+        const T dzHy = Hy - hym;
+        const T dzHx = Hx - hxm;
+        const T dxHz = Hz - sH[2 * FH + fh - 1];
+        const T dxHy = Hy - sH[FH + fh - 1];
+        const T dyHx = Hx - sH[fh - HX];
         T curl[3];
         const int ip = psiE_plane(k, p.nz, p.npml);
         if (ip >= 0) {
@@ -430,6 +522,7 @@ step3d_kernel(const Step3DParams<T> p) {
         // soft source current on this plane (per component, kept in scalars)
         T J0 = T(0), J1 = T(0), J2 = T(0);
         bool h0 = false, h1 = false, h2 = false;
+        if (info & kPlaneSrc)
         for (int s = 0; s < p.nsrc; ++s) {
           if (p.src_z[s] == k) {
             T v = p.src_a[s];
@@ -445,7 +538,7 @@ step3d_kernel(const Step3DParams<T> p) {
         if (mi < 0) {
 #pragma unroll
           for (int c = 0; c < 3; ++c) {
-            T e = e0[c * FE + own_fe] + dt * curl[c];
+            T e = e0[c * FE + own_fe] + S * curl[c];
             if (hasJ[c]) e = e + dt * J[c];
             Ev[c] = e;
             p.Eout[c * ncell + q] = e;
@@ -462,14 +555,14 @@ step3d_kernel(const Step3DParams<T> p) {
             const T Pa = rPa[c];
             const T Pb = rPb[c];
             if (!INC) {
-              // D^{n+1/2} = D^{n-1/2} + dt curl H^n (+ dt J);  E = (D - P^{n+1/2}) / eps_inf
-              T D = rD[c] + dt * curl[c];
+              // D^{n+1/2} = D^{n-1/2} + S [curl differences] (+ dt J);  E = (1/eps_inf)(D - P^{n+1/2})
+              T D = rD[c] + S * curl[c];
               if (hasJ[c]) D = D + dt * J[c];
               p.D[c * nmc + r] = D;
-              E = (D - Pa) / M.eps;
+              E = M.inv_eps * (D - Pa);
             } else {
               // D-free: E += (dt curl H + dt J - (P^{n+1/2} - P^{n-1/2})) / eps_inf
-              T inc = dt * curl[c];
+              T inc = S * curl[c];
               if (hasJ[c]) inc = inc + dt * J[c];
               E = e0[c * FE + own_fe] + (inc - (Pa - Pb)) * M.inv_eps;
             }
@@ -491,7 +584,8 @@ step3d_kernel(const Step3DParams<T> p) {
                   Yl[jj] = ya[yc + jj * mstride];
                   Vl[jj] = yb[yc + jj * mstride];
                 }
-                const T* cf = cfm + jj * kCoefStride;
+                T cf[6];
+                load_coef6(cfm + jj * kCoefStride, cf);
                 if (!INC) {
                   bsum = bsum + cf[0] * (cf[1] * Yl[jj] + cf[2] * Vl[jj]);   // k_j (a_j Y^n + b_j Y^{n-1})
                 } else {
@@ -503,10 +597,10 @@ step3d_kernel(const Step3DParams<T> p) {
             T Pn, Vn, V0;
             if (!INC) {
               // Eq. Pz_update-LB (Eq. Pz_1D_Lorentz when there is no bath):
-              // P^{n+1} = [cE E - (w0^2 dt^2 - 2) P^n - c2 P^{n-1} - dt/2 sum_j k_j(a_j Y^n + b_j Y^{n-1})] / A
+              // P^{n+1} = (1/A) [cE E - (w0^2 dt^2 - 2) P^n - c2 P^{n-1} - dt/2 sum_j k_j(a_j Y^n + b_j Y^{n-1})]
               T num = M.cE * E - M.c1m * Pa - M.c2 * Pb;
               if (bath) num = num - T(0.5) * dt * bsum;
-              Pn = num / M.A;
+              Pn = M.inv_A * num;
               p.Pb[c * nmc + r] = Pn;   // overwrites P^{n-1}
               Vn = Pn - Pa;
               V0 = Pa - Pb;
@@ -524,7 +618,8 @@ step3d_kernel(const Step3DParams<T> p) {
 #pragma unroll
             for (int jj = 0; jj < NBA; ++jj) {
               if (jj < nb) {
-                const T* cf = cfm + jj * kCoefStride;
+                T cf[6];
+                load_coef6(cfm + jj * kCoefStride, cf);
                 T Ynew, Vy;
                 if (!INC) {
                   // Eq. Yzj_finite_difference: Y^{n+1} = a Y^n + (b+1) Y^{n-1} + c (P^{n+1} - P^{n-1})
@@ -539,20 +634,21 @@ step3d_kernel(const Step3DParams<T> p) {
                 if (p.eE_on) ub += Vy * Vy + cf[5] * Ynew * Ynew;   // (w_j dt)^2 Y^2
               }
             }
-            if (p.eE_on && k >= p.ebox_lo && k < p.ebox_hi) {
+            if (p.eE_on && in_box) {
               // rho/dt^2 (V^2 + (w0 dt)^2 P^2) = rho (V/dt)^2 + rho w0^2 P^2, likewise per mode
               uP += M.rho_idt2 * (Vn * Vn + M.w0r2dt2 * Pn * Pn);
               uB += M.rho_idt2 * ub;
             }
           }
         }
-        if (p.eE_on && k >= p.ebox_lo && k < p.ebox_hi) {
+        if (p.eE_on && in_box) {
           T eps = T(1);
           if (mi >= 0) eps = p.mat[mi].eps;
           uE += eps * (Ev[0] * Ev[0] + Ev[1] * Ev[1] + Ev[2] * Ev[2]);
         }
       }
       // E-side monitor partials
+      if (info & kPlaneMonE)
       for (int m = 0; m < p.nmon; ++m) {
         if (k == p.mon_z[m]) {
           double sx = block_sum(own ? (double)Ev[0] : 0.0, sred);
@@ -574,8 +670,8 @@ step3d_kernel(const Step3DParams<T> p) {
     double c = block_sum((double)uB, sred);
     if (tid == 0) {
       p.en_partial_E[blin] = a;
-      p.en_partial_E[(int64_t)gridDim.x * gridDim.y * gridDim.z + blin] = b;
-      p.en_partial_E[(int64_t)2 * gridDim.x * gridDim.y * gridDim.z + blin] = c;
+      p.en_partial_E[(int64_t)nbxy * p.nchunks_total + blin] = b;
+      p.en_partial_E[(int64_t)2 * nbxy * p.nchunks_total + blin] = c;
     }
   }
   if (p.eH_on) {
@@ -585,9 +681,9 @@ step3d_kernel(const Step3DParams<T> p) {
 }
 
 inline size_t step3d_smem_bytes(int ty, int nmodes, size_t elem) {
-  const size_t n = (size_t)12 * (ty + 2) * (kTX + 2) + (size_t)9 * (ty + 1) * (kTX + 1) +
-                   (size_t)kCoefStride * nmodes;
-  return n * elem + 16 + 8 * sizeof(double);
+  const size_t fe = (size_t)(ty + 2) * (kTX + 8), fh = (size_t)(ty + 1) * (kTX + 4);
+  const size_t n = (size_t)kRingE * 3 * fe + (size_t)(kRingH + 1) * 3 * fh + (size_t)kCoefStride * nmodes;
+  return n * elem + kMaxChunk * sizeof(int) + 16 + 8 * sizeof(double);
 }
 
 }  // namespace fdtdbath
