@@ -41,6 +41,7 @@ struct HostSrc {
   double nu, fwidth, amp, t0;
   bool has_phase;
   void *dcos, *dsin;
+  double phase1d;   // the phase of a 1D run (one transverse cell)
 };
 
 struct HostMon {
@@ -106,6 +107,14 @@ struct fdtdbath_sim {
   // a bath-free kernel for the plain chunks runs beside the bath kernel on a forked stream
   cudaStream_t side = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  // 1D simulations (nx = ny = 1, at most one source and one monitor) run the persistent
+  // cavity kernel: one cluster of c1d CTAs, in place, all steps of a call per launch
+  bool path1d = false;
+  int c1d = 1;
+  int ncomp1d = 3;          // 1 while only Ex, Hy, P_x and its bath can be nonzero
+  std::vector<int> bounds1d;            // cell range of every CTA of the cluster
+  void* src_tab = nullptr;              // per-step source amplitudes of one launch (device)
+  int red_nbxy = 1, red_nblocks = 1;   // partial-sum layout seen by the reduction
   std::string err;
 };
 
@@ -412,6 +421,107 @@ int launch_all(fdtdbath_sim* s, int doH, int doE) {
   return (int)e;
 }
 
+template <typename T>
+Cav1DParams<T> make_params1d(fdtdbath_sim* s, int64_t nsteps) {
+  Cav1DParams<T> p{};
+  p.nz = (int)s->nz;
+  p.npml = s->npml;
+  for (int r = 0; r <= s->c1d; ++r) p.bounds[r] = s->bounds1d[(size_t)r];
+  p.S = (T)(s->dt / s->dx);
+  p.dt = (T)s->dt;
+  p.E = (T*)s->E[s->ecur];
+  p.H = (T*)s->H[s->hcur];
+  p.D = (T*)s->D;
+  p.Pslot[0] = (T*)s->Pslot[0];
+  p.Pslot[1] = (T*)s->Pslot[1];
+  p.Yslot[0] = (T*)s->Yslot[0];
+  p.Yslot[1] = (T*)s->Yslot[1];
+  p.pcur0 = s->pcur;
+  p.coef = (const T*)s->coef;
+  p.nmat = (int)s->mats.size();
+  int off = 0;
+  for (size_t m = 0; m < s->mats.size(); ++m) {
+    p.mat[m] = mat_k<T>(s->mats[m], off, s->dt);
+    off += s->mats[m].nb;
+  }
+  p.pmlE = (const T*)s->pmlE;
+  p.pmlH = (const T*)s->pmlH;
+  p.psiE = (T*)s->psiE;
+  p.psiH = (T*)s->psiH[s->psicur];
+  p.psiH_stride = 2 * s->npml + 1;
+  p.nsrc = (int)s->srcs.size();
+  p.src_z = p.nsrc ? (int)s->srcs[0].z : -1;
+  p.src_tab = (const double*)s->src_tab;
+  p.nmon = (int)s->mons.size();
+  p.mon_z = p.nmon ? (int)s->mons[0].z : -1;
+  p.energy_on = s->energy_on ? 1 : 0;
+  p.every = s->e_every;
+  p.ebox_lo = (int)s->e_lo;
+  p.ebox_hi = (int)s->e_hi;
+  p.partial = (double*)s->partial;
+  p.ring_cap = s->ring_cap;
+  p.ring_stride = s->ring_stride;
+  p.monE_off = s->monE_off;
+  p.monH_off = s->monH_off;
+  p.enE_off = s->enE_off;
+  p.enH_off = s->enH_off;
+  p.step0 = s->n;
+  p.nsteps = (int)nsteps;
+  return p;
+}
+
+// Cell ranges of the cluster's CTAs: contiguous, at most kCav1DThreads cells each, balanced by
+// work (vacuum 1, CPML 2, Lorentz / Drude 3, Lorentz-Bath 3 + N_b per cell).
+std::vector<int> balance_cells(const fdtdbath_sim* s, int C) {
+  std::vector<double> w((size_t)s->nz, 1.0);
+  for (int64_t z = 0; z < s->nz; ++z)
+    if (z < s->npml || z >= s->nz - s->npml) w[(size_t)z] = 2.0;
+  for (auto& m : s->mats)
+    for (int64_t z = m.zlo; z < m.zhi; ++z)
+      w[(size_t)z] = m.kind == FDTDBATH_VACUUM ? 1.0 : 3.0 + (m.kind == FDTDBATH_LORENTZ_BATH ? m.nb : 0);
+  double total = 0.0;
+  for (double v : w) total += v;
+  std::vector<int> b(1, 0);
+  double acc = 0.0;
+  int64_t z = 0;
+  for (int r = 0; r < C; ++r) {
+    const double target = total * (r + 1) / C;
+    const int64_t left_ctas = C - r - 1;
+    int64_t end = z;
+    while (end < s->nz && (end - z) < kCav1DThreads &&
+           (end == z || acc + w[(size_t)end] <= target + 1e-9 || s->nz - end > left_ctas * kCav1DThreads)) {
+      acc += w[(size_t)end];
+      ++end;
+    }
+    if (r == C - 1) end = s->nz;
+    b.push_back((int)end);
+    z = end;
+  }
+  return b;
+}
+
+int launch_1d(fdtdbath_sim* s, int64_t nsteps) {
+  // per-step source amplitudes, evaluated on the host exactly as for the 3D kernel
+  if (!s->srcs.empty()) {
+    std::vector<double> tab((size_t)nsteps);
+    const HostSrc& q = s->srcs[0];
+    const double tau = 1.0 / (2.0 * M_PI * q.fwidth);
+    for (int64_t i = 0; i < nsteps; ++i) {
+      const double t = (double)(s->n + i) * s->dt;   // host code is built without FP contraction
+      const double u = t - q.t0;
+      tab[(size_t)i] = q.amp * std::exp(-u * u / (2.0 * tau * tau)) * std::sin(2.0 * M_PI * q.nu * u + q.phase1d);
+    }
+    cudaError_t e = cudaMemcpyAsync(s->src_tab, tab.data(), tab.size() * 8, cudaMemcpyHostToDevice, s->stream);
+    if (e != cudaSuccess) return cuda_fail(s, e, "source table copy");
+  }
+  int rc;
+  if (s->prec == 64) rc = launch_cavity1d_f64(make_params1d<double>(s, nsteps), s->nbmax, s->c1d, s->stream);
+  else rc = launch_cavity1d_f32(make_params1d<float>(s, nsteps), s->nbmax, s->c1d, s->stream);
+  s->launches++;
+  if (rc) return cuda_fail(s, (cudaError_t)rc, "1D cavity kernel launch");
+  return 0;
+}
+
 int launch_step(fdtdbath_sim* s, int doH, int doE) {
   const int rc = s->prec == 64 ? launch_all<double>(s, doH, doE) : launch_all<float>(s, doH, doE);
   if (rc) return cuda_fail(s, (cudaError_t)rc, "step kernel launch");
@@ -430,7 +540,7 @@ int reduce_upto(fdtdbath_sim* s, int64_t upto) {
     s->reduced = upto;
     return 0;
   }
-  const int nbxy = s->nbx * s->nby, nblocks = nbxy * s->nchunks;
+  const int nbxy = s->red_nbxy, nblocks = s->red_nblocks;
   ReduceParams r{};
   r.partial = (const double*)s->partial;
   r.ring_stride = s->ring_stride;
@@ -718,7 +828,8 @@ int fdtdbath_create(const fdtdbath_grid* grid, double resolution, double courant
     if (S.component < 0 || S.component > 2 || S.z < 0 || S.z >= nz)
       return bail(FDTDBATH_ERR_ARG, "source component or plane out of range");
     if (!(S.fwidth > 0)) return bail(FDTDBATH_ERR_ARG, "source fwidth must be positive");
-    HostSrc h{S.component, S.z, S.center, S.fwidth, S.amplitude, S.t0, S.phase != nullptr, nullptr, nullptr};
+    HostSrc h{S.component, S.z, S.center, S.fwidth, S.amplitude, S.t0, S.phase != nullptr, nullptr, nullptr,
+              S.phase ? S.phase[0] : 0.0};
     s->srcs.push_back(h);
   }
   for (int q = 0; q < nmon; ++q) {
@@ -790,8 +901,30 @@ int fdtdbath_create(const fdtdbath_grid* grid, double resolution, double courant
       cudaEventCreateWithFlags(&s->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&s->ev_join, cudaEventDisableTiming) != cudaSuccess)
     return bail(FDTDBATH_ERR_CUDA, "stream/event creation failed");
+  // 1D path: one cluster of up to 8 CTAs of 256 threads
+  s->path1d = (nx == 1 && ny == 1 && nsrc <= 1 && nmon <= 1 &&
+                nz <= (int64_t)kCav1DMaxCluster * kCav1DThreads);
+  if (s->path1d) {
+    // FP64 bath arithmetic is slow on this part: spread the cavity over the largest cluster
+    int want = s->prec == 64 ? kCav1DMaxCluster : 8;
+    if (const char* e = std::getenv("FDTDBATH_C1D")) want = std::max(1, std::min(kCav1DMaxCluster, std::atoi(e)));
+    s->c1d = (int)std::max<int64_t>(want, (nz + kCav1DThreads - 1) / kCav1DThreads);
+    s->c1d = std::min(s->c1d, kCav1DMaxCluster);
+    s->bounds1d = balance_cells(s, s->c1d);
+    for (int r = 0; r < s->c1d; ++r)
+      if (s->bounds1d[(size_t)r + 1] - s->bounds1d[(size_t)r] > kCav1DThreads) s->path1d = false;
+    s->ncomp1d = 1;
+    for (auto& q : s->srcs)
+      if (q.comp != 0) s->ncomp1d = 3;
+    s->ring_cap = 4096;
+    s->red_nbxy = 1;
+    s->red_nblocks = s->c1d;
+  } else {
+    s->red_nbxy = s->nbx * s->nby;
+    s->red_nblocks = s->red_nbxy * s->nchunks;
+  }
   // partial-sum ring
-  const int64_t nbxy = (int64_t)s->nbx * s->nby, nblocks = nbxy * s->nchunks;
+  const int64_t nbxy = s->red_nbxy, nblocks = s->red_nblocks;
   s->monE_off = 0;
   s->monH_off = 2 * (int64_t)s->mons.size() * nbxy;
   s->enE_off = s->monH_off + 4 * (int64_t)s->mons.size() * nbxy;
@@ -800,6 +933,10 @@ int fdtdbath_create(const fdtdbath_grid* grid, double resolution, double courant
   s->partial = dalloc(s, (size_t)s->ring_cap * s->ring_stride * 8);
   s->series = dalloc(s, (size_t)s->ring_cap * (6 * s->mons.size() + 4) * 8);
   if (!s->partial || !s->series) return bail(FDTDBATH_ERR_OOM, "device allocation failed");
+  if (s->path1d) {
+    s->src_tab = dalloc(s, (size_t)s->ring_cap * 8);
+    if (!s->src_tab) return bail(FDTDBATH_ERR_OOM, "device allocation failed");
+  }
   if (s->energy_on) {
     s->trace = dalloc(s, (size_t)s->e_cap * 4 * 8);
     if (!s->trace) return bail(FDTDBATH_ERR_OOM, "device allocation failed");
@@ -861,6 +998,22 @@ int fdtdbath_create(const fdtdbath_grid* grid, double resolution, double courant
 int fdtdbath_step(fdtdbath_sim* s, int64_t nsteps) {
   if (!s || nsteps < 0) return fail(s, FDTDBATH_ERR_ARG, "bad arguments to fdtdbath_step");
   cudaSetDevice(s->device);
+  if (s->path1d && s->ncomp1d == 1) {
+    int64_t left = nsteps;
+    while (left > 0) {
+      if (s->n - s->reduced >= s->ring_cap / 2) {
+        int rc = reduce_upto(s, s->n);
+        if (rc) return rc;
+      }
+      const int64_t m = std::min<int64_t>(left, s->ring_cap - (s->n - s->reduced));
+      int rc = launch_1d(s, m);
+      if (rc) return rc;
+      s->n += m;
+      s->pcur ^= (int)(m & 1);
+      left -= m;
+    }
+    return FDTDBATH_OK;
+  }
   for (int64_t it = 0; it < nsteps; ++it) {
     // keep the ring from overwriting partials not yet reduced
     if (s->n + 1 - s->reduced > s->ring_cap) {
@@ -937,6 +1090,11 @@ int fdtdbath_write_fields(fdtdbath_sim* s, int32_t field, const void* src, size_
   FieldRef f;
   if (!parse_field(field, &f)) return fail(s, FDTDBATH_ERR_ARG, "unknown field id");
   if (src_bytes < (size_t)s->ncell * s->esz) return fail(s, FDTDBATH_ERR_ARG, "source too small");
+  {
+    // the 1D kernel skips the y/z polarization while it provably stays zero
+    const bool xpol = (f.kind == 0 && (f.comp == 0 || f.comp == 4)) || (f.kind != 0 && f.comp == 0);
+    if (!xpol) s->ncomp1d = 3;
+  }
   cudaSetDevice(s->device);
   int rc = flush_all(s);
   if (rc) return rc;

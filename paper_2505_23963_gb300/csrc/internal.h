@@ -103,6 +103,43 @@ struct Step3DParams {
   int vec16;              // nx is a multiple of 16 bytes' worth of elements: 16-byte staging
 };
 
+// Persistent 1D cavity kernel (nx = ny = 1, x polarization): all steps of a call in one launch,
+// one cluster of up to 16 CTAs of kCav1DThreads threads per cavity, one cell per thread, the
+// state in registers.
+constexpr int kCav1DThreads = 512;
+constexpr int kCav1DMaxCluster = 16;
+template <typename T>
+struct Cav1DParams {
+  int nz, npml;
+  int bounds[kCav1DMaxCluster + 1];   // cell range of CTA r: [bounds[r], bounds[r+1])
+  T S, dt;
+  T* E;                               // [3][nz]; only E_x (component 0) is used
+  T* H;                               // [3][nz]; only H_y (component 1) is used
+  T* D;
+  T* Pslot[2];
+  T* Yslot[2];
+  int pcur0;                          // slot holding P^{n+1/2} at the first step of the launch
+  const T* coef;
+  int nmat;
+  MatK<T> mat[kMaxMat];
+  const T* pmlE;
+  const T* pmlH;
+  T* psiE;
+  T* psiH;
+  int psiH_stride;
+  int nsrc, src_z;
+  const double* src_tab;              // source amplitude of each step of the launch
+  int nmon, mon_z;
+  int energy_on, every, ebox_lo, ebox_hi;
+  double* partial;
+  int ring_cap;
+  int64_t ring_stride, monE_off, monH_off, enE_off, enH_off;
+  int64_t step0;
+  int nsteps;
+};
+int launch_cavity1d_f32(const Cav1DParams<float>& p, int nbmax, int cluster, void* stream);
+int launch_cavity1d_f64(const Cav1DParams<double>& p, int nbmax, int cluster, void* stream);
+
 // Launchers (defined in step3d_f32.cu / step3d_f64.cu).
 int launch_step3d_f32(const Step3DParams<float>& p, int nbmax, int ty, int nbx, int nby,
                       int nchunks, void* stream);
