@@ -200,6 +200,99 @@ int64_t fdtdbath_query(const fdtdbath_sim *sim, int32_t key);
 int fdtdbath_box_energy_noalloc(fdtdbath_sim *sim, int64_t z_lo, int64_t z_hi, double *out,
                                 int32_t out_on_device);
 
+/* ---------------------------------------------------------------------------------------------
+ * Batched 1D cavities.  Many independent 1D cavities (nx = ny = 1, x polarization: E_x, H_y, P_x
+ * and its bath modes) of uneven length, each advanced by the same scheme as fdtdbath_create /
+ * fdtdbath_step (Eq. FDTD-1D with Eq. Pz_update-LB, Pz_1D_Lorentz, Yzj_finite_difference; the
+ * Rabi-splitting and bath-parameter sweeps of Sec. IV run one cavity per parameter set), all
+ * cavities in ONE persistent launch per chunk of steps.  The library packs the cavities over the
+ * thread-block clusters of that launch (whole cavities per cluster, contiguous cell ranges per
+ * CTA, the state held in shared memory for the whole chunk), picks the launch shape with its own
+ * autotuner unless the options fix it, and replays the chunks from captured CUDA graphs.
+ * --------------------------------------------------------------------------------------------- */
+typedef struct fdtdbath_batch fdtdbath_batch; /* opaque, owned by the library */
+
+/* One cavity: nz cells (64 <= nz <= 2^24) with a CPML of pml_cells cells at each end, its layers
+ * (z in the cavity's own cells, the same rules as fdtdbath_create), an optional soft source on
+ * component 0 (E_x; phase NULL or one value) and an optional energy box [energy_lo, energy_hi)
+ * (energy_hi <= energy_lo: none).  Host pointers, copied by fdtdbath_batch_create. */
+typedef struct {
+  int64_t nz;
+  int32_t pml_cells;
+  const fdtdbath_material *materials;
+  int32_t nmat;
+  const fdtdbath_source *source;
+  int64_t energy_lo, energy_hi;
+} fdtdbath_cavity;
+
+typedef struct {
+  int32_t precision;       /* 32: FP32 state, increment arithmetic; 64: FP64, the literal updates */
+  void *cuda_stream;       /* cudaStream_t to queue work on; NULL = legacy default stream */
+  void *(*alloc)(size_t bytes, void *ctx);   /* optional device allocator, as fdtdbath_options */
+  void (*free)(void *ptr, void *ctx);
+  void *alloc_ctx;
+  int32_t energy_every;    /* record the cavities' energies every this many steps (0 or 1: each) */
+  int64_t energy_capacity; /* records kept per cavity (0: 65536); later records are dropped */
+  int32_t cluster_ctas;    /* launch shape: CTAs per cluster (1..16) and threads per CTA (a */
+  int32_t block_threads;   /* multiple of 32, <= 512); 0 = chosen by the autotuner at the first step */
+  int32_t use_graph;       /* nonzero: replay each chunk of steps from a captured CUDA graph */
+  int32_t device;          /* CUDA device ordinal */
+} fdtdbath_batch_options;
+
+/* Validate every cavity (errors name the cavity), expand its coefficients exactly as
+ * fdtdbath_create does, tabulate each source's amplitude per step (until the Gaussian envelope
+ * underflows to exactly zero), allocate and zero the state.  resolution and courant are shared
+ * by the batch (dt = courant/resolution).  *out receives the handle. */
+int fdtdbath_batch_create(const fdtdbath_cavity *cavities, int32_t ncav, double resolution, double courant,
+                          const fdtdbath_batch_options *options, fdtdbath_batch **out);
+
+/* Autotuner: time probe_steps steps of every feasible launch shape (CTAs per cluster in
+ * {1,2,4,8,16} x threads in {128,256,512} x 1 or 2 CTAs per SM, each packed for this batch) and
+ * keep the fastest; the state is restored afterwards.  Outputs (optional) receive the shape and
+ * its time per step in milliseconds.  fdtdbath_batch_step runs it with 64 probe steps when no
+ * shape has been chosen yet. */
+int fdtdbath_batch_autotune(fdtdbath_batch *batch, int32_t probe_steps, int32_t *cluster_ctas,
+                            int32_t *block_threads, float *ms_per_step);
+
+/* Advance every cavity nsteps steps, asynchronously on the batch's stream: chunks of
+ * 1024 * energy_every steps (4096 without energy boxes), each one launch of the batch kernel
+ * plus the energy reduction, replayed from a CUDA graph when use_graph is set. */
+int fdtdbath_batch_step(fdtdbath_batch *batch, int64_t nsteps);
+
+/* Wait for queued work; returns a deferred device error, if any. */
+int fdtdbath_batch_sync(fdtdbath_batch *batch);
+
+/* Copy one field of one cavity, nz elements of the state type (float / double), into host dst:
+ * FDTDBATH_FIELD_E(0), FDTDBATH_FIELD_H(1), FDTDBATH_FIELD_P(0), FDTDBATH_FIELD_PM(0) or
+ * FDTDBATH_FIELD_Y(0, j, l) (zero outside the cavity's Lorentz-Bath layers).  Other ids:
+ * FDTDBATH_ERR_ARG.  Synchronizes the batch's stream. */
+int fdtdbath_batch_read_field(fdtdbath_batch *batch, int32_t cavity, int32_t field, void *dst,
+                              size_t dst_bytes);
+
+/* Energy records of one cavity, host trace[len][4] = (U_EM, U_P, U_bath, 0) with the
+ * definitions of fdtdbath_energy (dx weight), record r describing step r * energy_every.
+ * *len = records available (at most maxlen and energy_capacity). */
+int fdtdbath_batch_energy(fdtdbath_batch *batch, int32_t cavity, double *trace, int64_t maxlen, int64_t *len);
+
+/* Runtime facts: key 0 kernel launches, 1 clusters, 2 CTAs, 3 CTAs per cluster, 4 threads per
+ * CTA, 5 device bytes held, 6 graph replays, 7 completed steps, 8 dynamic shared memory per CTA,
+ * 9 total cells.  -1 for an unknown key. */
+int64_t fdtdbath_batch_query(const fdtdbath_batch *batch, int32_t key);
+
+/* Text of the last error of batch (or of the last failed batch create / plan when NULL). */
+const char *fdtdbath_batch_last_error(const fdtdbath_batch *batch);
+
+void fdtdbath_batch_destroy(fdtdbath_batch *batch);
+
+/* Host-only planning (no GPU needed): pack the cavities for cluster_ctas CTAs per cluster,
+ * at most nclusters clusters and smem_per_cta bytes of dynamic shared memory per CTA.  Returns
+ * the number of CTAs (nclusters_used * cluster_ctas, cluster-major) or a negative error; the
+ * optional outputs receive per CTA its work units, cells and shared-memory bytes, and per cavity
+ * its cluster. */
+int fdtdbath_batch_plan(const fdtdbath_cavity *cavities, int32_t ncav, double resolution, double courant,
+                        int32_t precision, int32_t cluster_ctas, int32_t nclusters, int32_t smem_per_cta,
+                        int64_t *cta_work, int32_t *cta_ncell, int32_t *cta_smem, int32_t *cav_cluster);
+
 #ifdef __cplusplus
 }
 #endif

@@ -30,6 +30,9 @@ UNITS = [
     ("noalloc.cu", ["--fmad=false"]),
     ("cavity1d_f32.cu", []),
     ("cavity1d_f64.cu", ["--fmad=false"]),
+    ("batch.cpp", []),
+    ("batch1d_f32.cu", []),
+    ("batch1d_f64.cu", ["--fmad=false"]),
 ]
 
 

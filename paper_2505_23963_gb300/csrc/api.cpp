@@ -17,6 +17,7 @@
 #include <vector>
 
 #include "../../include/fdtdbath.h"
+#include "host_common.h"
 #include "internal.h"
 
 using namespace fdtdbath;
@@ -24,16 +25,6 @@ using namespace fdtdbath;
 namespace {
 
 thread_local std::string g_create_error;
-
-struct HostMat {
-  int kind, nb;
-  int64_t zlo, zhi, ncell, base, ybase;
-  double eps, w0, g0, sigma;
-  std::vector<double> wj, gj, kj;
-  // derived (double)
-  double cE, c1m, W, c2, A, rho, w0r2;
-  std::vector<double> rowsLit, rowsInc;  // [nb][kCoefStride]
-};
 
 struct HostSrc {
   int comp;
@@ -171,105 +162,9 @@ int d2h(fdtdbath_sim* s, void* dst, const void* src, size_t bytes) {
   return 0;
 }
 
-// CPML profile (Roden-Gedney, kappa = 1) at a z position in cells.  The left absorber
-// interface sits at z = npml, the right one at z = nz-1-npml; depth d is clamped to npml;
-// sigma = 0.8 (m+1)/dx (d/npml)^m with m = 3; alpha = 2 pi 0.05 (1 - d/npml);
-// b = exp(-(sigma + alpha) dt), c = sigma/(sigma + alpha) (b - 1).
+// CPML profile of this simulation's z axis (see cpml_coeffs).
 void cpml_bc(const fdtdbath_sim* s, double zpos, double* b, double* c) {
-  *b = 1.0;
-  *c = 0.0;
-  if (s->npml <= 0) return;
-  const double zl = (double)s->npml, zr = (double)(s->nz - 1 - s->npml);
-  double d = 0.0;
-  if (zpos < zl) d = zl - zpos;
-  else if (zpos > zr) d = zpos - zr;
-  if (d > (double)s->npml) d = (double)s->npml;
-  if (d <= 0.0) return;
-  const double r = d / (double)s->npml;
-  const double sig = 0.8 * 4.0 / s->dx * r * r * r;
-  const double alpha = 2.0 * M_PI * 0.05 * (1.0 - r);
-  *b = std::exp(-(sig + alpha) * s->dt);
-  *c = sig / (sig + alpha) * (*b - 1.0);
-}
-
-// Coefficients of the explicit updates of one material (double precision).
-void expand_material(HostMat& m, double dt) {
-  const double dt2 = dt * dt;
-  double S = 0.0;
-  m.rowsLit.assign((size_t)m.nb * kCoefStride, 0.0);
-  m.rowsInc.assign((size_t)m.nb * kCoefStride, 0.0);
-  for (int j = 0; j < m.nb; ++j) {
-    const double wj = m.wj[j], gj = m.gj[j], kj = m.kj[j];
-    const double den = 1.0 + 0.5 * gj * dt;
-    const double a = (2.0 - wj * wj * dt * dt) / den;   // a_j
-    const double b = -2.0 / den;                        // b_j
-    const double c = kj * dt / (2.0 * den);             // c_j
-    S += kj * c;
-    const double apb = -(wj * wj * dt2) / den;          // a_j + b_j without cancellation
-    const double mbp1 = (1.0 - 0.5 * gj * dt) / den;    // -(b_j + 1)
-    double* L = &m.rowsLit[(size_t)j * kCoefStride];
-    L[0] = kj;
-    L[1] = a;
-    L[2] = b;
-    L[3] = b + 1.0;
-    L[4] = c;
-    L[5] = wj * wj * dt2;
-    double* I = &m.rowsInc[(size_t)j * kCoefStride];
-    I[0] = kj * apb;
-    I[1] = -kj * b;
-    I[2] = apb;
-    I[3] = mbp1;
-    I[4] = c;
-    I[5] = wj * wj * dt2;
-  }
-  const double w0 = m.w0, g0 = m.g0;
-  m.cE = w0 * w0 * dt * dt * m.sigma;
-  if (m.kind == FDTDBATH_DRUDE) {
-    m.c1m = 0.0 * dt * dt - 2.0;
-    m.W = 0.0;
-    m.w0r2 = 0.0;
-  } else {
-    m.c1m = w0 * w0 * dt * dt - 2.0;
-    m.W = w0 * w0 * dt * dt;
-    m.w0r2 = w0 * w0;
-  }
-  if (m.kind == FDTDBATH_LORENTZ_BATH) {
-    m.c2 = 1.0 - 0.5 * g0 * dt - 0.5 * dt * S;
-    m.A = 1.0 + 0.5 * g0 * dt + 0.5 * dt * S;
-  } else {
-    m.c2 = 1.0 - 0.5 * g0 * dt;
-    m.A = 1.0 + 0.5 * g0 * dt;
-  }
-  m.rho = (m.sigma > 0.0 && w0 > 0.0) ? 1.0 / (m.sigma * w0 * w0) : 0.0;
-  if (m.kind == FDTDBATH_VACUUM) {
-    m.cE = m.c1m = m.W = m.c2 = 0.0;
-    m.A = 1.0;
-    m.rho = 0.0;
-  }
-}
-
-template <typename T>
-MatK<T> mat_k(const HostMat& m, int coef_off, double dt) {
-  MatK<T> k{};
-  k.zlo = (int)m.zlo;
-  k.zhi = (int)m.zhi;
-  k.kind = m.kind;
-  k.nb = m.nb;
-  k.base = m.base;
-  k.ybase = m.ybase;
-  k.ncell = m.ncell;
-  k.coef_off = coef_off;
-  k.eps = (T)m.eps;
-  k.cE = (T)m.cE;
-  k.c1m = (T)m.c1m;
-  k.W = (T)m.W;
-  k.c2 = (T)m.c2;
-  k.A = (T)m.A;
-  k.inv_A = (T)(1.0 / m.A);
-  k.inv_eps = (T)(1.0 / m.eps);
-  k.rho_idt2 = (T)(m.rho / (dt * dt));
-  k.w0r2dt2 = (T)(m.w0r2 * dt * dt);
-  return k;
+  cpml_coeffs(s->npml, s->nz, s->dx, s->dt, zpos, b, c);
 }
 
 // z-chunks of about zc planes.  Chunk starts avoid the CPML planes (the chunk-start H
@@ -756,52 +651,13 @@ int fdtdbath_create(const fdtdbath_grid* grid, double resolution, double courant
   int64_t prev_hi = 0;
   for (int oi = 0; oi < nmat; ++oi) {
     const fdtdbath_material& M = materials[order[oi]];
-    if (M.kind < 0 || M.kind > 3) return bail(FDTDBATH_ERR_ARG, "unknown material kind");
     if (M.z_lo < 0 || M.z_hi > nz || M.z_lo >= M.z_hi) return bail(FDTDBATH_ERR_ARG, "material z-range outside the grid");
     if (M.z_lo < prev_hi) return bail(FDTDBATH_ERR_ARG, "material layers overlap");
     prev_hi = M.z_hi;
-    if (!(M.eps_inf > 0)) return bail(FDTDBATH_ERR_ARG, "eps_inf must be positive");
-    if (M.sigma < 0 || M.gamma < 0 || M.frequency < 0) return bail(FDTDBATH_ERR_ARG, "negative material parameter");
     HostMat h{};
-    h.kind = M.kind;
-    h.zlo = M.z_lo;
-    h.zhi = M.z_hi;
-    h.ncell = (M.z_hi - M.z_lo) * s->plane;
-    h.eps = M.eps_inf;
-    h.w0 = 2.0 * M_PI * M.frequency;
-    h.g0 = 2.0 * M_PI * M.gamma;
-    h.sigma = M.sigma;
-    h.nb = 0;
-    if (M.kind == FDTDBATH_LORENTZ_BATH) {
-      if (M.num_bath < 0 || M.num_bath > kMaxBath) return bail(FDTDBATH_ERR_ARG, "num_bath must be in [0, 32]");
-      if (M.num_bath && (!M.bath_frequencies || !M.bath_gammas || !M.bath_couplings))
-        return bail(FDTDBATH_ERR_ARG, "bath arrays missing");
-      h.nb = M.num_bath;
-      for (int j = 0; j < h.nb; ++j) {
-        if (M.bath_frequencies[j] < 0 || M.bath_gammas[j] < 0) return bail(FDTDBATH_ERR_ARG, "negative bath parameter");
-        h.wj.push_back(2.0 * M_PI * M.bath_frequencies[j]);
-        h.gj.push_back(2.0 * M_PI * M.bath_gammas[j]);
-        h.kj.push_back(2.0 * M_PI * M.bath_couplings[j]);
-      }
-    }
-    // explicit oscillator updates are stable only for w dt < 2
-    if (M.kind != FDTDBATH_DRUDE && M.kind != FDTDBATH_VACUUM && h.w0 * s->dt >= 2.0)
-      return bail(FDTDBATH_ERR_CFL, "w0 dt >= 2: oscillator update unstable");
-    for (double w : h.wj)
-      if (w * s->dt >= 2.0) return bail(FDTDBATH_ERR_CFL, "w_j dt >= 2: bath update unstable");
-    // coupled field + oscillator stability: a plane wave of the scheme obeys
-    // Omega^2 (eps_inf + chi_d) = K^2 with Omega = 2 sin(w dt/2)/dt and K^2 <= 4 dims/dx^2, and
-    // its largest Omega^2 is below w_max^2 + K^2/eps_inf (w_max^2 = w0^2 (1 + sigma) + sum k_j^2,
-    // or w0^2 sigma for Drude); every root stays on the unit circle while that is <= 4/dt^2.
-    {
-      double wmax2 = 0.0;
-      if (M.kind == FDTDBATH_DRUDE) wmax2 = h.w0 * h.w0 * h.sigma;
-      else if (M.kind != FDTDBATH_VACUUM) wmax2 = h.w0 * h.w0 * (1.0 + h.sigma);
-      for (double k : h.kj) wmax2 += k * k;
-      const double lhs = wmax2 * s->dt * s->dt + 4.0 * courant * courant * dims / h.eps;
-      if (lhs > 4.0 * (1.0 + 1e-12))
-        return bail(FDTDBATH_ERR_CFL, "field-oscillator update unstable: w_max^2 dt^2 + 4 S^2 dims/eps_inf > 4");
-    }
+    std::string why;
+    const int rc = build_material(M, s->plane, s->dt, courant, dims, h, why);
+    if (rc) return bail(rc, why);
     expand_material(h, s->dt);
     s->mats.push_back(h);
   }

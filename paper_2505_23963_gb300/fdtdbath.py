@@ -26,7 +26,10 @@ BATH_SHAPES = {"uniform": 0, "lorentzian": 1, "gaussian": 2}
 EXPORTED = ["fdtdbath_create", "fdtdbath_step", "fdtdbath_sync", "fdtdbath_read_fields",
             "fdtdbath_write_fields", "fdtdbath_dft", "fdtdbath_energy", "fdtdbath_steps_done",
             "fdtdbath_last_error", "fdtdbath_destroy", "fdtdbath_bath_form", "fdtdbath_query",
-            "fdtdbath_box_energy_noalloc"]
+            "fdtdbath_box_energy_noalloc", "fdtdbath_batch_create", "fdtdbath_batch_autotune",
+            "fdtdbath_batch_step", "fdtdbath_batch_sync", "fdtdbath_batch_read_field",
+            "fdtdbath_batch_energy", "fdtdbath_batch_query", "fdtdbath_batch_last_error",
+            "fdtdbath_batch_destroy", "fdtdbath_batch_plan"]
 
 
 def field_E(c): return 0 + c
@@ -68,6 +71,19 @@ class Options(C.Structure):
                 ("cuda_stream", C.c_void_p), ("alloc", ALLOC_FN), ("free", FREE_FN),
                 ("alloc_ctx", C.c_void_p), ("energy_lo", C.c_int64), ("energy_hi", C.c_int64),
                 ("energy_capacity", C.c_int64), ("device", C.c_int32)]
+
+
+class Cavity(C.Structure):
+    _fields_ = [("nz", C.c_int64), ("pml_cells", C.c_int32), ("materials", C.POINTER(Material)),
+                ("nmat", C.c_int32), ("source", C.POINTER(Source)), ("energy_lo", C.c_int64),
+                ("energy_hi", C.c_int64)]
+
+
+class BatchOptions(C.Structure):
+    _fields_ = [("precision", C.c_int32), ("cuda_stream", C.c_void_p), ("alloc", ALLOC_FN),
+                ("free", FREE_FN), ("alloc_ctx", C.c_void_p), ("energy_every", C.c_int32),
+                ("energy_capacity", C.c_int64), ("cluster_ctas", C.c_int32),
+                ("block_threads", C.c_int32), ("use_graph", C.c_int32), ("device", C.c_int32)]
 
 
 _lib = None
@@ -113,6 +129,29 @@ def lib(build_if_missing: bool = True):
         L.fdtdbath_query.argtypes = [vp, i32]
         L.fdtdbath_box_energy_noalloc.restype = i32
         L.fdtdbath_box_energy_noalloc.argtypes = [vp, i64, i64, vp, i32]
+        i32p, i64p = C.POINTER(i32), C.POINTER(i64)
+        L.fdtdbath_batch_create.restype = i32
+        L.fdtdbath_batch_create.argtypes = [C.POINTER(Cavity), i32, C.c_double, C.c_double,
+                                            C.POINTER(BatchOptions), C.POINTER(vp)]
+        L.fdtdbath_batch_autotune.restype = i32
+        L.fdtdbath_batch_autotune.argtypes = [vp, i32, i32p, i32p, C.POINTER(C.c_float)]
+        L.fdtdbath_batch_step.restype = i32
+        L.fdtdbath_batch_step.argtypes = [vp, i64]
+        L.fdtdbath_batch_sync.restype = i32
+        L.fdtdbath_batch_sync.argtypes = [vp]
+        L.fdtdbath_batch_read_field.restype = i32
+        L.fdtdbath_batch_read_field.argtypes = [vp, i32, i32, vp, C.c_size_t]
+        L.fdtdbath_batch_energy.restype = i32
+        L.fdtdbath_batch_energy.argtypes = [vp, i32, dp, i64, i64p]
+        L.fdtdbath_batch_query.restype = i64
+        L.fdtdbath_batch_query.argtypes = [vp, i32]
+        L.fdtdbath_batch_last_error.restype = C.c_char_p
+        L.fdtdbath_batch_last_error.argtypes = [vp]
+        L.fdtdbath_batch_destroy.restype = None
+        L.fdtdbath_batch_destroy.argtypes = [vp]
+        L.fdtdbath_batch_plan.restype = i32
+        L.fdtdbath_batch_plan.argtypes = [C.POINTER(Cavity), i32, C.c_double, C.c_double, i32,
+                                          i32, i32, i32, i64p, i32p, i32p, i32p]
         _lib = L
     return _lib
 
@@ -169,14 +208,7 @@ class _TorchAllocator:
         self.free = FREE_FN(_free)
 
 
-def create(prob: dict, precision: int = 64, stream=None, use_torch_allocator: bool = True,
-           energy: bool = True, energy_capacity: int = 0, device: int = 0, bath_storage: int = 0):
-    """fdtdbath_create from a problem dict; returns (handle, keepalive)."""
-    L = lib()
-    nx, ny, nz = (int(v) for v in prob["n"])
-    grid = Grid((C.c_int64 * 3)(nx, ny, nz), int(prob.get("pml", 0)))
-    keep = []
-    mats = prob.get("materials", [])
+def _materials(mats, keep):
     marr = (Material * max(1, len(mats)))()
     for i, m in enumerate(mats):
         nb = len(m.get("bath_frequencies", [])) if m["kind"] == "lorentz_bath" else 0
@@ -187,17 +219,34 @@ def create(prob: dict, precision: int = 64, stream=None, use_torch_allocator: bo
                            float(m.get("eps_inf", 1.0)), float(m.get("frequency", 0.0)),
                            float(m.get("gamma", 0.0)), float(m.get("sigma", 0.0)), nb,
                            _dptr(arrs[0]), _dptr(arrs[1]), _dptr(arrs[2]))
+    keep.append(marr)
+    return marr
+
+
+def _source(s, keep) -> "Source":
+    ph = s.get("phase")
+    php = None
+    if ph is not None:
+        ph = _f64(ph).reshape(-1)
+        keep.append(ph)
+        php = _dptr(ph)
+    return Source(int(s["component"]), int(s["z"]), float(s["center"]), float(s["fwidth"]),
+                  float(s.get("amplitude", 1.0)), float(s["t0"]), php)
+
+
+def create(prob: dict, precision: int = 64, stream=None, use_torch_allocator: bool = True,
+           energy: bool = True, energy_capacity: int = 0, device: int = 0, bath_storage: int = 0):
+    """fdtdbath_create from a problem dict; returns (handle, keepalive)."""
+    L = lib()
+    nx, ny, nz = (int(v) for v in prob["n"])
+    grid = Grid((C.c_int64 * 3)(nx, ny, nz), int(prob.get("pml", 0)))
+    keep = []
+    mats = prob.get("materials", [])
+    marr = _materials(mats, keep)
     srcs = prob.get("sources", [])
     sarr = (Source * max(1, len(srcs)))()
-    for i, s in enumerate(srcs):
-        ph = s.get("phase")
-        php = None
-        if ph is not None:
-            ph = _f64(ph).reshape(-1)
-            keep.append(ph)
-            php = _dptr(ph)
-        sarr[i] = Source(int(s["component"]), int(s["z"]), float(s["center"]), float(s["fwidth"]),
-                         float(s.get("amplitude", 1.0)), float(s["t0"]), php)
+    for i, src in enumerate(srcs):
+        sarr[i] = _source(src, keep)
     mons = prob.get("monitors", [])
     monarr = (Monitor * max(1, len(mons)))()
     for i, mo in enumerate(mons):
@@ -332,6 +381,140 @@ class Simulation:
     def close(self):
         if getattr(self, "h", None):
             destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ------------------------------------------------------------------ batched 1D cavities
+def _bcheck(rc: int, handle=None):
+    if rc < 0:
+        msg = lib().fdtdbath_batch_last_error(handle)
+        raise FdtdBathError(rc, msg.decode() if msg else "")
+
+
+def _cavities(probs, energy: bool, keep):
+    """Cavity array from 1D problem dicts (n = (1, 1, nz)) sharing resolution and Courant."""
+    res, cour = float(probs[0]["resolution"]), float(probs[0]["courant"])
+    cav = (Cavity * len(probs))()
+    for i, p in enumerate(probs):
+        if tuple(int(v) for v in p["n"][:2]) != (1, 1):
+            raise ValueError("batched cavities are 1D: n = (1, 1, nz)")
+        if float(p["resolution"]) != res or float(p["courant"]) != cour:
+            raise ValueError("the cavities of a batch share resolution and Courant number")
+        marr = _materials(p.get("materials", []), keep)
+        srcs = p.get("sources", [])
+        if len(srcs) > 1:
+            raise ValueError("a batched cavity takes at most one source")
+        sp = None
+        if srcs:
+            src = (Source * 1)(_source(srcs[0], keep))
+            keep.append(src)
+            sp = C.cast(src, C.POINTER(Source))
+        lo, hi = p.get("energy_box", (0, 0)) if energy else (0, 0)
+        cav[i] = Cavity(int(p["n"][2]), int(p.get("pml", 0)), C.cast(marr, C.POINTER(Material)),
+                        len(p.get("materials", [])), sp, int(lo), int(hi))
+    keep.append(cav)
+    return cav, res, cour
+
+
+def batch_plan(probs, precision: int, cluster_ctas: int, nclusters: int, smem_per_cta: int):
+    """fdtdbath_batch_plan (host only): per-CTA work / cells / shared-memory bytes and the
+    cluster of every cavity."""
+    keep = []
+    cav, res, cour = _cavities(probs, True, keep)
+    nmax = cluster_ctas * nclusters
+    work = np.zeros(nmax, np.int64)
+    cells = np.zeros(nmax, np.int32)
+    smem = np.zeros(nmax, np.int32)
+    clus = np.zeros(len(probs), np.int32)
+    rc = lib(build_if_missing=True).fdtdbath_batch_plan(
+        cav, len(probs), res, cour, int(precision), int(cluster_ctas), int(nclusters),
+        int(smem_per_cta), work.ctypes.data_as(C.POINTER(C.c_int64)),
+        cells.ctypes.data_as(C.POINTER(C.c_int32)), smem.ctypes.data_as(C.POINTER(C.c_int32)),
+        clus.ctypes.data_as(C.POINTER(C.c_int32)))
+    _bcheck(rc, None)
+    return {"work": work[:rc], "cells": cells[:rc], "smem": smem[:rc], "cluster": clus}
+
+
+class Batch:
+    """Batched 1D cavities (fdtdbath_batch_*): one persistent launch per chunk of steps."""
+
+    def __init__(self, probs, precision: int = 32, stream=None, energy: bool = True,
+                 energy_every: int = 1, energy_capacity: int = 0, cluster_ctas: int = 0,
+                 block_threads: int = 0, use_graph: bool = True, use_torch_allocator: bool = True,
+                 device: int = 0):
+        L = lib()
+        self.probs = list(probs)
+        self.precision = precision
+        self.dtype = np.float64 if precision == 64 else np.float32
+        self.every = max(1, int(energy_every))
+        self._keep = []
+        cav, res, cour = _cavities(self.probs, energy, self._keep)
+        opt = BatchOptions()
+        opt.precision = int(precision)
+        opt.device = int(device)
+        sptr = 0
+        if stream is not None:
+            sptr = int(getattr(stream, "cuda_stream", stream))
+        opt.cuda_stream = sptr or None
+        if use_torch_allocator:
+            alloc = _TorchAllocator(device, sptr)
+            self._keep.append(alloc)
+            opt.alloc, opt.free = alloc.alloc, alloc.free
+        opt.energy_every = self.every
+        steps = max(int(p.get("steps", 1024)) for p in self.probs)
+        opt.energy_capacity = int(energy_capacity or steps // self.every + 16)
+        opt.cluster_ctas = int(cluster_ctas)
+        opt.block_threads = int(block_threads)
+        opt.use_graph = int(bool(use_graph))
+        h = C.c_void_p()
+        _bcheck(L.fdtdbath_batch_create(cav, len(self.probs), res, cour, C.byref(opt), C.byref(h)))
+        self.h = h
+
+    def autotune(self, probe_steps: int = 64):
+        c, t, ms = C.c_int32(0), C.c_int32(0), C.c_float(0)
+        _bcheck(lib().fdtdbath_batch_autotune(self.h, int(probe_steps), C.byref(c), C.byref(t),
+                                              C.byref(ms)), self.h)
+        return c.value, t.value, ms.value
+
+    def step(self, n: int):
+        _bcheck(lib().fdtdbath_batch_step(self.h, int(n)), self.h)
+
+    def sync(self):
+        _bcheck(lib().fdtdbath_batch_sync(self.h), self.h)
+
+    def get(self, cavity: int, name: str, mode: int = 0, level: int = 0) -> np.ndarray:
+        f = {"E": field_E(0), "H": field_H(1), "P": field_P(0), "Pm": field_PM(0)}.get(name)
+        if f is None:
+            f = field_Y(0, mode, level)
+        out = np.empty(int(self.probs[cavity]["n"][2]), dtype=self.dtype)
+        _bcheck(lib().fdtdbath_batch_read_field(self.h, int(cavity), int(f), out.ctypes.data,
+                                                out.nbytes), self.h)
+        return out
+
+    def trace(self, cavity: int, maxlen: int | None = None) -> np.ndarray:
+        maxlen = maxlen or self.query(7) // self.every + 2
+        out = np.empty((max(1, maxlen), 4), dtype=np.float64)
+        n = C.c_int64(0)
+        _bcheck(lib().fdtdbath_batch_energy(self.h, int(cavity), _dptr(out), int(maxlen),
+                                            C.byref(n)), self.h)
+        return out[:n.value].copy()
+
+    def query(self, key: int) -> int:
+        return int(lib().fdtdbath_batch_query(self.h, int(key)))
+
+    def shape(self) -> dict:
+        return {"clusters": self.query(1), "ctas": self.query(2), "cluster_ctas": self.query(3),
+                "threads": self.query(4), "smem": self.query(8)}
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().fdtdbath_batch_destroy(self.h)
             self.h = None
 
     def __del__(self):

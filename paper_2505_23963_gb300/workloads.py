@@ -152,6 +152,65 @@ def small_3d(nx=40, ny=12, layout=(6, 5, 3, 10, 3, 5), nb=8, steps=60, seed=0) -
                        phase_seed=seed, nfreq=16, steps=steps, name=f"small3d_{nx}x{ny}_nb{nb}")
 
 
+def batch_cavity(L: int, *, rabi: float, num_bath: int, resolution: float = 100.0,
+                 pml: int = 16, mirror: int = 20, layer_frac: float = 0.4, steps: int = 50000,
+                 name: str = "") -> dict:
+    """One cavity of the batching form: L cells = CPML | vacuum | Drude | Lorentz-Bath (40% of L)
+    | Drude | vacuum | CPML, the vacuum remainder split evenly; sigma = (Omega_R / f0)^2 for the
+    requested Rabi splitting (ideal-cavity relation Omega_R = w0 sqrt(sigma)); bath frequencies
+    linspace(0.9, 1.1) with Ohmic-like couplings; the source 24 cells into the left vacuum, the
+    energy box = the layer between the mirrors."""
+    layer = int(round(layer_frac * L))
+    vac = L - 2 * pml - 2 * mirror - layer
+    if vac < 4:
+        raise ValueError("cavity too short for its layout")
+    vl = vac // 2
+    vr = vac - vl
+    return slab_cavity(1, 1, (pml, vl, mirror, layer, mirror, vr), resolution, num_bath=num_bath,
+                       sigma=float(rabi) ** 2, phase_seed=None, src_z=pml + min(24, vl // 2),
+                       mon_z=L - pml - min(24, vr // 2), nfreq=8, steps=steps,
+                       name=name or f"batch_L{L}_nb{num_bath}_rabi{rabi:.4f}")
+
+
+def batch_sweep(n: int = 64, steps: int = 50000, len_seed: int = 0, nb_seed: int = 1,
+                lmin: int = 1000, lmax: int = 8000, rabi_lo: float = 0.01,
+                rabi_hi: float = 0.2) -> list:
+    """Batching form: n independent 1D cavities, lengths default_rng(len_seed).integers(lmin,
+    lmax + 1), Rabi splittings linspace(rabi_lo, rabi_hi, n) (sigma = Omega_R^2), N_b drawn by
+    default_rng(nb_seed).choice([4, 8, 16, 32]); resolution 100, Courant 0.5."""
+    lengths = np.random.default_rng(len_seed).integers(lmin, lmax + 1, size=n)
+    nbs = np.random.default_rng(nb_seed).choice([4, 8, 16, 32], size=n)
+    rabis = np.linspace(rabi_lo, rabi_hi, n)
+    return [batch_cavity(int(L), rabi=float(r), num_bath=int(nb), steps=steps)
+            for L, r, nb in zip(lengths, rabis, nbs)]
+
+
+def batch_small(seed: int = 0, steps: int = 600) -> list:
+    """A small ragged batch for element-wise parity: lengths 64..700, N_b in {0 (plain Lorentz),
+    4, 8, 16, 32}, one cavity with a dielectric (eps_inf = 2.25) spacer, one without an energy
+    box."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i, nb in enumerate((0, 4, 8, 16, 32, 8)):
+        L = int(rng.integers(64, 701))
+        pml = 8
+        mir = 6
+        layer = max(8, int(0.35 * L))
+        vac = L - 2 * pml - 2 * mir - layer
+        vl = vac // 2
+        p = slab_cavity(1, 1, (pml, vl, mir, layer, mir, vac - vl), 100.0, num_bath=nb,
+                        sigma=float(rng.uniform(1e-4, 0.04)), bath_seed=seed + i,
+                        phase_seed=None, src_z=pml + max(1, vl // 2), mon_z=L - pml - 2,
+                        nfreq=4, steps=steps, name=f"batch_small_{i}")
+        if i == 2:
+            z0 = pml + 1
+            p["materials"] = [dict(kind="vacuum", z=(z0, z0 + max(2, vl // 3)), eps_inf=2.25)] + p["materials"]
+        if i == 5:
+            p["energy_box"] = (0, 0)
+        out.append(p)
+    return out
+
+
 # ----------------------------------------------------------------- random states
 def random_state(prob: dict, seed: int, scale: float = 1e-2, with_bath: bool = True) -> dict:
     """Seeded random E, H, P (two levels) and Y (two levels) for every material cell.
