@@ -114,7 +114,12 @@ typedef struct {
 
 typedef struct {
   int32_t precision;    /* 64: FP64 state and arithmetic; 32: FP32 state and arithmetic */
-  int32_t bath_storage; /* 0: bath modes in the state precision; 1: bf16-stored bath modes (precision 32) */
+  int32_t bath_storage; /* 0: bath modes in the state precision.  1 (precision 32 only): every bath
+                         * mode stored as a bf16 pair -- its value Y^{n+1/2} and its increment
+                         * Y^{n+1/2} - Y^{n-1/2} -- updated in place with FP32 arithmetic (8 bytes per
+                         * mode and component per step instead of 12); reading level 1 returns
+                         * value - increment.  fdtdbath_box_energy_noalloc refuses such simulations
+                         * with FDTDBATH_ERR_UNSUPPORTED. */
   void *cuda_stream;    /* cudaStream_t to queue work on; NULL = legacy default stream */
   /* Optional device allocator (e.g. a framework's caching allocator); NULL = cudaMalloc/cudaFree. */
   void *(*alloc)(size_t bytes, void *ctx);
@@ -234,7 +239,7 @@ typedef struct {
   int32_t energy_every;    /* record the cavities' energies every this many steps (0 or 1: each) */
   int64_t energy_capacity; /* records kept per cavity (0: 65536); later records are dropped */
   int32_t cluster_ctas;    /* launch shape: CTAs per cluster (1..16) and threads per CTA (a */
-  int32_t block_threads;   /* multiple of 32, <= 512); 0 = chosen by the autotuner at the first step */
+  int32_t block_threads;   /* multiple of 32, <= 1024); 0 = chosen by the autotuner at the first step */
   int32_t use_graph;       /* nonzero: replay each chunk of steps from a captured CUDA graph */
   int32_t device;          /* CUDA device ordinal */
 } fdtdbath_batch_options;
@@ -247,7 +252,7 @@ int fdtdbath_batch_create(const fdtdbath_cavity *cavities, int32_t ncav, double 
                           const fdtdbath_batch_options *options, fdtdbath_batch **out);
 
 /* Autotuner: time probe_steps steps of every feasible launch shape (CTAs per cluster in
- * {1,2,4,8,16} x threads in {128,256,512} x 1 or 2 CTAs per SM, each packed for this batch) and
+ * {1,2,4,8,16} x threads in {128,256,512,1024} x 1 or 2 CTAs per SM, each packed for this batch) and
  * keep the fastest; the state is restored afterwards.  Outputs (optional) receive the shape and
  * its time per step in milliseconds.  fdtdbath_batch_step runs it with 64 probe steps when no
  * shape has been chosen yet. */

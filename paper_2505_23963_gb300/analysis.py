@@ -40,3 +40,20 @@ def bath_share(trace: np.ndarray, dt_record: float, t_start: float) -> float:
     if not np.any(ok):
         return float("nan")
     return float(np.max(tr[ok, 2] / tot[ok]))
+
+
+def spectral_peaks(freqs: np.ndarray, power: np.ndarray, count: int = 2) -> np.ndarray:
+    """Positions of the `count` largest local maxima of a sampled spectrum, each refined by a
+    3-point parabola through the maximum and its neighbours; sorted by frequency."""
+    f = np.asarray(freqs, dtype=np.float64)
+    p = np.asarray(power, dtype=np.float64)
+    i = np.arange(1, p.size - 1)
+    loc = i[(p[i] >= p[i - 1]) & (p[i] > p[i + 1])]
+    loc = loc[np.argsort(p[loc])[::-1][:count]]
+    out = []
+    for k in loc:
+        y0, y1, y2 = p[k - 1], p[k], p[k + 1]
+        den = y0 - 2.0 * y1 + y2
+        d = 0.5 * (y0 - y2) / den if den != 0 else 0.0
+        out.append(f[k] + d * (f[k + 1] - f[k]))
+    return np.sort(np.array(out))

@@ -69,6 +69,10 @@ struct fdtdbath_sim {
   void* D = nullptr;
   void* Pslot[2] = {nullptr, nullptr};
   void* Yslot[2] = {nullptr, nullptr};
+  // bf16 bath storage (precision 32): Yslot[0] holds the values Y^{n+1/2}, Yslot[1] the increments
+  // Y^{n+1/2} - Y^{n-1/2}, both bf16 and updated in place (no slot swap)
+  bool ybf = false;
+  size_t yesz = 8;
   int pcur = 0;  // literal form: slot holding P^{n+1/2}
   void* coef = nullptr;
   int64_t nmatcell = 0, nybath = 0;
@@ -245,8 +249,8 @@ Step3DParams<T> make_params(fdtdbath_sim* s, int doH, int doE) {
   p.nmatcell = s->nmatcell;
   p.Pa = (T*)s->Pslot[s->pcur];
   p.Pb = (T*)s->Pslot[1 - s->pcur];
-  p.Ya = (T*)s->Yslot[s->pcur];
-  p.Yb = (T*)s->Yslot[1 - s->pcur];
+  p.Ya = (T*)s->Yslot[s->ybf ? 0 : s->pcur];
+  p.Yb = (T*)s->Yslot[s->ybf ? 1 : 1 - s->pcur];
   p.nsrc = (int)s->srcs.size();
   const double t = (double)s->n * s->dt;
   for (size_t q = 0; q < s->srcs.size(); ++q) {
@@ -280,10 +284,12 @@ Step3DParams<T> make_params(fdtdbath_sim* s, int doH, int doE) {
   return p;
 }
 
-int launch_typed(const Step3DParams<float>& p, int nbmax, int ty, int nbx, int nby, int n, cudaStream_t st) {
-  return launch_step3d_f32(p, nbmax, ty, nbx, nby, n, st);
+int launch_typed(const Step3DParams<float>& p, int nbmax, int ty, int nbx, int nby, int n, bool ybf,
+                 cudaStream_t st) {
+  return launch_step3d_f32(p, nbmax, ty, nbx, nby, n, ybf ? 1 : 0, st);
 }
-int launch_typed(const Step3DParams<double>& p, int nbmax, int ty, int nbx, int nby, int n, cudaStream_t st) {
+int launch_typed(const Step3DParams<double>& p, int nbmax, int ty, int nbx, int nby, int n, bool,
+                 cudaStream_t st) {
   return launch_step3d_f64(p, nbmax, ty, nbx, nby, n, st);
 }
 
@@ -291,7 +297,7 @@ template <typename T>
 int launch_chunks(fdtdbath_sim* s, Step3DParams<T> p, int nbmax, int id_off, int n, cudaStream_t st) {
   p.chunk_ids = (const int*)s->chunk_ids + id_off;
   s->launches++;
-  return launch_typed(p, nbmax, s->ty, s->nbx, s->nby, n, st);
+  return launch_typed(p, nbmax, s->ty, s->nbx, s->nby, n, s->ybf, st);
 }
 
 // One step's launches: without a pending E half-step, or without bath chunks, one launch over
@@ -538,6 +544,47 @@ int store(fdtdbath_sim* s, void* dptr, const std::vector<double>& in) {
 
 char* elem_ptr(void* base, int64_t idx, size_t esz) { return (char*)base + idx * (int64_t)esz; }
 
+// bf16 <-> float on the host (round to nearest even; no NaN payloads are produced by the kernels)
+float bf16_to_float(uint16_t h) {
+  uint32_t u = (uint32_t)h << 16;
+  float f;
+  std::memcpy(&f, &u, 4);
+  return f;
+}
+uint16_t float_to_bf16(float f) {
+  uint32_t u;
+  std::memcpy(&u, &f, 4);
+  u += 0x7FFFu + ((u >> 16) & 1u);
+  return (uint16_t)(u >> 16);
+}
+
+// Both levels of one bf16-stored bath mode block of `count` cells: Y^{n+1/2} = value,
+// Y^{n-1/2} = value - increment (FP32 arithmetic, as the kernel forms them).
+int fetch_bf16_levels(fdtdbath_sim* s, int64_t off, int64_t count, std::vector<float>& y0, std::vector<float>& y1) {
+  std::vector<uint16_t> a((size_t)count), b((size_t)count);
+  int rc = d2h(s, a.data(), elem_ptr(s->Yslot[0], off, 2), (size_t)count * 2);
+  if (!rc) rc = d2h(s, b.data(), elem_ptr(s->Yslot[1], off, 2), (size_t)count * 2);
+  if (rc) return rc;
+  y0.resize((size_t)count);
+  y1.resize((size_t)count);
+  for (int64_t i = 0; i < count; ++i) {
+    y0[(size_t)i] = bf16_to_float(a[(size_t)i]);
+    y1[(size_t)i] = y0[(size_t)i] - bf16_to_float(b[(size_t)i]);
+  }
+  return 0;
+}
+
+int store_bf16_levels(fdtdbath_sim* s, int64_t off, const std::vector<float>& y0, const std::vector<float>& y1) {
+  std::vector<uint16_t> a(y0.size()), b(y0.size());
+  for (size_t i = 0; i < y0.size(); ++i) {
+    a[i] = float_to_bf16(y0[i]);
+    b[i] = float_to_bf16(y0[i] - y1[i]);
+  }
+  int rc = h2d(s, elem_ptr(s->Yslot[0], off, 2), a.data(), a.size() * 2);
+  if (!rc) rc = h2d(s, elem_ptr(s->Yslot[1], off, 2), b.data(), b.size() * 2);
+  return rc;
+}
+
 }  // namespace
 
 int fdtdbath_internal_view(fdtdbath_sim* s, SimView* v) {
@@ -560,6 +607,7 @@ int fdtdbath_internal_view(fdtdbath_sim* s, SimView* v) {
   v->H = s->H[s->hcur];
   v->Pa = s->Pslot[s->pcur];
   v->Pb = s->Pslot[1 - s->pcur];
+  if (s->ybf) return fail(s, FDTDBATH_ERR_UNSUPPORTED, "this entry point does not read bf16 bath storage");
   v->Ya = s->Yslot[s->pcur];
   v->Yb = s->Yslot[1 - s->pcur];
   v->nmat = (int)s->mats.size();
@@ -604,8 +652,9 @@ int fdtdbath_create(const fdtdbath_grid* grid, double resolution, double courant
     return fail(nullptr, FDTDBATH_ERR_ARG, "resolution and courant must be positive");
   if (opt->precision != 32 && opt->precision != 64)
     return fail(nullptr, FDTDBATH_ERR_ARG, "precision must be 32 or 64");
-  if (opt->bath_storage != 0)
-    return fail(nullptr, FDTDBATH_ERR_UNSUPPORTED, "bf16 bath storage is not built yet");
+  if (opt->bath_storage != 0 && opt->bath_storage != 1) return fail(nullptr, FDTDBATH_ERR_ARG, "bath_storage must be 0 or 1");
+  if (opt->bath_storage == 1 && opt->precision != 32)
+    return fail(nullptr, FDTDBATH_ERR_ARG, "bf16 bath storage needs precision 32");
   if (nmat < 0 || nmat > kMaxMat || (nmat && !materials))
     return fail(nullptr, FDTDBATH_ERR_ARG, "0 <= nmat <= 8");
   if (nsrc < 0 || nsrc > kMaxSrc || (nsrc && !sources))
@@ -622,6 +671,8 @@ int fdtdbath_create(const fdtdbath_grid* grid, double resolution, double courant
   fdtdbath_sim* s = new fdtdbath_sim();
   s->prec = opt->precision;
   s->esz = s->prec == 64 ? 8 : 4;
+  s->ybf = opt->bath_storage == 1;
+  s->yesz = s->ybf ? 2 : s->esz;
   s->nx = nx;
   s->ny = ny;
   s->nz = nz;
@@ -725,7 +776,7 @@ int fdtdbath_create(const fdtdbath_grid* grid, double resolution, double courant
     s->H[b] = dalloc(s, 3 * s->ncell * esz);
     s->psiH[b] = dalloc(s, 2 * (size_t)(2 * s->npml + 1) * s->plane * esz);
     s->Pslot[b] = dalloc(s, 3 * (size_t)s->nmatcell * esz);
-    s->Yslot[b] = dalloc(s, (size_t)s->nybath * esz);
+    s->Yslot[b] = dalloc(s, (size_t)s->nybath * s->yesz);
     if (!s->E[b] || !s->H[b] || !s->psiH[b] || !s->Pslot[b] || !s->Yslot[b])
       return bail(FDTDBATH_ERR_OOM, "device allocation failed");
   }
@@ -758,7 +809,7 @@ int fdtdbath_create(const fdtdbath_grid* grid, double resolution, double courant
       cudaEventCreateWithFlags(&s->ev_join, cudaEventDisableTiming) != cudaSuccess)
     return bail(FDTDBATH_ERR_CUDA, "stream/event creation failed");
   // 1D path: one cluster of up to 8 CTAs of 256 threads
-  s->path1d = (nx == 1 && ny == 1 && nsrc <= 1 && nmon <= 1 &&
+  s->path1d = (nx == 1 && ny == 1 && nsrc <= 1 && nmon <= 1 && !s->ybf &&
                 nz <= (int64_t)kCav1DMaxCluster * kCav1DThreads);
   if (s->path1d) {
     // FP64 bath arithmetic is slow on this part: spread the cavity over the largest cluster
@@ -921,6 +972,14 @@ int fdtdbath_read_fields(fdtdbath_sim* s, int32_t field, void* dst, size_t dst_b
       } else {
         if (f.mode >= m.nb) continue;
         const int64_t off = m.ybase + ((int64_t)f.comp * m.nb + f.mode) * m.ncell;
+        if (s->ybf) {
+          std::vector<float> y0, y1;
+          rc = fetch_bf16_levels(s, off, m.ncell, y0, y1);
+          if (rc) return rc;
+          const std::vector<float>& y = f.level == 0 ? y0 : y1;
+          for (int64_t r = 0; r < m.ncell; ++r) full[(size_t)(m.zlo * s->plane + r)] = y[(size_t)r];
+          continue;
+        }
         pa = elem_ptr(s->Yslot[f.level == 0 ? s->pcur : 1 - s->pcur], off, s->esz);
       }
       rc = fetch(s, pa, m.ncell, a);
@@ -1000,6 +1059,17 @@ int fdtdbath_write_fields(fdtdbath_sim* s, int32_t field, const void* src, size_
     } else {
       if (f.mode >= m.nb) continue;
       const int64_t off = m.ybase + ((int64_t)f.comp * m.nb + f.mode) * m.ncell;
+      if (s->ybf) {
+        // replace one level, keep the other, store the (value, increment) pair again
+        std::vector<float> y0, y1;
+        rc = fetch_bf16_levels(s, off, m.ncell, y0, y1);
+        if (rc) return rc;
+        std::vector<float>& y = f.level == 0 ? y0 : y1;
+        for (int64_t r = 0; r < m.ncell; ++r) y[(size_t)r] = (float)in[(size_t)(m.zlo * s->plane + r)];
+        rc = store_bf16_levels(s, off, y0, y1);
+        if (rc) return rc;
+        continue;
+      }
       pa = elem_ptr(s->Yslot[f.level == 0 ? s->pcur : 1 - s->pcur], off, s->esz);
     }
     std::vector<double> v(in.begin() + m.zlo * s->plane, in.begin() + m.zlo * s->plane + m.ncell);

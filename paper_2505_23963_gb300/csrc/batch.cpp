@@ -701,7 +701,7 @@ int autotune(fdtdbath_batch* b, int probe_steps) {
   const char* ev = std::getenv("FDTDBATH_TUNE_VERBOSE");   // print every candidate's time
   const bool verbose = ev && *ev && *ev != '0';
   const int Cs[] = {1, 2, 4, 8, 16};
-  const int Ts[] = {128, 256, 512};
+  const int Ts[] = {128, 256, 512, 1024};
   for (int C : Cs)
     for (int T : Ts)
       for (int k = 1; k <= 2; ++k) {
@@ -805,7 +805,7 @@ int fdtdbath_batch_create(const fdtdbath_cavity* cavities, int32_t ncav, double 
   if (opt->energy_every < 0) return bfail(nullptr, FDTDBATH_ERR_ARG, "energy_every must be >= 0");
   if (opt->cluster_ctas < 0 || opt->cluster_ctas > kBatchMaxCluster || opt->block_threads < 0 ||
       opt->block_threads > kBatchMaxThreads || opt->block_threads % 32)
-    return bfail(nullptr, FDTDBATH_ERR_ARG, "bad launch shape (cluster 0..16 CTAs, threads a multiple of 32 up to 512)");
+    return bfail(nullptr, FDTDBATH_ERR_ARG, "bad launch shape (cluster 0..16 CTAs, threads a multiple of 32 up to 1024)");
   if ((opt->alloc == nullptr) != (opt->free == nullptr))
     return bfail(nullptr, FDTDBATH_ERR_ARG, "alloc and free must both be set or both NULL");
   fdtdbath_batch* b = new fdtdbath_batch();

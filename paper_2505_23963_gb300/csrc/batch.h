@@ -27,7 +27,7 @@ namespace fdtdbath {
 constexpr int kBatchMaxSeg = 8;      // segments per CTA
 constexpr int kBatchMaxRun = 64;     // runs per CTA
 constexpr int kBatchMaxMat = 16;     // material slots per CTA
-constexpr int kBatchMaxThreads = 512;
+constexpr int kBatchMaxThreads = 1024;
 constexpr int kBatchMaxWarps = kBatchMaxThreads / 32;
 constexpr int kBatchMaxCluster = 16;
 constexpr int kBatchChunk = 32;     // steps between the kernel's global-memory exchanges

@@ -7,19 +7,30 @@
 // two levels of P_x (and D_x on the FP64 path), CPML memories and the two levels of every bath
 // mode in shared memory; the canonical arrays are touched only at the start and the end.
 //
-// One step: the D/E half-step with the soft source, the polarization and bath updates of every
-// run (typed: vacuum, Lorentz/Drude, Lorentz-Bath with N_b a template bound); a barrier; the H
-// half-step; a barrier.  The barrier is the cluster barrier when the cluster has more than one CTA:
-// a cell at a CTA boundary reads its neighbour's field from the other CTA's shared memory.
-// Two-level recursions swap their level slots by step parity instead of copying.
+// One step, two phases separated by barriers (the cluster barrier when the cluster has more
+// than one CTA: a cell at a CTA boundary reads its neighbour's field from the other CTA's shared
+// memory):
+//   phase A  the D/E half-step of every cell with the soft source; Lorentz / Drude polarization
+//            updates (Eq. Pz_1D_Lorentz), which are per cell and cheap;
+//   phase B  the H half-step of every cell and, for Lorentz-Bath cells, the polarization and bath
+//            updates (Eq. Pz_update-LB, Yzj_finite_difference).  H does not read P, so the bath
+//            work shares the phase with H and needs no barrier of its own.
+// Cells are dealt to threads round-robin over the CTA's whole range (cell l to thread l mod T),
+// so per-run remainders do not pile up on the first threads.  A Lorentz-Bath cell is updated by
+// a group of G lanes (G = N_b rounded up to a power of two, <= 32), one bath mode per lane: each
+// lane keeps its mode's coefficients in registers for the whole run, the bath sum
+// sum_j k_j (...) is a butterfly reduction within the group, and every lane of the group
+// evaluates the (identical) P update.  Bath state is laid out [level][cell][mode] so a group
+// reads consecutive words.  Two-level recursions swap level slots by step parity.
 //
 // Energy records (every `every` steps): per segment of the CTA, the box sums of eps E^2, of the
 // oscillator energy rho/dt^2 ((P^{n+3/2}-P^{n+1/2})^2 + (w0 dt)^2 P^2), of the bath energy and of
 // H^2.  A thread accumulates in the state precision, a warp reduces by shuffles in that precision,
 // and the warp partials are summed in FP64 in a fixed order.
 //
-// The source amplitude of each cavity comes from a host-computed table, staged into shared
-// memory a chunk of steps at a time.
+// The step loop runs in chunks of kBatchChunk steps and touches no global memory inside a chunk:
+// the chunk's source amplitudes (a host-computed table) are staged into shared memory before it,
+// its energy records are buffered in shared memory and written out after it.
 #pragma once
 
 #include <cooperative_groups.h>
@@ -47,15 +58,15 @@ struct BatchCtx {
   int par;         // slot of P^{n+1/2} / Y^{n+1/2}
 };
 
-// D/E half-step of one run plus, for material runs, the polarization and bath updates.
-// KIND: kRunVacuum, kRunOsc, kRunBath; NBC: compile-time bound on the run's bath modes.
-template <typename T, bool INC, int KIND, int NBC>
-__device__ __forceinline__ void batch_e_run(const BatchRun& R, const BatchSeg& G, const MatK<T>* smat,
-                                            const BatchCtx<T>& c, T J, bool en, T& a0, T& a1, T& a2) {
-  constexpr int NBA = NBC > 0 ? NBC : 1;
+// l: this thread's next cell (cell l belongs to thread l mod T); runs are contiguous, so the
+// cursor left by one run is the thread's first cell of the next.
+template <typename T, bool INC, int KIND>
+__device__ __forceinline__ void batch_phase_a(const BatchRun& R, const BatchSeg& G, const MatK<T>* smat,
+                                              const BatchCtx<T>& c, T J, bool en, T& a0, T& a1, int& l) {
   const int len = R.l1 - R.l0;
   const T S = c.S, dt = c.dt;
-  for (int l = R.l0 + (int)threadIdx.x; l < R.l1; l += (int)blockDim.x) {
+  const int nt = (int)blockDim.x;
+  for (; l < R.l1; l += nt) {
     const int i = l - R.l0;
     const T h = c.sH[l];
     T hm;
@@ -93,81 +104,33 @@ __device__ __forceinline__ void batch_e_run(const BatchRun& R, const BatchSeg& G
         if (src) inc = inc + dt * J;
         e = e + (inc - (Pa - Pb)) * M.inv_eps;
       }
-      T bsum = T(0);
-      T Y[NBA], Ym[NBA];
-      const int nb = KIND == kRunBath ? R.nb : 0;
-      T* Yc = c.sm + R.y0 + c.par * nb * len + i;           // Y_j^{n+1/2} at Yc[j*len]
-      T* Yo = c.sm + R.y0 + (c.par ^ 1) * nb * len + i;     // Y_j^{n-1/2}, receives Y_j^{n+3/2}
-      const T* cfm = c.coef + M.coef_off * kCoefStride;
-      if (KIND == kRunBath) {
-#pragma unroll
-        for (int j = 0; j < NBA; ++j) {
-          Y[j] = T(0);
-          Ym[j] = T(0);
-          if (j < nb) {
-            Y[j] = Yc[j * len];
-            Ym[j] = Yo[j * len];
-            const T* cf = cfm + j * kCoefStride;
-            if (!INC) {
-              bsum = bsum + cf[0] * (cf[1] * Y[j] + cf[2] * Ym[j]);   // k_j (a_j Y^n + b_j Y^{n-1})
-            } else {
-              const T Vj = Y[j] - Ym[j];
-              bsum = bsum + (cf[0] * Y[j] + cf[1] * Vj);               // k_j ((a_j+b_j) Y - b_j V)
-            }
-          }
+      if (KIND == kRunOsc) {
+        T Pn, Vn;
+        if (!INC) {
+          const T num = M.cE * e - M.c1m * Pa - M.c2 * Pb;
+          Pn = M.inv_A * num;
+          Vn = Pn - Pa;
+        } else {
+          const T num = M.cE * e - M.W * Pa + M.c2 * (Pa - Pb);
+          Vn = num * M.inv_A;
+          Pn = Pa + Vn;
         }
+        Po[i] = Pn;
+        if (en && R.inbox) a1 += M.rho_idt2 * (Vn * Vn + M.w0r2dt2 * Pn * Pn);
       }
-      T Pn, Vn, V0;
-      if (!INC) {
-        T num = M.cE * e - M.c1m * Pa - M.c2 * Pb;
-        if (KIND == kRunBath) num = num - T(0.5) * dt * bsum;
-        Pn = M.inv_A * num;
-        Vn = Pn - Pa;
-        V0 = Pa - Pb;
-      } else {
-        V0 = Pa - Pb;
-        T num = M.cE * e - M.W * Pa + M.c2 * V0;
-        if (KIND == kRunBath) num = num - T(0.5) * dt * bsum;
-        Vn = num * M.inv_A;
-        Pn = Pa + Vn;
-      }
-      Po[i] = Pn;
-      T ub = T(0);
-      if (KIND == kRunBath) {
-        const T dP = Vn + V0;
-#pragma unroll
-        for (int j = 0; j < NBA; ++j) {
-          if (j < nb) {
-            const T* cf = cfm + j * kCoefStride;
-            T Yn, Vy;
-            if (!INC) {
-              Yn = cf[1] * Y[j] + cf[3] * Ym[j] + cf[4] * (Pn - Pb);
-              Vy = Yn - Y[j];
-            } else {
-              Vy = cf[2] * Y[j] + cf[3] * (Y[j] - Ym[j]) + cf[4] * dP;
-              Yn = Y[j] + Vy;
-            }
-            Yo[j * len] = Yn;
-            if (en) ub += Vy * Vy + cf[5] * Yn * Yn;
-          }
-        }
-      }
-      if (en && R.inbox) {
-        a0 += M.eps * (e * e);
-        a1 += M.rho_idt2 * (Vn * Vn + M.w0r2dt2 * Pn * Pn);
-        a2 += M.rho_idt2 * ub;
-      }
+      if (en && R.inbox) a0 += M.eps * (e * e);
     }
     c.sE[l] = e;
   }
 }
 
-// H half-step of one run.
+// Phase B, H half-step of one run.
 template <typename T>
-__device__ __forceinline__ void batch_h_run(const BatchRun& R, const BatchSeg& G, const BatchCtx<T>& c,
-                                            bool en, T& a3) {
+__device__ __forceinline__ void batch_phase_h(const BatchRun& R, const BatchSeg& G, const BatchCtx<T>& c,
+                                              bool en, T& a3, int& l) {
   const T S = c.S;
-  for (int l = R.l0 + (int)threadIdx.x; l < R.l1; l += (int)blockDim.x) {
+  const int nt = (int)blockDim.x;
+  for (; l < R.l1; l += nt) {
     const T e = c.sE[l];
     T ep;
     if (l + 1 < G.l1) ep = c.sE[l + 1];
@@ -187,6 +150,86 @@ __device__ __forceinline__ void batch_h_run(const BatchRun& R, const BatchSeg& G
   }
 }
 
+// Phase B, Lorentz-Bath polarization and bath update of one run, GS lanes per cell.
+template <typename T, bool INC, int GS>
+__device__ __forceinline__ void batch_phase_bath(const BatchRun& R, const MatK<T>* smat, const BatchCtx<T>& c,
+                                                 bool en, T& a1, T& a2) {
+  const int len = R.l1 - R.l0, nb = R.nb;
+  const int lane = (int)threadIdx.x & 31, warp = (int)threadIdx.x >> 5, nwarp = (int)blockDim.x >> 5;
+  constexpr int CPW = 32 / GS;   // cells per warp pass
+  const int j = lane % GS;       // this lane's bath mode
+  const bool mode = j < nb;
+  const MatK<T>& M = smat[R.mslot];
+  // this lane's coefficient row, kept in registers for the run
+  T cf0 = T(0), cf1 = T(0), cf2 = T(0), cf3 = T(0), cf4 = T(0), cf5 = T(0);
+  if (mode) {
+    const T* cf = c.coef + (M.coef_off + j) * kCoefStride;
+    cf0 = cf[0];
+    cf1 = cf[1];
+    cf2 = cf[2];
+    cf3 = cf[3];
+    cf4 = cf[4];
+    cf5 = cf[5];
+  }
+  const T dt = c.dt;
+  T* Pc = c.sm + R.p0 + c.par * len;
+  T* Po = c.sm + R.p0 + (c.par ^ 1) * len;
+  T* Yc = c.sm + R.y0 + c.par * len * nb;           // Y^{n+1/2}   [cell][mode]
+  T* Yo = c.sm + R.y0 + (c.par ^ 1) * len * nb;     // Y^{n-1/2}, receives Y^{n+3/2}
+  for (int g = warp; g * CPW < len; g += nwarp) {
+    const int i = g * CPW + lane / GS;
+    const bool cell = i < len;
+    const bool act = cell && mode;
+    T e = T(0), Pa = T(0), Pb = T(0), y = T(0), ym = T(0);
+    if (cell) {
+      e = c.sE[R.l0 + i];
+      Pa = Pc[i];
+      Pb = Po[i];
+    }
+    if (act) {
+      y = Yc[i * nb + j];
+      ym = Yo[i * nb + j];
+    }
+    // bath sum over the group's lanes
+    T term;
+    if (!INC) term = cf0 * (cf1 * y + cf2 * ym);      // k_j (a_j Y^n + b_j Y^{n-1})
+    else term = cf0 * y + cf1 * (y - ym);             // k_j ((a_j+b_j) Y - b_j V)
+#pragma unroll
+    for (int o = GS / 2; o > 0; o >>= 1) term += __shfl_xor_sync(0xffffffffu, term, o, GS);
+    const T bsum = term;
+    T Pn, Vn, V0;
+    if (!INC) {
+      T num = M.cE * e - M.c1m * Pa - M.c2 * Pb;
+      num = num - T(0.5) * dt * bsum;
+      Pn = M.inv_A * num;
+      Vn = Pn - Pa;
+      V0 = Pa - Pb;
+    } else {
+      V0 = Pa - Pb;
+      T num = M.cE * e - M.W * Pa + M.c2 * V0;
+      num = num - T(0.5) * dt * bsum;
+      Vn = num * M.inv_A;
+      Pn = Pa + Vn;
+    }
+    if (act) {
+      T Yn, Vy;
+      if (!INC) {
+        Yn = cf1 * y + cf3 * ym + cf4 * (Pn - Pb);
+        Vy = Yn - y;
+      } else {
+        Vy = cf2 * y + cf3 * (y - ym) + cf4 * (Vn + V0);
+        Yn = y + Vy;
+      }
+      Yo[i * nb + j] = Yn;
+      if (en && R.inbox) a2 += M.rho_idt2 * (Vy * Vy + cf5 * Yn * Yn);
+    }
+    if (cell && j == 0) {
+      Po[i] = Pn;
+      if (en && R.inbox) a1 += M.rho_idt2 * (Vn * Vn + M.w0r2dt2 * Pn * Pn);
+    }
+  }
+}
+
 template <typename T>
 __device__ __forceinline__ T warp_sum(T v) {
 #pragma unroll
@@ -203,10 +246,10 @@ __global__ void __launch_bounds__(kBatchMaxThreads) batch1d_kernel(const BatchPa
   __shared__ BatchSeg sseg[kBatchMaxSeg];
   __shared__ BatchRun srun[kBatchMaxRun];
   __shared__ MatK<T> smat[kBatchMaxMat];
-  __shared__ double sredE[kBatchMaxSeg][kBatchMaxWarps][3];
-  __shared__ double sredH[kBatchMaxSeg][kBatchMaxWarps];
-  __shared__ T sJ[kBatchChunk][kBatchMaxSeg];          // source amplitude per step of the chunk
-  __shared__ double srec[kBatchChunk][kBatchMaxSeg][4]; // energy records of the chunk
+  __shared__ double sredA[kBatchMaxSeg][kBatchMaxWarps][2];  // per warp: eps E^2, Lorentz/Drude P energy
+  __shared__ double sredB[kBatchMaxSeg][kBatchMaxWarps][3];  // per warp: bath-layer P energy, bath, H^2
+  __shared__ T sJ[kBatchChunk][kBatchMaxSeg];                // source amplitude per step of the chunk
+  __shared__ double srec[kBatchChunk][kBatchMaxSeg][4];      // energy records of the chunk
   __shared__ int scoef0[kBatchMaxMat];
 
   const int C = (int)cluster.num_blocks();
@@ -289,23 +332,19 @@ __global__ void __launch_bounds__(kBatchMaxThreads) batch1d_kernel(const BatchPa
         c.sm[R.p0 + len + i] = p.PM[g];
         if (!INC) c.sm[R.p0 + 2 * len + i] = p.D[g];
       }
-      if (R.kind == kRunBath) {
-        const MatK<T>& M = smat[R.mslot];
-        const int z = G.z0 + (l - G.l0);
-        const int64_t yg = M.ybase + (z - M.zlo);
-        for (int j = 0; j < R.nb; ++j) {
-          c.sm[R.y0 + j * len + i] = p.Y0[yg + (int64_t)j * M.ncell];
-          c.sm[R.y0 + (R.nb + j) * len + i] = p.Y1[yg + (int64_t)j * M.ncell];
-        }
+    }
+    if (R.kind == kRunBath) {
+      // bath block [level][cell][mode] from the canonical [mode][cell] arrays
+      const MatK<T>& M = smat[R.mslot];
+      const int64_t yg = M.ybase + (G.z0 + (R.l0 - G.l0) - M.zlo);
+      for (int q = t; q < len * R.nb; q += nt) {
+        const int j = q / len, i = q - j * len;
+        c.sm[R.y0 + i * R.nb + j] = p.Y0[yg + (int64_t)j * M.ncell + i];
+        c.sm[R.y0 + (len + i) * R.nb + j] = p.Y1[yg + (int64_t)j * M.ncell + i];
       }
     }
   }
 
-  // The step loop runs in chunks of kBatchChunk steps.  Inside a chunk it touches no global
-  // memory: the chunk's source amplitudes are staged into shared memory before it and its energy
-  // records are buffered in shared memory and written out after it.  (A cluster barrier has
-  // release semantics: a global access still in flight in any thread would hold the barrier for
-  // its whole latency, every step.)
   const int64_t step0 = *p.ctr;
   int ephase = (int)(step0 % p.every);
   int ering = (int)((step0 / p.every) % p.ring_cap);
@@ -325,91 +364,97 @@ __global__ void __launch_bounds__(kBatchMaxThreads) batch1d_kernel(const BatchPa
     bool en_prev = false;
     for (int k = 0; k < m; ++k) {
       const bool en = p.energy_on && ephase == 0;
-      // H-half sums of the previous step, complete since the last barrier
-      if (en_prev && t < nseg) {
+      // phase-B sums of the previous step, complete since the last barrier
+      if (en_prev && t < 3 * nseg) {
+        const int sg = t / 3, q = t - 3 * sg;
         double v = 0.0;
-        for (int w = 0; w < nwarp; ++w) v += sredH[t][w];
-        srec[nrec - 1][t][3] = v;
+        for (int w = 0; w < nwarp; ++w) v += sredB[sg][w][q];
+        if (q == 0) srec[nrec - 1][sg][1] += v;
+        else srec[nrec - 1][sg][q + 1] = v;
       }
-      // ---------------- D/E half-step, polarization and bath ----------------
+      // ---------------- phase A: D/E half-step, Lorentz / Drude polarization ----------------
       {
-        T a0 = T(0), a1 = T(0), a2 = T(0);
-        int cur = -1;
+        T a0 = T(0), a1 = T(0);
+        int cur = -1, l = t;
         for (int r = 0; r < nrun; ++r) {
           const BatchRun& R = srun[r];
           if (en && R.seg != cur) {
             if (cur >= 0) {
               a0 = warp_sum(a0);
               a1 = warp_sum(a1);
-              a2 = warp_sum(a2);
               if (lane == 0) {
-                sredE[cur][warp][0] = (double)a0;
-                sredE[cur][warp][1] = (double)a1;
-                sredE[cur][warp][2] = (double)a2;
+                sredA[cur][warp][0] = (double)a0;
+                sredA[cur][warp][1] = (double)a1;
               }
             }
             cur = R.seg;
-            a0 = a1 = a2 = T(0);
+            a0 = a1 = T(0);
           }
           const BatchSeg& G = sseg[R.seg];
           const T J = sJ[k][R.seg];
-          if (R.kind == kRunVacuum) {
-            batch_e_run<T, INC, kRunVacuum, 0>(R, G, smat, c, J, en, a0, a1, a2);
-          } else if (R.kind == kRunOsc) {
-            batch_e_run<T, INC, kRunOsc, 0>(R, G, smat, c, J, en, a0, a1, a2);
-          } else if (R.nb <= 4) {
-            batch_e_run<T, INC, kRunBath, 4>(R, G, smat, c, J, en, a0, a1, a2);
-          } else if (R.nb <= 8) {
-            batch_e_run<T, INC, kRunBath, 8>(R, G, smat, c, J, en, a0, a1, a2);
-          } else if (R.nb <= 16) {
-            batch_e_run<T, INC, kRunBath, 16>(R, G, smat, c, J, en, a0, a1, a2);
-          } else {
-            batch_e_run<T, INC, kRunBath, 32>(R, G, smat, c, J, en, a0, a1, a2);
-          }
+          if (R.kind == kRunVacuum) batch_phase_a<T, INC, kRunVacuum>(R, G, smat, c, J, en, a0, a1, l);
+          else if (R.kind == kRunOsc) batch_phase_a<T, INC, kRunOsc>(R, G, smat, c, J, en, a0, a1, l);
+          else batch_phase_a<T, INC, kRunBath>(R, G, smat, c, J, en, a0, a1, l);
         }
         if (en && cur >= 0) {
           a0 = warp_sum(a0);
           a1 = warp_sum(a1);
-          a2 = warp_sum(a2);
           if (lane == 0) {
-            sredE[cur][warp][0] = (double)a0;
-            sredE[cur][warp][1] = (double)a1;
-            sredE[cur][warp][2] = (double)a2;
+            sredA[cur][warp][0] = (double)a0;
+            sredA[cur][warp][1] = (double)a1;
+          }
+        }
+      }
+      if (C > 1) cluster.sync();
+      else __syncthreads();
+      if (en && t < 2 * nseg) {
+        const int sg = t >> 1, q = t & 1;
+        double v = 0.0;
+        for (int w = 0; w < nwarp; ++w) v += sredA[sg][w][q];
+        srec[nrec][sg][q] = v;
+      }
+      // ---------------- phase B: H half-step, Lorentz-Bath polarization and bath ----------------
+      {
+        T a1 = T(0), a2 = T(0), a3 = T(0);
+        int cur = -1, l = t;
+        for (int r = 0; r < nrun; ++r) {
+          const BatchRun& R = srun[r];
+          if (en && R.seg != cur) {
+            if (cur >= 0) {
+              a1 = warp_sum(a1);
+              a2 = warp_sum(a2);
+              a3 = warp_sum(a3);
+              if (lane == 0) {
+                sredB[cur][warp][0] = (double)a1;
+                sredB[cur][warp][1] = (double)a2;
+                sredB[cur][warp][2] = (double)a3;
+              }
+            }
+            cur = R.seg;
+            a1 = a2 = a3 = T(0);
+          }
+          batch_phase_h<T>(R, sseg[R.seg], c, en, a3, l);
+          if (R.kind == kRunBath) {
+            if (R.nb <= 4) batch_phase_bath<T, INC, 4>(R, smat, c, en, a1, a2);
+            else if (R.nb <= 8) batch_phase_bath<T, INC, 8>(R, smat, c, en, a1, a2);
+            else if (R.nb <= 16) batch_phase_bath<T, INC, 16>(R, smat, c, en, a1, a2);
+            else batch_phase_bath<T, INC, 32>(R, smat, c, en, a1, a2);
+          }
+        }
+        if (en && cur >= 0) {
+          a1 = warp_sum(a1);
+          a2 = warp_sum(a2);
+          a3 = warp_sum(a3);
+          if (lane == 0) {
+            sredB[cur][warp][0] = (double)a1;
+            sredB[cur][warp][1] = (double)a2;
+            sredB[cur][warp][2] = (double)a3;
           }
         }
       }
       if (C > 1) cluster.sync();
       else __syncthreads();
       c.par ^= 1;   // P^{n+3/2} / Y^{n+3/2} now sit in the other slot
-      // ---------------- H half-step ----------------
-      if (en && t < 3 * nseg) {
-        const int sg = t / 3, q = t - 3 * sg;
-        double v = 0.0;
-        for (int w = 0; w < nwarp; ++w) v += sredE[sg][w][q];
-        srec[nrec][sg][q] = v;
-      }
-      {
-        T a3 = T(0);
-        int cur = -1;
-        for (int r = 0; r < nrun; ++r) {
-          const BatchRun& R = srun[r];
-          if (en && R.seg != cur) {
-            if (cur >= 0) {
-              a3 = warp_sum(a3);
-              if (lane == 0) sredH[cur][warp] = (double)a3;
-            }
-            cur = R.seg;
-            a3 = T(0);
-          }
-          batch_h_run<T>(R, sseg[R.seg], c, en, a3);
-        }
-        if (en && cur >= 0) {
-          a3 = warp_sum(a3);
-          if (lane == 0) sredH[cur][warp] = (double)a3;
-        }
-      }
-      if (C > 1) cluster.sync();
-      else __syncthreads();
       if (en) ++nrec;
       en_prev = en;
       if (++ephase == p.every) {
@@ -417,11 +462,13 @@ __global__ void __launch_bounds__(kBatchMaxThreads) batch1d_kernel(const BatchPa
         if (++ering == p.ring_cap) ering = 0;
       }
     }
-    // the chunk's last H-half sums, then its records out to the ring
-    if (en_prev && t < nseg) {
+    // the chunk's last phase-B sums, then its records out to the ring
+    if (en_prev && t < 3 * nseg) {
+      const int sg = t / 3, q = t - 3 * sg;
       double v = 0.0;
-      for (int w = 0; w < nwarp; ++w) v += sredH[t][w];
-      srec[nrec - 1][t][3] = v;
+      for (int w = 0; w < nwarp; ++w) v += sredB[sg][w][q];
+      if (q == 0) srec[nrec - 1][sg][1] += v;
+      else srec[nrec - 1][sg][q + 1] = v;
     }
     __syncthreads();
     for (int i = t; i < nrec * nseg * 4; i += nt) {
@@ -451,14 +498,14 @@ __global__ void __launch_bounds__(kBatchMaxThreads) batch1d_kernel(const BatchPa
         p.PM[g] = c.sm[R.p0 + (c.par ^ 1) * len + i];
         if (!INC) p.D[g] = c.sm[R.p0 + 2 * len + i];
       }
-      if (R.kind == kRunBath) {
-        const MatK<T>& M = smat[R.mslot];
-        const int z = G.z0 + (l - G.l0);
-        const int64_t yg = M.ybase + (z - M.zlo);
-        for (int j = 0; j < R.nb; ++j) {
-          p.Y0[yg + (int64_t)j * M.ncell] = c.sm[R.y0 + (c.par * R.nb + j) * len + i];
-          p.Y1[yg + (int64_t)j * M.ncell] = c.sm[R.y0 + ((c.par ^ 1) * R.nb + j) * len + i];
-        }
+    }
+    if (R.kind == kRunBath) {
+      const MatK<T>& M = smat[R.mslot];
+      const int64_t yg = M.ybase + (G.z0 + (R.l0 - G.l0) - M.zlo);
+      for (int q = t; q < len * R.nb; q += nt) {
+        const int j = q / len, i = q - j * len;
+        p.Y0[yg + (int64_t)j * M.ncell + i] = c.sm[R.y0 + (c.par * len + i) * R.nb + j];
+        p.Y1[yg + (int64_t)j * M.ncell + i] = c.sm[R.y0 + ((c.par ^ 1) * len + i) * R.nb + j];
       }
     }
   }

@@ -142,7 +142,7 @@ int launch_cavity1d_f64(const Cav1DParams<double>& p, int nbmax, int cluster, vo
 
 // Launchers (defined in step3d_f32.cu / step3d_f64.cu).
 int launch_step3d_f32(const Step3DParams<float>& p, int nbmax, int ty, int nbx, int nby,
-                      int nchunks, void* stream);
+                      int nchunks, int bath_bf16, void* stream);
 int launch_step3d_f64(const Step3DParams<double>& p, int nbmax, int ty, int nbx, int nby,
                       int nchunks, void* stream);
 

@@ -26,6 +26,7 @@
 //     representing 2 - w^2 dt^2, whose FP32 rounding would shift every oscillator frequency.
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include "internal.h"
@@ -149,15 +150,32 @@ struct Tile {
   static constexpr int FH = HY * HX;                 // H frame elements per component
 };
 
+// Bath-mode storage: the state precision, or bf16 (value Y and increment V = Y^n - Y^{n-1} of
+// every mode, both bf16, updated in place; the arithmetic stays FP32).
+template <typename T, bool YB>
+struct BathStore {
+  using S = T;
+  static __device__ __forceinline__ T load(const S* p) { return *p; }
+  static __device__ __forceinline__ void put(S* p, T v) { *p = v; }
+};
+template <>
+struct BathStore<float, true> {
+  using S = __nv_bfloat16;
+  static __device__ __forceinline__ float load(const S* p) { return __bfloat162float(*p); }
+  static __device__ __forceinline__ void put(S* p, float v) { *p = __float2bfloat16_rn(v); }
+};
+
 template <typename T, int NBMAX, int TY>
 struct StepBounds {
   static constexpr int threads = kTX * TY;
   static constexpr int min_blocks = TY == 8 ? (NBMAX == 0 ? (sizeof(T) == 4 ? 4 : 2) : ((sizeof(T) == 8 && NBMAX >= 16) ? 1 : 2)) : 8;
 };
 
-template <typename T, bool INC, int NBMAX, int TY>
+template <typename T, bool INC, int NBMAX, int TY, bool YB = false>
 __global__ void __launch_bounds__(StepBounds<T, NBMAX, TY>::threads, StepBounds<T, NBMAX, TY>::min_blocks)
 step3d_kernel(const Step3DParams<T> p) {
+  using YS = BathStore<T, YB>;   // bath-mode storage (YB: bf16 value / increment pairs)
+  using YT = typename YS::S;
   using G = Tile<TY>;
   constexpr int TX = G::TX, FX = G::FX, HX = G::HX, NTHR = G::NTHR, FE = G::FE, FH = G::FH;
   constexpr int FY = G::FY, HY = G::HY;
@@ -426,15 +444,15 @@ step3d_kernel(const Step3DParams<T> p) {
         if (!INC) rD[c] = p.D[c * nmc + r];
       }
       if (NBP > 0 && M.kind == kLorentzBath) {
-        const T* ya = p.Ya + yb0;
-        const T* yb = p.Yb + yb0;
+        const YT* ya = reinterpret_cast<const YT*>(p.Ya) + yb0;
+        const YT* yb = reinterpret_cast<const YT*>(p.Yb) + yb0;
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
 #pragma unroll
           for (int jj = 0; jj < (NBP > 0 ? NBP : 1); ++jj) {
             if (jj < M.nb) {
-              rY[c][jj] = ya[(c * M.nb + jj) * mstride];
-              rV[c][jj] = yb[(c * M.nb + jj) * mstride];
+              rY[c][jj] = YS::load(ya + (c * M.nb + jj) * mstride);
+              rV[c][jj] = YS::load(yb + (c * M.nb + jj) * mstride);
             }
           }
         }
@@ -547,8 +565,8 @@ step3d_kernel(const Step3DParams<T> p) {
           const MatK<T>& M = p.mat[mi];
           const bool bath = (M.kind == kLorentzBath) && (NBMAX > 0);
           const T* cfm = sCoef + M.coef_off * kCoefStride;
-          T* const ya = p.Ya + yb0;
-          T* const yb = p.Yb + yb0;
+          YT* const ya = reinterpret_cast<YT*>(p.Ya) + yb0;
+          YT* const yb = reinterpret_cast<YT*>(p.Yb) + yb0;
 #pragma unroll
           for (int c = 0; c < 3; ++c) {
             T E;
@@ -581,15 +599,15 @@ step3d_kernel(const Step3DParams<T> p) {
                   Yl[jj] = rY[c][jj < NBP ? jj : 0];
                   Vl[jj] = rV[c][jj < NBP ? jj : 0];
                 } else {
-                  Yl[jj] = ya[yc + jj * mstride];
-                  Vl[jj] = yb[yc + jj * mstride];
+                  Yl[jj] = YS::load(ya + yc + jj * mstride);
+                  Vl[jj] = YS::load(yb + yc + jj * mstride);
                 }
                 T cf[6];
                 load_coef6(cfm + jj * kCoefStride, cf);
                 if (!INC) {
                   bsum = bsum + cf[0] * (cf[1] * Yl[jj] + cf[2] * Vl[jj]);   // k_j (a_j Y^n + b_j Y^{n-1})
                 } else {
-                  Vl[jj] = Yl[jj] - Vl[jj];                                  // V_j = Y^n - Y^{n-1}
+                  if (!YB) Vl[jj] = Yl[jj] - Vl[jj];                         // V_j = Y^n - Y^{n-1}
                   bsum = bsum + (cf[0] * Yl[jj] + cf[1] * Vl[jj]);           // k_j ((a_j+b_j) Y - b_j V)
                 }
               }
@@ -630,7 +648,12 @@ step3d_kernel(const Step3DParams<T> p) {
                   Vy = cf[2] * Yl[jj] + cf[3] * Vl[jj] + cf[4] * dP;
                   Ynew = Yl[jj] + Vy;
                 }
-                yb[yc + jj * mstride] = Ynew;   // overwrites Y^{n-1}
+                if (YB) {
+                  YS::put(ya + yc + jj * mstride, Ynew);   // in place: Y^{n+1} and V^{n+1}
+                  YS::put(yb + yc + jj * mstride, Vy);
+                } else {
+                  YS::put(yb + yc + jj * mstride, Ynew);   // overwrites Y^{n-1}
+                }
                 if (p.eE_on) ub += Vy * Vy + cf[5] * Ynew * Ynew;   // (w_j dt)^2 Y^2
               }
             }

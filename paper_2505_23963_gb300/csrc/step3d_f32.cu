@@ -1,13 +1,14 @@
-// step3d_f32.cu -- float instantiations of the fused 3D step kernel.
+// step3d_f32.cu -- float instantiations of the fused 3D step kernel (bath modes stored in FP32,
+// or as bf16 value / increment pairs).
 #include <cuda_runtime.h>
 
 #include "step3d.cuh"
 
 namespace fdtdbath {
 
-template <int NB, int TY>
+template <int NB, int TY, bool YB>
 static int launch_nb(const Step3DParams<float>& p, int nbx, int nby, int nchunks, void* stream) {
-  auto kern = step3d_kernel<float, true, NB, TY>;
+  auto kern = step3d_kernel<float, true, NB, TY, YB>;
   const size_t smem = step3d_smem_bytes(TY, p.nmodes, sizeof(float));
   static size_t smem_set = 0;   // opt in once per instantiation for more than 48 KB
   if (smem > smem_set) {
@@ -20,22 +21,27 @@ static int launch_nb(const Step3DParams<float>& p, int nbx, int nby, int nchunks
   return (int)cudaGetLastError();
 }
 
-template <int TY>
+template <int TY, bool YB>
 static int launch_ty(const Step3DParams<float>& p, int nbmax, int nbx, int nby, int nchunks, void* stream) {
   switch (nbmax) {
-    case 0: return launch_nb<0, TY>(p, nbx, nby, nchunks, stream);
-    case 4: return launch_nb<4, TY>(p, nbx, nby, nchunks, stream);
-    case 8: return launch_nb<8, TY>(p, nbx, nby, nchunks, stream);
-    case 16: return launch_nb<16, TY>(p, nbx, nby, nchunks, stream);
-    case 32: return launch_nb<32, TY>(p, nbx, nby, nchunks, stream);
+    case 0: return launch_nb<0, TY, false>(p, nbx, nby, nchunks, stream);
+    case 4: return launch_nb<4, TY, YB>(p, nbx, nby, nchunks, stream);
+    case 8: return launch_nb<8, TY, YB>(p, nbx, nby, nchunks, stream);
+    case 16: return launch_nb<16, TY, YB>(p, nbx, nby, nchunks, stream);
+    case 32: return launch_nb<32, TY, YB>(p, nbx, nby, nchunks, stream);
     default: return (int)cudaErrorInvalidValue;
   }
 }
 
 int launch_step3d_f32(const Step3DParams<float>& p, int nbmax, int ty, int nbx, int nby, int nchunks,
-                       void* stream) {
-  if (ty == 8) return launch_ty<8>(p, nbmax, nbx, nby, nchunks, stream);
-  if (ty == 1) return launch_ty<1>(p, nbmax, nbx, nby, nchunks, stream);
+                      int bath_bf16, void* stream) {
+  if (bath_bf16) {
+    if (ty == 8) return launch_ty<8, true>(p, nbmax, nbx, nby, nchunks, stream);
+    if (ty == 1) return launch_ty<1, true>(p, nbmax, nbx, nby, nchunks, stream);
+  } else {
+    if (ty == 8) return launch_ty<8, false>(p, nbmax, nbx, nby, nchunks, stream);
+    if (ty == 1) return launch_ty<1, false>(p, nbmax, nbx, nby, nchunks, stream);
+  }
   return (int)cudaErrorInvalidValue;
 }
 

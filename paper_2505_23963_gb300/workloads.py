@@ -138,11 +138,15 @@ def precision_3d(steps: int = 3000) -> dict:
                        name="precision3d_512x512x384_nb16")
 
 
-def precision_crop(steps: int = 400) -> dict:
-    """64^3 crop of the precision form at resolution 8 (layer 16, mirrors 2, CPML 16)."""
+def precision_crop(steps: int = 1600) -> dict:
+    """64^3 crop of the precision form at resolution 8 (layer 16, mirrors 2, CPML 16), N_b = 16,
+    sigma = 0.1^2.  The mirrors' plasma strength is sigma_D = 4 (nu_p = 2): the cavity workloads'
+    sigma_D = 25 gives w_p dt = 1.96 at this resolution, outside the stability limit
+    w_max^2 dt^2 + 4 S^2 dims / eps_inf <= 4.  1600 steps (T = 100) resolve the 0.1 Rabi
+    splitting in the monitor spectrum."""
     return slab_cavity(64, 64, (16, 6, 2, 16, 2, 6), 8.0, num_bath=16, sigma=0.1 ** 2,
                        phase_seed=0, src_z=18, mon_z=46, nfreq=256, steps=steps,
-                       name="crop64_nb16")
+                       name="crop64_nb16", drude_sigma=4.0)
 
 
 def small_3d(nx=40, ny=12, layout=(6, 5, 3, 10, 3, 5), nb=8, steps=60, seed=0) -> dict:
