@@ -64,7 +64,8 @@ def test_create_validates_before_touching_the_gpu():
     over = dict(p, materials=[p["materials"][0], dict(p["materials"][1], z=(p["materials"][0]["z"][0], 30))])
     assert _create_err(over) == fb.ERR_ARG
     assert _create_err(dict(p, pml=40)) == fb.ERR_ARG
-    assert _create_err(p, bath_storage=1) == fb.ERR_UNSUPPORTED
+    assert _create_err(p, precision=64, bath_storage=1) == fb.ERR_ARG   # bf16 bath modes need FP32
+    assert _create_err(p, precision=32, bath_storage=2) == fb.ERR_ARG
     fast = dict(p, materials=[dict(p["materials"][1], frequency=40.0)])   # w0 dt >= 2
     assert _create_err(fast) == fb.ERR_CFL
     assert _create_err(dict(p, monitors=[dict(z=0, freqs=np.ones(3))])) == fb.ERR_ARG
