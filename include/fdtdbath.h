@@ -206,6 +206,31 @@ int fdtdbath_box_energy_noalloc(fdtdbath_sim *sim, int64_t z_lo, int64_t z_hi, d
                                 int32_t out_on_device);
 
 /* ---------------------------------------------------------------------------------------------
+ * Discrete adjoint (differentiation form).  The gradient of a scalar loss L of one monitor's
+ * spectra with respect to the oscillator parameters of one layer -- sigma, gamma (gamma0 of a
+ * Lorentz-Bath layer) and every bath coupling k_j, in the nu-units of fdtdbath_material -- by the
+ * exact transpose of the discrete step (the reverse-time adjoint of Eq. FDTD-1D generalised to the
+ * Yee grid with Eq. Pz_update-LB and Yzj_finite_difference), with checkpointing: the forward run
+ * keeps a full state every checkpoint_every steps; the reverse sweep recomputes one segment at a
+ * time from its checkpoint, recording the layer's E, P and bath modes, and walks it backwards.
+ * Device memory: one state per checkpoint, plus the adjoint state and the records of one segment
+ * (checkpoint_every + 2 steps of the layer's E, P and bath modes).
+ * --------------------------------------------------------------------------------------------- */
+
+/* Advance nsteps steps (as fdtdbath_step), saving the checkpoints of the run; the spectra and
+ * energy traces accumulate as usual.  Not available with bf16 bath storage
+ * (FDTDBATH_ERR_UNSUPPORTED).  A later fdtdbath_step invalidates the recording. */
+int fdtdbath_adjoint_forward(fdtdbath_sim *sim, int64_t nsteps, int32_t checkpoint_every);
+
+/* Reverse sweep of the recorded run.  dL_dF: host array nfreq x 4 x 2 with dL/dRe and dL/dIm of
+ * the monitor's spectra in the layout of fdtdbath_dft (Ex, Ey, Hx, Hy).  material: index of the
+ * layer in the list given to fdtdbath_create (not vacuum).  grad receives 2 + num_bath doubles:
+ * dL/dsigma, dL/dgamma, dL/dcoupling_j.  The simulation is left in the state at the end of the
+ * recorded run (spectra unchanged). */
+int fdtdbath_adjoint_backward(fdtdbath_sim *sim, int32_t monitor, const double *dL_dF, int32_t material,
+                              double *grad);
+
+/* ---------------------------------------------------------------------------------------------
  * Batched 1D cavities.  Many independent 1D cavities (nx = ny = 1, x polarization: E_x, H_y, P_x
  * and its bath modes) of uneven length, each advanced by the same scheme as fdtdbath_create /
  * fdtdbath_step (Eq. FDTD-1D with Eq. Pz_update-LB, Pz_1D_Lorentz, Yzj_finite_difference; the

@@ -33,6 +33,8 @@ UNITS = [
     ("batch.cpp", []),
     ("batch1d_f32.cu", []),
     ("batch1d_f64.cu", ["--fmad=false"]),
+    ("adjoint_f32.cu", []),
+    ("adjoint_f64.cu", ["--fmad=false"]),
 ]
 
 

@@ -44,6 +44,18 @@ struct HostMon {
 
 }  // namespace
 
+// Checkpoints of the adjoint driver: full states every `every` steps of the recorded forward run
+// (plus the state at its end), and the buffers of the reverse sweep.
+struct AdjState {
+  bool recorded = false;
+  int64_t n0 = 0, nsteps = 0;
+  int every = 0;
+  size_t cp_bytes = 0;
+  std::vector<void*> cps;
+  std::vector<int64_t> cp_n;
+  std::vector<int> cp_pcur;
+};
+
 struct fdtdbath_sim {
   int prec = 64;
   size_t esz = 8;
@@ -110,6 +122,10 @@ struct fdtdbath_sim {
   std::vector<int> bounds1d;            // cell range of every CTA of the cluster
   void* src_tab = nullptr;              // per-step source amplitudes of one launch (device)
   int red_nbxy = 1, red_nblocks = 1;   // partial-sum layout seen by the reduction
+  int nblk3d = 1;                       // energy partials per step of the 3D kernel
+  // quiet: steps record no monitor or energy partials (the adjoint's recomputed segments)
+  bool quiet = false;
+  AdjState adj;
   std::string err;
 };
 
@@ -263,15 +279,15 @@ Step3DParams<T> make_params(fdtdbath_sim* s, int doH, int doE) {
     p.src_cos[q] = (const T*)s->srcs[q].dcos;
     p.src_sin[q] = (const T*)s->srcs[q].dsin;
   }
-  p.nmon = (int)s->mons.size();
+  p.nmon = s->quiet ? 0 : (int)s->mons.size();
   for (size_t m = 0; m < s->mons.size(); ++m) p.mon_z[m] = (int)s->mons[m].z;
   double* part = (double*)s->partial;
   const int64_t eslot = s->n % s->ring_cap;
   const int64_t hslot = (s->n - 1 + s->ring_cap) % s->ring_cap;
   p.mon_partial_E = doE ? part + eslot * s->ring_stride + s->monE_off : nullptr;
   p.mon_partial_H = doH ? part + hslot * s->ring_stride + s->monH_off : nullptr;
-  p.eE_on = (doE && s->energy_on && (s->n % s->e_every) == 0) ? 1 : 0;
-  p.eH_on = (doH && s->energy_on && ((s->n - 1) % s->e_every) == 0) ? 1 : 0;
+  p.eE_on = (!s->quiet && doE && s->energy_on && (s->n % s->e_every) == 0) ? 1 : 0;
+  p.eH_on = (!s->quiet && doH && s->energy_on && ((s->n - 1) % s->e_every) == 0) ? 1 : 0;
   p.ebox_lo = (int)s->e_lo;
   p.ebox_hi = (int)s->e_hi;
   p.en_partial_E = part + eslot * s->ring_stride + s->enE_off;
@@ -437,7 +453,7 @@ int launch_step(fdtdbath_sim* s, int doH, int doE) {
 // Fold the partial sums of complete steps [reduced, upto) into the DFT accumulators / trace.
 int reduce_upto(fdtdbath_sim* s, int64_t upto) {
   if (upto <= s->reduced) return 0;
-  if (s->mons.empty() && !s->energy_on) {
+  if ((s->mons.empty() && !s->energy_on) || s->quiet) {
     s->reduced = upto;
     return 0;
   }
@@ -499,6 +515,17 @@ int flush_all(fdtdbath_sim* s) {
   int rc = flush_h(s);
   if (rc) return rc;
   return reduce_upto(s, s->n);
+}
+
+// A 1D simulation leaves the persistent 1D kernel for the 3D one (for good): the partials the
+// 1D kernel left are reduced in its layout first, later ones use the 3D kernel's block count.
+int switch_to_3d(fdtdbath_sim* s) {
+  if (!(s->path1d && s->ncomp1d == 1)) return 0;
+  int rc = reduce_upto(s, s->n);
+  if (rc) return rc;
+  s->ncomp1d = 3;
+  s->red_nblocks = s->nblk3d;
+  return 0;
 }
 
 // ---- field access ------------------------------------------------------------------
@@ -709,6 +736,7 @@ int fdtdbath_create(const fdtdbath_grid* grid, double resolution, double courant
     std::string why;
     const int rc = build_material(M, s->plane, s->dt, courant, dims, h, why);
     if (rc) return bail(rc, why);
+    h.user_index = order[oi];
     expand_material(h, s->dt);
     s->mats.push_back(h);
   }
@@ -824,14 +852,14 @@ int fdtdbath_create(const fdtdbath_grid* grid, double resolution, double courant
     for (auto& q : s->srcs)
       if (q.comp != 0) s->ncomp1d = 3;
     s->ring_cap = 4096;
-    s->red_nbxy = 1;
-    s->red_nblocks = s->c1d;
-  } else {
-    s->red_nbxy = s->nbx * s->nby;
-    s->red_nblocks = s->red_nbxy * s->nchunks;
   }
-  // partial-sum ring
-  const int64_t nbxy = s->red_nbxy, nblocks = s->red_nblocks;
+  // partial-sum ring: the 3D kernel's layout (nbxy per monitor quantity, nblk3d per energy
+  // quantity), or the 1D kernel's (one per CTA of its cluster); space for the larger of the two,
+  // since a 1D simulation moves to the 3D kernel once a y/z component is set (switch_to_3d)
+  s->nblk3d = s->nbx * s->nby * s->nchunks;
+  s->red_nbxy = s->nbx * s->nby;
+  s->red_nblocks = (s->path1d && s->ncomp1d == 1) ? s->c1d : s->nblk3d;
+  const int64_t nbxy = s->red_nbxy, nblocks = std::max(s->nblk3d, s->path1d ? s->c1d : 1);
   s->monE_off = 0;
   s->monH_off = 2 * (int64_t)s->mons.size() * nbxy;
   s->enE_off = s->monH_off + 4 * (int64_t)s->mons.size() * nbxy;
@@ -1008,7 +1036,11 @@ int fdtdbath_write_fields(fdtdbath_sim* s, int32_t field, const void* src, size_
   {
     // the 1D kernel skips the y/z polarization while it provably stays zero
     const bool xpol = (f.kind == 0 && (f.comp == 0 || f.comp == 4)) || (f.kind != 0 && f.comp == 0);
-    if (!xpol) s->ncomp1d = 3;
+    cudaSetDevice(s->device);
+    if (!xpol) {
+      const int rc0 = switch_to_3d(s);
+      if (rc0) return rc0;
+    }
   }
   cudaSetDevice(s->device);
   int rc = flush_all(s);
@@ -1159,3 +1191,330 @@ int64_t fdtdbath_query(const fdtdbath_sim* s, int32_t key) {
 }
 
 }  // extern "C"
+
+// ---- discrete adjoint driver ---------------------------------------------------------
+namespace {
+
+void dfree(fdtdbath_sim* s, void* p) {
+  if (!p) return;
+  for (size_t i = 0; i < s->allocs.size(); ++i)
+    if (s->allocs[i] == p) {
+      s->allocs.erase(s->allocs.begin() + (long)i);
+      break;
+    }
+  if (s->ufree) s->ufree(p, s->uctx);
+  else cudaFree(p);
+}
+
+struct StateRef {
+  void* p;
+  size_t bytes;
+};
+
+// The buffers that make up the state after a flushed step (the order of a checkpoint).
+std::vector<StateRef> state_refs(fdtdbath_sim* s) {
+  const size_t e = s->esz;
+  std::vector<StateRef> v;
+  v.push_back({s->E[s->ecur], 3 * (size_t)s->ncell * e});
+  v.push_back({s->H[s->hcur], 3 * (size_t)s->ncell * e});
+  v.push_back({s->psiE, 2 * (size_t)(2 * s->npml) * s->plane * e});
+  v.push_back({s->psiH[s->psicur], 2 * (size_t)(2 * s->npml + 1) * s->plane * e});
+  if (s->prec == 64) v.push_back({s->D, 3 * (size_t)s->nmatcell * e});
+  for (int b = 0; b < 2; ++b) v.push_back({s->Pslot[b], 3 * (size_t)s->nmatcell * e});
+  for (int b = 0; b < 2; ++b) v.push_back({s->Yslot[b], (size_t)s->nybath * s->yesz});
+  return v;
+}
+
+int checkpoint_io(fdtdbath_sim* s, void* buf, bool save) {
+  size_t off = 0;
+  for (const StateRef& r : state_refs(s)) {
+    if (r.bytes) {
+      char* c = (char*)buf + off;
+      cudaError_t e = save ? cudaMemcpyAsync(c, r.p, r.bytes, cudaMemcpyDeviceToDevice, s->stream)
+                           : cudaMemcpyAsync(r.p, c, r.bytes, cudaMemcpyDeviceToDevice, s->stream);
+      if (e != cudaSuccess) return cuda_fail(s, e, "checkpoint copy");
+    }
+    off += (r.bytes + 255) & ~size_t(255);
+  }
+  return 0;
+}
+
+size_t checkpoint_bytes(fdtdbath_sim* s) {
+  size_t n = 0;
+  for (const StateRef& r : state_refs(s)) n += (r.bytes + 255) & ~size_t(255);
+  return n;
+}
+
+int save_checkpoint(fdtdbath_sim* s, size_t idx) {
+  int rc = flush_h(s);
+  if (rc) return rc;
+  AdjState& a = s->adj;
+  if (idx >= a.cps.size()) {
+    void* p = dalloc(s, a.cp_bytes);
+    if (!p) return fail(s, FDTDBATH_ERR_OOM, "checkpoint allocation failed");
+    a.cps.push_back(p);
+    a.cp_n.push_back(0);
+    a.cp_pcur.push_back(0);
+  }
+  a.cp_n[idx] = s->n;
+  a.cp_pcur[idx] = s->pcur;
+  return checkpoint_io(s, a.cps[idx], true);
+}
+
+int restore_checkpoint(fdtdbath_sim* s, size_t idx) {
+  AdjState& a = s->adj;
+  s->h_pending = false;
+  int rc = checkpoint_io(s, a.cps[idx], false);
+  if (rc) return rc;
+  s->n = a.cp_n[idx];
+  s->pcur = a.cp_pcur[idx];
+  s->reduced = s->n;
+  return 0;
+}
+
+int launch_adjoint(const AdjParams<float>& p, int nbmax, cudaStream_t st) { return launch_adjoint_f32(p, nbmax, st); }
+int launch_adjoint(const AdjParams<double>& p, int nbmax, cudaStream_t st) { return launch_adjoint_f64(p, nbmax, st); }
+
+template <typename T>
+int adjoint_sweep(fdtdbath_sim* s, const HostMon& mon, const std::vector<double>& freqs, const double* dLdF,
+                  int gm, std::vector<double>& grad) {
+  AdjState& A = s->adj;
+  const int64_t N = s->ncell, plane = s->plane;
+  const size_t e = s->esz;
+  const HostMat& G = s->mats[(size_t)gm];
+  const int64_t ncm = G.ncell;
+  const int nb = G.nb;
+  const int L = A.every;
+  // ---- buffers ----
+  std::vector<void*> bufs;
+  auto get = [&](size_t bytes) -> void* {
+    void* p = dalloc(s, bytes);
+    if (p) bufs.push_back(p);
+    return p;
+  };
+  T* Eb = (T*)get(3 * (size_t)N * e);
+  T* Hb = (T*)get(3 * (size_t)N * e);
+  T* psE[2] = {(T*)get(2 * (size_t)(2 * s->npml) * plane * e), (T*)get(2 * (size_t)(2 * s->npml) * plane * e)};
+  T* psH[2] = {(T*)get(2 * (size_t)(2 * s->npml + 1) * plane * e), (T*)get(2 * (size_t)(2 * s->npml + 1) * plane * e)};
+  T* Pb = (T*)get(3 * (size_t)s->nmatcell * e);
+  T* Pmb = (T*)get(3 * (size_t)s->nmatcell * e);
+  T* Yb0 = (T*)get((size_t)s->nybath * e);
+  T* Yb1 = (T*)get((size_t)s->nybath * e);
+  T* snapE = (T*)get((size_t)L * 3 * ncm * e);
+  T* snapP = (T*)get((size_t)(L + 2) * 3 * ncm * e);
+  T* snapY = (T*)get((size_t)(L + 2) * 3 * std::max(1, nb) * ncm * e);
+  const int64_t nblk = adjoint_blocks(N);
+  double* gpart = (double*)get((size_t)nblk * kAdjMaxGrad * sizeof(double));
+  int nrows = 0;
+  for (auto& m : s->mats) nrows += m.nb;
+  T* coefLit = (T*)get((size_t)std::max(1, nrows) * kCoefStride * e);
+  auto release = [&]() {
+    for (void* p : bufs) dfree(s, p);
+  };
+  for (void* p : bufs)
+    if (!p) {
+      release();
+      return fail(s, FDTDBATH_ERR_OOM, "adjoint buffer allocation failed");
+    }
+  // literal coefficient rows in the state precision
+  {
+    std::vector<T> rows;
+    for (auto& m : s->mats)
+      for (double v : m.rowsLit) rows.push_back((T)v);
+    if (rows.empty()) rows.assign(kCoefStride, T(0));
+    int rc = h2d(s, coefLit, rows.data(), rows.size() * e);
+    if (rc) {
+      release();
+      return rc;
+    }
+  }
+  // ---- monitor adjoint sources per step: dL/d(plane mean) / plane ----
+  const int64_t n0 = A.n0, NS = A.nsteps;
+  std::vector<double> gE((size_t)NS * 2, 0.0), gH((size_t)NS * 2, 0.0);
+  for (int64_t m = 0; m < NS; ++m) {
+    const double tE = ((double)(n0 + m) + 0.5) * s->dt, tH = ((double)(n0 + m) + 1.0) * s->dt;
+    for (int f = 0; f < mon.nfreq; ++f) {
+      const double aE = 2.0 * M_PI * freqs[(size_t)f] * tE, aH = 2.0 * M_PI * freqs[(size_t)f] * tH;
+      const double cE = std::cos(aE), sE = std::sin(aE), cH = std::cos(aH), sH = std::sin(aH);
+      const double* d = dLdF + (size_t)f * 8;
+      gE[(size_t)m * 2 + 0] += (d[0] * cE + d[1] * sE) * s->dt;
+      gE[(size_t)m * 2 + 1] += (d[2] * cE + d[3] * sE) * s->dt;
+      gH[(size_t)m * 2 + 0] += (d[4] * cH + d[5] * sH) * s->dt;
+      gH[(size_t)m * 2 + 1] += (d[6] * cH + d[7] * sH) * s->dt;
+    }
+  }
+  // ---- constant part of the kernel parameters ----
+  AdjParams<T> p{};
+  p.nx = (int)s->nx;
+  p.ny = (int)s->ny;
+  p.nz = (int)s->nz;
+  p.npml = s->npml;
+  p.plane = plane;
+  p.ncell = N;
+  p.nmatcell = s->nmatcell;
+  p.S = (T)(s->dt / s->dx);
+  p.dt = (T)s->dt;
+  p.pmlE = (const T*)s->pmlE;
+  p.pmlH = (const T*)s->pmlH;
+  p.Eb = Eb;
+  p.Hb = Hb;
+  p.Pb = Pb;
+  p.Pmb = Pmb;
+  p.Yb0 = Yb0;
+  p.Yb1 = Yb1;
+  p.coefLit = coefLit;
+  p.nmat = (int)s->mats.size();
+  int off = 0;
+  for (size_t m = 0; m < s->mats.size(); ++m) {
+    p.mat[m] = mat_k<T>(s->mats[m], off, s->dt);
+    off += s->mats[m].nb;
+  }
+  p.zm = (int)mon.z;
+  p.gm = gm;
+  const double dt = s->dt;
+  p.dcE = G.w0 * G.w0 * dt * dt;
+  p.halfdt = 0.5 * dt;
+  p.invA = 1.0 / G.A;
+  for (int j = 0; j < nb; ++j) {
+    const double den = 1.0 + 0.5 * G.gj[(size_t)j] * dt;
+    p.ga[j] = (2.0 - G.wj[(size_t)j] * G.wj[(size_t)j] * dt * dt) / den;
+    p.gb[j] = -2.0 / den;
+    p.gk[j] = G.kj[(size_t)j];
+    p.gdc[j] = dt / (2.0 * den);
+    p.gds[j] = G.kj[(size_t)j] * dt / den;
+  }
+  p.gpart = gpart;
+  // every adjoint buffer starts at zero (dalloc zeroes them)
+  const bool save_quiet = s->quiet;
+  s->quiet = true;
+  int ps = 0;   // current psi adjoint buffers
+  int rc = 0;
+  auto snap = [&](T* dst, const void* src, size_t count) -> int {
+    cudaError_t ce = cudaMemcpyAsync(dst, src, count * e, cudaMemcpyDeviceToDevice, s->stream);
+    return ce == cudaSuccess ? 0 : cuda_fail(s, ce, "adjoint snapshot");
+  };
+  const int64_t ncp = (NS + L - 1) / L;
+  for (int64_t c = ncp - 1; c >= 0 && !rc; --c) {
+    rc = restore_checkpoint(s, (size_t)c);
+    if (rc) break;
+    const int64_t s0 = c * L;
+    const int Lc = (int)std::min<int64_t>(L, NS - s0);
+    // levels n-1/2 and n+1/2 of the material at the segment start
+    for (int lv = 0; lv < 2 && !rc; ++lv) {
+      const int slot = lv == 0 ? 1 - s->pcur : s->pcur;
+      for (int cc = 0; cc < 3 && !rc; ++cc)
+        rc = snap(snapP + ((size_t)lv * 3 + cc) * ncm, elem_ptr(s->Pslot[slot], cc * s->nmatcell + G.base, e), (size_t)ncm);
+      if (!rc && nb) rc = snap(snapY + (size_t)lv * 3 * nb * ncm, elem_ptr(s->Yslot[slot], G.ybase, e), (size_t)3 * nb * ncm);
+    }
+    // recompute the segment, recording the material's E, P and Y after every step
+    for (int m = 0; m < Lc && !rc; ++m) {
+      rc = launch_step(s, s->h_pending ? 1 : 0, 1);
+      if (rc) break;
+      s->pcur = 1 - s->pcur;
+      s->n += 1;
+      s->h_pending = true;
+      s->reduced = s->n;
+      for (int cc = 0; cc < 3 && !rc; ++cc) {
+        rc = snap(snapE + ((size_t)m * 3 + cc) * ncm, elem_ptr(s->E[s->ecur], cc * N + G.zlo * plane, e), (size_t)ncm);
+        if (!rc)
+          rc = snap(snapP + ((size_t)(m + 2) * 3 + cc) * ncm, elem_ptr(s->Pslot[s->pcur], cc * s->nmatcell + G.base, e),
+                    (size_t)ncm);
+      }
+      if (!rc && nb)
+        rc = snap(snapY + (size_t)(m + 2) * 3 * nb * ncm, elem_ptr(s->Yslot[s->pcur], G.ybase, e), (size_t)3 * nb * ncm);
+    }
+    // reverse sweep over the segment
+    for (int m = Lc - 1; m >= 0 && !rc; --m) {
+      const int64_t ng = s0 + m;
+      p.fE = snapE + (size_t)m * 3 * ncm;
+      p.fPn = snapP + (size_t)(m + 2) * 3 * ncm;
+      p.fPm = snapP + (size_t)m * 3 * ncm;
+      p.fY = snapY + (size_t)(m + 1) * 3 * std::max(1, nb) * ncm;
+      p.fYm = snapY + (size_t)m * 3 * std::max(1, nb) * ncm;
+      const double ip = 1.0 / (double)plane;
+      p.gEx = (T)(gE[(size_t)ng * 2] * ip);
+      p.gEy = (T)(gE[(size_t)ng * 2 + 1] * ip);
+      p.gHx = (T)(gH[(size_t)ng * 2] * ip);
+      p.gHy = (T)(gH[(size_t)ng * 2 + 1] * ip);
+      p.psiEb = psE[ps];
+      p.psiEb_out = psE[1 - ps];
+      p.psiHb = psH[ps];
+      p.psiHb_out = psH[1 - ps];
+      const int lr = launch_adjoint(p, s->nbmax, s->stream);
+      s->launches += 2;
+      if (lr) rc = cuda_fail(s, (cudaError_t)lr, "adjoint kernel launch");
+      ps = 1 - ps;
+    }
+  }
+  // gradient: fixed-order sum of the per-block partials
+  if (!rc) {
+    std::vector<double> h((size_t)nblk * kAdjMaxGrad);
+    rc = d2h(s, h.data(), gpart, h.size() * sizeof(double));
+    grad.assign((size_t)(2 + nb), 0.0);
+    for (int64_t b = 0; b < nblk && !rc; ++b)
+      for (int t = 0; t < 2 + nb; ++t) grad[(size_t)t] += h[(size_t)b * kAdjMaxGrad + t];
+  }
+  s->quiet = save_quiet;
+  release();
+  return rc;
+}
+
+}  // namespace
+
+int fdtdbath_adjoint_forward(fdtdbath_sim* s, int64_t nsteps, int32_t checkpoint_every) {
+  if (!s || nsteps < 1 || checkpoint_every < 1) return fail(s, FDTDBATH_ERR_ARG, "bad arguments to fdtdbath_adjoint_forward");
+  if (s->ybf) return fail(s, FDTDBATH_ERR_UNSUPPORTED, "the adjoint does not run on bf16 bath storage");
+  cudaSetDevice(s->device);
+  AdjState& a = s->adj;
+  {
+    const int rc0 = switch_to_3d(s);   // single-step launches: the persistent 1D kernel is not used
+    if (rc0) return rc0;
+  }
+  a.recorded = false;
+  a.n0 = s->n;
+  a.nsteps = nsteps;
+  a.every = checkpoint_every;
+  a.cp_bytes = checkpoint_bytes(s);
+  const int64_t ncp = (nsteps + checkpoint_every - 1) / checkpoint_every;
+  for (int64_t c = 0; c < ncp; ++c) {
+    int rc = save_checkpoint(s, (size_t)c);
+    if (rc) return rc;
+    rc = fdtdbath_step(s, std::min<int64_t>(checkpoint_every, nsteps - c * checkpoint_every));
+    if (rc) return rc;
+  }
+  int rc = flush_all(s);
+  if (rc) return rc;
+  rc = save_checkpoint(s, (size_t)ncp);   // the state at the end, put back after the reverse sweep
+  if (rc) return rc;
+  a.recorded = true;
+  return FDTDBATH_OK;
+}
+
+int fdtdbath_adjoint_backward(fdtdbath_sim* s, int32_t monitor, const double* dL_dF, int32_t material, double* grad) {
+  if (!s || !dL_dF || !grad) return fail(s, FDTDBATH_ERR_ARG, "NULL argument");
+  AdjState& a = s->adj;
+  if (!a.recorded) return fail(s, FDTDBATH_ERR_ARG, "no recorded forward run: call fdtdbath_adjoint_forward first");
+  if (monitor < 0 || monitor >= (int)s->mons.size()) return fail(s, FDTDBATH_ERR_ARG, "bad monitor");
+  int gm = -1;
+  for (size_t m = 0; m < s->mats.size(); ++m)
+    if (s->mats[m].user_index == material) gm = (int)m;
+  if (gm < 0) return fail(s, FDTDBATH_ERR_ARG, "bad material index");
+  if (s->mats[(size_t)gm].kind == FDTDBATH_VACUUM) return fail(s, FDTDBATH_ERR_ARG, "a vacuum layer has no oscillator parameters");
+  if (s->n != a.n0 + a.nsteps) return fail(s, FDTDBATH_ERR_ARG, "the simulation has moved since the recorded forward run");
+  cudaSetDevice(s->device);
+  const HostMon& mon = s->mons[(size_t)monitor];
+  std::vector<double> freqs((size_t)mon.nfreq);
+  int rc = d2h(s, freqs.data(), mon.dfreq, freqs.size() * sizeof(double));
+  if (rc) return rc;
+  std::vector<double> g;
+  rc = s->prec == 64 ? adjoint_sweep<double>(s, mon, freqs, dL_dF, gm, g) : adjoint_sweep<float>(s, mon, freqs, dL_dF, gm, g);
+  // put the recorded end state back in every case
+  const int rc2 = restore_checkpoint(s, a.cps.size() - 1);
+  if (rc) return rc;
+  if (rc2) return rc2;
+  // the caller's parameters are in nu-units: gamma0 = 2 pi gamma, k_j = 2 pi coupling_j
+  grad[0] = g[0];
+  grad[1] = 2.0 * M_PI * g[1];
+  for (size_t j = 2; j < g.size(); ++j) grad[j] = 2.0 * M_PI * g[j];
+  return FDTDBATH_OK;
+}

@@ -22,6 +22,7 @@ struct HostMat {
   // derived (double)
   double cE, c1m, W, c2, A, rho, w0r2;
   std::vector<double> rowsLit, rowsInc;  // [nb][kCoefStride]
+  int user_index = -1;                    // position in the caller's material list
 };
 
 // CPML profile (Roden-Gedney, kappa = 1) at a z position in cells of an nz-cell axis with npml

@@ -146,6 +146,49 @@ int launch_step3d_f32(const Step3DParams<float>& p, int nbmax, int ty, int nbx, 
 int launch_step3d_f64(const Step3DParams<double>& p, int nbmax, int ty, int nbx, int nby,
                       int nchunks, void* stream);
 
+// ---- discrete adjoint (adjoint.cu) ----
+// One reverse step of the exact transpose of the forward step (D-free form), applied to the
+// adjoint state (Eb, Hb, psi memories, P / P_m and bath-mode adjoints); see adjoint.cu.
+constexpr int kAdjMaxGrad = 2 + kMaxBath;   // dL/dsigma, dL/dgamma0, dL/dk_j
+template <typename T>
+struct AdjParams {
+  int nx, ny, nz, npml;
+  int64_t plane, ncell, nmatcell;
+  T S, dt;
+  const T* pmlE;            // [nz][2] (b, c) at integer z
+  const T* pmlH;            // [nz][2] (b, c) at z + 1/2
+  T* Eb;                    // [3][ncell] adjoint of E
+  T* Hb;                    // [3][ncell] adjoint of H
+  T* psiEb;                 // [2][2 npml][plane]   adjoint of the E-side CPML memories (in place)
+  T* psiEb_out;             // [2][2 npml][plane]   b_E-scaled copy for the next reverse step
+  const T* psiHb;           // [2][2 npml + 1][plane]
+  T* psiHb_out;
+  int nmat;
+  MatK<T> mat[kMaxMat];
+  const T* coefLit;         // [rows][kCoefStride] literal rows {k, a, b, b+1, c, (w dt)^2}
+  T* Pb;                    // [3][nmatcell] adjoint of P^{n+3/2} on entry, of P^{n+1/2} on exit
+  T* Pmb;                   // adjoint of P^{n+1/2} on entry, of P^{n-1/2} on exit
+  T* Yb0;                   // bath modes, the same two roles as Pb / Pmb
+  T* Yb1;
+  // monitor sources of this reverse step (dL/d of the plane means, divided by the plane size)
+  int zm;                   // monitor plane, -1 for none
+  T gEx, gEy, gHx, gHy;
+  // gradient of the material gm (-1: none) from the forward values recorded for this step
+  int gm;
+  const T* fE;              // E^{n+1/2}   [3][ncell_gm]
+  const T* fPn;             // P^{n+3/2}
+  const T* fPm;             // P^{n-1/2}
+  const T* fY;              // Y^{n+1/2}   [3][nb][ncell_gm]
+  const T* fYm;             // Y^{n-1/2}
+  double dcE;               // d cE / d sigma = (w0 dt)^2
+  double halfdt, invA;
+  double ga[kMaxBath], gb[kMaxBath], gk[kMaxBath], gdc[kMaxBath], gds[kMaxBath];
+  double* gpart;            // [gridDim][kAdjMaxGrad] per-block running sums (FP64)
+};
+int launch_adjoint_f32(const AdjParams<float>& p, int nbmax, void* stream);
+int launch_adjoint_f64(const AdjParams<double>& p, int nbmax, void* stream);
+int64_t adjoint_blocks(int64_t ncell);
+
 // reduce.cu: fixed-order reduction of the per-block partials into per-step series,
 // running DFT accumulation and energy traces.
 struct ReduceParams {

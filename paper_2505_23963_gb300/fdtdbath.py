@@ -29,7 +29,8 @@ EXPORTED = ["fdtdbath_create", "fdtdbath_step", "fdtdbath_sync", "fdtdbath_read_
             "fdtdbath_box_energy_noalloc", "fdtdbath_batch_create", "fdtdbath_batch_autotune",
             "fdtdbath_batch_step", "fdtdbath_batch_sync", "fdtdbath_batch_read_field",
             "fdtdbath_batch_energy", "fdtdbath_batch_query", "fdtdbath_batch_last_error",
-            "fdtdbath_batch_destroy", "fdtdbath_batch_plan"]
+            "fdtdbath_batch_destroy", "fdtdbath_batch_plan", "fdtdbath_adjoint_forward",
+            "fdtdbath_adjoint_backward"]
 
 
 def field_E(c): return 0 + c
@@ -129,6 +130,10 @@ def lib(build_if_missing: bool = True):
         L.fdtdbath_query.argtypes = [vp, i32]
         L.fdtdbath_box_energy_noalloc.restype = i32
         L.fdtdbath_box_energy_noalloc.argtypes = [vp, i64, i64, vp, i32]
+        L.fdtdbath_adjoint_forward.restype = i32
+        L.fdtdbath_adjoint_forward.argtypes = [vp, i64, i32]
+        L.fdtdbath_adjoint_backward.restype = i32
+        L.fdtdbath_adjoint_backward.argtypes = [vp, i32, dp, i32, dp]
         i32p, i64p = C.POINTER(i32), C.POINTER(i64)
         L.fdtdbath_batch_create.restype = i32
         L.fdtdbath_batch_create.argtypes = [C.POINTER(Cavity), i32, C.c_double, C.c_double,
@@ -377,6 +382,20 @@ class Simulation:
 
     def launches(self) -> int:
         return query(self.h, 1)
+
+    def adjoint_forward(self, nsteps: int, checkpoint_every: int = 256):
+        """fdtdbath_adjoint_forward: advance nsteps steps keeping checkpoints for the adjoint."""
+        _check(lib().fdtdbath_adjoint_forward(self.h, int(nsteps), int(checkpoint_every)), self.h)
+
+    def adjoint_backward(self, dL_dF, material: int, monitor: int = 0) -> np.ndarray:
+        """fdtdbath_adjoint_backward: dL_dF (nfreq, 4, 2) = dL/d(Re, Im) of the monitor spectra
+        (Ex, Ey, Hx, Hy); returns dL/d(sigma, gamma, coupling_1..N_b) of layer `material`."""
+        g = _f64(dL_dF).reshape(-1)
+        nb = len(self.prob["materials"][material].get("bath_frequencies", [])) \
+            if self.prob["materials"][material]["kind"] == "lorentz_bath" else 0
+        out = np.zeros(2 + nb)
+        _check(lib().fdtdbath_adjoint_backward(self.h, int(monitor), _dptr(g), int(material), _dptr(out)), self.h)
+        return out
 
     def close(self):
         if getattr(self, "h", None):

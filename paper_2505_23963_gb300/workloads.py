@@ -215,6 +215,46 @@ def batch_small(seed: int = 0, steps: int = 600) -> list:
     return out
 
 
+def adjoint_2d(steps: int = 8000) -> dict:
+    """Differentiation form: 2D TE cavity, 2048 x 2048 cells (x periodic, CPML along z),
+    resolution 64, out-of-plane E (E_y here, with the in-plane H_x, H_z), z: CPML 16 | vacuum 744
+    | Drude 16 | Lorentz-Bath 512 (N_b = 8, sigma = 0.05^2) | Drude 16 | vacuum 728 | CPML 16;
+    E_y plane source with the seeded transverse phase; 128 DFT frequencies.  The mirrors take
+    sigma_D = 4 (nu_p = 2): with the cavity workloads' sigma_D = 25 a 0.25-unit mirror is ~8 skin
+    depths thick and the cavity transmits below 2e-9, which leaves a transmission loss without
+    signal; at sigma_D = 4 the transmission peaks near 0.15."""
+    return slab_cavity(2048, 1, (16, 744, 16, 512, 16, 728), 64.0, num_bath=8, sigma=0.05 ** 2,
+                       phase_seed=0, src_z=16 + 372, mon_z=2048 - 16 - 364, nfreq=128, steps=steps,
+                       source_component=1, name="adjoint2d_2048x2048_nb8", drude_sigma=4.0)
+
+
+def adjoint_crop(steps: int = 2000, nb: int = 8) -> dict:
+    """128 x 128 crop of the differentiation form at resolution 16 (32-cell layer, 4-cell
+    mirrors with sigma_D = 4), for oracle and finite-difference gradients."""
+    return slab_cavity(128, 1, (16, 24, 4, 32, 4, 32), 16.0, num_bath=nb, sigma=0.05 ** 2,
+                       phase_seed=0, src_z=28, mon_z=96, nfreq=128, steps=steps,
+                       source_component=1, name=f"adjoint_crop128_nb{nb}", drude_sigma=4.0)
+
+
+def vacuum_of(prob: dict) -> dict:
+    """The same problem with every layer removed (the flux normalization run)."""
+    q = dict(prob)
+    q["materials"] = []
+    q["name"] = prob.get("name", "") + "_vacuum"
+    return q
+
+
+def adjoint_target_params(params: np.ndarray, seed: int = 0) -> np.ndarray:
+    """Perturbed parameters of the seeded target spectrum: sigma x 1.1, gamma x 0.9,
+    coupling_j x (1 + 0.1 N(0, 1)) from default_rng(seed)."""
+    p = np.array(params, dtype=np.float64)
+    rng = np.random.default_rng(seed)
+    p[0] *= 1.1
+    p[1] *= 0.9
+    p[2:] *= 1.0 + 0.1 * rng.standard_normal(p.size - 2)
+    return p
+
+
 # ----------------------------------------------------------------- random states
 def random_state(prob: dict, seed: int, scale: float = 1e-2, with_bath: bool = True) -> dict:
     """Seeded random E, H, P (two levels) and Y (two levels) for every material cell.

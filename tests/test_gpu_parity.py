@@ -223,3 +223,31 @@ def test_bad_step_argument_and_empty_step():
     g.step(0)
     assert g.steps_done == 0
     assert np.all(g.get("E", comp=0) == 0)
+
+
+@pytest.mark.parametrize("precision", [64, 32])
+def test_1d_cavity_moving_to_3d_kernel_keeps_traces(precision):
+    """A 1D cavity runs on the persistent 1D kernel until a y component is written, then on the
+    3D kernel, whose energy partials have their own layout: the trace must stay the oracle's."""
+    prob = wl.slab_cavity(1, 1, (8, 200, 10, 200, 10, 164), 100.0, num_bath=4, sigma=0.01,
+                          bath_seed=3, phase_seed=None, src_z=60, mon_z=560, nfreq=16, steps=600)
+    g = fb.Simulation(prob, precision=precision, energy_capacity=700)
+    o = O.OracleSim(prob, trace_cap=700)
+    g.step(300)
+    o.step(300)
+    ey = 1e-3 * np.random.default_rng(5).standard_normal(prob["n"][::-1])
+    if precision == 32:
+        ey = ey.astype(np.float32).astype(np.float64)
+    g.set("E", ey, comp=1)
+    o.set("E", ey, comp=1)
+    eps = eps_grid(prob)
+    o.set("D", eps * o.get("E", comp=1) + o.get("Pm", comp=1), comp=1)
+    g.step(300)
+    o.step(300)
+    tol = TOL[precision]
+    tg, to = g.trace(), o.trace()
+    assert tg.shape == to.shape == (600, 4)
+    for col in range(3):
+        assert rel(tg[:, col], to[:, col]) < tol, col
+    assert rel(g.dft(0), o.dft(0)) < tol
+    assert rel(stack(g, "E"), stack(o, "E")) < tol
