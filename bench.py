@@ -45,11 +45,13 @@ def peaks():
         return 6800.0, "fallback"
 
 
-def algorithmic_bytes(prob: dict, esz: int) -> float:
+def algorithmic_bytes(prob: dict, esz: int, bath_bytes: float | None = None) -> float:
     """Bytes per launch with every state word read once and written once: E, H (6 words
     per cell), +4 CPML memories in the absorber planes, +3 x (2 reads + 1 write) of P in
     Drude/Lorentz planes and additionally +3 x 3 N_b words for the bath modes (two levels
-    read, one written) in Lorentz-Bath planes.  Coefficient tables are not counted."""
+    read, one written) in Lorentz-Bath planes.  Coefficient tables are not counted.
+    bath_bytes overrides the bytes per bath mode and component (bf16 value/increment pairs
+    read and written: 8)."""
     nx, ny, nz = prob["n"]
     pml = prob.get("pml", 0)
     words = np.full(nz, 12.0)
@@ -60,7 +62,8 @@ def algorithmic_bytes(prob: dict, esz: int) -> float:
         if m["kind"] in ("lorentz", "drude"):
             words[lo:hi] += 9
         elif m["kind"] == "lorentz_bath":
-            words[lo:hi] += 9 + 9 * len(m["bath_frequencies"])
+            nb = len(m["bath_frequencies"])
+            words[lo:hi] += 9 + (9 * nb if bath_bytes is None else 3 * nb * bath_bytes / esz)
     return float(words.sum()) * nx * ny * esz
 
 
@@ -138,7 +141,7 @@ def oracle_sample(prob: dict, ny_sample: int) -> dict:
     return smp
 
 
-def oracle_rate(prob: dict, min_seconds: float = 10.0, max_steps: int = 40, ny_sample: int = 16):
+def oracle_rate(prob: dict, min_seconds: float = 10.0, max_steps: int = 4000, ny_sample: int = 16):
     """Cell-updates/s of the FP64 CPU oracle on a bounded sample (see oracle_sample)."""
     from oracle import oracle as O
     smp = oracle_sample(prob, ny_sample)
@@ -193,6 +196,167 @@ def run_reference(args):
     }
     print(json.dumps(line), flush=True)
     return 0
+
+
+def form_precision(fb, stream, torch):
+    """Precision form: the 512 x 512 x 384 workload (N_b = 16, Rabi 0.1) in FP32 and in FP32 with
+    bf16-stored bath modes (throughput, roofline), and both against the FP64 GPU path on the 64^3
+    crop (field, spectrum and polariton-peak errors)."""
+    from paper_2505_23963_gb300 import analysis
+    hbm, _ = peaks()
+    prob = wl.precision_3d(steps=40)
+    cells = float(np.prod(prob["n"]))
+    out = {"workload": prob["name"]}
+    for tag, bs in (("fp32", 0), ("bf16_bath", 1)):
+        with torch.cuda.stream(stream):
+            sim = fb.Simulation(prob, precision=32, stream=stream, bath_storage=bs, energy_capacity=64)
+        sim.step(3)
+        sim.sync()
+        k = 20
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        ev[0].record(stream)
+        sim.step(k)
+        ev[1].record(stream)
+        torch.cuda.synchronize()
+        ms = ev[0].elapsed_time(ev[1]) / k
+        byts = algorithmic_bytes(prob, 4, None if bs == 0 else 8.0)
+        out[tag] = {"value": cells / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms,
+                    "bytes_per_cell": byts / cells, "achieved_GBs": byts / (ms * 1e-3) / 1e9,
+                    "frac_hbm": byts / (ms * 1e-3) / 1e9 / hbm}
+        sim.close()
+    crop = wl.precision_crop()
+    runs = {}
+    for tag, prec, bs in (("fp64", 64, 0), ("fp32", 32, 0), ("bf16_bath", 32, 1)):
+        sim = fb.Simulation(crop, precision=prec, bath_storage=bs, energy=False)
+        sim.step(crop["steps"])
+        spec = sim.dft(0)
+        runs[tag] = (np.asarray(sim.get("E", comp=0), np.float64), spec,
+                     analysis.spectral_peaks(crop["monitors"][0]["freqs"], np.abs(spec[:, 0]) ** 2, 2))
+        sim.close()
+    E0, S0, P0 = runs["fp64"]
+    for tag in ("fp32", "bf16_bath"):
+        E, S, P = runs[tag]
+        out[tag]["crop_errors_vs_fp64"] = {
+            "E": float(np.linalg.norm(E - E0) / np.linalg.norm(E0)),
+            "spectrum": float(np.linalg.norm(S - S0) / np.linalg.norm(S0)),
+            "peaks": float(np.max(np.abs(P - P0) / P0))}
+    return out
+
+
+def form_batch(fb, torch):
+    """Batching form: 64 independent 1D cavities (lengths 1000-8000, Rabi 0.01-0.2, N_b in
+    {4, 8, 16, 32}), 50000 FP32 steps in persistent launches replayed from CUDA graphs, energy every
+    10 steps; per-cavity relaxation rate and bath share; the plain FP64 GPU path's time for the
+    same cell-updates, measured on one cavity and scaled."""
+    from paper_2505_23963_gb300 import analysis
+    steps = 50000
+    probs = wl.batch_sweep(steps=steps)
+    cells = float(sum(p["n"][2] for p in probs))
+    b = fb.Batch(probs, precision=32, energy_every=10)
+    t0 = time.perf_counter()
+    C, T, tuned = b.autotune(200)
+    tune_s = time.perf_counter() - t0
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    b.step(steps)
+    b.sync()
+    secs = time.perf_counter() - t0
+    dtr = 10 * probs[0]["courant"] / probs[0]["resolution"]
+    gam, share = [], []
+    for i, p in enumerate(probs):
+        tr = b.trace(i)
+        t0p = 2 * p["sources"][0]["t0"]
+        gam.append(analysis.relaxation_rate(tr, dtr, t0p))
+        share.append(analysis.bath_share(tr, dtr, t0p))
+    shape = b.shape()
+    b.close()
+    # the plain FP64 path on one cavity of the sweep
+    ref = probs[int(np.argsort([p["n"][2] for p in probs])[len(probs) // 2])]
+    sim = fb.Simulation(ref, precision=64, energy_capacity=2100)
+    sim.step(100)
+    sim.sync()
+    t0 = time.perf_counter()
+    sim.step(2000)
+    sim.sync()
+    rate64 = ref["n"][2] * 2000 / (time.perf_counter() - t0)
+    sim.close()
+    g = np.asarray(gam)
+    return {"workload": "batch sweep: 64 cavities x 50000 steps", "value": cells * steps / secs,
+            "unit": UNIT, "seconds": secs, "steps": steps, "cells": cells,
+            "launch_shape": {"cluster_ctas": C, "threads": T, **shape}, "autotune_s": tune_s,
+            "gamma_pol": {"min": float(np.nanmin(g)), "median": float(np.nanmedian(g)),
+                          "max": float(np.nanmax(g))},
+            "bath_share": {"min": float(np.nanmin(share)), "median": float(np.nanmedian(share)),
+                           "max": float(np.nanmax(share))},
+            "plain_fp64_path": {"value": rate64, "unit": UNIT,
+                                "seconds_for_same_work": cells * steps / rate64}}
+
+
+def form_adjoint(fb, torch):
+    """Differentiation form: 2D TE cavity 2048 x 2048 (N_b = 8), 8000 FP32 steps with checkpoints
+    every 256, loss = sum (T - T*)^2 over 128 frequencies; gradient w.r.t. sigma, gamma and the 8
+    couplings through torch.autograd (forward and backward wall times); the target T* is the
+    transmission at the seeded perturbed parameters."""
+    from paper_2505_23963_gb300 import adjoint as adj
+    prob = wl.adjoint_2d(steps=8000)
+    n = prob["steps"]
+    cells = float(np.prod(prob["n"]))
+    p0 = adj.layer_params(prob, 1)
+    s = fb.Simulation(wl.vacuum_of(prob), precision=32, energy=False)
+    s.step(n)
+    fv = np.real(_flux(s.dft(0)))
+    s.close()
+    s = fb.Simulation(adj.with_params(prob, 1, wl.adjoint_target_params(p0)), precision=32, energy=False)
+    s.step(n)
+    target = _flux(s.dft(0)) / fv
+    s.close()
+    x = torch.tensor(p0, dtype=torch.float64, requires_grad=True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    L = adj.transmission_loss(x, prob, 1, fv, target, n, 256, 32)
+    torch.cuda.synchronize()
+    tf = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    L.backward()
+    torch.cuda.synchronize()
+    tb = time.perf_counter() - t0
+    g = x.grad.numpy()
+    return {"workload": prob["name"], "steps": n, "checkpoint_every": 256,
+            "forward_s": tf, "backward_s": tb,
+            "value": cells * n / (tf + tb), "unit": UNIT + " (forward + reverse sweep)",
+            "loss": float(L.detach()), "grad_finite": bool(np.all(np.isfinite(g))),
+            "grad": [float(v) for v in g]}
+
+
+def profile_form(name: str) -> int:
+    """Short runs of one form for profiler captures: the 64-cavity batch for 64 steps in a fixed
+    launch shape (C = 8, 256 threads), or 16 steps of the 2048^2 differentiation form forward and
+    reverse (checkpoints every 8 steps: about 2 GB of device memory)."""
+    import torch
+    from paper_2505_23963_gb300 import fdtdbath as fb
+    torch.cuda.set_device(0)
+    if name == "batch":
+        b = fb.Batch(wl.batch_sweep(steps=64), precision=32, energy_every=10, cluster_ctas=8,
+                     block_threads=256, use_graph=False)
+        b.step(64)
+        b.sync()
+        print(json.dumps({"form": "batch", "steps": 64, **b.shape()}), flush=True)
+        b.close()
+        return 0
+    from paper_2505_23963_gb300 import adjoint as adj
+    prob = wl.adjoint_2d(steps=16)
+    p0 = adj.layer_params(prob, 1)
+    x = torch.tensor(p0, dtype=torch.float64, requires_grad=True)
+    nf = len(prob["monitors"][0]["freqs"])
+    L = adj.transmission_loss(x, prob, 1, np.ones(nf), np.zeros(nf), 16, 8, 32)
+    L.backward()
+    print(json.dumps({"form": "adjoint", "steps": 16, "grad_finite": bool(np.all(np.isfinite(x.grad.numpy())))}),
+          flush=True)
+    return 0
+
+
+def _flux(spec):
+    return np.real(spec[:, 0] * np.conj(spec[:, 3]) - spec[:, 1] * np.conj(spec[:, 2]))
 
 
 def run_ours(args):
@@ -347,6 +511,16 @@ def run_ours(args):
         "clocks": clocks,
         "finite": ok32,
     }
+    if ws == 1 and not args.no_forms:
+        forms = {}
+        for name, fn in (("precision", lambda: form_precision(fb, stream, torch)),
+                         ("batch", lambda: form_batch(fb, torch)),
+                         ("adjoint", lambda: form_adjoint(fb, torch))):
+            try:
+                forms[name] = fn()
+            except Exception as exc:   # reported, not hidden: the line says which form failed
+                forms[name] = {"error": f"{type(exc).__name__}: {exc}"}
+        line["forms"] = forms
     if rank == 0:
         print(json.dumps(line), flush=True)
     if ws > 1:
@@ -363,14 +537,20 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--ref-ny", type=int, default=8, help="y rows of the reference arm's sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-forms", action="store_true",
+                    help="skip the precision / batching / differentiation forms")
     ap.add_argument("--quick", action="store_true",
                     help="FP32 step timing only (for profiler captures)")
     ap.add_argument("--grid", default="", help="override nx,ny of the workload (profiling)")
+    ap.add_argument("--profile-form", default="", choices=["", "batch", "adjoint"],
+                    help="run a short version of one form only (for profiler captures)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.profile_form:
+        return profile_form(args.profile_form)
     return run_ours(args)
 
 

@@ -3,10 +3,11 @@
 Plain numpy on recorded traces (any producer: the CUDA library or the CPU oracle), not part of
 the simulated path.  Definitions (the paper shows energy traces but fixes no estimator):
 
-* gamma_pol: U_cav(t) is the electromagnetic energy inside the cavity's energy box.  After the
-  source has ended (t > 2 t0) take the local maxima of U_cav, fit ln U_cav at those maxima by
-  least squares against t, and report minus the slope (an energy decay rate, 1/time).  With
-  fewer than three maxima the fit uses every record after 2 t0.
+* gamma_pol: U_cav(t) is the electromagnetic energy inside the cavity's energy box.  From the
+  largest value of U_cav after the source has ended (t > 2 t0) -- the pulse needs time to reach
+  and fill a long cavity -- take the local maxima of U_cav, fit ln U_cav at those maxima by least
+  squares against t, and report minus the slope (an energy decay rate, 1/time).  With fewer than
+  three maxima the fit uses every record from that point on.
 * bath_share: the largest fraction of the box energy held by the bath modes after the source,
   max_t U_bath / (U_EM + U_P + U_bath).
 """
@@ -20,7 +21,11 @@ def relaxation_rate(trace: np.ndarray, dt_record: float, t_start: float) -> floa
     t = r * dt_record), using records after t_start."""
     u = np.asarray(trace, dtype=np.float64)[:, 0]
     t = np.arange(u.size) * dt_record
-    keep = (t > t_start) & (u > 0)
+    after = np.nonzero(t > t_start)[0]
+    if after.size == 0:
+        return float("nan")
+    top = after[np.argmax(u[after])]
+    keep = (np.arange(u.size) >= top) & (u > 0)
     idx = np.nonzero(keep)[0]
     if idx.size < 3:
         return float("nan")

@@ -31,6 +31,7 @@ constexpr int kBatchMaxThreads = 1024;
 constexpr int kBatchMaxWarps = kBatchMaxThreads / 32;
 constexpr int kBatchMaxCluster = 16;
 constexpr int kBatchChunk = 32;     // steps between the kernel's global-memory exchanges
+constexpr int kBatchMaxCellsPerThread = 16;   // cells of one Lorentz-Bath run per thread
 
 enum BatchRunKind { kRunVacuum = 0, kRunOsc = 1, kRunBath = 2 };
 

@@ -16,12 +16,10 @@
 //            updates (Eq. Pz_update-LB, Yzj_finite_difference).  H does not read P, so the bath
 //            work shares the phase with H and needs no barrier of its own.
 // Cells are dealt to threads round-robin over the CTA's whole range (cell l to thread l mod T),
-// so per-run remainders do not pile up on the first threads.  A Lorentz-Bath cell is updated by
-// a group of G lanes (G = N_b rounded up to a power of two, <= 32), one bath mode per lane: each
-// lane keeps its mode's coefficients in registers for the whole run, the bath sum
-// sum_j k_j (...) is a butterfly reduction within the group, and every lane of the group
-// evaluates the (identical) P update.  Bath state is laid out [level][cell][mode] so a group
-// reads consecutive words.  Two-level recursions swap level slots by step parity.
+// so per-run remainders do not pile up on the first threads.  A thread updates the bath of its
+// Lorentz-Bath cells mode by mode (the mode's coefficients read once, the cells' bath sums in
+// registers); bath state is laid out [level][mode][cell], so a warp reads consecutive words.
+// Two-level recursions swap level slots by step parity.
 //
 // Energy records (every `every` steps): per segment of the CTA, the box sums of eps E^2, of the
 // oscillator energy rho/dt^2 ((P^{n+3/2}-P^{n+1/2})^2 + (w0 dt)^2 P^2), of the bath energy and of
@@ -61,7 +59,7 @@ struct BatchCtx {
 // l: this thread's next cell (cell l belongs to thread l mod T); runs are contiguous, so the
 // cursor left by one run is the thread's first cell of the next.
 template <typename T, bool INC, int KIND>
-__device__ __forceinline__ void batch_phase_a(const BatchRun& R, const BatchSeg& G, const MatK<T>* smat,
+__device__ __forceinline__ void batch_phase_a(const BatchRun R, const BatchSeg G, const MatK<T>* smat,
                                               const BatchCtx<T>& c, T J, bool en, T& a0, T& a1, int& l) {
   const int len = R.l1 - R.l0;
   const T S = c.S, dt = c.dt;
@@ -89,7 +87,7 @@ __device__ __forceinline__ void batch_phase_a(const BatchRun& R, const BatchSeg&
       if (src) e = e + dt * J;
       if (en && R.inbox) a0 += e * e;
     } else {
-      const MatK<T>& M = smat[R.mslot];
+      const MatK<T> M = smat[R.mslot];            // by value: registers, not shared-memory reloads
       T* Pc = c.sm + R.p0 + c.par * len;          // P^{n+1/2}
       T* Po = c.sm + R.p0 + (c.par ^ 1) * len;    // P^{n-1/2}, receives P^{n+3/2}
       const T Pa = Pc[i], Pb = Po[i];
@@ -126,7 +124,7 @@ __device__ __forceinline__ void batch_phase_a(const BatchRun& R, const BatchSeg&
 
 // Phase B, H half-step of one run.
 template <typename T>
-__device__ __forceinline__ void batch_phase_h(const BatchRun& R, const BatchSeg& G, const BatchCtx<T>& c,
+__device__ __forceinline__ void batch_phase_h(const BatchRun R, const BatchSeg G, const BatchCtx<T>& c,
                                               bool en, T& a3, int& l) {
   const T S = c.S;
   const int nt = (int)blockDim.x;
@@ -150,84 +148,91 @@ __device__ __forceinline__ void batch_phase_h(const BatchRun& R, const BatchSeg&
   }
 }
 
-// Phase B, Lorentz-Bath polarization and bath update of one run, GS lanes per cell.
-template <typename T, bool INC, int GS>
-__device__ __forceinline__ void batch_phase_bath(const BatchRun& R, const MatK<T>* smat, const BatchCtx<T>& c,
+// Phase B, Lorentz-Bath polarization and bath update of one run.  The thread owns the run's cells
+// i = i0 + k T (k < K <= KMAX), the same cells as in the other phases.  Modes are the outer loop so
+// each mode's coefficient row is read once per thread; per-cell bath sums live in registers.  The
+// sums run over j in ascending order, the order of Eq. Pz_update-LB as the FP64 oracle evaluates it.
+template <typename T, bool INC, int KMAX>
+__device__ __forceinline__ void batch_phase_bath(const BatchRun R, const MatK<T>* smat, const BatchCtx<T>& c,
                                                  bool en, T& a1, T& a2) {
-  const int len = R.l1 - R.l0, nb = R.nb;
-  const int lane = (int)threadIdx.x & 31, warp = (int)threadIdx.x >> 5, nwarp = (int)blockDim.x >> 5;
-  constexpr int CPW = 32 / GS;   // cells per warp pass
-  const int j = lane % GS;       // this lane's bath mode
-  const bool mode = j < nb;
-  const MatK<T>& M = smat[R.mslot];
-  // this lane's coefficient row, kept in registers for the run
-  T cf0 = T(0), cf1 = T(0), cf2 = T(0), cf3 = T(0), cf4 = T(0), cf5 = T(0);
-  if (mode) {
-    const T* cf = c.coef + (M.coef_off + j) * kCoefStride;
-    cf0 = cf[0];
-    cf1 = cf[1];
-    cf2 = cf[2];
-    cf3 = cf[3];
-    cf4 = cf[4];
-    cf5 = cf[5];
-  }
+  const int len = R.l1 - R.l0, nb = R.nb, nt = (int)blockDim.x;
+  int i0 = ((int)threadIdx.x - R.l0) % nt;
+  if (i0 < 0) i0 += nt;
+  const int K = i0 < len ? (len - 1 - i0) / nt + 1 : 0;
+  const MatK<T> M = smat[R.mslot];
+  const T* cfm = c.coef + M.coef_off * kCoefStride;
   const T dt = c.dt;
   T* Pc = c.sm + R.p0 + c.par * len;
   T* Po = c.sm + R.p0 + (c.par ^ 1) * len;
-  T* Yc = c.sm + R.y0 + c.par * len * nb;           // Y^{n+1/2}   [cell][mode]
-  T* Yo = c.sm + R.y0 + (c.par ^ 1) * len * nb;     // Y^{n-1/2}, receives Y^{n+3/2}
-  for (int g = warp; g * CPW < len; g += nwarp) {
-    const int i = g * CPW + lane / GS;
-    const bool cell = i < len;
-    const bool act = cell && mode;
-    T e = T(0), Pa = T(0), Pb = T(0), y = T(0), ym = T(0);
-    if (cell) {
-      e = c.sE[R.l0 + i];
-      Pa = Pc[i];
-      Pb = Po[i];
-    }
-    if (act) {
-      y = Yc[i * nb + j];
-      ym = Yo[i * nb + j];
-    }
-    // bath sum over the group's lanes
-    T term;
-    if (!INC) term = cf0 * (cf1 * y + cf2 * ym);      // k_j (a_j Y^n + b_j Y^{n-1})
-    else term = cf0 * y + cf1 * (y - ym);             // k_j ((a_j+b_j) Y - b_j V)
-#pragma unroll
-    for (int o = GS / 2; o > 0; o >>= 1) term += __shfl_xor_sync(0xffffffffu, term, o, GS);
-    const T bsum = term;
-    T Pn, Vn, V0;
-    if (!INC) {
-      T num = M.cE * e - M.c1m * Pa - M.c2 * Pb;
-      num = num - T(0.5) * dt * bsum;
-      Pn = M.inv_A * num;
-      Vn = Pn - Pa;
-      V0 = Pa - Pb;
-    } else {
-      V0 = Pa - Pb;
-      T num = M.cE * e - M.W * Pa + M.c2 * V0;
-      num = num - T(0.5) * dt * bsum;
-      Vn = num * M.inv_A;
-      Pn = Pa + Vn;
-    }
-    if (act) {
-      T Yn, Vy;
-      if (!INC) {
-        Yn = cf1 * y + cf3 * ym + cf4 * (Pn - Pb);
-        Vy = Yn - y;
-      } else {
-        Vy = cf2 * y + cf3 * (y - ym) + cf4 * (Vn + V0);
-        Yn = y + Vy;
+  const T* Yc = c.sm + R.y0 + c.par * nb * len;   // Y^{n+1/2}   [mode][cell]
+  T* Yo = c.sm + R.y0 + (c.par ^ 1) * nb * len;   // Y^{n-1/2}, receives Y^{n+3/2}
+  T ub = T(0);
+  for (int kb = 0; kb < K; kb += KMAX) {   // blocks of KMAX cells of this thread
+    const int Kc = min(KMAX, K - kb);
+    T acc[KMAX];
+  #pragma unroll
+    for (int k = 0; k < KMAX; ++k) acc[k] = T(0);
+    for (int j = 0; j < nb; ++j) {
+      const T* cf = cfm + j * kCoefStride;
+      const T c0 = cf[0], c1 = cf[1], c2 = cf[2];
+  #pragma unroll
+      for (int k = 0; k < KMAX; ++k) {
+        if (k < Kc) {
+          const int i = i0 + (kb + k) * nt;
+          const T y = Yc[j * len + i], ym = Yo[j * len + i];
+          if (!INC) acc[k] = acc[k] + c0 * (c1 * y + c2 * ym);   // k_j (a_j Y^n + b_j Y^{n-1})
+          else acc[k] = acc[k] + (c0 * y + c1 * (y - ym));       // k_j ((a_j+b_j) Y - b_j V)
+        }
       }
-      Yo[i * nb + j] = Yn;
-      if (en && R.inbox) a2 += M.rho_idt2 * (Vy * Vy + cf5 * Yn * Yn);
     }
-    if (cell && j == 0) {
-      Po[i] = Pn;
-      if (en && R.inbox) a1 += M.rho_idt2 * (Vn * Vn + M.w0r2dt2 * Pn * Pn);
+    // polarization; acc becomes the increment P^{n+3/2} - P^{n-1/2} the bath update needs
+  #pragma unroll
+    for (int k = 0; k < KMAX; ++k) {
+      if (k < Kc) {
+        const int i = i0 + (kb + k) * nt;
+        const T e = c.sE[R.l0 + i], Pa = Pc[i], Pb = Po[i];
+        T Pn, Vn;
+        if (!INC) {
+          T num = M.cE * e - M.c1m * Pa - M.c2 * Pb;
+          num = num - T(0.5) * dt * acc[k];
+          Pn = M.inv_A * num;
+          Vn = Pn - Pa;
+          acc[k] = Pn - Pb;
+        } else {
+          const T V0 = Pa - Pb;
+          T num = M.cE * e - M.W * Pa + M.c2 * V0;
+          num = num - T(0.5) * dt * acc[k];
+          Vn = num * M.inv_A;
+          Pn = Pa + Vn;
+          acc[k] = Vn + V0;
+        }
+        Po[i] = Pn;
+        if (en && R.inbox) a1 += M.rho_idt2 * (Vn * Vn + M.w0r2dt2 * Pn * Pn);
+      }
+    }
+    for (int j = 0; j < nb; ++j) {
+      const T* cf = cfm + j * kCoefStride;
+      const T c1 = cf[1], c2 = cf[2], c3 = cf[3], c4 = cf[4], c5 = cf[5];
+  #pragma unroll
+      for (int k = 0; k < KMAX; ++k) {
+        if (k < Kc) {
+          const int i = i0 + (kb + k) * nt;
+          const T y = Yc[j * len + i], ym = Yo[j * len + i];
+          T Yn, Vy;
+          if (!INC) {
+            Yn = c1 * y + c3 * ym + c4 * acc[k];
+            Vy = Yn - y;
+          } else {
+            Vy = c2 * y + c3 * (y - ym) + c4 * acc[k];
+            Yn = y + Vy;
+          }
+          Yo[j * len + i] = Yn;
+          if (en) ub += Vy * Vy + c5 * Yn * Yn;
+        }
+      }
     }
   }
+  if (en && R.inbox) a2 += M.rho_idt2 * ub;
 }
 
 template <typename T>
@@ -339,8 +344,8 @@ __global__ void __launch_bounds__(kBatchMaxThreads) batch1d_kernel(const BatchPa
       const int64_t yg = M.ybase + (G.z0 + (R.l0 - G.l0) - M.zlo);
       for (int q = t; q < len * R.nb; q += nt) {
         const int j = q / len, i = q - j * len;
-        c.sm[R.y0 + i * R.nb + j] = p.Y0[yg + (int64_t)j * M.ncell + i];
-        c.sm[R.y0 + (len + i) * R.nb + j] = p.Y1[yg + (int64_t)j * M.ncell + i];
+        c.sm[R.y0 + q] = p.Y0[yg + (int64_t)j * M.ncell + i];
+        c.sm[R.y0 + R.nb * len + q] = p.Y1[yg + (int64_t)j * M.ncell + i];
       }
     }
   }
@@ -377,7 +382,7 @@ __global__ void __launch_bounds__(kBatchMaxThreads) batch1d_kernel(const BatchPa
         T a0 = T(0), a1 = T(0);
         int cur = -1, l = t;
         for (int r = 0; r < nrun; ++r) {
-          const BatchRun& R = srun[r];
+          const BatchRun R = srun[r];
           if (en && R.seg != cur) {
             if (cur >= 0) {
               a0 = warp_sum(a0);
@@ -390,7 +395,7 @@ __global__ void __launch_bounds__(kBatchMaxThreads) batch1d_kernel(const BatchPa
             cur = R.seg;
             a0 = a1 = T(0);
           }
-          const BatchSeg& G = sseg[R.seg];
+          const BatchSeg G = sseg[R.seg];
           const T J = sJ[k][R.seg];
           if (R.kind == kRunVacuum) batch_phase_a<T, INC, kRunVacuum>(R, G, smat, c, J, en, a0, a1, l);
           else if (R.kind == kRunOsc) batch_phase_a<T, INC, kRunOsc>(R, G, smat, c, J, en, a0, a1, l);
@@ -418,7 +423,7 @@ __global__ void __launch_bounds__(kBatchMaxThreads) batch1d_kernel(const BatchPa
         T a1 = T(0), a2 = T(0), a3 = T(0);
         int cur = -1, l = t;
         for (int r = 0; r < nrun; ++r) {
-          const BatchRun& R = srun[r];
+          const BatchRun R = srun[r];
           if (en && R.seg != cur) {
             if (cur >= 0) {
               a1 = warp_sum(a1);
@@ -435,10 +440,11 @@ __global__ void __launch_bounds__(kBatchMaxThreads) batch1d_kernel(const BatchPa
           }
           batch_phase_h<T>(R, sseg[R.seg], c, en, a3, l);
           if (R.kind == kRunBath) {
-            if (R.nb <= 4) batch_phase_bath<T, INC, 4>(R, smat, c, en, a1, a2);
-            else if (R.nb <= 8) batch_phase_bath<T, INC, 8>(R, smat, c, en, a1, a2);
-            else if (R.nb <= 16) batch_phase_bath<T, INC, 16>(R, smat, c, en, a1, a2);
-            else batch_phase_bath<T, INC, 32>(R, smat, c, en, a1, a2);
+            const int kc = (R.l1 - R.l0 + nt - 1) / nt;   // cells of the run per thread
+            if (kc <= 2) batch_phase_bath<T, INC, 2>(R, smat, c, en, a1, a2);
+            else if (kc <= 4) batch_phase_bath<T, INC, 4>(R, smat, c, en, a1, a2);
+            else if (kc <= 8) batch_phase_bath<T, INC, 8>(R, smat, c, en, a1, a2);
+            else batch_phase_bath<T, INC, kBatchMaxCellsPerThread>(R, smat, c, en, a1, a2);
           }
         }
         if (en && cur >= 0) {
@@ -504,8 +510,8 @@ __global__ void __launch_bounds__(kBatchMaxThreads) batch1d_kernel(const BatchPa
       const int64_t yg = M.ybase + (G.z0 + (R.l0 - G.l0) - M.zlo);
       for (int q = t; q < len * R.nb; q += nt) {
         const int j = q / len, i = q - j * len;
-        p.Y0[yg + (int64_t)j * M.ncell + i] = c.sm[R.y0 + (c.par * len + i) * R.nb + j];
-        p.Y1[yg + (int64_t)j * M.ncell + i] = c.sm[R.y0 + ((c.par ^ 1) * len + i) * R.nb + j];
+        p.Y0[yg + (int64_t)j * M.ncell + i] = c.sm[R.y0 + c.par * R.nb * len + q];
+        p.Y1[yg + (int64_t)j * M.ncell + i] = c.sm[R.y0 + (c.par ^ 1) * R.nb * len + q];
       }
     }
   }
