@@ -477,7 +477,7 @@ def run_ours(args):
             with open(os.path.join(ROOT, "paper_2505_23963_gb300", "csrc", "step3d.cuh"), "rb") as f:
                 cur = hashlib.sha256(f.read()).hexdigest()[:16]
             # counters describe the kernel they were taken on: none once it has changed
-            traffic = rec.get("dram_bytes_per_launch") if rec.get("source_sha256_16") == cur else None
+            traffic = rec.get("dram_bytes_per_step") if rec.get("source_sha256_16") == cur else None
         except Exception:
             traffic = None
 

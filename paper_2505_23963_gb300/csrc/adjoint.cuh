@@ -27,6 +27,8 @@
 //   dL/dgamma0 += P_bar_new (dt/2) (P_m - P_new) / A
 //   dL/dk_j    += P_bar_new (dt/2)/A [dS/dk_j (P_m - P_new) - (a_j Y_j + b_j Y_m,j)] + Y_bar_new,j dc_j/dk_j (P_new - P_m)
 // with S = sum_j k_j c_j, dS/dk_j = k_j dt/(1 + gamma_j dt/2), dc_j/dk_j = dt/(2 (1 + gamma_j dt/2)).
+// These terms are summed in the state precision within a thread and a warp (FP64 arithmetic is
+// slow on this part), then in FP64 across warps, blocks and steps.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -64,9 +66,11 @@ __global__ void __launch_bounds__(kAdjThreads) adjoint_k1(const AdjParams<T> p) 
   const bool own = q < p.ncell;
   const int64_t N = p.ncell, plane = p.plane;
   const int nx = p.nx, ny = p.ny, nz = p.nz;
-  double gsig = 0.0, ggam = 0.0, gk[NBA];
+  // gradient terms: summed in the state precision over a thread's components and a warp's cells,
+  // in FP64 from the warp partials on
+  T gsig = T(0), ggam = T(0), gk[NBA];
 #pragma unroll
-  for (int j = 0; j < NBA; ++j) gk[j] = 0.0;
+  for (int j = 0; j < NBA; ++j) gk[j] = T(0);
   if (own) {
     const int k = (int)(q / plane);
     const int r = (int)(q - (int64_t)k * plane);
@@ -168,17 +172,17 @@ __global__ void __launch_bounds__(kAdjThreads) adjoint_k1(const AdjParams<T> p) 
           }
           if (grad) {
             const int64_t ig = (int64_t)c * M.ncell + rm;
-            const double E = (double)p.fE[ig], Pn = (double)p.fPn[ig], Pm = (double)p.fPm[ig];
-            const double pnd = (double)pn;
-            gsig += pnd * p.dcE * E * p.invA;
-            ggam += pnd * p.halfdt * (Pm - Pn) * p.invA;
+            const T E = p.fE[ig], Pn = p.fPn[ig], Pm = p.fPm[ig];
+            const T hA = T(p.halfdt * p.invA);
+            gsig += pn * E * T(p.dcE * p.invA);
+            ggam += pn * hA * (Pm - Pn);
 #pragma unroll
             for (int jj = 0; jj < NBA; ++jj) {
               if (jj < nb) {
                 const int64_t iy = ((int64_t)c * nb + jj) * M.ncell + rm;
-                const double Y = (double)p.fY[iy], Ym = (double)p.fYm[iy];
-                gk[jj] += pnd * p.halfdt * p.invA * (p.gds[jj] * (Pm - Pn) - (p.ga[jj] * Y + p.gb[jj] * Ym)) +
-                          (double)ynb[jj] * p.gdc[jj] * (Pn - Pm);
+                const T Y = p.fY[iy], Ym = p.fYm[iy];
+                gk[jj] += pn * hA * (T(p.gds[jj]) * (Pm - Pn) - (T(p.ga[jj]) * Y + T(p.gb[jj]) * Ym)) +
+                          ynb[jj] * T(p.gdc[jj]) * (Pn - Pm);
               }
             }
           }
@@ -229,10 +233,10 @@ __global__ void __launch_bounds__(kAdjThreads) adjoint_k1(const AdjParams<T> p) 
 #pragma unroll
       for (int t = 0; t < 2 + NBA; ++t) {
         if (t < np) {
-          double v = t == 0 ? gsig : (t == 1 ? ggam : gk[t - 2 < NBA ? t - 2 : 0]);
+          T v = t == 0 ? gsig : (t == 1 ? ggam : gk[t - 2 < NBA ? t - 2 : 0]);
 #pragma unroll
           for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-          if (lane == 0) sg[warp][t] = v;
+          if (lane == 0) sg[warp][t] = (double)v;
         }
       }
       __syncthreads();
