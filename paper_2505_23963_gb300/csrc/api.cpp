@@ -296,6 +296,7 @@ Step3DParams<T> make_params(fdtdbath_sim* s, int doH, int doE) {
   p.zstart = (const int*)s->zstart;
   p.chunk_ids = (const int*)s->chunk_ids;
   p.nchunks_total = s->nchunks;
+  p.nbxy = s->nbx * s->nby;
   p.vec16 = (s->nx % (int64_t)(16 / sizeof(T)) == 0) ? 1 : 0;
   return p;
 }

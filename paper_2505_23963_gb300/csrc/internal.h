@@ -100,6 +100,7 @@ struct Step3DParams {
   const int* zstart;      // [nchunks_total + 1]
   const int* chunk_ids;
   int nchunks_total;
+  int nbxy;               // partial-sum slots per z-chunk (the (x, y) tiles of the 32 x 8 tiling)
   int vec16;              // nx is a multiple of 16 bytes' worth of elements: 16-byte staging
 };
 

@@ -50,14 +50,16 @@ __device__ __forceinline__ int psiH_plane(int k, int nz, int npml) {
   return -1;
 }
 
-// Fixed-order block reduction of a double; the result is valid in thread 0.
-__device__ __forceinline__ double block_sum(double v, double* scratch) {
+// Fixed-order block reduction; the result (FP64) is valid in thread 0.  Within a warp the sum runs
+// in the argument's precision (FP64 arithmetic is slow on this part), across warps in FP64.
+template <typename V>
+__device__ __forceinline__ double block_sum(V v, double* scratch) {
   const int tid = threadIdx.y * blockDim.x + threadIdx.x;
   const int nw = (blockDim.x * blockDim.y) >> 5;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
   __syncthreads();
-  if ((tid & 31) == 0) scratch[tid >> 5] = v;
+  if ((tid & 31) == 0) scratch[tid >> 5] = (double)v;
   __syncthreads();
   double s = 0.0;
   if (tid == 0)
@@ -209,9 +211,21 @@ step3d_kernel(const Step3DParams<T> p) {
   const int plane = (int)p.plane, ncell = (int)p.ncell;
   const int qxy = own ? j * p.nx + i : 0;
   const T dt = p.dt, S = p.S;
-  const int nbxy = gridDim.x * gridDim.y;
-  const int bxy = blockIdx.y * gridDim.x + blockIdx.x;
-  const int blin = chunk * nbxy + bxy;   // unique over the launches of one step
+  // partial-sum slots: p.nbxy per z-chunk and quantity, one per tile of the 32 x TYS tiling
+  // (TYS = 8, or 1 for grids with fewer than 8 rows) whatever this launch's tile height: a block of
+  // a taller tile writes its sum into the slot of its first TYS-row tile and zero into the others,
+  // so every slot of a chunk is rewritten by whichever kernel processes the chunk
+  constexpr int TYS = TY >= 8 ? 8 : TY;
+  constexpr int RS = TY / TYS;                       // slots per block (rows of TYS-row tiles)
+  const int nbxy = p.nbxy;
+  const int nrow_s = nbxy / gridDim.x;               // TYS-row tiles along y
+  const int bxy = (blockIdx.y * RS) * gridDim.x + blockIdx.x;
+  auto put_slot = [&](double* row, double v) {      // row: slot 0 of this chunk's quantity
+    row[bxy] = v;
+#pragma unroll
+    for (int r = 1; r < RS; ++r)
+      if ((int)blockIdx.y * RS + r < nrow_s) row[bxy + r * (int)gridDim.x] = 0.0;
+  };
   const T* __restrict__ Ein = p.Ein;
   const T* __restrict__ Hin = p.Hin;
 
@@ -494,8 +508,8 @@ step3d_kernel(const Step3DParams<T> p) {
           double sx = block_sum((double)vx, sred);
           double sy = block_sum((double)vy, sred);
           if (tid == 0 && p.mon_partial_H) {
-            p.mon_partial_H[(int64_t)(4 * m + off) * nbxy + bxy] = sx;
-            p.mon_partial_H[(int64_t)(4 * m + 2 + off) * nbxy + bxy] = sy;
+            put_slot(p.mon_partial_H + (int64_t)(4 * m + off) * nbxy, sx);
+            put_slot(p.mon_partial_H + (int64_t)(4 * m + 2 + off) * nbxy, sy);
           }
         }
       }
@@ -677,8 +691,8 @@ step3d_kernel(const Step3DParams<T> p) {
           double sx = block_sum(own ? (double)Ev[0] : 0.0, sred);
           double sy = block_sum(own ? (double)Ev[1] : 0.0, sred);
           if (tid == 0 && p.mon_partial_E) {
-            p.mon_partial_E[(int64_t)(2 * m) * nbxy + bxy] = sx;
-            p.mon_partial_E[(int64_t)(2 * m + 1) * nbxy + bxy] = sy;
+            put_slot(p.mon_partial_E + (int64_t)(2 * m) * nbxy, sx);
+            put_slot(p.mon_partial_E + (int64_t)(2 * m + 1) * nbxy, sy);
           }
         }
       }
@@ -688,25 +702,25 @@ step3d_kernel(const Step3DParams<T> p) {
   }
   // energy partials of this block (every block writes, zero when outside the box)
   if (p.eE_on) {
-    double a = block_sum((double)uE, sred);
-    double b = block_sum((double)uP, sred);
-    double c = block_sum((double)uB, sred);
+    double a = block_sum(uE, sred);
+    double b = block_sum(uP, sred);
+    double c = block_sum(uB, sred);
     if (tid == 0) {
-      p.en_partial_E[blin] = a;
-      p.en_partial_E[(int64_t)nbxy * p.nchunks_total + blin] = b;
-      p.en_partial_E[(int64_t)2 * nbxy * p.nchunks_total + blin] = c;
+      put_slot(p.en_partial_E + (int64_t)chunk * nbxy, a);
+      put_slot(p.en_partial_E + ((int64_t)nbxy * p.nchunks_total + chunk * nbxy), b);
+      put_slot(p.en_partial_E + ((int64_t)2 * nbxy * p.nchunks_total + chunk * nbxy), c);
     }
   }
   if (p.eH_on) {
-    double a = block_sum((double)uH, sred);
-    if (tid == 0) p.en_partial_H[blin] = a;
+    double a = block_sum(uH, sred);
+    if (tid == 0) put_slot(p.en_partial_H + (int64_t)chunk * nbxy, a);
   }
 }
 
 inline size_t step3d_smem_bytes(int ty, int nmodes, size_t elem) {
   const size_t fe = (size_t)(ty + 2) * (kTX + 8), fh = (size_t)(ty + 1) * (kTX + 4);
   const size_t n = (size_t)kRingE * 3 * fe + (size_t)(kRingH + 1) * 3 * fh + (size_t)kCoefStride * nmodes;
-  return n * elem + kMaxChunk * sizeof(int) + 16 + 8 * sizeof(double);
+  return n * elem + kMaxChunk * sizeof(int) + 16 + 8 * sizeof(double);   // block-sum scratch: a double per warp (<= 8)
 }
 
 }  // namespace fdtdbath
