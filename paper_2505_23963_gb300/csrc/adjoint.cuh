@@ -81,7 +81,7 @@ __global__ void __launch_bounds__(kAdjThreads) adjoint_k1(const AdjParams<T> p) 
     // adjoint of H^{n+1}, with this step's H-monitor source added on the fly
     auto Hb = [&](int c, int ii, int jj, int kk) -> T {
       if (kk < 0 || kk >= nz) return T(0);
-      T v = p.Hb[c * N + (int64_t)kk * plane + (int64_t)jj * nx + ii];
+      T v = __ldg(p.Hb + c * N + (int64_t)kk * plane + (int64_t)jj * nx + ii);   // read-only here
       if (p.zm >= 0 && (kk == p.zm - 1 || kk == p.zm)) {
         if (c == 0) v += hsrc * p.gHx;
         if (c == 1) v += hsrc * p.gHy;
@@ -98,9 +98,9 @@ __global__ void __launch_bounds__(kAdjThreads) adjoint_k1(const AdjParams<T> p) 
     const int64_t nph = (int64_t)(2 * p.npml + 1) * plane;
     if (kp >= 0) {
       const int64_t o = (int64_t)kp * plane + r;
-      const T px = p.psiHb[o] + S * hx;
-      const T py = p.psiHb[nph + o] - S * hy;
-      const T bH = p.pmlH[2 * k], cH = p.pmlH[2 * k + 1];
+      const T px = __ldg(p.psiHb + o) + S * hx;
+      const T py = __ldg(p.psiHb + nph + o) - S * hy;
+      const T bH = __ldg(p.pmlH + 2 * k), cH = __ldg(p.pmlH + 2 * k + 1);
       ey -= cH * px;
       ex -= cH * py;
       p.psiHb_out[o] = bH * px;
@@ -110,9 +110,9 @@ __global__ void __launch_bounds__(kAdjThreads) adjoint_k1(const AdjParams<T> p) 
       const int kpm = adj_psiH_plane(k - 1, nz, p.npml);
       if (kpm >= 0) {
         const int64_t o = (int64_t)kpm * plane + r;
-        const T px = p.psiHb[o] + S * Hb(0, i, j, k - 1);
-        const T py = p.psiHb[nph + o] - S * Hb(1, i, j, k - 1);
-        const T cH = p.pmlH[2 * (k - 1) + 1];
+        const T px = __ldg(p.psiHb + o) + S * Hb(0, i, j, k - 1);
+        const T py = __ldg(p.psiHb + nph + o) - S * Hb(1, i, j, k - 1);
+        const T cH = __ldg(p.pmlH + 2 * (k - 1) + 1);
         ey += cH * px;
         ex += cH * py;
       }
@@ -129,14 +129,20 @@ __global__ void __launch_bounds__(kAdjThreads) adjoint_k1(const AdjParams<T> p) 
         haveP = true;
         const int64_t rm = (int64_t)(k - M.zlo) * plane + r;
         const int nb = M.kind == kLorentzBath ? M.nb : 0;
-        const T* cfm = p.coefLit + M.coef_off * kCoefStride;
+        const T* __restrict__ cfm = p.coefLit + M.coef_off * kCoefStride;
         const bool grad = mi == p.gm;
+        // each of these adjoint arrays is read and then written at the same index by this thread
+        // only, and no two of them overlap
+        T* __restrict__ Pb_ = p.Pb;
+        T* __restrict__ Pmb_ = p.Pmb;
+        T* __restrict__ Y0_ = p.Yb0;
+        T* __restrict__ Y1_ = p.Yb1;
         T ec[3] = {ex, ey, ez};
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
           const int64_t ip = c * p.nmatcell + M.base + rm;
-          T pn = p.Pb[ip];           // adjoint of P^{n+3/2}
-          T pold = p.Pmb[ip];        // adjoint of P^{n+1/2} (the shift P_m <- P)
+          T pn = Pb_[ip];           // adjoint of P^{n+3/2}
+          T pold = Pmb_[ip];        // adjoint of P^{n+1/2} (the shift P_m <- P)
           T pmold = T(0);
           T yold[NBA], ymold[NBA], ynb[NBA];
           const int64_t yc = M.ybase + (int64_t)c * nb * M.ncell + rm;
@@ -147,43 +153,43 @@ __global__ void __launch_bounds__(kAdjThreads) adjoint_k1(const AdjParams<T> p) 
             ynb[jj] = T(0);
             if (jj < nb) {
               const T* cf = cfm + jj * kCoefStride;
-              const T yn = p.Yb0[yc + jj * M.ncell];   // adjoint of Y^{n+3/2}
+              const T yn = Y0_[yc + jj * M.ncell];                 // adjoint of Y^{n+3/2}
               ynb[jj] = yn;
-              yold[jj] = p.Yb1[yc + jj * M.ncell] + cf[1] * yn;   // shift + a_j
-              ymold[jj] = cf[3] * yn;                              // (b_j + 1)
-              pn += cf[4] * yn;                                    // c_j (P_new - P_m)
-              pmold -= cf[4] * yn;
+              yold[jj] = Y1_[yc + jj * M.ncell] + __ldg(cf + 1) * yn;   // shift + a_j
+              ymold[jj] = __ldg(cf + 3) * yn;                           // (b_j + 1)
+              const T c4 = __ldg(cf + 4);
+              pn += c4 * yn;                                            // c_j (P_new - P_m)
+              pmold -= c4 * yn;
             }
           }
           const T f = pn * M.inv_A;
           ec[c] += M.cE * f;
           pold += -M.c1m * f;
           pmold += -M.c2 * f;
-#pragma unroll
-          for (int jj = 0; jj < NBA; ++jj) {
-            if (jj < nb) {
-              const T* cf = cfm + jj * kCoefStride;
-              const T w = T(-0.5) * p.dt * cf[0] * f;   // -(dt/2) k_j / A * P_bar_new
-              yold[jj] += w * cf[1];
-              ymold[jj] += w * cf[2];
-              p.Yb0[yc + jj * M.ncell] = yold[jj];
-              p.Yb1[yc + jj * M.ncell] = ymold[jj];
-            }
-          }
+          // gradient terms first: they need pn and the incoming bath adjoints ynb
           if (grad) {
             const int64_t ig = (int64_t)c * M.ncell + rm;
-            const T E = p.fE[ig], Pn = p.fPn[ig], Pm = p.fPm[ig];
-            const T hA = T(p.halfdt * p.invA);
-            gsig += pn * E * T(p.dcE * p.invA);
+            const T E = __ldg(p.fE + ig), Pn = __ldg(p.fPn + ig), Pm = __ldg(p.fPm + ig);
+            const T hA = p.thA;
+            gsig += pn * E * p.tsig;
             ggam += pn * hA * (Pm - Pn);
 #pragma unroll
             for (int jj = 0; jj < NBA; ++jj) {
               if (jj < nb) {
                 const int64_t iy = ((int64_t)c * nb + jj) * M.ncell + rm;
-                const T Y = p.fY[iy], Ym = p.fYm[iy];
-                gk[jj] += pn * hA * (T(p.gds[jj]) * (Pm - Pn) - (T(p.ga[jj]) * Y + T(p.gb[jj]) * Ym)) +
-                          ynb[jj] * T(p.gdc[jj]) * (Pn - Pm);
+                const T Y = __ldg(p.fY + iy), Ym = __ldg(p.fYm + iy);
+                gk[jj] += pn * hA * (p.tds[jj] * (Pm - Pn) - (p.ta[jj] * Y + p.tb[jj] * Ym)) +
+                          ynb[jj] * p.tdc[jj] * (Pn - Pm);
               }
+            }
+          }
+#pragma unroll
+          for (int jj = 0; jj < NBA; ++jj) {
+            if (jj < nb) {
+              const T* cf = cfm + jj * kCoefStride;
+              const T w = T(-0.5) * p.dt * __ldg(cf) * f;   // -(dt/2) k_j / A * P_bar_new
+              Y0_[yc + jj * M.ncell] = yold[jj] + w * __ldg(cf + 1);
+              Y1_[yc + jj * M.ncell] = ymold[jj] + w * __ldg(cf + 2);
             }
           }
           Pold[c] = pold;

@@ -1383,7 +1383,13 @@ int adjoint_sweep(fdtdbath_sim* s, const HostMon& mon, const std::vector<double>
     p.gk[j] = G.kj[(size_t)j];
     p.gdc[j] = dt / (2.0 * den);
     p.gds[j] = G.kj[(size_t)j] * dt / den;
+    p.ta[j] = (T)p.ga[j];
+    p.tb[j] = (T)p.gb[j];
+    p.tdc[j] = (T)p.gdc[j];
+    p.tds[j] = (T)p.gds[j];
   }
+  p.tsig = (T)(p.dcE * p.invA);
+  p.thA = (T)(p.halfdt * p.invA);
   p.gpart = gpart;
   // every adjoint buffer starts at zero (dalloc zeroes them)
   const bool save_quiet = s->quiet;

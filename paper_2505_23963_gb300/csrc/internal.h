@@ -184,6 +184,9 @@ struct AdjParams {
   double dcE;               // d cE / d sigma = (w0 dt)^2
   double halfdt, invA;
   double ga[kMaxBath], gb[kMaxBath], gk[kMaxBath], gdc[kMaxBath], gds[kMaxBath];
+  // the same factors rounded once to the state type on the host, as the kernel uses them
+  T tsig, thA;              // (T)(dcE invA), (T)(halfdt invA)
+  T ta[kMaxBath], tb[kMaxBath], tdc[kMaxBath], tds[kMaxBath];
   double* gpart;            // [gridDim][kAdjMaxGrad] per-block running sums (FP64)
 };
 int launch_adjoint_f32(const AdjParams<float>& p, int nbmax, void* stream);
