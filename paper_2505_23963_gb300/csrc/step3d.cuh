@@ -600,8 +600,9 @@ step3d_kernel(const Step3DParams<T> p) {
             }
             Ev[c] = E;
             p.Eout[c * ncell + q] = E;
-            if (!mat_here) continue;
-            // ---- polarization (and bath) update ----
+            // bath modes already in registers: all three components together below
+            if (!mat_here || (NBP > 0 && bath)) continue;
+            // ---- polarization (and bath) update, one component at a time ----
             T Yl[NBA], Vl[NBA];
             const int nb = bath ? M.nb : 0;
             const int yc = c * M.nb * mstride;
@@ -675,6 +676,86 @@ step3d_kernel(const Step3DParams<T> p) {
               // rho/dt^2 (V^2 + (w0 dt)^2 P^2) = rho (V/dt)^2 + rho w0^2 P^2, likewise per mode
               uP += M.rho_idt2 * (Vn * Vn + M.w0r2dt2 * Pn * Pn);
               uB += M.rho_idt2 * ub;
+            }
+          }
+          if (NBP > 0 && bath && mat_here) {
+            // ---- polarization and bath update of the three components together, modes outer:
+            // each mode's coefficient row is read once for the three components; per component
+            // the arithmetic and its order are those of the loop above (sums over ascending j) ----
+            const int nb = M.nb;
+            T bsum[3] = {T(0), T(0), T(0)};
+#pragma unroll
+            for (int jj = 0; jj < (NBP > 0 ? NBP : 1); ++jj) {
+              if (jj < nb) {
+                T cf[6];
+                load_coef6(cfm + jj * kCoefStride, cf);
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                  const T y = rY[c][jj];
+                  if (!INC) {
+                    bsum[c] = bsum[c] + cf[0] * (cf[1] * y + cf[2] * rV[c][jj]);
+                  } else {
+                    if (!YB) rV[c][jj] = y - rV[c][jj];   // V_j = Y^n - Y^{n-1}
+                    bsum[c] = bsum[c] + (cf[0] * y + cf[1] * rV[c][jj]);
+                  }
+                }
+              }
+            }
+            T Pn[3], Vn[3], dP[3];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+              const T Pa = rPa[c], Pb = rPb[c];
+              T V0;
+              if (!INC) {
+                T num = M.cE * Ev[c] - M.c1m * Pa - M.c2 * Pb;
+                num = num - T(0.5) * dt * bsum[c];
+                Pn[c] = M.inv_A * num;
+                Vn[c] = Pn[c] - Pa;
+                V0 = Pa - Pb;
+              } else {
+                V0 = Pa - Pb;
+                T num = M.cE * Ev[c] - M.W * Pa + M.c2 * V0;
+                num = num - T(0.5) * dt * bsum[c];
+                Vn[c] = num * M.inv_A;
+                Pn[c] = Pa + Vn[c];
+              }
+              p.Pb[c * nmc + r] = Pn[c];   // overwrites P^{n-1}
+              dP[c] = Vn[c] + V0;          // P^{n+1} - P^{n-1}
+            }
+            T ub[3] = {T(0), T(0), T(0)};
+#pragma unroll
+            for (int jj = 0; jj < (NBP > 0 ? NBP : 1); ++jj) {
+              if (jj < nb) {
+                T cf[6];
+                load_coef6(cfm + jj * kCoefStride, cf);
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                  const int yo = c * nb * mstride + jj * mstride;
+                  const T y = rY[c][jj], v = rV[c][jj];
+                  T Ynew, Vy;
+                  if (!INC) {
+                    Ynew = cf[1] * y + cf[3] * v + cf[4] * (Pn[c] - rPb[c]);
+                    Vy = Ynew - y;
+                  } else {
+                    Vy = cf[2] * y + cf[3] * v + cf[4] * dP[c];
+                    Ynew = y + Vy;
+                  }
+                  if (YB) {
+                    YS::put(ya + yo, Ynew);
+                    YS::put(yb + yo, Vy);
+                  } else {
+                    YS::put(yb + yo, Ynew);
+                  }
+                  if (p.eE_on) ub[c] += Vy * Vy + cf[5] * Ynew * Ynew;
+                }
+              }
+            }
+            if (p.eE_on && in_box) {
+#pragma unroll
+              for (int c = 0; c < 3; ++c) {
+                uP += M.rho_idt2 * (Vn[c] * Vn[c] + M.w0r2dt2 * Pn[c] * Pn[c]);
+                uB += M.rho_idt2 * ub[c];
+              }
             }
           }
         }
