@@ -187,30 +187,44 @@ void cpml_bc(const fdtdbath_sim* s, double zpos, double* b, double* c) {
   cpml_coeffs(s->npml, s->nz, s->dx, s->dt, zpos, b, c);
 }
 
-// z-chunks of about zc planes.  Chunk starts avoid the CPML planes (the chunk-start H
-// recompute needs no CPML memory) and fall on every Lorentz-Bath layer boundary inside the
-// allowed range, so that a chunk holds either no bath plane or only bath planes (plus
-// whatever the boundary rule forces in).
-int plan_chunks(fdtdbath_sim* s, int zc, std::vector<int>& starts) {
+// Does any Lorentz-Bath layer with bath modes overlap planes [lo, hi)?
+bool chunk_has_bath(const fdtdbath_sim* s, int64_t lo, int64_t hi) {
+  for (auto& m : s->mats)
+    if (m.kind == FDTDBATH_LORENTZ_BATH && m.nb > 0 && m.zlo < hi && m.zhi > lo) return true;
+  return false;
+}
+
+// z-chunks.  Chunk starts avoid the CPML planes (the chunk-start H recompute needs no CPML
+// memory) and fall on every Lorentz-Bath layer boundary inside the allowed range, so that a chunk
+// holds either no bath plane or only bath planes (plus whatever the boundary rule forces in).
+// Between those cuts, a range of L planes is split into chunks of zc planes (uniform plan), or
+// (balanced plan) into a head chunk of ceil(3L/4) planes and a tail chunk of the rest: dispatched
+// longest first, the tail chunks of a launch fill its last partial wave of CTAs.
+int plan_chunks(fdtdbath_sim* s, int zc, bool balanced, std::vector<int>& starts) {
   starts.clear();
-  int64_t z = 0;
   starts.push_back(0);
   const int64_t lo_ok = s->npml + 1, hi_ok = s->nz - 1 - s->npml;
-  std::vector<int64_t> cuts;
+  std::vector<int64_t> bounds{0, s->nz};
   for (auto& m : s->mats)
     if (m.kind == FDTDBATH_LORENTZ_BATH) {
-      if (m.zlo >= lo_ok && m.zlo <= hi_ok) cuts.push_back(m.zlo);
-      if (m.zhi >= lo_ok && m.zhi <= hi_ok) cuts.push_back(m.zhi);
+      if (m.zlo >= lo_ok && m.zlo <= hi_ok) bounds.push_back(m.zlo);
+      if (m.zhi >= lo_ok && m.zhi <= hi_ok) bounds.push_back(m.zhi);
     }
-  while (z < s->nz) {
-    int64_t nx = z + zc;
-    for (int64_t c : cuts)
-      if (c > z && c < nx) nx = c;
-    if (nx < lo_ok) nx = lo_ok;
-    if (nx > hi_ok) nx = s->nz;
-    if (nx > s->nz) nx = s->nz;
-    starts.push_back((int)nx);
-    z = nx;
+  std::sort(bounds.begin(), bounds.end());
+  bounds.erase(std::unique(bounds.begin(), bounds.end()), bounds.end());
+  int64_t z = 0;
+  for (size_t b = 0; b + 1 < bounds.size(); ++b) {
+    const int64_t a = bounds[b], e = bounds[b + 1];
+    if (z >= e) continue;   // already covered by a chunk the boundary rule extended
+    const int64_t step = balanced ? std::max<int64_t>(1, (3 * (e - a) + 3) / 4) : zc;
+    while (z < e) {
+      int64_t nx = std::min(z + step, e);
+      if (nx < lo_ok) nx = lo_ok;
+      if (nx > hi_ok) nx = s->nz;
+      if (nx > s->nz) nx = s->nz;
+      starts.push_back((int)nx);
+      z = nx;
+    }
   }
   return (int)starts.size() - 1;
 }
@@ -787,10 +801,30 @@ int fdtdbath_create(const fdtdbath_grid* grid, double resolution, double courant
   s->ty = ny >= 8 ? 8 : 1;
   s->nbx = (int)((nx + kTX - 1) / kTX);
   s->nby = (int)((ny + s->ty - 1) / s->ty);
+  // balanced chunks when every launch still gets at least a full wave of CTAs (4 bath-free or 2
+  // bath CTAs per SM), otherwise uniform 32-plane chunks; FDTDBATH_ZCHUNK forces a uniform plan
   int zc = 32;
-  if (const char* e = std::getenv("FDTDBATH_ZCHUNK")) zc = std::min(64, std::max(1, std::atoi(e)));
+  bool balanced = true;
+  if (const char* e = std::getenv("FDTDBATH_ZCHUNK")) {
+    zc = std::min(64, std::max(1, std::atoi(e)));
+    balanced = false;
+  }
   std::vector<int> starts;
-  s->nchunks = plan_chunks(s, zc, starts);
+  if (balanced) {
+    int sms = 0;
+    balanced = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s->device) == cudaSuccess && sms > 0;
+    if (balanced) {
+      const int n = plan_chunks(s, zc, true, starts);
+      int64_t nplain = 0, nbath = 0;
+      for (int c = 0; c < n; ++c) {
+        if (starts[c + 1] - starts[c] > 128) balanced = false;
+        (chunk_has_bath(s, starts[c], starts[c + 1]) ? nbath : nplain) += 1;
+      }
+      const int64_t tiles = (int64_t)s->nbx * s->nby;
+      if ((nplain > 0 && nplain * tiles < 4LL * sms) || (nbath > 0 && nbath * tiles < 2LL * sms)) balanced = false;
+    }
+  }
+  s->nchunks = plan_chunks(s, zc, balanced, starts);
   for (size_t c = 0; c + 1 < starts.size(); ++c)
     if (starts[c + 1] - starts[c] > 128) return bail(FDTDBATH_ERR_ARG, "z-chunk longer than 128 planes");
   if ((int64_t)s->nbx * s->nby > 65535 * 64) return bail(FDTDBATH_ERR_ARG, "grid too large for the launch plan");
@@ -823,12 +857,11 @@ int fdtdbath_create(const fdtdbath_grid* grid, double resolution, double courant
   std::vector<int> ids;
   for (int c = 0; c < s->nchunks; ++c) ids.push_back(c);
   std::vector<int> plain, bathc;
-  for (int c = 0; c < s->nchunks; ++c) {
-    bool has_bath = false;
-    for (auto& m : s->mats)
-      if (m.kind == FDTDBATH_LORENTZ_BATH && m.nb > 0 && m.zlo < starts[c + 1] && m.zhi > starts[c]) has_bath = true;
-    (has_bath ? bathc : plain).push_back(c);
-  }
+  for (int c = 0; c < s->nchunks; ++c) (chunk_has_bath(s, starts[c], starts[c + 1]) ? bathc : plain).push_back(c);
+  // each launch dispatches its longest chunks first (blocks go out in grid order, chunk-major)
+  auto clen = [&](int c) { return starts[c + 1] - starts[c]; };
+  std::stable_sort(plain.begin(), plain.end(), [&](int a, int b) { return clen(a) > clen(b); });
+  std::stable_sort(bathc.begin(), bathc.end(), [&](int a, int b) { return clen(a) > clen(b); });
   s->nplain = (int)plain.size();
   s->nbath = (int)bathc.size();
   ids.insert(ids.end(), plain.begin(), plain.end());
