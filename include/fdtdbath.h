@@ -188,7 +188,12 @@ int fdtdbath_bath_form(int32_t shape, double frequency, double gamma, int32_t nu
                        double *gammas, double *couplings);
 
 /* Runtime facts of a simulation: key 0 element size of the state, 1 kernel launches issued
- * so far, 2 bytes of device memory held, 3 blocks of the 3D step kernel, 4 z-chunks. */
+ * so far, 2 bytes of device memory held, 3 blocks of the 3D step kernel, 4 z-chunks, 5 whether
+ * the step kernel runs the TE form (1) or the general form (0).  The TE form is taken by a
+ * y-invariant grid (ny = 1) whose sources all drive E_y (Sec. II.C, the 2D case): E_x, E_z, H_y,
+ * P_x, P_z and the x / z bath modes then stay exactly zero and are neither read nor written; the
+ * live components are bit-identical to the general form's.  A write_fields call on any of those
+ * components returns the simulation to the general form for good. */
 int64_t fdtdbath_query(const fdtdbath_sim *sim, int32_t key);
 
 /* Energy (U_EM, U_P, U_bath) of planes z_lo <= k < z_hi of the current state -- the same

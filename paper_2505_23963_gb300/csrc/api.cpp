@@ -125,6 +125,10 @@ struct fdtdbath_sim {
   int nblk3d = 1;                       // energy partials per step of the 3D kernel
   // quiet: steps record no monitor or energy partials (the adjoint's recomputed segments)
   bool quiet = false;
+  // y-invariant TE form: ny = 1 and every source on E_y, so E_x, E_z, H_y, P_x, P_z and the x / z
+  // bath modes stay exactly zero and the single-row kernels skip them; cleared for good when a
+  // write could make one of them nonzero
+  bool te = false;
   AdjState adj;
   std::string err;
 };
@@ -316,19 +320,19 @@ Step3DParams<T> make_params(fdtdbath_sim* s, int doH, int doE) {
 }
 
 int launch_typed(const Step3DParams<float>& p, int nbmax, int ty, int nbx, int nby, int n, bool ybf,
-                 cudaStream_t st) {
-  return launch_step3d_f32(p, nbmax, ty, nbx, nby, n, ybf ? 1 : 0, st);
+                 bool te, cudaStream_t st) {
+  return launch_step3d_f32(p, nbmax, ty, nbx, nby, n, ybf ? 1 : 0, te ? 1 : 0, st);
 }
 int launch_typed(const Step3DParams<double>& p, int nbmax, int ty, int nbx, int nby, int n, bool,
-                 cudaStream_t st) {
-  return launch_step3d_f64(p, nbmax, ty, nbx, nby, n, st);
+                 bool te, cudaStream_t st) {
+  return launch_step3d_f64(p, nbmax, ty, nbx, nby, n, te ? 1 : 0, st);
 }
 
 template <typename T>
 int launch_chunks(fdtdbath_sim* s, Step3DParams<T> p, int nbmax, int id_off, int n, cudaStream_t st) {
   p.chunk_ids = (const int*)s->chunk_ids + id_off;
   s->launches++;
-  return launch_typed(p, nbmax, s->ty, s->nbx, s->nby, n, s->ybf, st);
+  return launch_typed(p, nbmax, s->ty, s->nbx, s->nby, n, s->ybf, s->te && s->ty == 1, st);
 }
 
 // One step's launches: without a pending E half-step, or without bath chunks, one launch over
@@ -871,6 +875,9 @@ int fdtdbath_create(const fdtdbath_grid* grid, double resolution, double courant
       cudaEventCreateWithFlags(&s->ev_join, cudaEventDisableTiming) != cudaSuccess)
     return bail(FDTDBATH_ERR_CUDA, "stream/event creation failed");
   // 1D path: one cluster of up to 8 CTAs of 256 threads
+  s->te = ny == 1;
+  for (auto& q : s->srcs)
+    if (q.comp != 1) s->te = false;
   s->path1d = (nx == 1 && ny == 1 && nsrc <= 1 && nmon <= 1 && !s->ybf &&
                 nz <= (int64_t)kCav1DMaxCluster * kCav1DThreads);
   if (s->path1d) {
@@ -1067,6 +1074,8 @@ int fdtdbath_write_fields(fdtdbath_sim* s, int32_t field, const void* src, size_
   FieldRef f;
   if (!parse_field(field, &f)) return fail(s, FDTDBATH_ERR_ARG, "unknown field id");
   if (src_bytes < (size_t)s->ncell * s->esz) return fail(s, FDTDBATH_ERR_ARG, "source too small");
+  // the TE form carries only E_y, H_x, H_z and the y polarization / bath modes
+  if ((f.kind == 0 && f.comp != 1 && f.comp != 3 && f.comp != 5) || (f.kind != 0 && f.comp != 1)) s->te = false;
   {
     // the 1D kernel skips the y/z polarization while it provably stays zero
     const bool xpol = (f.kind == 0 && (f.comp == 0 || f.comp == 4)) || (f.kind != 0 && f.comp == 0);
@@ -1220,6 +1229,7 @@ int64_t fdtdbath_query(const fdtdbath_sim* s, int32_t key) {
     case 2: return (int64_t)s->bytes_held;
     case 3: return (int64_t)s->nbx * s->nby * s->nchunks;
     case 4: return s->nchunks;
+    case 5: return s->te && s->ty == 1 ? 1 : 0;
     default: return -1;
   }
 }

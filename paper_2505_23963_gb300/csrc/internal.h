@@ -142,10 +142,12 @@ int launch_cavity1d_f32(const Cav1DParams<float>& p, int nbmax, int cluster, voi
 int launch_cavity1d_f64(const Cav1DParams<double>& p, int nbmax, int cluster, void* stream);
 
 // Launchers (defined in step3d_f32.cu / step3d_f64.cu).
+// te = 1: the y-invariant TE form (ny = 1, sources on E_y only): E_x, E_z, H_y, P_x, P_z and the
+// x / z bath modes are known to be zero and are neither read nor written.
 int launch_step3d_f32(const Step3DParams<float>& p, int nbmax, int ty, int nbx, int nby,
-                      int nchunks, int bath_bf16, void* stream);
+                      int nchunks, int bath_bf16, int te, void* stream);
 int launch_step3d_f64(const Step3DParams<double>& p, int nbmax, int ty, int nbx, int nby,
-                      int nchunks, void* stream);
+                      int nchunks, int te, void* stream);
 
 // ---- discrete adjoint (adjoint.cu) ----
 // One reverse step of the exact transpose of the forward step (D-free form), applied to the

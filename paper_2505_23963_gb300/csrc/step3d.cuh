@@ -173,9 +173,16 @@ struct StepBounds {
   static constexpr int min_blocks = TY == 8 ? (NBMAX == 0 ? (sizeof(T) == 4 ? 4 : 2) : ((sizeof(T) == 8 && NBMAX >= 16) ? 1 : 2)) : 8;
 };
 
-template <typename T, bool INC, int NBMAX, int TY, bool YB = false>
+template <typename T, bool INC, int NBMAX, int TY, bool YB = false, bool TE = false>
 __global__ void __launch_bounds__(StepBounds<T, NBMAX, TY>::threads, StepBounds<T, NBMAX, TY>::min_blocks)
 step3d_kernel(const Step3DParams<T> p) {
+  // TE: a y-invariant grid (ny = 1) driven only through E_y, whose E_x, E_z, H_y, P_x, P_z and
+  // x / z bath modes are exactly zero at every step (the host checks that they start at zero and
+  // that nothing writes them).  Those components are constants here: never staged, loaded or
+  // stored, and every expression that uses one sees T(0), so the live components come out
+  // bit-identical to the general form's.
+  auto liveE = [](int c) { return !TE || c == 1; };   // E, P, bath components carried
+  auto liveH = [](int c) { return !TE || c != 1; };   // H components carried
   using YS = BathStore<T, YB>;   // bath-mode storage (YB: bf16 value / increment pairs)
   using YT = typename YS::S;
   using G = Tile<TY>;
@@ -306,6 +313,7 @@ step3d_kernel(const Step3DParams<T> p) {
         if (ce_s[r] < 0) continue;
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
+          if (!liveE(c)) continue;
           if (in) {
             cp_async16(dst + c * FE + ce_s[r], src + c * ncell + ce_g[r]);
           } else {
@@ -320,6 +328,7 @@ step3d_kernel(const Step3DParams<T> p) {
         const int g = wrapi(y0 - 1 + yy, p.ny) * p.nx + wrapi(x0 - 1 + hx, p.nx);
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
+          if (!liveE(c)) continue;
           T* d = dst + c * FE + yy * FX + hx + kXO;
           if (in) cp_async_elem(d, src + c * ncell + g);
           else *d = T(0);
@@ -336,14 +345,16 @@ step3d_kernel(const Step3DParams<T> p) {
       for (int r = 0; r < CH; ++r) {
         if (ch_s[r] < 0) continue;
 #pragma unroll
-        for (int c = 0; c < 3; ++c) cp_async16(dst + c * FH + ch_s[r], src + c * ncell + ch_g[r]);
+        for (int c = 0; c < 3; ++c)
+          if (liveH(c)) cp_async16(dst + c * FH + ch_s[r], src + c * ncell + ch_g[r]);
       }
     } else {
       for (int idx = tid; idx < HY * (kTX + 1); idx += NTHR) {
         const int yy = idx / (kTX + 1), hx = idx - yy * (kTX + 1);
         const int g = wrapi(y0 - 1 + yy, p.ny) * p.nx + wrapi(x0 - 1 + hx, p.nx);
 #pragma unroll
-        for (int c = 0; c < 3; ++c) cp_async_elem(dst + c * FH + yy * HX + hx + kXO, src + c * ncell + g);
+        for (int c = 0; c < 3; ++c)
+          if (liveH(c)) cp_async_elem(dst + c * FH + yy * HX + hx + kXO, src + c * ncell + g);
       }
     }
   };
@@ -352,18 +363,18 @@ step3d_kernel(const Step3DParams<T> p) {
   // planes k and k+1 (the E frame's origin is the H frame's, (x0-1, y0-1), one cell wider)
   auto computeH = [&](int fe, int fh, int gxy, int k, bool write_out, const T* e0, const T* e1,
                       const T* hin) {
-    T hx_ = hin[fh], hy_ = hin[FH + fh], hz_ = hin[2 * FH + fh];
+    T hx_ = hin[fh], hy_ = TE ? T(0) : hin[FH + fh], hz_ = hin[2 * FH + fh];
     if (p.doH) {
       HIn<T> e;
-      e.ex0 = e0[fe];
-      e.ex_k1 = e1[fe];
-      e.ex_j1 = e0[fe + FX];
+      e.ex0 = TE ? T(0) : e0[fe];
+      e.ex_k1 = TE ? T(0) : e1[fe];
+      e.ex_j1 = TE ? T(0) : e0[fe + FX];
       e.ey0 = e0[FE + fe];
       e.ey_k1 = e1[FE + fe];
       e.ey_i1 = e0[FE + fe + 1];
-      e.ez0 = e0[2 * FE + fe];
-      e.ez_j1 = e0[2 * FE + fe + FX];
-      e.ez_i1 = e0[2 * FE + fe + 1];
+      e.ez0 = TE ? T(0) : e0[2 * FE + fe];
+      e.ez_j1 = TE ? T(0) : e0[2 * FE + fe + FX];
+      e.ez_i1 = TE ? T(0) : e0[2 * FE + fe + 1];
       const int ip = psiH_plane(k, p.nz, p.npml);
       T psx = T(0), psy = T(0), b = T(1), c = T(0);
       const int pstride = (2 * p.npml + 1) * plane;
@@ -372,17 +383,17 @@ step3d_kernel(const Step3DParams<T> p) {
         b = p.pmlH[2 * k];
         c = p.pmlH[2 * k + 1];
         psx = p.psiHin[pq];
-        psy = p.psiHin[pstride + pq];
+        psy = TE ? T(0) : p.psiHin[pstride + pq];
       }
       h_update<T>(e, hx_, hy_, hz_, &psx, &psy, b, c, ip >= 0, S);
       if (write_out) {
         const int q = k * plane + gxy;
         p.Hout[q] = hx_;
-        p.Hout[ncell + q] = hy_;
+        if (!TE) p.Hout[ncell + q] = hy_;
         p.Hout[2 * ncell + q] = hz_;
         if (ip >= 0) {
           p.psiHout[pq] = psx;
-          p.psiHout[pstride + pq] = psy;
+          if (!TE) p.psiHout[pstride + pq] = psy;
         }
       }
     }
@@ -396,22 +407,22 @@ step3d_kernel(const Step3DParams<T> p) {
   if (p.doE && zb > 0 && own) {
     const int q = (zb - 1) * plane + qxy;
     hxm = Hin[q];
-    hym = Hin[ncell + q];
+    hym = TE ? T(0) : Hin[ncell + q];
     if (p.doH) {
       // zb-1 is never inside the CPML (chunk starts are planned that way)
       const int ip1 = (i + 1) % p.nx, jp1 = (j + 1) % p.ny;
       const int qj1 = (zb - 1) * plane + jp1 * p.nx + i;
       const int qi1 = (zb - 1) * plane + j * p.nx + ip1;
       HIn<T> e;
-      e.ex0 = Ein[q];
-      e.ex_k1 = Ein[q + plane];
-      e.ex_j1 = Ein[qj1];
+      e.ex0 = TE ? T(0) : Ein[q];
+      e.ex_k1 = TE ? T(0) : Ein[q + plane];
+      e.ex_j1 = TE ? T(0) : Ein[qj1];
       e.ey0 = Ein[ncell + q];
       e.ey_k1 = Ein[ncell + q + plane];
       e.ey_i1 = Ein[ncell + qi1];
-      e.ez0 = Ein[2 * ncell + q];
-      e.ez_j1 = Ein[2 * ncell + qj1];
-      e.ez_i1 = Ein[2 * ncell + qi1];
+      e.ez0 = TE ? T(0) : Ein[2 * ncell + q];
+      e.ez_j1 = TE ? T(0) : Ein[2 * ncell + qj1];
+      e.ez_i1 = TE ? T(0) : Ein[2 * ncell + qi1];
       T hz_dummy = T(0), psx = T(0), psy = T(0);
       h_update<T>(e, hxm, hym, hz_dummy, &psx, &psy, T(1), T(0), false, S);
     }
@@ -453,6 +464,8 @@ step3d_kernel(const Step3DParams<T> p) {
       yb0 = (int)M.ybase + rl;
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
+        rPa[c] = rPb[c] = rD[c] = T(0);
+        if (!liveE(c)) continue;
         rPa[c] = p.Pa[c * nmc + r];
         rPb[c] = p.Pb[c * nmc + r];
         if (!INC) rD[c] = p.D[c * nmc + r];
@@ -462,6 +475,7 @@ step3d_kernel(const Step3DParams<T> p) {
         const YT* yb = reinterpret_cast<const YT*>(p.Yb) + yb0;
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
+          if (!liveE(c)) continue;
 #pragma unroll
           for (int jj = 0; jj < (NBP > 0 ? NBP : 1); ++jj) {
             if (jj < M.nb) {
@@ -540,9 +554,9 @@ step3d_kernel(const Step3DParams<T> p) {
           const T b = p.pmlE[2 * k], c = p.pmlE[2 * k + 1];
           const int pq = ip * plane + qxy;
           const int pstride = 2 * p.npml * plane;
-          T px = b * p.psiE[pq] + c * dzHy;
+          T px = TE ? T(0) : b * p.psiE[pq] + c * dzHy;
           T py = b * p.psiE[pstride + pq] + c * dzHx;
-          p.psiE[pq] = px;
+          if (!TE) p.psiE[pq] = px;
           p.psiE[pstride + pq] = py;
           curl[0] = dyHz - (dzHy + px);
           curl[1] = (dzHx + py) - dxHz;
@@ -570,6 +584,7 @@ step3d_kernel(const Step3DParams<T> p) {
         if (mi < 0) {
 #pragma unroll
           for (int c = 0; c < 3; ++c) {
+            if (!liveE(c)) continue;   // Ev[c] stays 0
             T e = e0[c * FE + own_fe] + S * curl[c];
             if (hasJ[c]) e = e + dt * J[c];
             Ev[c] = e;
@@ -583,6 +598,7 @@ step3d_kernel(const Step3DParams<T> p) {
           YT* const yb = reinterpret_cast<YT*>(p.Yb) + yb0;
 #pragma unroll
           for (int c = 0; c < 3; ++c) {
+            if (!liveE(c)) continue;   // Ev[c] stays 0
             T E;
             const T Pa = rPa[c];
             const T Pb = rPb[c];
@@ -691,6 +707,7 @@ step3d_kernel(const Step3DParams<T> p) {
                 load_coef6(cfm + jj * kCoefStride, cf);
 #pragma unroll
                 for (int c = 0; c < 3; ++c) {
+                  if (!liveE(c)) continue;
                   const T y = rY[c][jj];
                   if (!INC) {
                     bsum[c] = bsum[c] + cf[0] * (cf[1] * y + cf[2] * rV[c][jj]);
@@ -704,6 +721,7 @@ step3d_kernel(const Step3DParams<T> p) {
             T Pn[3], Vn[3], dP[3];
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
+              if (!liveE(c)) continue;
               const T Pa = rPa[c], Pb = rPb[c];
               T V0;
               if (!INC) {
@@ -730,6 +748,7 @@ step3d_kernel(const Step3DParams<T> p) {
                 load_coef6(cfm + jj * kCoefStride, cf);
 #pragma unroll
                 for (int c = 0; c < 3; ++c) {
+                  if (!liveE(c)) continue;
                   const int yo = c * nb * mstride + jj * mstride;
                   const T y = rY[c][jj], v = rV[c][jj];
                   T Ynew, Vy;
@@ -753,6 +772,7 @@ step3d_kernel(const Step3DParams<T> p) {
             if (p.eE_on && in_box) {
 #pragma unroll
               for (int c = 0; c < 3; ++c) {
+                if (!liveE(c)) continue;
                 uP += M.rho_idt2 * (Vn[c] * Vn[c] + M.w0r2dt2 * Pn[c] * Pn[c]);
                 uB += M.rho_idt2 * ub[c];
               }

@@ -5,9 +5,9 @@
 
 namespace fdtdbath {
 
-template <int NB, int TY>
+template <int NB, int TY, bool TE>
 static int launch_nb(const Step3DParams<double>& p, int nbx, int nby, int nchunks, void* stream) {
-  auto kern = step3d_kernel<double, false, NB, TY>;
+  auto kern = step3d_kernel<double, false, NB, TY, false, TE>;
   const size_t smem = step3d_smem_bytes(TY, p.nmodes, sizeof(double));
   static size_t smem_set = 0;   // opt in once per instantiation for more than 48 KB
   if (smem > smem_set) {
@@ -20,22 +20,24 @@ static int launch_nb(const Step3DParams<double>& p, int nbx, int nby, int nchunk
   return (int)cudaGetLastError();
 }
 
-template <int TY>
+template <int TY, bool TE>
 static int launch_ty(const Step3DParams<double>& p, int nbmax, int nbx, int nby, int nchunks, void* stream) {
   switch (nbmax) {
-    case 0: return launch_nb<0, TY>(p, nbx, nby, nchunks, stream);
-    case 4: return launch_nb<4, TY>(p, nbx, nby, nchunks, stream);
-    case 8: return launch_nb<8, TY>(p, nbx, nby, nchunks, stream);
-    case 16: return launch_nb<16, TY>(p, nbx, nby, nchunks, stream);
-    case 32: return launch_nb<32, TY>(p, nbx, nby, nchunks, stream);
+    case 0: return launch_nb<0, TY, TE>(p, nbx, nby, nchunks, stream);
+    case 4: return launch_nb<4, TY, TE>(p, nbx, nby, nchunks, stream);
+    case 8: return launch_nb<8, TY, TE>(p, nbx, nby, nchunks, stream);
+    case 16: return launch_nb<16, TY, TE>(p, nbx, nby, nchunks, stream);
+    case 32: return launch_nb<32, TY, TE>(p, nbx, nby, nchunks, stream);
     default: return (int)cudaErrorInvalidValue;
   }
 }
 
 int launch_step3d_f64(const Step3DParams<double>& p, int nbmax, int ty, int nbx, int nby, int nchunks,
-                       void* stream) {
-  if (ty == 8) return launch_ty<8>(p, nbmax, nbx, nby, nchunks, stream);
-  if (ty == 1) return launch_ty<1>(p, nbmax, nbx, nby, nchunks, stream);
+                      int te, void* stream) {
+  // te: the y-invariant TE form (ny = 1, single-row tiles only)
+  if (ty == 8) return launch_ty<8, false>(p, nbmax, nbx, nby, nchunks, stream);
+  if (ty == 1) return te ? launch_ty<1, true>(p, nbmax, nbx, nby, nchunks, stream)
+                         : launch_ty<1, false>(p, nbmax, nbx, nby, nchunks, stream);
   return (int)cudaErrorInvalidValue;
 }
 

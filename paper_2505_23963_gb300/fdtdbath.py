@@ -383,6 +383,10 @@ class Simulation:
     def launches(self) -> int:
         return query(self.h, 1)
 
+    def te_form(self) -> bool:
+        """Whether the step kernel runs the y-invariant TE form (query key 5)."""
+        return query(self.h, 5) == 1
+
     def adjoint_forward(self, nsteps: int, checkpoint_every: int = 256):
         """fdtdbath_adjoint_forward: advance nsteps steps keeping checkpoints for the adjoint."""
         _check(lib().fdtdbath_adjoint_forward(self.h, int(nsteps), int(checkpoint_every)), self.h)
