@@ -193,7 +193,9 @@ int fdtdbath_bath_form(int32_t shape, double frequency, double gamma, int32_t nu
  * y-invariant grid (ny = 1) whose sources all drive E_y (Sec. II.C, the 2D case): E_x, E_z, H_y,
  * P_x, P_z and the x / z bath modes then stay exactly zero and are neither read nor written; the
  * live components are bit-identical to the general form's.  A write_fields call on any of those
- * components returns the simulation to the general form for good. */
+ * components returns the simulation to the general form for good.  Key 6: whether the last
+ * fdtdbath_adjoint_backward ran the TE form of the reverse sweep (a TE forward run and dL_dF zero
+ * for the E_x and H_y spectra). */
 int64_t fdtdbath_query(const fdtdbath_sim *sim, int32_t key);
 
 /* Energy (U_EM, U_P, U_bath) of planes z_lo <= k < z_hi of the current state -- the same

@@ -58,7 +58,11 @@ __device__ __forceinline__ int adj_mat_of(const AdjParams<T>& p, int k) {
   return -1;
 }
 
-template <typename T, int NBMAX>
+// TE: the forward run was the y-invariant TE form (ny = 1, E_y sources) and the monitor sources
+// of the adjoint sit on E_y and H_x only.  Then the adjoints of E_x, E_z, H_y and of the x / z
+// polarization and bath modes stay exactly zero (their y-differences vanish on the single row);
+// they are constants here, and the carried components are bit-identical to the general form's.
+template <typename T, int NBMAX, bool TE = false>
 __global__ void __launch_bounds__(kAdjThreads) adjoint_k1(const AdjParams<T> p) {
   __shared__ double sg[kAdjThreads / 32][kAdjMaxGrad];
   constexpr int NBA = NBMAX > 0 ? NBMAX : 1;
@@ -80,7 +84,7 @@ __global__ void __launch_bounds__(kAdjThreads) adjoint_k1(const AdjParams<T> p) 
     const T hsrc = T(0.5);
     // adjoint of H^{n+1}, with this step's H-monitor source added on the fly
     auto Hb = [&](int c, int ii, int jj, int kk) -> T {
-      if (kk < 0 || kk >= nz) return T(0);
+      if (kk < 0 || kk >= nz || (TE && c == 1)) return T(0);
       T v = __ldg(p.Hb + c * N + (int64_t)kk * plane + (int64_t)jj * nx + ii);   // read-only here
       if (p.zm >= 0 && (kk == p.zm - 1 || kk == p.zm)) {
         if (c == 0) v += hsrc * p.gHx;
@@ -90,31 +94,31 @@ __global__ void __launch_bounds__(kAdjThreads) adjoint_k1(const AdjParams<T> p) 
     };
     const T hx = Hb(0, i, j, k), hy = Hb(1, i, j, k), hz = Hb(2, i, j, k);
     // F6^T: curl^T of H_bar
-    T ex = p.Eb[q] + S * ((hy - Hb(1, i, j, k - 1)) - (hz - Hb(2, i, jm, k)));
+    T ex = TE ? T(0) : p.Eb[q] + S * ((hy - Hb(1, i, j, k - 1)) - (hz - Hb(2, i, jm, k)));
     T ey = p.Eb[N + q] + S * ((hz - Hb(2, im, j, k)) - (hx - Hb(0, i, j, k - 1)));
-    T ez = p.Eb[2 * N + q] + S * ((hx - Hb(0, i, jm, k)) - (hy - Hb(1, im, j, k)));
+    T ez = TE ? T(0) : p.Eb[2 * N + q] + S * ((hx - Hb(0, i, jm, k)) - (hy - Hb(1, im, j, k)));
     // F6^T into psi_H_bar, then F5^T
     const int kp = adj_psiH_plane(k, nz, p.npml);
     const int64_t nph = (int64_t)(2 * p.npml + 1) * plane;
     if (kp >= 0) {
       const int64_t o = (int64_t)kp * plane + r;
       const T px = __ldg(p.psiHb + o) + S * hx;
-      const T py = __ldg(p.psiHb + nph + o) - S * hy;
+      const T py = TE ? T(0) : __ldg(p.psiHb + nph + o) - S * hy;
       const T bH = __ldg(p.pmlH + 2 * k), cH = __ldg(p.pmlH + 2 * k + 1);
       ey -= cH * px;
-      ex -= cH * py;
+      if (!TE) ex -= cH * py;
       p.psiHb_out[o] = bH * px;
-      p.psiHb_out[nph + o] = bH * py;
+      if (!TE) p.psiHb_out[nph + o] = bH * py;
     }
     if (k > 0) {
       const int kpm = adj_psiH_plane(k - 1, nz, p.npml);
       if (kpm >= 0) {
         const int64_t o = (int64_t)kpm * plane + r;
         const T px = __ldg(p.psiHb + o) + S * Hb(0, i, j, k - 1);
-        const T py = __ldg(p.psiHb + nph + o) - S * Hb(1, i, j, k - 1);
+        const T py = TE ? T(0) : __ldg(p.psiHb + nph + o) - S * Hb(1, i, j, k - 1);
         const T cH = __ldg(p.pmlH + 2 * (k - 1) + 1);
         ey += cH * px;
-        ex += cH * py;
+        if (!TE) ex += cH * py;
       }
     }
     // F3^T (polarization and bath), with the gradient of material gm
@@ -140,6 +144,7 @@ __global__ void __launch_bounds__(kAdjThreads) adjoint_k1(const AdjParams<T> p) 
         T ec[3] = {ex, ey, ez};
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
+          if (TE && c != 1) continue;
           const int64_t ip = c * p.nmatcell + M.base + rm;
           T pn = Pb_[ip];           // adjoint of P^{n+3/2}
           T pold = Pmb_[ip];        // adjoint of P^{n+1/2} (the shift P_m <- P)
@@ -202,7 +207,7 @@ __global__ void __launch_bounds__(kAdjThreads) adjoint_k1(const AdjParams<T> p) 
     }
     // E-monitor source (adjoint of the plane mean of E^{n+1/2})
     if (k == p.zm) {
-      ex += p.gEx;
+      if (!TE) ex += p.gEx;
       ey += p.gEy;
     }
     // pointwise parts of F2^T
@@ -212,6 +217,7 @@ __global__ void __launch_bounds__(kAdjThreads) adjoint_k1(const AdjParams<T> p) 
       const T e3[3] = {ex, ey, ez};
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
+        if (TE && c != 1) continue;
         const int64_t ip = c * p.nmatcell + M.base + rm;
         p.Pb[ip] = Pold[c] - e3[c] * inv_eps;
         p.Pmb[ip] = Pmold[c] + e3[c] * inv_eps;
@@ -221,12 +227,12 @@ __global__ void __launch_bounds__(kAdjThreads) adjoint_k1(const AdjParams<T> p) 
     if (kq >= 0) {
       const int64_t npe = (int64_t)(2 * p.npml) * plane;
       const int64_t o = (int64_t)kq * plane + r;
-      p.psiEb[o] += -S * inv_eps * ex;
+      if (!TE) p.psiEb[o] += -S * inv_eps * ex;
       p.psiEb[npe + o] += S * inv_eps * ey;
     }
-    p.Eb[q] = ex;
+    if (!TE) p.Eb[q] = ex;
     p.Eb[N + q] = ey;
-    p.Eb[2 * N + q] = ez;
+    if (!TE) p.Eb[2 * N + q] = ez;
   }
   // per-block gradient partials of material gm (blocks holding none of its cells skip)
   if (p.gm >= 0) {
@@ -255,7 +261,7 @@ __global__ void __launch_bounds__(kAdjThreads) adjoint_k1(const AdjParams<T> p) 
   }
 }
 
-template <typename T>
+template <typename T, bool TE = false>
 __global__ void __launch_bounds__(kAdjThreads) adjoint_k2(const AdjParams<T> p) {
   const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= p.ncell) return;
@@ -277,15 +283,15 @@ __global__ void __launch_bounds__(kAdjThreads) adjoint_k2(const AdjParams<T> p) 
   }();
   // E_bar / eps_inf of a cell (zero outside the grid)
   auto Et = [&](int c, int ii, int jj, int kk, T inv) -> T {
-    if (kk >= nz) return T(0);
+    if (kk >= nz || (TE && c != 1)) return T(0);
     return p.Eb[c * N + (int64_t)kk * plane + (int64_t)jj * nx + ii] * inv;
   };
   const T ex = Et(0, i, j, k, inv0), ey = Et(1, i, j, k, inv0), ez = Et(2, i, j, k, inv0);
-  T hx = p.Hb[q], hy = p.Hb[N + q], hz = p.Hb[2 * N + q];
+  T hx = p.Hb[q], hy = TE ? T(0) : p.Hb[N + q], hz = p.Hb[2 * N + q];
   // this step's H-monitor source
   if (p.zm >= 0 && (k == p.zm - 1 || k == p.zm)) {
     hx += T(0.5) * p.gHx;
-    hy += T(0.5) * p.gHy;
+    if (!TE) hy += T(0.5) * p.gHy;
   }
   // curl^T of F2
   hx += S * ((ey - Et(1, i, j, k + 1, inv1)) - (ez - Et(2, i, jp, k, inv0)));
@@ -296,11 +302,11 @@ __global__ void __launch_bounds__(kAdjThreads) adjoint_k2(const AdjParams<T> p) 
   const int kq = adj_psiE_plane(k, nz, p.npml);
   if (kq >= 0) {
     const int64_t o = (int64_t)kq * plane + r;
-    const T px = p.psiEb[o], py = p.psiEb[npe + o];
+    const T px = TE ? T(0) : p.psiEb[o], py = p.psiEb[npe + o];
     const T bE = p.pmlE[2 * k], cE = p.pmlE[2 * k + 1];
-    hy += cE * px;
+    if (!TE) hy += cE * px;
     hx += cE * py;
-    p.psiEb_out[o] = bE * px;
+    if (!TE) p.psiEb_out[o] = bE * px;
     p.psiEb_out[npe + o] = bE * py;
   }
   if (k + 1 < nz) {
@@ -308,30 +314,36 @@ __global__ void __launch_bounds__(kAdjThreads) adjoint_k2(const AdjParams<T> p) 
     if (kq1 >= 0) {
       const int64_t o = (int64_t)kq1 * plane + r;
       const T cE1 = p.pmlE[2 * (k + 1) + 1];
-      hy -= cE1 * p.psiEb[o];
+      if (!TE) hy -= cE1 * p.psiEb[o];
       hx -= cE1 * p.psiEb[npe + o];
     }
   }
   p.Hb[q] = hx;
-  p.Hb[N + q] = hy;
+  if (!TE) p.Hb[N + q] = hy;
   p.Hb[2 * N + q] = hz;
 }
 
-template <typename T>
-int launch_adjoint_impl(const AdjParams<T>& p, int nbmax, void* stream) {
+template <typename T, bool TE>
+int launch_adjoint_form(const AdjParams<T>& p, int nbmax, void* stream) {
   const int64_t nblk = (p.ncell + kAdjThreads - 1) / kAdjThreads;
   cudaStream_t st = (cudaStream_t)stream;
   switch (nbmax) {
-    case 0: adjoint_k1<T, 0><<<(unsigned)nblk, kAdjThreads, 0, st>>>(p); break;
-    case 4: adjoint_k1<T, 4><<<(unsigned)nblk, kAdjThreads, 0, st>>>(p); break;
-    case 8: adjoint_k1<T, 8><<<(unsigned)nblk, kAdjThreads, 0, st>>>(p); break;
-    case 16: adjoint_k1<T, 16><<<(unsigned)nblk, kAdjThreads, 0, st>>>(p); break;
-    default: adjoint_k1<T, 32><<<(unsigned)nblk, kAdjThreads, 0, st>>>(p); break;
+    case 0: adjoint_k1<T, 0, TE><<<(unsigned)nblk, kAdjThreads, 0, st>>>(p); break;
+    case 4: adjoint_k1<T, 4, TE><<<(unsigned)nblk, kAdjThreads, 0, st>>>(p); break;
+    case 8: adjoint_k1<T, 8, TE><<<(unsigned)nblk, kAdjThreads, 0, st>>>(p); break;
+    case 16: adjoint_k1<T, 16, TE><<<(unsigned)nblk, kAdjThreads, 0, st>>>(p); break;
+    default: adjoint_k1<T, 32, TE><<<(unsigned)nblk, kAdjThreads, 0, st>>>(p); break;
   }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return (int)e;
-  adjoint_k2<T><<<(unsigned)nblk, kAdjThreads, 0, st>>>(p);
+  adjoint_k2<T, TE><<<(unsigned)nblk, kAdjThreads, 0, st>>>(p);
   return (int)cudaGetLastError();
+}
+
+// te = 1: the TE form (y-invariant TE forward run, adjoint sources on E_y and H_x only)
+template <typename T>
+int launch_adjoint_impl(const AdjParams<T>& p, int nbmax, int te, void* stream) {
+  return te ? launch_adjoint_form<T, true>(p, nbmax, stream) : launch_adjoint_form<T, false>(p, nbmax, stream);
 }
 
 }  // namespace fdtdbath

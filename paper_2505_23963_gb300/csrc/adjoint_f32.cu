@@ -3,8 +3,8 @@
 
 namespace fdtdbath {
 
-int launch_adjoint_f32(const AdjParams<float>& p, int nbmax, void* stream) {
-  return launch_adjoint_impl<float>(p, nbmax, stream);
+int launch_adjoint_f32(const AdjParams<float>& p, int nbmax, int te, void* stream) {
+  return launch_adjoint_impl<float>(p, nbmax, te, stream);
 }
 
 int64_t adjoint_blocks(int64_t ncell) { return (ncell + kAdjThreads - 1) / kAdjThreads; }

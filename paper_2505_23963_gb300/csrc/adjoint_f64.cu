@@ -4,8 +4,8 @@
 
 namespace fdtdbath {
 
-int launch_adjoint_f64(const AdjParams<double>& p, int nbmax, void* stream) {
-  return launch_adjoint_impl<double>(p, nbmax, stream);
+int launch_adjoint_f64(const AdjParams<double>& p, int nbmax, int te, void* stream) {
+  return launch_adjoint_impl<double>(p, nbmax, te, stream);
 }
 
 }  // namespace fdtdbath

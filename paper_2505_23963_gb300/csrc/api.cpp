@@ -129,6 +129,7 @@ struct fdtdbath_sim {
   // bath modes stay exactly zero and the single-row kernels skip them; cleared for good when a
   // write could make one of them nonzero
   bool te = false;
+  bool adj_te = false;      // the last reverse sweep ran the TE form
   AdjState adj;
   std::string err;
 };
@@ -1230,6 +1231,7 @@ int64_t fdtdbath_query(const fdtdbath_sim* s, int32_t key) {
     case 3: return (int64_t)s->nbx * s->nby * s->nchunks;
     case 4: return s->nchunks;
     case 5: return s->te && s->ty == 1 ? 1 : 0;
+    case 6: return s->adj_te ? 1 : 0;
     default: return -1;
   }
 }
@@ -1316,8 +1318,12 @@ int restore_checkpoint(fdtdbath_sim* s, size_t idx) {
   return 0;
 }
 
-int launch_adjoint(const AdjParams<float>& p, int nbmax, cudaStream_t st) { return launch_adjoint_f32(p, nbmax, st); }
-int launch_adjoint(const AdjParams<double>& p, int nbmax, cudaStream_t st) { return launch_adjoint_f64(p, nbmax, st); }
+int launch_adjoint(const AdjParams<float>& p, int nbmax, bool te, cudaStream_t st) {
+  return launch_adjoint_f32(p, nbmax, te ? 1 : 0, st);
+}
+int launch_adjoint(const AdjParams<double>& p, int nbmax, bool te, cudaStream_t st) {
+  return launch_adjoint_f64(p, nbmax, te ? 1 : 0, st);
+}
 
 template <typename T>
 int adjoint_sweep(fdtdbath_sim* s, const HostMon& mon, const std::vector<double>& freqs, const double* dLdF,
@@ -1387,6 +1393,12 @@ int adjoint_sweep(fdtdbath_sim* s, const HostMon& mon, const std::vector<double>
       gH[(size_t)m * 2 + 1] += (d[6] * cH + d[7] * sH) * s->dt;
     }
   }
+  // TE form of the reverse sweep: the forward run was the TE form and nothing drives the
+  // adjoints of E_x or H_y, so those (and E_z, P_x, P_z, the x / z bath modes) stay zero
+  bool te = s->te && s->ty == 1;
+  for (int64_t m = 0; m < NS && te; ++m)
+    if (gE[(size_t)m * 2] != 0.0 || gH[(size_t)m * 2 + 1] != 0.0) te = false;
+  s->adj_te = te;
   // ---- constant part of the kernel parameters ----
   AdjParams<T> p{};
   p.nx = (int)s->nx;
@@ -1490,7 +1502,7 @@ int adjoint_sweep(fdtdbath_sim* s, const HostMon& mon, const std::vector<double>
       p.psiEb_out = psE[1 - ps];
       p.psiHb = psH[ps];
       p.psiHb_out = psH[1 - ps];
-      const int lr = launch_adjoint(p, s->nbmax, s->stream);
+      const int lr = launch_adjoint(p, s->nbmax, te, s->stream);
       s->launches += 2;
       if (lr) rc = cuda_fail(s, (cudaError_t)lr, "adjoint kernel launch");
       ps = 1 - ps;

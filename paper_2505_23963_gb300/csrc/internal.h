@@ -191,8 +191,10 @@ struct AdjParams {
   T ta[kMaxBath], tb[kMaxBath], tdc[kMaxBath], tds[kMaxBath];
   double* gpart;            // [gridDim][kAdjMaxGrad] per-block running sums (FP64)
 };
-int launch_adjoint_f32(const AdjParams<float>& p, int nbmax, void* stream);
-int launch_adjoint_f64(const AdjParams<double>& p, int nbmax, void* stream);
+// te = 1: the TE form (the forward run was the y-invariant TE form and the adjoint sources sit
+// on E_y and H_x only): the adjoints of E_x, E_z, H_y, P_x, P_z and the x / z bath modes are zero
+int launch_adjoint_f32(const AdjParams<float>& p, int nbmax, int te, void* stream);
+int launch_adjoint_f64(const AdjParams<double>& p, int nbmax, int te, void* stream);
 int64_t adjoint_blocks(int64_t ncell);
 
 // reduce.cu: fixed-order reduction of the per-block partials into per-step series,

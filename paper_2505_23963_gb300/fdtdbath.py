@@ -387,6 +387,10 @@ class Simulation:
         """Whether the step kernel runs the y-invariant TE form (query key 5)."""
         return query(self.h, 5) == 1
 
+    def adjoint_te_form(self) -> bool:
+        """Whether the last reverse sweep ran the TE form (query key 6)."""
+        return query(self.h, 6) == 1
+
     def adjoint_forward(self, nsteps: int, checkpoint_every: int = 256):
         """fdtdbath_adjoint_forward: advance nsteps steps keeping checkpoints for the adjoint."""
         _check(lib().fdtdbath_adjoint_forward(self.h, int(nsteps), int(checkpoint_every)), self.h)
