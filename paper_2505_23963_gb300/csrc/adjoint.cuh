@@ -62,8 +62,10 @@ __device__ __forceinline__ int adj_mat_of(const AdjParams<T>& p, int k) {
 // of the adjoint sit on E_y and H_x only.  Then the adjoints of E_x, E_z, H_y and of the x / z
 // polarization and bath modes stay exactly zero (their y-differences vanish on the single row);
 // they are constants here, and the carried components are bit-identical to the general form's.
+// The TE form carries one component's P / bath adjoints: up to N_b = 8 it fits in 64 registers,
+// so four blocks share an SM (the kernel waits on memory, and more warps hide more of it).
 template <typename T, int NBMAX, bool TE = false>
-__global__ void __launch_bounds__(kAdjThreads) adjoint_k1(const AdjParams<T> p) {
+__global__ void __launch_bounds__(kAdjThreads, (TE && NBMAX <= 8) ? 4 : 0) adjoint_k1(const AdjParams<T> p) {
   __shared__ double sg[kAdjThreads / 32][kAdjMaxGrad];
   constexpr int NBA = NBMAX > 0 ? NBMAX : 1;
   const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;

@@ -144,10 +144,10 @@ __device__ __forceinline__ void load_coef6(const double* cf, double* o) {
 // y0-1 .. y0+TY-1 (the tile and its -x / -y halo).  Frame column = x - (x0 - 4), so the
 // halo-relative column hx (x = x0-1+hx) sits at hx + kXO.
 constexpr int kXO = 3;
-template <int TY>
+template <int TY, int TXW = kTX>
 struct Tile {
-  static constexpr int TX = kTX, FX = kTX + 8, FY = TY + 2, HX = kTX + 4, HY = TY + 1;
-  static constexpr int NTHR = kTX * TY;
+  static constexpr int TX = TXW, FX = TXW + 8, FY = TY + 2, HX = TXW + 4, HY = TY + 1;
+  static constexpr int NTHR = TXW * TY;
   static constexpr int FE = FY * FX;                 // E frame elements per component
   static constexpr int FH = HY * HX;                 // H frame elements per component
 };
@@ -167,14 +167,16 @@ struct BathStore<float, true> {
   static __device__ __forceinline__ void put(S* p, float v) { *p = __float2bfloat16_rn(v); }
 };
 
-template <typename T, int NBMAX, int TY>
+template <typename T, int NBMAX, int TY, int TXW = kTX>
 struct StepBounds {
-  static constexpr int threads = kTX * TY;
-  static constexpr int min_blocks = TY == 8 ? (NBMAX == 0 ? (sizeof(T) == 4 ? 4 : 2) : ((sizeof(T) == 8 && NBMAX >= 16) ? 1 : 2)) : 8;
+  static constexpr int threads = TXW * TY;
+  // wide single-row tiles (the TE form): four CTAs of TXW threads per SM
+  static constexpr int min_blocks = TXW > kTX ? 4
+      : (TY == 8 ? (NBMAX == 0 ? (sizeof(T) == 4 ? 4 : 2) : ((sizeof(T) == 8 && NBMAX >= 16) ? 1 : 2)) : 8);
 };
 
-template <typename T, bool INC, int NBMAX, int TY, bool YB = false, bool TE = false>
-__global__ void __launch_bounds__(StepBounds<T, NBMAX, TY>::threads, StepBounds<T, NBMAX, TY>::min_blocks)
+template <typename T, bool INC, int NBMAX, int TY, bool YB = false, bool TE = false, int TXW = kTX>
+__global__ void __launch_bounds__(StepBounds<T, NBMAX, TY, TXW>::threads, StepBounds<T, NBMAX, TY, TXW>::min_blocks)
 step3d_kernel(const Step3DParams<T> p) {
   // TE: a y-invariant grid (ny = 1) driven only through E_y, whose E_x, E_z, H_y, P_x, P_z and
   // x / z bath modes are exactly zero at every step (the host checks that they start at zero and
@@ -183,9 +185,12 @@ step3d_kernel(const Step3DParams<T> p) {
   // bit-identical to the general form's.
   auto liveE = [](int c) { return !TE || c == 1; };   // E, P, bath components carried
   auto liveH = [](int c) { return !TE || c != 1; };   // H components carried
+  // With ny = 1 the TE form needs no y neighbour (the y-differences it keeps are of E_x, E_z,
+  // H_y, all zero): of the frames it stages only the tile's own row, and of the halo only the
+  // -x column.
   using YS = BathStore<T, YB>;   // bath-mode storage (YB: bf16 value / increment pairs)
   using YT = typename YS::S;
-  using G = Tile<TY>;
+  using G = Tile<TY, TXW>;
   constexpr int TX = G::TX, FX = G::FX, HX = G::HX, NTHR = G::NTHR, FE = G::FE, FH = G::FH;
   constexpr int FY = G::FY, HY = G::HY;
   constexpr int VE = 16 / (int)sizeof(T);      // elements per 16-byte copy
@@ -223,15 +228,36 @@ step3d_kernel(const Step3DParams<T> p) {
   // a taller tile writes its sum into the slot of its first TYS-row tile and zero into the others,
   // so every slot of a chunk is rewritten by whichever kernel processes the chunk
   constexpr int TYS = TY >= 8 ? 8 : TY;
-  constexpr int RS = TY / TYS;                       // slots per block (rows of TYS-row tiles)
+  constexpr int RS = TY / TYS;                       // slot rows per block (TYS-row tiles)
+  constexpr int WS = TX / kTX;                       // slot columns per block (32-wide tiles)
   const int nbxy = p.nbxy;
-  const int nrow_s = nbxy / gridDim.x;               // TYS-row tiles along y
-  const int bxy = (blockIdx.y * RS) * gridDim.x + blockIdx.x;
+  const int ncol_s = (p.nx + kTX - 1) / kTX;         // 32-wide tiles along x
+  const int nrow_s = nbxy / ncol_s;                  // TYS-row tiles along y
+  const int sx0 = blockIdx.x * WS, sy0 = blockIdx.y * RS;
+  const int bxy = sy0 * ncol_s + sx0;
   auto put_slot = [&](double* row, double v) {      // row: slot 0 of this chunk's quantity
     row[bxy] = v;
 #pragma unroll
-    for (int r = 1; r < RS; ++r)
-      if ((int)blockIdx.y * RS + r < nrow_s) row[bxy + r * (int)gridDim.x] = 0.0;
+    for (int r = 0; r < RS; ++r)
+#pragma unroll
+      for (int w = 0; w < WS; ++w)
+        if ((r || w) && sy0 + r < nrow_s && sx0 + w < ncol_s) row[bxy + r * ncol_s + w] = 0.0;
+  };
+  // the block's sum of v (every thread's value) into its slot of row, or nothing when row is
+  // null.  Wide single-row tiles write one warp sum per 32-wide slot tile instead: a warp is one
+  // such tile, and its value is the one a 32-wide block produces, so the sums and their order
+  // do not depend on the tile width.
+  static_assert(WS == 1 || TY == 1, "wide tiles are single-row");
+  auto sum_to_slot = [&](double* row, auto v) {
+    if constexpr (WS > 1) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+      const int w = tid >> 5;
+      if ((tid & 31) == 0 && row && sx0 + w < ncol_s) row[bxy + w] = 0.0 + (double)v;
+    } else {
+      const double sum = block_sum(v, sred);
+      if (tid == 0 && row) put_slot(row, sum);
+    }
   };
   const T* __restrict__ Ein = p.Ein;
   const T* __restrict__ Hin = p.Hin;
@@ -264,8 +290,8 @@ step3d_kernel(const Step3DParams<T> p) {
     const int idx = tid + r * NTHR;
     ce_s[r] = -1;
     ce_g[r] = 0;
-    if (idx < NCE && p.vec16) {
-      const int yy = idx / cpr_e, cx = idx - yy * cpr_e;
+    if (idx < (TE ? cpr_e : NCE) && p.vec16) {
+      const int yy = TE ? 1 : idx / cpr_e, cx = TE ? idx : idx - yy * cpr_e;   // TE: own row only
       ce_s[r] = yy * FX + cx * VE;
       ce_g[r] = wrapi(y0 - 1 + yy, p.ny) * p.nx + wrapi(x0 - 4 + cx * VE, p.nx);
     }
@@ -275,8 +301,8 @@ step3d_kernel(const Step3DParams<T> p) {
     const int idx = (NTHR - 1 - tid) + r * NTHR;
     ch_s[r] = -1;
     ch_g[r] = 0;
-    if (idx < NCH && p.vec16) {
-      const int yy = idx / cpr_h, cx = idx - yy * cpr_h;
+    if (idx < (TE ? cpr_h : NCH) && p.vec16) {
+      const int yy = TE ? 1 : idx / cpr_h, cx = TE ? idx : idx - yy * cpr_h;   // TE: own row only
       ch_s[r] = yy * HX + cx * VE;
       ch_g[r] = wrapi(y0 - 1 + yy, p.ny) * p.nx + wrapi(x0 - 4 + cx * VE, p.nx);
     }
@@ -284,7 +310,9 @@ step3d_kernel(const Step3DParams<T> p) {
 
   // H tasks of this thread: its own cell, and up to two cells of the -y row / -x column halo
   const int own_fe = (ty + 1) * FX + (tx + 1 + kXO), own_fh = (ty + 1) * HX + (tx + 1 + kXO);
-  constexpr int NHT = (TX + TY + NTHR - 1) / NTHR;
+  // (TE: the -x column only)
+  constexpr int NHALO = TE ? TY : TX + TY;
+  constexpr int NHT = (NHALO + NTHR - 1) / NTHR;
   int ht_fe[NHT], ht_fh[NHT], ht_g[NHT];
 #pragma unroll
   for (int r = 0; r < NHT; ++r) {
@@ -292,8 +320,8 @@ step3d_kernel(const Step3DParams<T> p) {
     ht_fe[r] = -1;
     ht_fh[r] = 0;
     ht_g[r] = 0;
-    if (t < TX + TY) {
-      const int hy = t < TX ? 0 : t - TX + 1, hx = t < TX ? t + 1 : 0;
+    if (t < NHALO) {
+      const int hy = TE ? t + 1 : (t < TX ? 0 : t - TX + 1), hx = TE ? 0 : (t < TX ? t + 1 : 0);
       ht_fe[r] = hy * FX + hx + kXO;
       ht_fh[r] = hy * HX + hx + kXO;
       ht_g[r] = wrapi(y0 - 1 + hy, p.ny) * p.nx + wrapi(x0 - 1 + hx, p.nx);
@@ -323,8 +351,9 @@ step3d_kernel(const Step3DParams<T> p) {
         }
       }
     } else {
-      for (int idx = tid; idx < FY * (kTX + 2); idx += NTHR) {
-        const int yy = idx / (kTX + 2), hx = idx - yy * (kTX + 2);
+      for (int idx = tid; idx < FY * (TX + 2); idx += NTHR) {
+        const int yy = idx / (TX + 2), hx = idx - yy * (TX + 2);
+        if (TE && yy != 1) continue;
         const int g = wrapi(y0 - 1 + yy, p.ny) * p.nx + wrapi(x0 - 1 + hx, p.nx);
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
@@ -349,8 +378,9 @@ step3d_kernel(const Step3DParams<T> p) {
           if (liveH(c)) cp_async16(dst + c * FH + ch_s[r], src + c * ncell + ch_g[r]);
       }
     } else {
-      for (int idx = tid; idx < HY * (kTX + 1); idx += NTHR) {
-        const int yy = idx / (kTX + 1), hx = idx - yy * (kTX + 1);
+      for (int idx = tid; idx < HY * (TX + 1); idx += NTHR) {
+        const int yy = idx / (TX + 1), hx = idx - yy * (TX + 1);
+        if (TE && yy != 1) continue;
         const int g = wrapi(y0 - 1 + yy, p.ny) * p.nx + wrapi(x0 - 1 + hx, p.nx);
 #pragma unroll
         for (int c = 0; c < 3; ++c)
@@ -519,12 +549,9 @@ step3d_kernel(const Step3DParams<T> p) {
           const int off = (k == zm) ? 1 : 0;
           T vx = own ? sH[own_fh] : T(0);
           T vy = own ? sH[FH + own_fh] : T(0);
-          double sx = block_sum((double)vx, sred);
-          double sy = block_sum((double)vy, sred);
-          if (tid == 0 && p.mon_partial_H) {
-            put_slot(p.mon_partial_H + (int64_t)(4 * m + off) * nbxy, sx);
-            put_slot(p.mon_partial_H + (int64_t)(4 * m + 2 + off) * nbxy, sy);
-          }
+          double* rows = p.mon_partial_H;
+          sum_to_slot(rows ? rows + (int64_t)(4 * m + off) * nbxy : nullptr, (double)vx);
+          sum_to_slot(rows ? rows + (int64_t)(4 * m + 2 + off) * nbxy : nullptr, (double)vy);
         }
       }
       if (p.eH_on && own && in_box) {
@@ -789,12 +816,9 @@ step3d_kernel(const Step3DParams<T> p) {
       if (info & kPlaneMonE)
       for (int m = 0; m < p.nmon; ++m) {
         if (k == p.mon_z[m]) {
-          double sx = block_sum(own ? (double)Ev[0] : 0.0, sred);
-          double sy = block_sum(own ? (double)Ev[1] : 0.0, sred);
-          if (tid == 0 && p.mon_partial_E) {
-            put_slot(p.mon_partial_E + (int64_t)(2 * m) * nbxy, sx);
-            put_slot(p.mon_partial_E + (int64_t)(2 * m + 1) * nbxy, sy);
-          }
+          double* rows = p.mon_partial_E;
+          sum_to_slot(rows ? rows + (int64_t)(2 * m) * nbxy : nullptr, own ? (double)Ev[0] : 0.0);
+          sum_to_slot(rows ? rows + (int64_t)(2 * m + 1) * nbxy : nullptr, own ? (double)Ev[1] : 0.0);
         }
       }
       hxm = sH[own_fh];
@@ -803,23 +827,17 @@ step3d_kernel(const Step3DParams<T> p) {
   }
   // energy partials of this block (every block writes, zero when outside the box)
   if (p.eE_on) {
-    double a = block_sum(uE, sred);
-    double b = block_sum(uP, sred);
-    double c = block_sum(uB, sred);
-    if (tid == 0) {
-      put_slot(p.en_partial_E + (int64_t)chunk * nbxy, a);
-      put_slot(p.en_partial_E + ((int64_t)nbxy * p.nchunks_total + chunk * nbxy), b);
-      put_slot(p.en_partial_E + ((int64_t)2 * nbxy * p.nchunks_total + chunk * nbxy), c);
-    }
+    sum_to_slot(p.en_partial_E + (int64_t)chunk * nbxy, uE);
+    sum_to_slot(p.en_partial_E + ((int64_t)nbxy * p.nchunks_total + chunk * nbxy), uP);
+    sum_to_slot(p.en_partial_E + ((int64_t)2 * nbxy * p.nchunks_total + chunk * nbxy), uB);
   }
   if (p.eH_on) {
-    double a = block_sum(uH, sred);
-    if (tid == 0) put_slot(p.en_partial_H + (int64_t)chunk * nbxy, a);
+    sum_to_slot(p.en_partial_H + (int64_t)chunk * nbxy, uH);
   }
 }
 
-inline size_t step3d_smem_bytes(int ty, int nmodes, size_t elem) {
-  const size_t fe = (size_t)(ty + 2) * (kTX + 8), fh = (size_t)(ty + 1) * (kTX + 4);
+inline size_t step3d_smem_bytes(int ty, int nmodes, size_t elem, int tx = kTX) {
+  const size_t fe = (size_t)(ty + 2) * (tx + 8), fh = (size_t)(ty + 1) * (tx + 4);
   const size_t n = (size_t)kRingE * 3 * fe + (size_t)(kRingH + 1) * 3 * fh + (size_t)kCoefStride * nmodes;
   return n * elem + kMaxChunk * sizeof(int) + 16 + 8 * sizeof(double);   // block-sum scratch: a double per warp (<= 8)
 }

@@ -8,15 +8,17 @@ namespace fdtdbath {
 
 template <int NB, int TY, bool YB, bool TE>
 static int launch_nb(const Step3DParams<float>& p, int nbx, int nby, int nchunks, void* stream) {
-  auto kern = step3d_kernel<float, true, NB, TY, YB, TE>;
-  const size_t smem = step3d_smem_bytes(TY, p.nmodes, sizeof(float));
+  // the TE form runs 128-wide single-row tiles, every other form 32-wide tiles
+  constexpr int TX = TE ? 4 * kTX : kTX;
+  auto kern = step3d_kernel<float, true, NB, TY, YB, TE, TX>;
+  const size_t smem = step3d_smem_bytes(TY, p.nmodes, sizeof(float), TX);
   static size_t smem_set = 0;   // opt in once per instantiation for more than 48 KB
   if (smem > smem_set) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return (int)e;
     smem_set = smem;
   }
-  dim3 grid(nbx, nby, nchunks), block(kTX, TY);
+  dim3 grid(TX == kTX ? nbx : (p.nx + TX - 1) / TX, nby, nchunks), block(TX, TY);
   kern<<<grid, block, smem, (cudaStream_t)stream>>>(p);
   return (int)cudaGetLastError();
 }
