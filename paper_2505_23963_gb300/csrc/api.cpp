@@ -829,6 +829,15 @@ int fdtdbath_create(const fdtdbath_grid* grid, double resolution, double courant
       if ((nplain > 0 && nplain * tiles < 4LL * sms) || (nbath > 0 && nbath * tiles < 2LL * sms)) balanced = false;
     }
   }
+  // uniform plan on grids with few tiles per plane (the 2D cavities: one row of 32-wide tiles, or
+  // 128-wide tiles in the TE form): 16-plane chunks, so that each launch still has CTAs for
+  // every SM
+  if (!balanced && !std::getenv("FDTDBATH_ZCHUNK")) {
+    const bool te0 = s->ty == 1 && ny == 1 && std::all_of(s->srcs.begin(), s->srcs.end(),
+                                                             [](const HostSrc& q) { return q.comp == 1; });
+    const int64_t ktiles = te0 ? (nx + 4 * kTX - 1) / (4 * kTX) : (int64_t)s->nbx * s->nby;
+    if (ktiles < 64) zc = 16;
+  }
   s->nchunks = plan_chunks(s, zc, balanced, starts);
   for (size_t c = 0; c + 1 < starts.size(); ++c)
     if (starts[c + 1] - starts[c] > 128) return bail(FDTDBATH_ERR_ARG, "z-chunk longer than 128 planes");

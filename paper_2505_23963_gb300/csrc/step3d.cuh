@@ -71,6 +71,15 @@ __device__ __forceinline__ double block_sum(V v, double* scratch) {
 // Eq. FDTD-1D (S = dt/dx times differences of neighbours):
 //   Hx -= S (dEz|y - (dEy|z + psi_x)),  Hy -= S ((dEx|z + psi_y) - dEz|x),  Hz -= S (dEy|x - dEx|y);
 // psi <- b psi + c dE|z inside the CPML (memory in units of a field difference).
+// Warp-wide sum of v written by lane 0 to dst (skipped when dst is null), as the one-warp
+// block_sum would produce it (0.0 + the warp's sum).
+template <typename V>
+__device__ __forceinline__ void warp_sum_to(V v, double* dst) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0 && dst) *dst = 0.0 + (double)v;
+}
+
 template <typename T>
 struct HIn {
   T ex0, ex_k1, ex_j1;  // Ex(i,j,k), Ex(i,j,k+1), Ex(i,j+1,k)
@@ -231,33 +240,27 @@ step3d_kernel(const Step3DParams<T> p) {
   constexpr int RS = TY / TYS;                       // slot rows per block (TYS-row tiles)
   constexpr int WS = TX / kTX;                       // slot columns per block (32-wide tiles)
   const int nbxy = p.nbxy;
-  const int ncol_s = (p.nx + kTX - 1) / kTX;         // 32-wide tiles along x
+  // 32-wide tiles along x: the launch's blocks, or WS of them per block of wide tiles
+  const int ncol_s = WS == 1 ? (int)gridDim.x : (p.nx + kTX - 1) / kTX;
   const int nrow_s = nbxy / ncol_s;                  // TYS-row tiles along y
   const int sx0 = blockIdx.x * WS, sy0 = blockIdx.y * RS;
   const int bxy = sy0 * ncol_s + sx0;
   auto put_slot = [&](double* row, double v) {      // row: slot 0 of this chunk's quantity
     row[bxy] = v;
 #pragma unroll
-    for (int r = 0; r < RS; ++r)
+    for (int r = 1; r < RS; ++r)
+      if (sy0 + r < nrow_s) row[bxy + r * ncol_s] = 0.0;
 #pragma unroll
-      for (int w = 0; w < WS; ++w)
-        if ((r || w) && sy0 + r < nrow_s && sx0 + w < ncol_s) row[bxy + r * ncol_s + w] = 0.0;
+    for (int w = 1; w < WS; ++w)   // wide tiles are single-row (RS = 1)
+      if (sx0 + w < ncol_s) row[bxy + w] = 0.0;
   };
-  // the block's sum of v (every thread's value) into its slot of row, or nothing when row is
-  // null.  Wide single-row tiles write one warp sum per 32-wide slot tile instead: a warp is one
-  // such tile, and its value is the one a 32-wide block produces, so the sums and their order
-  // do not depend on the tile width.
+  // Wide single-row tiles write one warp sum per 32-wide slot tile (warp_sum_to): a warp is one
+  // such tile and its value is the one a 32-wide block produces, so the sums and their order do
+  // not depend on the tile width.  wslot(row): this warp's slot of row, or null.
   static_assert(WS == 1 || TY == 1, "wide tiles are single-row");
-  auto sum_to_slot = [&](double* row, auto v) {
-    if constexpr (WS > 1) {
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-      const int w = tid >> 5;
-      if ((tid & 31) == 0 && row && sx0 + w < ncol_s) row[bxy + w] = 0.0 + (double)v;
-    } else {
-      const double sum = block_sum(v, sred);
-      if (tid == 0 && row) put_slot(row, sum);
-    }
+  auto wslot = [&](double* row) -> double* {
+    const int w = tid >> 5;
+    return (row && sx0 + w < ncol_s) ? row + bxy + w : nullptr;
   };
   const T* __restrict__ Ein = p.Ein;
   const T* __restrict__ Hin = p.Hin;
@@ -494,8 +497,10 @@ step3d_kernel(const Step3DParams<T> p) {
       yb0 = (int)M.ybase + rl;
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
-        rPa[c] = rPb[c] = rD[c] = T(0);
-        if (!liveE(c)) continue;
+        if (!liveE(c)) {
+          rPa[c] = rPb[c] = rD[c] = T(0);
+          continue;
+        }
         rPa[c] = p.Pa[c * nmc + r];
         rPb[c] = p.Pb[c * nmc + r];
         if (!INC) rD[c] = p.D[c * nmc + r];
@@ -549,9 +554,18 @@ step3d_kernel(const Step3DParams<T> p) {
           const int off = (k == zm) ? 1 : 0;
           T vx = own ? sH[own_fh] : T(0);
           T vy = own ? sH[FH + own_fh] : T(0);
-          double* rows = p.mon_partial_H;
-          sum_to_slot(rows ? rows + (int64_t)(4 * m + off) * nbxy : nullptr, (double)vx);
-          sum_to_slot(rows ? rows + (int64_t)(4 * m + 2 + off) * nbxy : nullptr, (double)vy);
+          if constexpr (WS > 1) {
+            double* rows = p.mon_partial_H;
+            warp_sum_to((double)vx, wslot(rows ? rows + (int64_t)(4 * m + off) * nbxy : nullptr));
+            warp_sum_to((double)vy, wslot(rows ? rows + (int64_t)(4 * m + 2 + off) * nbxy : nullptr));
+          } else {
+            double sx = block_sum((double)vx, sred);
+            double sy = block_sum((double)vy, sred);
+            if (tid == 0 && p.mon_partial_H) {
+              put_slot(p.mon_partial_H + (int64_t)(4 * m + off) * nbxy, sx);
+              put_slot(p.mon_partial_H + (int64_t)(4 * m + 2 + off) * nbxy, sy);
+            }
+          }
         }
       }
       if (p.eH_on && own && in_box) {
@@ -816,9 +830,18 @@ step3d_kernel(const Step3DParams<T> p) {
       if (info & kPlaneMonE)
       for (int m = 0; m < p.nmon; ++m) {
         if (k == p.mon_z[m]) {
-          double* rows = p.mon_partial_E;
-          sum_to_slot(rows ? rows + (int64_t)(2 * m) * nbxy : nullptr, own ? (double)Ev[0] : 0.0);
-          sum_to_slot(rows ? rows + (int64_t)(2 * m + 1) * nbxy : nullptr, own ? (double)Ev[1] : 0.0);
+          if constexpr (WS > 1) {
+            double* rows = p.mon_partial_E;
+            warp_sum_to(own ? (double)Ev[0] : 0.0, wslot(rows ? rows + (int64_t)(2 * m) * nbxy : nullptr));
+            warp_sum_to(own ? (double)Ev[1] : 0.0, wslot(rows ? rows + (int64_t)(2 * m + 1) * nbxy : nullptr));
+          } else {
+            double sx = block_sum(own ? (double)Ev[0] : 0.0, sred);
+            double sy = block_sum(own ? (double)Ev[1] : 0.0, sred);
+            if (tid == 0 && p.mon_partial_E) {
+              put_slot(p.mon_partial_E + (int64_t)(2 * m) * nbxy, sx);
+              put_slot(p.mon_partial_E + (int64_t)(2 * m + 1) * nbxy, sy);
+            }
+          }
         }
       }
       hxm = sH[own_fh];
@@ -827,12 +850,28 @@ step3d_kernel(const Step3DParams<T> p) {
   }
   // energy partials of this block (every block writes, zero when outside the box)
   if (p.eE_on) {
-    sum_to_slot(p.en_partial_E + (int64_t)chunk * nbxy, uE);
-    sum_to_slot(p.en_partial_E + ((int64_t)nbxy * p.nchunks_total + chunk * nbxy), uP);
-    sum_to_slot(p.en_partial_E + ((int64_t)2 * nbxy * p.nchunks_total + chunk * nbxy), uB);
+    if constexpr (WS > 1) {
+      warp_sum_to(uE, wslot(p.en_partial_E + (int64_t)chunk * nbxy));
+      warp_sum_to(uP, wslot(p.en_partial_E + ((int64_t)nbxy * p.nchunks_total + chunk * nbxy)));
+      warp_sum_to(uB, wslot(p.en_partial_E + ((int64_t)2 * nbxy * p.nchunks_total + chunk * nbxy)));
+    } else {
+      double a = block_sum(uE, sred);
+      double b = block_sum(uP, sred);
+      double c = block_sum(uB, sred);
+      if (tid == 0) {
+        put_slot(p.en_partial_E + (int64_t)chunk * nbxy, a);
+        put_slot(p.en_partial_E + ((int64_t)nbxy * p.nchunks_total + chunk * nbxy), b);
+        put_slot(p.en_partial_E + ((int64_t)2 * nbxy * p.nchunks_total + chunk * nbxy), c);
+      }
+    }
   }
   if (p.eH_on) {
-    sum_to_slot(p.en_partial_H + (int64_t)chunk * nbxy, uH);
+    if constexpr (WS > 1) {
+      warp_sum_to(uH, wslot(p.en_partial_H + (int64_t)chunk * nbxy));
+    } else {
+      double a = block_sum(uH, sred);
+      if (tid == 0) put_slot(p.en_partial_H + (int64_t)chunk * nbxy, a);
+    }
   }
 }
 
