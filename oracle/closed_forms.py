@@ -178,35 +178,54 @@ def transmission_discrete(nu, prob, k_left=None, k_right=None):
     return out
 
 
-def transmission_continuum(nu, prob):
-    """|t|^2 of the layered structure with continuum susceptibilities (normal incidence).
+def _continuum_matrix(f, layers, dx):
+    """Characteristic matrix of the layered structure at frequency f (normal incidence):
+    the product over layers (and vacuum gaps) of [[cos d, -i sin d / n], [-i n sin d, cos d]],
+    d = n w L, n = sqrt(eps_inf + chi)."""
+    w = TWO_PI * f
+    Mt = np.eye(2, dtype=np.complex128)
+    prev_hi = None
+    for m in layers:
+        lo, hi = m["z"]
+        if prev_hi is not None and lo > prev_hi:  # vacuum gap
+            d = w * (lo - prev_hi) * dx
+            Mt = Mt @ np.array([[math.cos(d), -1j * math.sin(d)],
+                                [-1j * math.sin(d), math.cos(d)]])
+        eps = m.get("eps_inf", 1.0) + complex(chi_material(f, m))
+        n = np.sqrt(eps)
+        if n.imag < 0:
+            n = -n
+        d = n * w * (hi - lo) * dx
+        Mt = Mt @ np.array([[np.cos(d), -1j * np.sin(d) / n], [-1j * n * np.sin(d), np.cos(d)]])
+        prev_hi = hi
+    return Mt
 
-    Each material spans (hi - lo) dx; characteristic matrix per layer
-    [[cos d, -i sin d / n], [-i n sin d, cos d]], d = n w L, n = sqrt(eps_inf + chi).
-    """
+
+def transmission_continuum(nu, prob):
+    """|t|^2 of the layered structure with continuum susceptibilities (normal incidence,
+    vacuum on both sides): t = 2 / (M00 + M01 + M10 + M11) of the characteristic matrix."""
     nu = np.atleast_1d(np.asarray(nu, dtype=np.float64))
     dx = 1.0 / float(prob["resolution"])
     layers = sorted(prob.get("materials", []), key=lambda m: m["z"][0])
     out = np.empty(nu.shape)
     for q, f in enumerate(nu):
-        w = TWO_PI * f
-        Mt = np.eye(2, dtype=np.complex128)
-        prev_hi = None
-        for m in layers:
-            lo, hi = m["z"]
-            if prev_hi is not None and lo > prev_hi:  # vacuum gap
-                d = w * (lo - prev_hi) * dx
-                Mt = Mt @ np.array([[math.cos(d), -1j * math.sin(d)],
-                                    [-1j * math.sin(d), math.cos(d)]])
-            eps = m.get("eps_inf", 1.0) + complex(chi_material(f, m))
-            n = np.sqrt(eps)
-            if n.imag < 0:
-                n = -n
-            d = n * w * (hi - lo) * dx
-            Mt = Mt @ np.array([[np.cos(d), -1j * np.sin(d) / n], [-1j * n * np.sin(d), np.cos(d)]])
-            prev_hi = hi
+        Mt = _continuum_matrix(f, layers, dx)
         t = 2.0 / (Mt[0, 0] + Mt[0, 1] + Mt[1, 0] + Mt[1, 1])
         out[q] = abs(t) ** 2
+    return out
+
+
+def reflectance_continuum(nu, prob):
+    """|r|^2 of the same structure: r = (M00 + M01 - M10 - M11) / (M00 + M01 + M10 + M11).
+    The absorbed fraction is 1 - |t|^2 - |r|^2."""
+    nu = np.atleast_1d(np.asarray(nu, dtype=np.float64))
+    dx = 1.0 / float(prob["resolution"])
+    layers = sorted(prob.get("materials", []), key=lambda m: m["z"][0])
+    out = np.empty(nu.shape)
+    for q, f in enumerate(nu):
+        Mt = _continuum_matrix(f, layers, dx)
+        r = (Mt[0, 0] + Mt[0, 1] - Mt[1, 0] - Mt[1, 1]) / (Mt[0, 0] + Mt[0, 1] + Mt[1, 0] + Mt[1, 1])
+        out[q] = abs(r) ** 2
     return out
 
 

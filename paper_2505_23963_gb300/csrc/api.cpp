@@ -567,7 +567,7 @@ bool parse_field(int32_t f, FieldRef* r) {
     const int q = f - 1024;
     const int cl = q / 256;
     *r = {2, cl / 2, q % 256, cl % 2};
-    return r->mode < kMaxBath;
+    return r->mode < kMaxBathStep;
   }
   return false;
 }
@@ -775,7 +775,7 @@ int fdtdbath_create(const fdtdbath_grid* grid, double resolution, double courant
   if (3 * s->ncell > lim || 3 * s->nmatcell > lim || s->nybath > lim ||
       2 * (2 * (int64_t)s->npml + 1) * s->plane > lim)
     return bail(FDTDBATH_ERR_ARG, "state arrays above 2^31 elements are not supported");
-  if (s->nbmax > 0) s->nbmax = s->nbmax <= 4 ? 4 : s->nbmax <= 8 ? 8 : s->nbmax <= 16 ? 16 : 32;
+  if (s->nbmax > 0) s->nbmax = s->nbmax <= 4 ? 4 : s->nbmax <= 8 ? 8 : s->nbmax <= 16 ? 16 : s->nbmax <= 32 ? 32 : 128;
 
   // ---- sources / monitors / energy box ----
   for (int q = 0; q < nsrc; ++q) {
@@ -888,7 +888,7 @@ int fdtdbath_create(const fdtdbath_grid* grid, double resolution, double courant
   s->te = ny == 1;
   for (auto& q : s->srcs)
     if (q.comp != 1) s->te = false;
-  s->path1d = (nx == 1 && ny == 1 && nsrc <= 1 && nmon <= 1 && !s->ybf &&
+  s->path1d = (nx == 1 && ny == 1 && nsrc <= 1 && nmon <= 1 && !s->ybf && s->nbmax <= kMaxBath &&
                 nz <= (int64_t)kCav1DMaxCluster * kCav1DThreads);
   if (s->path1d) {
     // FP64 bath arithmetic is slow on this part: spread the cavity over the largest cluster
@@ -1535,6 +1535,7 @@ int adjoint_sweep(fdtdbath_sim* s, const HostMon& mon, const std::vector<double>
 int fdtdbath_adjoint_forward(fdtdbath_sim* s, int64_t nsteps, int32_t checkpoint_every) {
   if (!s || nsteps < 1 || checkpoint_every < 1) return fail(s, FDTDBATH_ERR_ARG, "bad arguments to fdtdbath_adjoint_forward");
   if (s->ybf) return fail(s, FDTDBATH_ERR_UNSUPPORTED, "the adjoint does not run on bf16 bath storage");
+  if (s->nbmax > kMaxBath) return fail(s, FDTDBATH_ERR_UNSUPPORTED, "the adjoint handles at most 32 bath modes per material");
   cudaSetDevice(s->device);
   AdjState& a = s->adj;
   {

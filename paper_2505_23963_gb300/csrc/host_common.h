@@ -121,7 +121,7 @@ inline int build_material(const fdtdbath_material& M, int64_t plane, double dt, 
   h.sigma = M.sigma;
   h.nb = 0;
   if (M.kind == FDTDBATH_LORENTZ_BATH) {
-    if (M.num_bath < 0 || M.num_bath > kMaxBath) return why = "num_bath must be in [0, 32]", FDTDBATH_ERR_ARG;
+    if (M.num_bath < 0 || M.num_bath > kMaxBathStep) return why = "num_bath must be in [0, 128]", FDTDBATH_ERR_ARG;
     if (M.num_bath && (!M.bath_frequencies || !M.bath_gammas || !M.bath_couplings))
       return why = "bath arrays missing", FDTDBATH_ERR_ARG;
     h.nb = M.num_bath;

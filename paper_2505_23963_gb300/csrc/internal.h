@@ -21,7 +21,8 @@ namespace fdtdbath {
 constexpr int kMaxMat = 8;
 constexpr int kMaxSrc = 4;
 constexpr int kMaxMon = 4;
-constexpr int kMaxBath = 32;
+constexpr int kMaxBath = 32;       // bath modes per material: 1D cavity kernel, batch and adjoint
+constexpr int kMaxBathStep = 128;  // bath modes per material: the 3D / 2D step kernel (streamed above 32)
 constexpr int kTX = 32;
 constexpr int kCoefStride = 8;  // coefficient row per bath mode
 
@@ -236,7 +237,7 @@ struct SimViewMat {
   int kind, nb;
   int64_t zlo, zhi, ncell, base, ybase;
   double eps, rho, w0r2;
-  double wj2[kMaxBath];
+  double wj2[kMaxBathStep];
 };
 struct SimView {
   int prec;                 // 32 or 64

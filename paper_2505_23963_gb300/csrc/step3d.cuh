@@ -208,6 +208,7 @@ step3d_kernel(const Step3DParams<T> p) {
   // bath modes preloaded for all three components with the rest of the plane's state
   constexpr int NBP = NBMAX <= (sizeof(T) == 4 ? 8 : 4) ? NBMAX : 0;
   constexpr int NBA = NBMAX > 0 ? NBMAX : 1;
+  constexpr bool kStream = NBMAX > 32;   // bath modes streamed from memory (N_b up to kMaxBathStep)
   extern __shared__ __align__(16) unsigned char smem_raw[];
   // E_in frames, ring of kRingE planes [kRingE][3][FE]: planes k, k+1 feed H^n(k), plane k
   // also the E update of k (after the second barrier), planes up to k+kAheadE are in flight;
@@ -660,12 +661,30 @@ step3d_kernel(const Step3DParams<T> p) {
             // bath modes already in registers: all three components together below
             if (!mat_here || (NBP > 0 && bath)) continue;
             // ---- polarization (and bath) update, one component at a time ----
-            T Yl[NBA], Vl[NBA];
+            // Up to 32 modes the component's modes are held in registers between the bath sum and
+            // the mode update; above (kStream) they are streamed twice from memory, the second
+            // pass re-reading what the first read (about 200 words per cell, an L2 hit).
+            T Yl[kStream ? 1 : NBA], Vl[kStream ? 1 : NBA];
             const int nb = bath ? M.nb : 0;
             const int yc = c * M.nb * mstride;
             T bsum = T(0);
+            if constexpr (kStream) {
+#pragma unroll 4
+              for (int jj = 0; jj < nb; ++jj) {
+                const T y = YS::load(ya + yc + jj * mstride);
+                T v = YS::load(yb + yc + jj * mstride);
+                T cf[6];
+                load_coef6(cfm + jj * kCoefStride, cf);
+                if (!INC) {
+                  bsum = bsum + cf[0] * (cf[1] * y + cf[2] * v);
+                } else {
+                  if (!YB) v = y - v;
+                  bsum = bsum + (cf[0] * y + cf[1] * v);
+                }
+              }
+            }
 #pragma unroll
-            for (int jj = 0; jj < NBA; ++jj) {
+            for (int jj = 0; jj < (kStream ? 0 : NBA); ++jj) {
               if (jj < nb) {
                 if (NBP > 0) {
                   Yl[jj] = rY[c][jj < NBP ? jj : 0];
@@ -705,8 +724,33 @@ step3d_kernel(const Step3DParams<T> p) {
             }
             T ub = T(0);
             const T dP = Vn + V0;   // P^{n+1} - P^{n-1}
+            if constexpr (kStream) {
+#pragma unroll 4
+              for (int jj = 0; jj < nb; ++jj) {
+                const T y = YS::load(ya + yc + jj * mstride);
+                T v = YS::load(yb + yc + jj * mstride);
+                if (INC && !YB) v = y - v;
+                T cf[6];
+                load_coef6(cfm + jj * kCoefStride, cf);
+                T Ynew, Vy;
+                if (!INC) {
+                  Ynew = cf[1] * y + cf[3] * v + cf[4] * (Pn - Pb);
+                  Vy = Ynew - y;
+                } else {
+                  Vy = cf[2] * y + cf[3] * v + cf[4] * dP;
+                  Ynew = y + Vy;
+                }
+                if (YB) {
+                  YS::put(ya + yc + jj * mstride, Ynew);
+                  YS::put(yb + yc + jj * mstride, Vy);
+                } else {
+                  YS::put(yb + yc + jj * mstride, Ynew);
+                }
+                if (p.eE_on) ub += Vy * Vy + cf[5] * Ynew * Ynew;
+              }
+            }
 #pragma unroll
-            for (int jj = 0; jj < NBA; ++jj) {
+            for (int jj = 0; jj < (kStream ? 0 : NBA); ++jj) {
               if (jj < nb) {
                 T cf[6];
                 load_coef6(cfm + jj * kCoefStride, cf);

@@ -31,6 +31,7 @@ static int launch_ty(const Step3DParams<float>& p, int nbmax, int nbx, int nby, 
     case 8: return launch_nb<8, TY, YB, TE>(p, nbx, nby, nchunks, stream);
     case 16: return launch_nb<16, TY, YB, TE>(p, nbx, nby, nchunks, stream);
     case 32: return launch_nb<32, TY, YB, TE>(p, nbx, nby, nchunks, stream);
+    case 128: return launch_nb<128, TY, YB, TE>(p, nbx, nby, nchunks, stream);
     default: return (int)cudaErrorInvalidValue;
   }
 }

@@ -30,6 +30,7 @@ static int launch_ty(const Step3DParams<double>& p, int nbmax, int nbx, int nby,
     case 8: return launch_nb<8, TY, TE>(p, nbx, nby, nchunks, stream);
     case 16: return launch_nb<16, TY, TE>(p, nbx, nby, nchunks, stream);
     case 32: return launch_nb<32, TY, TE>(p, nbx, nby, nchunks, stream);
+    case 128: return launch_nb<128, TY, TE>(p, nbx, nby, nchunks, stream);
     default: return (int)cudaErrorInvalidValue;
   }
 }

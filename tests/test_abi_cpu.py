@@ -71,3 +71,8 @@ def test_create_validates_before_touching_the_gpu():
     assert _create_err(dict(p, monitors=[dict(z=0, freqs=np.ones(3))])) == fb.ERR_ARG
     # Drude mirrors with w_p dt too large for the coupled field-oscillator update
     assert _create_err(dict(p, resolution=10.0)) == fb.ERR_CFL
+    # at most 128 bath modes per material (the step kernel streams them above 32)
+    lb = p["materials"][1]
+    many = dict(p, materials=[dict(lb, bath_frequencies=np.linspace(0.9, 1.1, 129),
+                                   bath_gammas=np.full(129, 0.005), bath_couplings=np.full(129, 0.001))])
+    assert _create_err(many) == fb.ERR_ARG

@@ -1,0 +1,102 @@
+"""N_b = 100 bath modes per Lorentz-Bath cell (the baths of the paper's Fig. 2: Table I's
+Lorentzian form, N = 100 over nu0 +/- 0.2, bath damping 4e-4, dephasing 0.0396).  Above 32
+modes the step kernel streams the bath modes from memory instead of holding them in registers.
+
+Parity against the FP64 oracle at the tolerances of test_gpu_parity (normwise relative):
+FP64 1e-12 for E, H, the layer's P and bath modes, spectra and energy traces; FP32 1e-5 for
+E, H and spectra, 1e-4 for the layer's P and bath modes.  Cases: a ragged 3D cavity (tiles cut
+in x and y) and the paper's free-space slab of Fig. 2a in 1D (600 cells at dx = 0.01, 50-cell
+CPML, a 1-unit slab), which runs on the step kernel (the register-resident 1D kernel holds at
+most 32 modes).  The bath arrays come from the oracle's Table I expansion (pinned by P7)."""
+import numpy as np
+import pytest
+
+from oracle import closed_forms as cf
+from oracle import oracle as O
+from paper_2505_23963_gb300 import fdtdbath as fb
+from paper_2505_23963_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+TOL = {64: 1e-12, 32: 1e-5}
+TOL_Y = {64: 1e-12, 32: 1e-4}
+NB = 100
+
+
+def rel(a, b):
+    a, b = np.asarray(a, dtype=np.complex128), np.asarray(b, dtype=np.complex128)
+    nb = np.linalg.norm(b.ravel())
+    return np.linalg.norm((a - b).ravel()) / (nb if nb > 0 else 1.0)
+
+
+def with_paper_bath(prob, mat, sigma):
+    f, g, k = cf.bath_form("lorentzian", 1.0, 4e-4, NB, 0.4, 4e-4, 0.0396)
+    mats = list(prob["materials"])
+    mats[mat] = dict(mats[mat], kind="lorentz_bath", gamma=4e-4, sigma=sigma, bath_frequencies=f,
+                     bath_gammas=g, bath_couplings=k)
+    return dict(prob, materials=mats)
+
+
+def ragged_3d(steps):
+    p = wl.small_3d(nx=40, ny=12, layout=(6, 5, 3, 10, 3, 5), nb=8, steps=steps, seed=4)
+    return with_paper_bath(p, 1, 2e-2), 1
+
+
+def paper_slab_1d(steps):
+    # cell 6 at dx = 0.01: CPML 50 | vacuum 200 | slab 100 | vacuum 200 | CPML 50
+    p = wl.slab_cavity(1, 1, (50, 200, 0, 100, 0, 200), 100.0, num_bath=8, sigma=5e-3,
+                       phase_seed=None, nfreq=64, steps=steps, name="paper_slab_fig2a")
+    return with_paper_bath(p, 0, 5e-3), 0
+
+
+def compare(prob, mat, precision, steps):
+    s = fb.Simulation(prob, precision=precision, energy_capacity=steps + 8)
+    s.step(steps)
+    o = O.OracleSim(prob, trace_cap=steps + 8)
+    o.step(steps)
+    lo, hi = prob["materials"][mat]["z"]
+    for name in ("E", "H"):
+        g = np.stack([s.get(name, comp=c) for c in range(3)])
+        r = np.stack([o.get(name, comp=c) for c in range(3)])
+        assert rel(g, r) < TOL[precision], (name, rel(g, r))
+    for name in ("P", "Pm"):
+        g = np.stack([s.get(name, comp=c)[lo:hi] for c in range(3)])
+        r = np.stack([o.get(name, comp=c)[lo:hi] for c in range(3)])
+        assert rel(g, r) < TOL_Y[precision], (name, rel(g, r))
+    for j in (0, 37, NB - 1):
+        for lvl in (0, 1):
+            g = np.stack([s.get("Y", comp=c, mode=j, level=lvl)[lo:hi] for c in range(3)])
+            r = np.stack([o.get("Y", comp=c, mode=j, level=lvl)[lo:hi] for c in range(3)])
+            assert rel(g, r) < TOL_Y[precision], (j, lvl, rel(g, r))
+    assert rel(s.dft(0), o.dft(0)) < TOL[precision]
+    tg, to = s.trace(), o.trace()
+    n = min(len(tg), len(to))
+    for col in range(3):
+        if np.any(to[:n, col]):
+            assert rel(tg[:n, col], to[:n, col]) < 2 * TOL[precision], col
+    s.close()
+
+
+@pytest.mark.parametrize("precision", [64, 32])
+def test_many_bath_modes_3d(precision):
+    prob, mat = ragged_3d(120)
+    compare(prob, mat, precision, 120)
+
+
+@pytest.mark.parametrize("precision", [64, 32])
+def test_paper_slab_fig2a_1d(precision):
+    prob, mat = paper_slab_1d(1500)
+    compare(prob, mat, precision, 1500)
+
+
+def test_forms_limited_to_32_modes():
+    """The batch and the adjoint hold at most 32 bath modes per material."""
+    prob, _ = paper_slab_1d(10)
+    with pytest.raises(fb.FdtdBathError) as e:
+        fb.Batch([prob])
+    assert e.value.code == fb.ERR_ARG
+    s = fb.Simulation(prob, precision=32)
+    with pytest.raises(fb.FdtdBathError) as e:
+        s.adjoint_forward(10, 4)
+    assert e.value.code == fb.ERR_UNSUPPORTED
+    s.close()
