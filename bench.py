@@ -243,6 +243,47 @@ def form_precision(fb, stream, torch):
     return out
 
 
+def many_bath_slab(fb, nxy: int = 256, steps: int = 40) -> dict:
+    """nxy x nxy x 160 slab cavity (resolution 32, CPML 16 | 40 | Drude 8 | Lorentz-Bath 32 |
+    Drude 8 | 40 | CPML 16) whose layer carries the paper's Fig. 2 bath: N_b = 100 modes of
+    Table I's Lorentzian form over nu0 +/- 0.2 (fdtdbath_bath_form), bath damping 4e-4,
+    dephasing 0.0396, gamma0 = 4e-4, sigma = 2e-2."""
+    f, g, k = fb.bath_form("lorentzian", 1.0, 4e-4, 100, 0.4, 4e-4, 0.0396)
+    prob = wl.slab_cavity(nxy, nxy, (16, 40, 8, 32, 8, 40), 32.0, num_bath=8, sigma=2e-2,
+                          steps=steps, name=f"slab3d_{nxy}x{nxy}x160_nb100")
+    mats = list(prob["materials"])
+    mats[1] = dict(mats[1], gamma=4e-4, bath_frequencies=f, bath_gammas=g, bath_couplings=k)
+    return dict(prob, materials=mats)
+
+
+def form_many_bath(fb, stream, torch):
+    """N_b = 100 (the paper's Fig. 2 bath) on the 256 x 256 x 160 slab, FP32: above 32 modes the
+    step kernel streams the bath modes twice per step (bath sum, then update); the algorithmic
+    bytes count every state word once, so the roofline fraction shows what the second pass
+    costs."""
+    hbm, _ = peaks()
+    prob = many_bath_slab(fb)
+    cells = float(np.prod(prob["n"]))
+    with torch.cuda.stream(stream):
+        sim = fb.Simulation(prob, precision=32, stream=stream, energy_capacity=64)
+    sim.step(3)
+    sim.sync()
+    k = 20
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    ev[0].record(stream)
+    sim.step(k)
+    ev[1].record(stream)
+    torch.cuda.synchronize()
+    ms = ev[0].elapsed_time(ev[1]) / k
+    finite = bool(np.all(np.isfinite(sim.dft(0))))
+    sim.close()
+    byts = algorithmic_bytes(prob, 4)
+    return {"workload": prob["name"], "value": cells / (ms * 1e-3), "unit": UNIT,
+            "ms_per_step": ms, "bytes_per_cell": byts / cells,
+            "achieved_GBs": byts / (ms * 1e-3) / 1e9, "frac_hbm": byts / (ms * 1e-3) / 1e9 / hbm,
+            "finite": finite}
+
+
 def form_batch(fb, torch):
     """Batching form: 64 independent 1D cavities (lengths 1000-8000, Rabi 0.01-0.2, N_b in
     {4, 8, 16, 32}), 50000 FP32 steps in persistent launches replayed from CUDA graphs, energy every
@@ -330,11 +371,19 @@ def form_adjoint(fb, torch):
 
 def profile_form(name: str) -> int:
     """Short runs of one form for profiler captures: the 64-cavity batch for 64 steps in a fixed
-    launch shape (C = 8, 256 threads), or 16 steps of the 2048^2 differentiation form forward and
-    reverse (checkpoints every 8 steps: about 2 GB of device memory)."""
+    launch shape (C = 8, 256 threads), 16 steps of the 2048^2 differentiation form forward and
+    reverse (checkpoints every 8 steps: about 2 GB of device memory), or 8 steps of the N_b = 100
+    slab at 128 x 128 (about 1.5 GB)."""
     import torch
     from paper_2505_23963_gb300 import fdtdbath as fb
     torch.cuda.set_device(0)
+    if name == "manybath":
+        sim = fb.Simulation(many_bath_slab(fb, nxy=128, steps=8), precision=32, energy_capacity=16)
+        sim.step(8)
+        sim.sync()
+        print(json.dumps({"form": "manybath", "steps": 8}), flush=True)
+        sim.close()
+        return 0
     if name == "batch":
         b = fb.Batch(wl.batch_sweep(steps=64), precision=32, energy_every=10, cluster_ctas=8,
                      block_threads=256, use_graph=False)
@@ -519,6 +568,7 @@ def run_ours(args):
     if ws == 1 and not args.no_forms:
         forms = {}
         for name, fn in (("precision", lambda: form_precision(fb, stream, torch)),
+                         ("many_bath", lambda: form_many_bath(fb, stream, torch)),
                          ("batch", lambda: form_batch(fb, torch)),
                          ("adjoint", lambda: form_adjoint(fb, torch))):
             try:
@@ -547,7 +597,7 @@ def main():
     ap.add_argument("--quick", action="store_true",
                     help="FP32 step timing only (for profiler captures)")
     ap.add_argument("--grid", default="", help="override nx,ny of the workload (profiling)")
-    ap.add_argument("--profile-form", default="", choices=["", "batch", "adjoint"],
+    ap.add_argument("--profile-form", default="", choices=["", "batch", "adjoint", "manybath"],
                     help="run a short version of one form only (for profiler captures)")
     args = ap.parse_args()
     if args.warmup < 3:

@@ -209,6 +209,7 @@ step3d_kernel(const Step3DParams<T> p) {
   constexpr int NBP = NBMAX <= (sizeof(T) == 4 ? 8 : 4) ? NBMAX : 0;
   constexpr int NBA = NBMAX > 0 ? NBMAX : 1;
   constexpr bool kStream = NBMAX > 32;   // bath modes streamed from memory (N_b up to kMaxBathStep)
+  constexpr int kStreamBatch = 16;      // modes whose loads are issued together when streaming
   extern __shared__ __align__(16) unsigned char smem_raw[];
   // E_in frames, ring of kRingE planes [kRingE][3][FE]: planes k, k+1 feed H^n(k), plane k
   // also the E update of k (after the second barrier), planes up to k+kAheadE are in flight;
@@ -669,17 +670,28 @@ step3d_kernel(const Step3DParams<T> p) {
             const int yc = c * M.nb * mstride;
             T bsum = T(0);
             if constexpr (kStream) {
-#pragma unroll 4
-              for (int jj = 0; jj < nb; ++jj) {
-                const T y = YS::load(ya + yc + jj * mstride);
-                T v = YS::load(yb + yc + jj * mstride);
-                T cf[6];
-                load_coef6(cfm + jj * kCoefStride, cf);
-                if (!INC) {
-                  bsum = bsum + cf[0] * (cf[1] * y + cf[2] * v);
-                } else {
-                  if (!YB) v = y - v;
-                  bsum = bsum + (cf[0] * y + cf[1] * v);
+              // batches of kStreamBatch modes: all their loads issued before any is used
+              for (int j0 = 0; j0 < nb; j0 += kStreamBatch) {
+                T ys[kStreamBatch], vs[kStreamBatch];
+#pragma unroll
+                for (int u = 0; u < kStreamBatch; ++u) {
+                  if (j0 + u < nb) {
+                    ys[u] = YS::load(ya + yc + (j0 + u) * mstride);
+                    vs[u] = YS::load(yb + yc + (j0 + u) * mstride);
+                  }
+                }
+#pragma unroll
+                for (int u = 0; u < kStreamBatch; ++u) {
+                  if (j0 + u < nb) {
+                    T cf[6];
+                    load_coef6(cfm + (j0 + u) * kCoefStride, cf);
+                    if (!INC) {
+                      bsum = bsum + cf[0] * (cf[1] * ys[u] + cf[2] * vs[u]);
+                    } else {
+                      const T v = YB ? vs[u] : ys[u] - vs[u];
+                      bsum = bsum + (cf[0] * ys[u] + cf[1] * v);
+                    }
+                  }
                 }
               }
             }
@@ -725,28 +737,40 @@ step3d_kernel(const Step3DParams<T> p) {
             T ub = T(0);
             const T dP = Vn + V0;   // P^{n+1} - P^{n-1}
             if constexpr (kStream) {
-#pragma unroll 4
-              for (int jj = 0; jj < nb; ++jj) {
-                const T y = YS::load(ya + yc + jj * mstride);
-                T v = YS::load(yb + yc + jj * mstride);
-                if (INC && !YB) v = y - v;
-                T cf[6];
-                load_coef6(cfm + jj * kCoefStride, cf);
-                T Ynew, Vy;
-                if (!INC) {
-                  Ynew = cf[1] * y + cf[3] * v + cf[4] * (Pn - Pb);
-                  Vy = Ynew - y;
-                } else {
-                  Vy = cf[2] * y + cf[3] * v + cf[4] * dP;
-                  Ynew = y + Vy;
+              for (int j0 = 0; j0 < nb; j0 += kStreamBatch) {
+                T ys[kStreamBatch], vs[kStreamBatch];
+#pragma unroll
+                for (int u = 0; u < kStreamBatch; ++u) {
+                  if (j0 + u < nb) {
+                    ys[u] = YS::load(ya + yc + (j0 + u) * mstride);
+                    vs[u] = YS::load(yb + yc + (j0 + u) * mstride);
+                  }
                 }
-                if (YB) {
-                  YS::put(ya + yc + jj * mstride, Ynew);
-                  YS::put(yb + yc + jj * mstride, Vy);
-                } else {
-                  YS::put(yb + yc + jj * mstride, Ynew);
+#pragma unroll
+                for (int u = 0; u < kStreamBatch; ++u) {
+                  const int jj = j0 + u;
+                  if (jj >= nb) break;
+                  const T y = ys[u];
+                  T v = vs[u];
+                  if (INC && !YB) v = y - v;
+                  T cf[6];
+                  load_coef6(cfm + jj * kCoefStride, cf);
+                  T Ynew, Vy;
+                  if (!INC) {
+                    Ynew = cf[1] * y + cf[3] * v + cf[4] * (Pn - Pb);
+                    Vy = Ynew - y;
+                  } else {
+                    Vy = cf[2] * y + cf[3] * v + cf[4] * dP;
+                    Ynew = y + Vy;
+                  }
+                  if (YB) {
+                    YS::put(ya + yc + jj * mstride, Ynew);
+                    YS::put(yb + yc + jj * mstride, Vy);
+                  } else {
+                    YS::put(yb + yc + jj * mstride, Ynew);
+                  }
+                  if (p.eE_on) ub += Vy * Vy + cf[5] * Ynew * Ynew;
                 }
-                if (p.eE_on) ub += Vy * Vy + cf[5] * Ynew * Ynew;
               }
             }
 #pragma unroll
