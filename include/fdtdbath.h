@@ -80,7 +80,10 @@ typedef struct {
 
 /* One planar layer (Sec. III: MEEP's LorentzianSusceptibility / BathLorentzianSusceptibility
  * keywords).  For FDTDBATH_LORENTZ_BATH, gamma is gamma0 and the three bath arrays give
- * {w_j}, {gamma_j}, {k_j} (host pointers, num_bath entries each, 1 <= num_bath <= 32). */
+ * {w_j}, {gamma_j}, {k_j} (host pointers, num_bath entries each, 1 <= num_bath <= 128; the
+ * paper's Fig. 2 baths have 100).  Up to 32 modes the step kernel keeps a cell's modes in
+ * registers, above it streams them from memory; the batch form and the adjoint take at most 32
+ * (FDTDBATH_ERR_ARG / FDTDBATH_ERR_UNSUPPORTED). */
 typedef struct {
   int32_t kind;
   int64_t z_lo, z_hi;
@@ -225,8 +228,8 @@ int fdtdbath_box_energy_noalloc(fdtdbath_sim *sim, int64_t z_lo, int64_t z_hi, d
  * --------------------------------------------------------------------------------------------- */
 
 /* Advance nsteps steps (as fdtdbath_step), saving the checkpoints of the run; the spectra and
- * energy traces accumulate as usual.  Not available with bf16 bath storage
- * (FDTDBATH_ERR_UNSUPPORTED).  A later fdtdbath_step invalidates the recording. */
+ * energy traces accumulate as usual.  Not available with bf16 bath storage or with more than 32
+ * bath modes in a material (FDTDBATH_ERR_UNSUPPORTED).  A later fdtdbath_step invalidates the recording. */
 int fdtdbath_adjoint_forward(fdtdbath_sim *sim, int64_t nsteps, int32_t checkpoint_every);
 
 /* Reverse sweep of the recorded run.  dL_dF: host array nfreq x 4 x 2 with dL/dRe and dL/dIm of
@@ -250,7 +253,8 @@ int fdtdbath_adjoint_backward(fdtdbath_sim *sim, int32_t monitor, const double *
 typedef struct fdtdbath_batch fdtdbath_batch; /* opaque, owned by the library */
 
 /* One cavity: nz cells (64 <= nz <= 2^24) with a CPML of pml_cells cells at each end, its layers
- * (z in the cavity's own cells, the same rules as fdtdbath_create), an optional soft source on
+ * (z in the cavity's own cells, the same rules as fdtdbath_create, at most 32 bath modes per
+ * layer), an optional soft source on
  * component 0 (E_x; phase NULL or one value) and an optional energy box [energy_lo, energy_hi)
  * (energy_hi <= energy_lo: none).  Host pointers, copied by fdtdbath_batch_create. */
 typedef struct {

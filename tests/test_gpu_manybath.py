@@ -100,3 +100,34 @@ def test_forms_limited_to_32_modes():
         s.adjoint_forward(10, 4)
     assert e.value.code == fb.ERR_UNSUPPORTED
     s.close()
+
+
+def test_many_bath_modes_2d_te_form():
+    """A y-invariant, E_y-driven 2D crop with N_b = 100: the TE form of the streamed kernel
+    (128-wide single-row tiles) against the FP64 oracle."""
+    p = wl.adjoint_crop(steps=300, nb=8)
+    prob = with_paper_bath(p, 1, 2e-2)
+    s = fb.Simulation(prob, precision=64, energy_capacity=308)
+    assert s.te_form()
+    s.close()
+    compare(prob, 1, 64, 300)
+
+
+def test_many_bath_modes_bf16_storage():
+    """bf16 bath storage with N_b = 100 (value / increment pairs, streamed): fields, spectrum
+    and the layer's polarization within the bf16 bounds of the precision form (1e-3)."""
+    prob, mat = ragged_3d(120)
+    s = fb.Simulation(prob, precision=32, bath_storage=1, energy_capacity=128)
+    s.step(120)
+    o = O.OracleSim(prob, trace_cap=128)
+    o.step(120)
+    lo, hi = prob["materials"][mat]["z"]
+    for name in ("E", "H"):
+        g = np.stack([s.get(name, comp=c) for c in range(3)])
+        r = np.stack([o.get(name, comp=c) for c in range(3)])
+        assert rel(g, r) < 1e-3, (name, rel(g, r))
+    g = np.stack([s.get("P", comp=c)[lo:hi] for c in range(3)])
+    r = np.stack([o.get("P", comp=c)[lo:hi] for c in range(3)])
+    assert rel(g, r) < 1e-3, rel(g, r)
+    assert rel(s.dft(0), o.dft(0)) < 1e-3
+    s.close()
