@@ -1465,6 +1465,11 @@ int adjoint_sweep(fdtdbath_sim* s, const HostMon& mon, const std::vector<double>
     return ce == cudaSuccess ? 0 : cuda_fail(s, ce, "adjoint snapshot");
   };
   const int64_t ncp = (NS + L - 1) / L;
+  // a TE forward run keeps the x / z components of E, P and the bath modes at zero: only the
+  // y component is recorded (the record buffers start at zero and the others stay so)
+  const bool te_rec = s->te && s->ty == 1;
+  auto live = [&](int cc) { return !te_rec || cc == 1; };
+  const size_t yoff = te_rec ? (size_t)nb * ncm : 0, ycount = (te_rec ? 1 : 3) * (size_t)nb * ncm;
   for (int64_t c = ncp - 1; c >= 0 && !rc; --c) {
     rc = restore_checkpoint(s, (size_t)c);
     if (rc) break;
@@ -1474,8 +1479,10 @@ int adjoint_sweep(fdtdbath_sim* s, const HostMon& mon, const std::vector<double>
     for (int lv = 0; lv < 2 && !rc; ++lv) {
       const int slot = lv == 0 ? 1 - s->pcur : s->pcur;
       for (int cc = 0; cc < 3 && !rc; ++cc)
-        rc = snap(snapP + ((size_t)lv * 3 + cc) * ncm, elem_ptr(s->Pslot[slot], cc * s->nmatcell + G.base, e), (size_t)ncm);
-      if (!rc && nb) rc = snap(snapY + (size_t)lv * 3 * nb * ncm, elem_ptr(s->Yslot[slot], G.ybase, e), (size_t)3 * nb * ncm);
+        if (live(cc))
+          rc = snap(snapP + ((size_t)lv * 3 + cc) * ncm, elem_ptr(s->Pslot[slot], cc * s->nmatcell + G.base, e), (size_t)ncm);
+      if (!rc && nb)
+        rc = snap(snapY + (size_t)lv * 3 * nb * ncm + yoff, elem_ptr(s->Yslot[slot], G.ybase + (int64_t)yoff, e), ycount);
     }
     // recompute the segment, recording the material's E, P and Y after every step
     for (int m = 0; m < Lc && !rc; ++m) {
@@ -1486,13 +1493,15 @@ int adjoint_sweep(fdtdbath_sim* s, const HostMon& mon, const std::vector<double>
       s->h_pending = true;
       s->reduced = s->n;
       for (int cc = 0; cc < 3 && !rc; ++cc) {
+        if (!live(cc)) continue;
         rc = snap(snapE + ((size_t)m * 3 + cc) * ncm, elem_ptr(s->E[s->ecur], cc * N + G.zlo * plane, e), (size_t)ncm);
         if (!rc)
           rc = snap(snapP + ((size_t)(m + 2) * 3 + cc) * ncm, elem_ptr(s->Pslot[s->pcur], cc * s->nmatcell + G.base, e),
                     (size_t)ncm);
       }
       if (!rc && nb)
-        rc = snap(snapY + (size_t)(m + 2) * 3 * nb * ncm, elem_ptr(s->Yslot[s->pcur], G.ybase, e), (size_t)3 * nb * ncm);
+        rc = snap(snapY + (size_t)(m + 2) * 3 * nb * ncm + yoff, elem_ptr(s->Yslot[s->pcur], G.ybase + (int64_t)yoff, e),
+                  ycount);
     }
     // reverse sweep over the segment
     for (int m = Lc - 1; m >= 0 && !rc; --m) {
