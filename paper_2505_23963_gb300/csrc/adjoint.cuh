@@ -153,16 +153,43 @@ __global__ void __launch_bounds__(kAdjThreads, (TE && NBMAX <= 8) ? 4 : 0) adjoi
           T pmold = T(0);
           T yold[NBA], ymold[NBA], ynb[NBA];
           const int64_t yc = M.ybase + (int64_t)c * nb * M.ncell + rm;
+          // the TE form (one component, registers to spare) issues every load of the cell before
+          // any arithmetic: the bath adjoints and, for the differentiated layer, the recorded
+          // forward values; the arithmetic below is the same either way
+          T y1v[NBA], fEv = T(0), fPnv = T(0), fPmv = T(0), fYv[NBA], fYmv[NBA];
+          if constexpr (TE) {
+            const int64_t ig = (int64_t)c * M.ncell + rm;
+#pragma unroll
+            for (int jj = 0; jj < NBA; ++jj) {
+              if (jj < nb) {
+                ynb[jj] = Y0_[yc + jj * M.ncell];
+                y1v[jj] = Y1_[yc + jj * M.ncell];
+              }
+            }
+            if (grad) {
+              fEv = __ldg(p.fE + ig);
+              fPnv = __ldg(p.fPn + ig);
+              fPmv = __ldg(p.fPm + ig);
+#pragma unroll
+              for (int jj = 0; jj < NBA; ++jj) {
+                if (jj < nb) {
+                  const int64_t iy = ((int64_t)c * nb + jj) * M.ncell + rm;
+                  fYv[jj] = __ldg(p.fY + iy);
+                  fYmv[jj] = __ldg(p.fYm + iy);
+                }
+              }
+            }
+          }
 #pragma unroll
           for (int jj = 0; jj < NBA; ++jj) {
             yold[jj] = T(0);
             ymold[jj] = T(0);
-            ynb[jj] = T(0);
+            if (!TE) ynb[jj] = T(0);
             if (jj < nb) {
               const T* cf = cfm + jj * kCoefStride;
-              const T yn = Y0_[yc + jj * M.ncell];                 // adjoint of Y^{n+3/2}
+              const T yn = TE ? ynb[jj] : Y0_[yc + jj * M.ncell];   // adjoint of Y^{n+3/2}
               ynb[jj] = yn;
-              yold[jj] = Y1_[yc + jj * M.ncell] + __ldg(cf + 1) * yn;   // shift + a_j
+              yold[jj] = (TE ? y1v[jj] : Y1_[yc + jj * M.ncell]) + __ldg(cf + 1) * yn;   // shift + a_j
               ymold[jj] = __ldg(cf + 3) * yn;                           // (b_j + 1)
               const T c4 = __ldg(cf + 4);
               pn += c4 * yn;                                            // c_j (P_new - P_m)
@@ -176,7 +203,8 @@ __global__ void __launch_bounds__(kAdjThreads, (TE && NBMAX <= 8) ? 4 : 0) adjoi
           // gradient terms first: they need pn and the incoming bath adjoints ynb
           if (grad) {
             const int64_t ig = (int64_t)c * M.ncell + rm;
-            const T E = __ldg(p.fE + ig), Pn = __ldg(p.fPn + ig), Pm = __ldg(p.fPm + ig);
+            const T E = TE ? fEv : __ldg(p.fE + ig), Pn = TE ? fPnv : __ldg(p.fPn + ig);
+            const T Pm = TE ? fPmv : __ldg(p.fPm + ig);
             const T hA = p.thA;
             gsig += pn * E * p.tsig;
             ggam += pn * hA * (Pm - Pn);
@@ -184,7 +212,7 @@ __global__ void __launch_bounds__(kAdjThreads, (TE && NBMAX <= 8) ? 4 : 0) adjoi
             for (int jj = 0; jj < NBA; ++jj) {
               if (jj < nb) {
                 const int64_t iy = ((int64_t)c * nb + jj) * M.ncell + rm;
-                const T Y = __ldg(p.fY + iy), Ym = __ldg(p.fYm + iy);
+                const T Y = TE ? fYv[jj] : __ldg(p.fY + iy), Ym = TE ? fYmv[jj] : __ldg(p.fYm + iy);
                 gk[jj] += pn * hA * (p.tds[jj] * (Pm - Pn) - (p.ta[jj] * Y + p.tb[jj] * Ym)) +
                           ynb[jj] * p.tdc[jj] * (Pn - Pm);
               }
