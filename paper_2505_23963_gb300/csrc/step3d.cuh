@@ -200,7 +200,15 @@ step3d_kernel(const Step3DParams<T> p) {
   using YS = BathStore<T, YB>;   // bath-mode storage (YB: bf16 value / increment pairs)
   using YT = typename YS::S;
   using G = Tile<TY, TXW>;
-  constexpr int TX = G::TX, FX = G::FX, HX = G::HX, NTHR = G::NTHR, FE = G::FE, FH = G::FH;
+  constexpr int TX = G::TX, FX = G::FX, HX = G::HX, NTHR = G::NTHR;
+  // Stored frames.  The general form keeps the three components of E rows y0-1 .. y0+TY and of H
+  // rows y0-1 .. y0+TY-1; the TE form only the tile's own row of E_y and of H_x, H_z.  RO is the
+  // first stored frame row, FE / FH the stored elements per component, eo / ho component offsets.
+  constexpr int RO = TE ? 1 : 0;
+  constexpr int FE = TE ? FX : G::FE, FH = TE ? HX : G::FH;
+  constexpr int NEC = TE ? 1 : 3, NHC = TE ? 2 : 3;   // stored components per frame slot
+  auto eo = [](int c) { return TE ? 0 : c * FE; };
+  auto ho = [](int c) { return TE ? (c == 2 ? FH : 0) : c * FH; };
   constexpr int FY = G::FY, HY = G::HY;
   constexpr int VE = 16 / (int)sizeof(T);      // elements per 16-byte copy
   constexpr int NCE = FY * (FX / VE), NCH = HY * (HX / VE);   // 16-byte chunks per frame component
@@ -216,9 +224,9 @@ step3d_kernel(const Step3DParams<T> p) {
   // the slot refilled at the top of step k+1 held plane k+1+kAheadE-kRingE <= k-1, last read
   // before this step's first barrier.  H_in frames likewise, ring of kRingH planes.
   T* sE = reinterpret_cast<T*>(smem_raw);
-  T* sHin = sE + kRingE * 3 * FE;                // H_in frames: [kRingH][3][FH]
-  T* sH = sHin + kRingH * 3 * FH;                // H^n of the current plane: [3][FH]
-  T* sCoef = sH + 3 * FH;                        // bath coefficients:            [modes][8]
+  T* sHin = sE + kRingE * NEC * FE;              // H_in frames: [kRingH][3][FH]
+  T* sH = sHin + kRingH * NHC * FH;              // H^n of the current plane: [3][FH]
+  T* sCoef = sH + NHC * FH;                      // bath coefficients:            [modes][8]
   int* sInfo = reinterpret_cast<int*>(sCoef + kCoefStride * p.nmodes);   // [kMaxChunk]
   double* sred = reinterpret_cast<double*>(
       (reinterpret_cast<uintptr_t>(sInfo + kMaxChunk) + 15) & ~uintptr_t(15));
@@ -297,7 +305,7 @@ step3d_kernel(const Step3DParams<T> p) {
     ce_g[r] = 0;
     if (idx < (TE ? cpr_e : NCE) && p.vec16) {
       const int yy = TE ? 1 : idx / cpr_e, cx = TE ? idx : idx - yy * cpr_e;   // TE: own row only
-      ce_s[r] = yy * FX + cx * VE;
+      ce_s[r] = (yy - RO) * FX + cx * VE;
       ce_g[r] = wrapi(y0 - 1 + yy, p.ny) * p.nx + wrapi(x0 - 4 + cx * VE, p.nx);
     }
   }
@@ -308,13 +316,13 @@ step3d_kernel(const Step3DParams<T> p) {
     ch_g[r] = 0;
     if (idx < (TE ? cpr_h : NCH) && p.vec16) {
       const int yy = TE ? 1 : idx / cpr_h, cx = TE ? idx : idx - yy * cpr_h;   // TE: own row only
-      ch_s[r] = yy * HX + cx * VE;
+      ch_s[r] = (yy - RO) * HX + cx * VE;
       ch_g[r] = wrapi(y0 - 1 + yy, p.ny) * p.nx + wrapi(x0 - 4 + cx * VE, p.nx);
     }
   }
 
   // H tasks of this thread: its own cell, and up to two cells of the -y row / -x column halo
-  const int own_fe = (ty + 1) * FX + (tx + 1 + kXO), own_fh = (ty + 1) * HX + (tx + 1 + kXO);
+  const int own_fe = (ty + 1 - RO) * FX + (tx + 1 + kXO), own_fh = (ty + 1 - RO) * HX + (tx + 1 + kXO);
   // (TE: the -x column only)
   constexpr int NHALO = TE ? TY : TX + TY;
   constexpr int NHT = (NHALO + NTHR - 1) / NTHR;
@@ -327,13 +335,13 @@ step3d_kernel(const Step3DParams<T> p) {
     ht_g[r] = 0;
     if (t < NHALO) {
       const int hy = TE ? t + 1 : (t < TX ? 0 : t - TX + 1), hx = TE ? 0 : (t < TX ? t + 1 : 0);
-      ht_fe[r] = hy * FX + hx + kXO;
-      ht_fh[r] = hy * HX + hx + kXO;
+      ht_fe[r] = (hy - RO) * FX + hx + kXO;
+      ht_fh[r] = (hy - RO) * HX + hx + kXO;
       ht_g[r] = wrapi(y0 - 1 + hy, p.ny) * p.nx + wrapi(x0 - 1 + hx, p.nx);
     }
   }
-  auto slotE = [&](int k) -> T* { return sE + (k % kRingE) * 3 * FE; };
-  auto slotH = [&](int k) -> T* { return sHin + (k & (kRingH - 1)) * 3 * FH; };
+  auto slotE = [&](int k) -> T* { return sE + (k % kRingE) * NEC * FE; };
+  auto slotH = [&](int k) -> T* { return sHin + (k & (kRingH - 1)) * NHC * FH; };
 
   // asynchronous staging of the E_in frame of plane k (tile + 1 cell, periodic in x, y)
   auto issueE = [&](int k) {
@@ -348,10 +356,10 @@ step3d_kernel(const Step3DParams<T> p) {
         for (int c = 0; c < 3; ++c) {
           if (!liveE(c)) continue;
           if (in) {
-            cp_async16(dst + c * FE + ce_s[r], src + c * ncell + ce_g[r]);
+            cp_async16(dst + eo(c) + ce_s[r], src + c * ncell + ce_g[r]);
           } else {
 #pragma unroll
-            for (int v = 0; v < VE; ++v) dst[c * FE + ce_s[r] + v] = T(0);
+            for (int v = 0; v < VE; ++v) dst[eo(c) + ce_s[r] + v] = T(0);
           }
         }
       }
@@ -363,7 +371,7 @@ step3d_kernel(const Step3DParams<T> p) {
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
           if (!liveE(c)) continue;
-          T* d = dst + c * FE + yy * FX + hx + kXO;
+          T* d = dst + eo(c) + (yy - RO) * FX + hx + kXO;
           if (in) cp_async_elem(d, src + c * ncell + g);
           else *d = T(0);
         }
@@ -380,7 +388,7 @@ step3d_kernel(const Step3DParams<T> p) {
         if (ch_s[r] < 0) continue;
 #pragma unroll
         for (int c = 0; c < 3; ++c)
-          if (liveH(c)) cp_async16(dst + c * FH + ch_s[r], src + c * ncell + ch_g[r]);
+          if (liveH(c)) cp_async16(dst + ho(c) + ch_s[r], src + c * ncell + ch_g[r]);
       }
     } else {
       for (int idx = tid; idx < HY * (TX + 1); idx += NTHR) {
@@ -389,7 +397,7 @@ step3d_kernel(const Step3DParams<T> p) {
         const int g = wrapi(y0 - 1 + yy, p.ny) * p.nx + wrapi(x0 - 1 + hx, p.nx);
 #pragma unroll
         for (int c = 0; c < 3; ++c)
-          if (liveH(c)) cp_async_elem(dst + c * FH + yy * HX + hx + kXO, src + c * ncell + g);
+          if (liveH(c)) cp_async_elem(dst + ho(c) + (yy - RO) * HX + hx + kXO, src + c * ncell + g);
       }
     }
   };
@@ -398,18 +406,18 @@ step3d_kernel(const Step3DParams<T> p) {
   // planes k and k+1 (the E frame's origin is the H frame's, (x0-1, y0-1), one cell wider)
   auto computeH = [&](int fe, int fh, int gxy, int k, bool write_out, const T* e0, const T* e1,
                       const T* hin) {
-    T hx_ = hin[fh], hy_ = TE ? T(0) : hin[FH + fh], hz_ = hin[2 * FH + fh];
+    T hx_ = hin[ho(0) + fh], hy_ = TE ? T(0) : hin[ho(1) + fh], hz_ = hin[ho(2) + fh];
     if (p.doH) {
       HIn<T> e;
       e.ex0 = TE ? T(0) : e0[fe];
       e.ex_k1 = TE ? T(0) : e1[fe];
       e.ex_j1 = TE ? T(0) : e0[fe + FX];
-      e.ey0 = e0[FE + fe];
-      e.ey_k1 = e1[FE + fe];
-      e.ey_i1 = e0[FE + fe + 1];
-      e.ez0 = TE ? T(0) : e0[2 * FE + fe];
-      e.ez_j1 = TE ? T(0) : e0[2 * FE + fe + FX];
-      e.ez_i1 = TE ? T(0) : e0[2 * FE + fe + 1];
+      e.ey0 = e0[eo(1) + fe];
+      e.ey_k1 = e1[eo(1) + fe];
+      e.ey_i1 = e0[eo(1) + fe + 1];
+      e.ez0 = TE ? T(0) : e0[eo(2) + fe];
+      e.ez_j1 = TE ? T(0) : e0[eo(2) + fe + FX];
+      e.ez_i1 = TE ? T(0) : e0[eo(2) + fe + 1];
       const int ip = psiH_plane(k, p.nz, p.npml);
       T psx = T(0), psy = T(0), b = T(1), c = T(0);
       const int pstride = (2 * p.npml + 1) * plane;
@@ -432,9 +440,9 @@ step3d_kernel(const Step3DParams<T> p) {
         }
       }
     }
-    sH[fh] = hx_;
-    sH[FH + fh] = hy_;
-    sH[2 * FH + fh] = hz_;
+    sH[ho(0) + fh] = hx_;
+    if (!TE) sH[ho(1) + fh] = hy_;
+    sH[ho(2) + fh] = hz_;
   };
 
   // ---- prologue: H^n of plane zb-1 at the own cell (for d/dz of the E update at zb) ----
@@ -555,7 +563,7 @@ step3d_kernel(const Step3DParams<T> p) {
         if (k == zm - 1 || k == zm) {
           const int off = (k == zm) ? 1 : 0;
           T vx = own ? sH[own_fh] : T(0);
-          T vy = own ? sH[FH + own_fh] : T(0);
+          T vy = own && !TE ? sH[ho(1) + own_fh] : T(0);
           if constexpr (WS > 1) {
             double* rows = p.mon_partial_H;
             warp_sum_to((double)vx, wslot(rows ? rows + (int64_t)(4 * m + off) * nbxy : nullptr));
@@ -571,7 +579,7 @@ step3d_kernel(const Step3DParams<T> p) {
         }
       }
       if (p.eH_on && own && in_box) {
-        T a = sH[own_fh], b = sH[FH + own_fh], c = sH[2 * FH + own_fh];
+        T a = sH[ho(0) + own_fh], b = TE ? T(0) : sH[ho(1) + own_fh], c = sH[ho(2) + own_fh];
         uH += a * a + b * b + c * c;
       }
     }
@@ -583,14 +591,15 @@ step3d_kernel(const Step3DParams<T> p) {
         const int q = k * plane + qxy;
         const T* e0 = slotE(k);
         const int fh = own_fh;
-        const T Hx = sH[fh], Hy = sH[FH + fh], Hz = sH[2 * FH + fh];
+        const T Hx = sH[ho(0) + fh], Hy = TE ? T(0) : sH[ho(1) + fh], Hz = sH[ho(2) + fh];
         // differences of H^n for dt curl H^n = S [...] (Eq. FDTD-1D form)
-        const T dyHz = Hz - sH[2 * FH + fh - HX];
+        // (TE: ny = 1, the row above is this row and the y-differences vanish)
+        const T dyHz = Hz - (TE ? Hz : sH[ho(2) + fh - HX]);
         const T dzHy = Hy - hym;
         const T dzHx = Hx - hxm;
-        const T dxHz = Hz - sH[2 * FH + fh - 1];
-        const T dxHy = Hy - sH[FH + fh - 1];
-        const T dyHx = Hx - sH[fh - HX];
+        const T dxHz = Hz - sH[ho(2) + fh - 1];
+        const T dxHy = Hy - (TE ? T(0) : sH[ho(1) + fh - 1]);
+        const T dyHx = Hx - (TE ? Hx : sH[ho(0) + fh - HX]);
         T curl[3];
         const int ip = psiE_plane(k, p.nz, p.npml);
         if (ip >= 0) {
@@ -628,7 +637,7 @@ step3d_kernel(const Step3DParams<T> p) {
 #pragma unroll
           for (int c = 0; c < 3; ++c) {
             if (!liveE(c)) continue;   // Ev[c] stays 0
-            T e = e0[c * FE + own_fe] + S * curl[c];
+            T e = e0[eo(c) + own_fe] + S * curl[c];
             if (hasJ[c]) e = e + dt * J[c];
             Ev[c] = e;
             p.Eout[c * ncell + q] = e;
@@ -655,7 +664,7 @@ step3d_kernel(const Step3DParams<T> p) {
               // D-free: E += (dt curl H + dt J - (P^{n+1/2} - P^{n-1/2})) / eps_inf
               T inc = S * curl[c];
               if (hasJ[c]) inc = inc + dt * J[c];
-              E = e0[c * FE + own_fe] + (inc - (Pa - Pb)) * M.inv_eps;
+              E = e0[eo(c) + own_fe] + (inc - (Pa - Pb)) * M.inv_eps;
             }
             Ev[c] = E;
             p.Eout[c * ncell + q] = E;
@@ -912,8 +921,8 @@ step3d_kernel(const Step3DParams<T> p) {
           }
         }
       }
-      hxm = sH[own_fh];
-      hym = sH[FH + own_fh];
+      hxm = sH[ho(0) + own_fh];
+      hym = TE ? T(0) : sH[ho(1) + own_fh];
     }
   }
   // energy partials of this block (every block writes, zero when outside the box)
@@ -943,9 +952,11 @@ step3d_kernel(const Step3DParams<T> p) {
   }
 }
 
-inline size_t step3d_smem_bytes(int ty, int nmodes, size_t elem, int tx = kTX) {
-  const size_t fe = (size_t)(ty + 2) * (tx + 8), fh = (size_t)(ty + 1) * (tx + 4);
-  const size_t n = (size_t)kRingE * 3 * fe + (size_t)(kRingH + 1) * 3 * fh + (size_t)kCoefStride * nmodes;
+inline size_t step3d_smem_bytes(int ty, int nmodes, size_t elem, int tx = kTX, bool te = false) {
+  // the TE form stores one row of E_y and of H_x, H_z per frame
+  const size_t fe = (size_t)(te ? 1 : ty + 2) * (tx + 8), fh = (size_t)(te ? 1 : ty + 1) * (tx + 4);
+  const size_t n = (size_t)kRingE * (te ? 1 : 3) * fe + (size_t)(kRingH + 1) * (te ? 2 : 3) * fh +
+                   (size_t)kCoefStride * nmodes;
   return n * elem + kMaxChunk * sizeof(int) + 16 + 8 * sizeof(double);   // block-sum scratch: a double per warp (<= 8)
 }
 

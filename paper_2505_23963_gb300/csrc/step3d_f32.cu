@@ -11,7 +11,7 @@ static int launch_nb(const Step3DParams<float>& p, int nbx, int nby, int nchunks
   // the TE form runs 128-wide single-row tiles, every other form 32-wide tiles
   constexpr int TX = TE ? 4 * kTX : kTX;
   auto kern = step3d_kernel<float, true, NB, TY, YB, TE, TX>;
-  const size_t smem = step3d_smem_bytes(TY, p.nmodes, sizeof(float), TX);
+  const size_t smem = step3d_smem_bytes(TY, p.nmodes, sizeof(float), TX, TE);
   static size_t smem_set = 0;   // opt in once per instantiation for more than 48 KB
   if (smem > smem_set) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
