@@ -53,10 +53,11 @@ __device__ __forceinline__ int adj_psiH_plane(int k, int nz, int npml) {
 
 template <typename T>
 __device__ __forceinline__ int adj_mat_of(const AdjParams<T>& p, int k) {
-  for (int m = 0; m < p.nmat; ++m)
-    if (k >= p.mat[m].zlo && k < p.mat[m].zhi) return m;
-  return -1;
+  return p.zmat[k];
 }
+
+// n / d for n < 2^31 (FastDiv, internal.h)
+__device__ __forceinline__ uint32_t adj_div(uint32_t n, FastDiv f) { return (__umulhi(f.m, n) + n) >> f.l; }
 
 // TE: the forward run was the y-invariant TE form (ny = 1, E_y sources) and the monitor sources
 // of the adjoint sit on E_y and H_x only.  Then the adjoints of E_x, E_z, H_y and of the x / z
@@ -78,9 +79,10 @@ __global__ void __launch_bounds__(kAdjThreads, (TE && NBMAX <= 8) ? 4 : 0) adjoi
 #pragma unroll
   for (int j = 0; j < NBA; ++j) gk[j] = T(0);
   if (own) {
-    const int k = (int)(q / plane);
-    const int r = (int)(q - (int64_t)k * plane);
-    const int j = r / nx, i = r - j * nx;
+    // cell indices fit in 31 bits (checked when the simulation is created)
+    const int k = (int)adj_div((uint32_t)q, p.fd_plane);
+    const int r = (int)q - k * (int)plane;
+    const int j = (int)adj_div((uint32_t)r, p.fd_nx), i = r - j * nx;
     const int im = i > 0 ? i - 1 : nx - 1, jm = j > 0 ? j - 1 : ny - 1;
     const T S = p.S;
     const T hsrc = T(0.5);
@@ -297,9 +299,9 @@ __global__ void __launch_bounds__(kAdjThreads) adjoint_k2(const AdjParams<T> p) 
   if (q >= p.ncell) return;
   const int64_t N = p.ncell, plane = p.plane;
   const int nx = p.nx, ny = p.ny, nz = p.nz;
-  const int k = (int)(q / plane);
-  const int r = (int)(q - (int64_t)k * plane);
-  const int j = r / nx, i = r - j * nx;
+  const int k = (int)adj_div((uint32_t)q, p.fd_plane);
+  const int r = (int)q - k * (int)plane;
+  const int j = (int)adj_div((uint32_t)r, p.fd_nx), i = r - j * nx;
   const int ip = i + 1 < nx ? i + 1 : 0, jp = j + 1 < ny ? j + 1 : 0;
   const T S = p.S;
   const T inv0 = [&] {

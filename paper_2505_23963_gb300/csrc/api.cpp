@@ -1346,9 +1346,11 @@ int adjoint_sweep(fdtdbath_sim* s, const HostMon& mon, const std::vector<double>
   const int L = A.every;
   // ---- buffers ----
   std::vector<void*> bufs;
+  bool oom = false;
   auto get = [&](size_t bytes) -> void* {
     void* p = dalloc(s, bytes);
     if (p) bufs.push_back(p);
+    else oom = true;
     return p;
   };
   T* Eb = (T*)get(3 * (size_t)N * e);
@@ -1367,14 +1369,25 @@ int adjoint_sweep(fdtdbath_sim* s, const HostMon& mon, const std::vector<double>
   int nrows = 0;
   for (auto& m : s->mats) nrows += m.nb;
   T* coefLit = (T*)get((size_t)std::max(1, nrows) * kCoefStride * e);
+  signed char* zmat = (signed char*)get((size_t)s->nz);
   auto release = [&]() {
     for (void* p : bufs) dfree(s, p);
   };
-  for (void* p : bufs)
-    if (!p) {
+  if (oom) {
+    release();
+    return fail(s, FDTDBATH_ERR_OOM, "adjoint buffer allocation failed");
+  }
+  // material index of every plane
+  {
+    std::vector<signed char> zm((size_t)s->nz, (signed char)-1);
+    for (size_t m = 0; m < s->mats.size(); ++m)
+      for (int64_t z = s->mats[m].zlo; z < s->mats[m].zhi; ++z) zm[(size_t)z] = (signed char)m;
+    const int rc = h2d(s, zmat, zm.data(), zm.size());
+    if (rc) {
       release();
-      return fail(s, FDTDBATH_ERR_OOM, "adjoint buffer allocation failed");
+      return rc;
     }
+  }
   // literal coefficient rows in the state precision
   {
     std::vector<T> rows;
@@ -1455,6 +1468,9 @@ int adjoint_sweep(fdtdbath_sim* s, const HostMon& mon, const std::vector<double>
   p.tsig = (T)(p.dcE * p.invA);
   p.thA = (T)(p.halfdt * p.invA);
   p.gpart = gpart;
+  p.fd_plane = make_fastdiv((uint32_t)plane);
+  p.fd_nx = make_fastdiv((uint32_t)s->nx);
+  p.zmat = zmat;
   // every adjoint buffer starts at zero (dalloc zeroes them)
   const bool save_quiet = s->quiet;
   s->quiet = true;

@@ -154,6 +154,22 @@ int launch_step3d_f64(const Step3DParams<double>& p, int nbmax, int ty, int nbx,
 // One reverse step of the exact transpose of the forward step (D-free form), applied to the
 // adjoint state (Eb, Hb, psi memories, P / P_m and bath-mode adjoints); see adjoint.cu.
 constexpr int kAdjMaxGrad = 2 + kMaxBath;   // dL/dsigma, dL/dgamma0, dL/dk_j
+
+// Division of dividends n < 2^31 by a run-time invariant divisor 1 <= d < 2^31 with a
+// multiply-high (Granlund and Montgomery, "Division by invariant integers using
+// multiplication", PLDI 1994): l = ceil(log2 d), m = floor(2^32 (2^l - d) / d) + 1, and
+// n / d = (mulhi(m, n) + n) >> l; the 33-bit multiplier 2^32 + m is split so that the sum
+// stays below 2^32 for n < 2^31.
+struct FastDiv {
+  uint32_t m;
+  int l;
+};
+inline FastDiv make_fastdiv(uint32_t d) {
+  int l = 0;
+  while ((uint64_t(1) << l) < d) ++l;
+  const uint64_t m = ((uint64_t(1) << 32) * ((uint64_t(1) << l) - d)) / d + 1;
+  return FastDiv{(uint32_t)m, l};
+}
 template <typename T>
 struct AdjParams {
   int nx, ny, nz, npml;
@@ -191,6 +207,8 @@ struct AdjParams {
   T tsig, thA;              // (T)(dcE invA), (T)(halfdt invA)
   T ta[kMaxBath], tb[kMaxBath], tdc[kMaxBath], tds[kMaxBath];
   double* gpart;            // [gridDim][kAdjMaxGrad] per-block running sums (FP64)
+  FastDiv fd_plane, fd_nx;  // division by plane = nx ny and by nx (cell index -> i, j, k)
+  const signed char* zmat;  // [nz] material index of every plane, -1 for none
 };
 // te = 1: the TE form (the forward run was the y-invariant TE form and the adjoint sources sit
 // on E_y and H_x only): the adjoints of E_x, E_z, H_y, P_x, P_z and the x / z bath modes are zero
