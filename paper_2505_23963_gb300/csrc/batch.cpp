@@ -702,7 +702,9 @@ int autotune(fdtdbath_batch* b, int probe_steps) {
   const char* ev = std::getenv("FDTDBATH_TUNE_VERBOSE");   // print every candidate's time
   const bool verbose = ev && *ev && *ev != '0';
   const int Cs[] = {1, 2, 4, 8, 16};
-  const int Ts[] = {128, 256, 512, 1024};
+  // thread counts between the powers of two too: a Lorentz-Bath run's cells are dealt round-robin,
+  // so the count decides how evenly its remainder spreads over the threads
+  const int Ts[] = {128, 256, 384, 512, 640, 768, 896, 1024};
   for (int C : Cs)
     for (int T : Ts)
       for (int k = 1; k <= 2; ++k) {
