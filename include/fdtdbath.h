@@ -118,8 +118,8 @@ typedef struct {
 typedef struct {
   int32_t precision;    /* 64: FP64 state and arithmetic; 32: FP32 state and arithmetic */
   int32_t bath_storage; /* 0: bath modes in the state precision.  1 (precision 32 only): every bath
-                         * mode stored as a bf16 pair -- its value Y^{n+1/2} and its increment
-                         * Y^{n+1/2} - Y^{n-1/2} -- updated in place with FP32 arithmetic (8 bytes per
+                         * mode stored as a bf16 pair in one 32-bit word -- its value Y^{n+1/2} and
+                         * its increment Y^{n+1/2} - Y^{n-1/2} -- updated in place with FP32 arithmetic (8 bytes per
                          * mode and component per step instead of 12); reading level 1 returns
                          * value - increment.  fdtdbath_box_energy_noalloc refuses such simulations
                          * with FDTDBATH_ERR_UNSUPPORTED. */

@@ -81,8 +81,9 @@ struct fdtdbath_sim {
   void* D = nullptr;
   void* Pslot[2] = {nullptr, nullptr};
   void* Yslot[2] = {nullptr, nullptr};
-  // bf16 bath storage (precision 32): Yslot[0] holds the values Y^{n+1/2}, Yslot[1] the increments
-  // Y^{n+1/2} - Y^{n-1/2}, both bf16 and updated in place (no slot swap)
+  // bf16 bath storage (precision 32): Yslot[0] holds, per mode and cell, the pair (value Y^{n+1/2},
+  // increment Y^{n+1/2} - Y^{n-1/2}) of bf16 in one 32-bit word, updated in place (no slot swap);
+  // Yslot[1] is unused
   bool ybf = false;
   size_t yesz = 8;
   int pcur = 0;  // literal form: slot holding P^{n+1/2}
@@ -285,7 +286,7 @@ Step3DParams<T> make_params(fdtdbath_sim* s, int doH, int doE) {
   p.Pa = (T*)s->Pslot[s->pcur];
   p.Pb = (T*)s->Pslot[1 - s->pcur];
   p.Ya = (T*)s->Yslot[s->ybf ? 0 : s->pcur];
-  p.Yb = (T*)s->Yslot[s->ybf ? 1 : 1 - s->pcur];
+  p.Yb = (T*)s->Yslot[s->ybf ? 0 : 1 - s->pcur];   // bf16 pairs: one array
   p.nsrc = (int)s->srcs.size();
   const double t = (double)s->n * s->dt;
   for (size_t q = 0; q < s->srcs.size(); ++q) {
@@ -608,28 +609,25 @@ uint16_t float_to_bf16(float f) {
 // Both levels of one bf16-stored bath mode block of `count` cells: Y^{n+1/2} = value,
 // Y^{n-1/2} = value - increment (FP32 arithmetic, as the kernel forms them).
 int fetch_bf16_levels(fdtdbath_sim* s, int64_t off, int64_t count, std::vector<float>& y0, std::vector<float>& y1) {
-  std::vector<uint16_t> a((size_t)count), b((size_t)count);
-  int rc = d2h(s, a.data(), elem_ptr(s->Yslot[0], off, 2), (size_t)count * 2);
-  if (!rc) rc = d2h(s, b.data(), elem_ptr(s->Yslot[1], off, 2), (size_t)count * 2);
+  std::vector<uint16_t> ab(2 * (size_t)count);   // (value, increment) per cell
+  int rc = d2h(s, ab.data(), elem_ptr(s->Yslot[0], off, 4), (size_t)count * 4);
   if (rc) return rc;
   y0.resize((size_t)count);
   y1.resize((size_t)count);
   for (int64_t i = 0; i < count; ++i) {
-    y0[(size_t)i] = bf16_to_float(a[(size_t)i]);
-    y1[(size_t)i] = y0[(size_t)i] - bf16_to_float(b[(size_t)i]);
+    y0[(size_t)i] = bf16_to_float(ab[2 * (size_t)i]);
+    y1[(size_t)i] = y0[(size_t)i] - bf16_to_float(ab[2 * (size_t)i + 1]);
   }
   return 0;
 }
 
 int store_bf16_levels(fdtdbath_sim* s, int64_t off, const std::vector<float>& y0, const std::vector<float>& y1) {
-  std::vector<uint16_t> a(y0.size()), b(y0.size());
+  std::vector<uint16_t> ab(2 * y0.size());
   for (size_t i = 0; i < y0.size(); ++i) {
-    a[i] = float_to_bf16(y0[i]);
-    b[i] = float_to_bf16(y0[i] - y1[i]);
+    ab[2 * i] = float_to_bf16(y0[i]);
+    ab[2 * i + 1] = float_to_bf16(y0[i] - y1[i]);
   }
-  int rc = h2d(s, elem_ptr(s->Yslot[0], off, 2), a.data(), a.size() * 2);
-  if (!rc) rc = h2d(s, elem_ptr(s->Yslot[1], off, 2), b.data(), b.size() * 2);
-  return rc;
+  return h2d(s, elem_ptr(s->Yslot[0], off, 4), ab.data(), ab.size() * 2);
 }
 
 }  // namespace
@@ -853,7 +851,7 @@ int fdtdbath_create(const fdtdbath_grid* grid, double resolution, double courant
     s->H[b] = dalloc(s, 3 * s->ncell * esz);
     s->psiH[b] = dalloc(s, 2 * (size_t)(2 * s->npml + 1) * s->plane * esz);
     s->Pslot[b] = dalloc(s, 3 * (size_t)s->nmatcell * esz);
-    s->Yslot[b] = dalloc(s, (size_t)s->nybath * s->yesz);
+    s->Yslot[b] = dalloc(s, s->ybf ? (b == 0 ? (size_t)s->nybath * 4 : 16) : (size_t)s->nybath * s->yesz);
     if (!s->E[b] || !s->H[b] || !s->psiH[b] || !s->Pslot[b] || !s->Yslot[b])
       return bail(FDTDBATH_ERR_OOM, "device allocation failed");
   }
@@ -1276,7 +1274,8 @@ std::vector<StateRef> state_refs(fdtdbath_sim* s) {
   v.push_back({s->psiH[s->psicur], 2 * (size_t)(2 * s->npml + 1) * s->plane * e});
   if (s->prec == 64) v.push_back({s->D, 3 * (size_t)s->nmatcell * e});
   for (int b = 0; b < 2; ++b) v.push_back({s->Pslot[b], 3 * (size_t)s->nmatcell * e});
-  for (int b = 0; b < 2; ++b) v.push_back({s->Yslot[b], (size_t)s->nybath * s->yesz});
+  for (int b = 0; b < 2; ++b)
+    v.push_back({s->Yslot[b], s->ybf ? (b == 0 ? (size_t)s->nybath * 4 : 16) : (size_t)s->nybath * s->yesz});
   return v;
 }
 

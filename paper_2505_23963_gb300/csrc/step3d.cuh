@@ -161,19 +161,33 @@ struct Tile {
   static constexpr int FH = HY * HX;                 // H frame elements per component
 };
 
-// Bath-mode storage: the state precision, or bf16 (value Y and increment V = Y^n - Y^{n-1} of
-// every mode, both bf16, updated in place; the arithmetic stays FP32).
+// Bath-mode storage: the state precision (two levels Y^n, Y^{n-1} in two arrays: load2 reads
+// both, put writes the new level over the older one), or bf16 pairs (value Y and increment
+// V = Y^n - Y^{n-1} of a mode side by side in one 32-bit word, updated in place by put_pair;
+// the arithmetic stays FP32).
 template <typename T, bool YB>
 struct BathStore {
   using S = T;
   static __device__ __forceinline__ T load(const S* p) { return *p; }
+  static __device__ __forceinline__ void load2(const S* pa, const S* pb, T& a, T& b) {
+    a = *pa;
+    b = *pb;
+  }
   static __device__ __forceinline__ void put(S* p, T v) { *p = v; }
+  static __device__ __forceinline__ void put_pair(S* p, T y, T v) { *p = y; }   // not used
 };
 template <>
 struct BathStore<float, true> {
-  using S = __nv_bfloat16;
-  static __device__ __forceinline__ float load(const S* p) { return __bfloat162float(*p); }
-  static __device__ __forceinline__ void put(S* p, float v) { *p = __float2bfloat16_rn(v); }
+  using S = __nv_bfloat162;
+  static __device__ __forceinline__ void load2(const S* pa, const S*, float& y, float& v) {
+    const __nv_bfloat162 q = *pa;
+    y = __low2float(q);
+    v = __high2float(q);
+  }
+  static __device__ __forceinline__ void put(S* p, float v) {}   // not used
+  static __device__ __forceinline__ void put_pair(S* p, float y, float v) {
+    *p = __halves2bfloat162(__float2bfloat16_rn(y), __float2bfloat16_rn(v));
+  }
 };
 
 template <typename T, int NBMAX, int TY, int TXW = kTX>
@@ -524,8 +538,7 @@ step3d_kernel(const Step3DParams<T> p) {
 #pragma unroll
           for (int jj = 0; jj < (NBP > 0 ? NBP : 1); ++jj) {
             if (jj < M.nb) {
-              rY[c][jj] = YS::load(ya + (c * M.nb + jj) * mstride);
-              rV[c][jj] = YS::load(yb + (c * M.nb + jj) * mstride);
+              YS::load2(ya + (c * M.nb + jj) * mstride, yb + (c * M.nb + jj) * mstride, rY[c][jj], rV[c][jj]);
             }
           }
         }
@@ -685,8 +698,7 @@ step3d_kernel(const Step3DParams<T> p) {
 #pragma unroll
                 for (int u = 0; u < kStreamBatch; ++u) {
                   if (j0 + u < nb) {
-                    ys[u] = YS::load(ya + yc + (j0 + u) * mstride);
-                    vs[u] = YS::load(yb + yc + (j0 + u) * mstride);
+                    YS::load2(ya + yc + (j0 + u) * mstride, yb + yc + (j0 + u) * mstride, ys[u], vs[u]);
                   }
                 }
 #pragma unroll
@@ -711,8 +723,7 @@ step3d_kernel(const Step3DParams<T> p) {
                   Yl[jj] = rY[c][jj < NBP ? jj : 0];
                   Vl[jj] = rV[c][jj < NBP ? jj : 0];
                 } else {
-                  Yl[jj] = YS::load(ya + yc + jj * mstride);
-                  Vl[jj] = YS::load(yb + yc + jj * mstride);
+                  YS::load2(ya + yc + jj * mstride, yb + yc + jj * mstride, Yl[jj], Vl[jj]);
                 }
                 T cf[6];
                 load_coef6(cfm + jj * kCoefStride, cf);
@@ -751,8 +762,7 @@ step3d_kernel(const Step3DParams<T> p) {
 #pragma unroll
                 for (int u = 0; u < kStreamBatch; ++u) {
                   if (j0 + u < nb) {
-                    ys[u] = YS::load(ya + yc + (j0 + u) * mstride);
-                    vs[u] = YS::load(yb + yc + (j0 + u) * mstride);
+                    YS::load2(ya + yc + (j0 + u) * mstride, yb + yc + (j0 + u) * mstride, ys[u], vs[u]);
                   }
                 }
 #pragma unroll
@@ -773,8 +783,7 @@ step3d_kernel(const Step3DParams<T> p) {
                     Ynew = y + Vy;
                   }
                   if (YB) {
-                    YS::put(ya + yc + jj * mstride, Ynew);
-                    YS::put(yb + yc + jj * mstride, Vy);
+                    YS::put_pair(ya + yc + jj * mstride, Ynew, Vy);
                   } else {
                     YS::put(yb + yc + jj * mstride, Ynew);
                   }
@@ -798,8 +807,7 @@ step3d_kernel(const Step3DParams<T> p) {
                   Ynew = Yl[jj] + Vy;
                 }
                 if (YB) {
-                  YS::put(ya + yc + jj * mstride, Ynew);   // in place: Y^{n+1} and V^{n+1}
-                  YS::put(yb + yc + jj * mstride, Vy);
+                  YS::put_pair(ya + yc + jj * mstride, Ynew, Vy);   // in place: Y^{n+1} and V^{n+1}
                 } else {
                   YS::put(yb + yc + jj * mstride, Ynew);   // overwrites Y^{n-1}
                 }
@@ -878,8 +886,7 @@ step3d_kernel(const Step3DParams<T> p) {
                     Ynew = y + Vy;
                   }
                   if (YB) {
-                    YS::put(ya + yo, Ynew);
-                    YS::put(yb + yo, Vy);
+                    YS::put_pair(ya + yo, Ynew, Vy);
                   } else {
                     YS::put(yb + yo, Ynew);
                   }
