@@ -6,7 +6,7 @@
 // Eq. Pz_update-LB) and the bath-mode update (Eq. Yzj_finite_difference), with one
 // independent bath set per P component (Sec. II.C, 3D extension).
 //
-// Decomposition: a CTA owns a 32 x TY column tile in (x, y) and marches along a chunk of
+// Decomposition: a CTA owns a TX x TY column tile in (x, y) and marches along a chunk of
 // z planes.  Per plane it stages E^{n-1/2} of plane k+1 (tile + 1-cell frame) in shared
 // memory, recomputes H^n on the tile plus the -x / -y halo (H is read by neighbours'
 // E updates), writes H^n of its own cells, then updates E, P and the bath modes of its own
@@ -14,6 +14,14 @@
 // memories are double-buffered so neighbouring CTAs never see a half-updated plane;
 // P, Y, D and the E-side CPML memories are cell-local and updated in place.  Every state
 // word is read once and written once per step; halo re-reads hit L1/L2.
+//
+// Bath modes: up to 8 per component (FP32; 4 in FP64) the plane's bath state is loaded into
+// registers before the stencil and the three components go through the modes together; up to
+// 32 each component's modes are held in registers between the bath sum and the mode update;
+// above 32 (up to 128) they are streamed from memory twice, in batches of 16.
+//
+// Tiles: 32 x 8 (32 x 1 when ny < 8); the TE form of y-invariant grids (ny = 1, E_y sources)
+// uses 128 x 1 tiles and carries only E_y, H_x, H_z and the y polarization and bath modes.
 //
 // Two arithmetic forms:
 //   INC = false (FP64): the literal form -- D stored in material cells, E = (D - P)/eps,
