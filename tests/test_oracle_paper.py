@@ -11,20 +11,26 @@ transmission), the uniform bath next, the Lorentz medium of the same total width
 The reflectance used for the absorption is pinned first: for a lossless dielectric slab the
 transfer matrix gives the Airy formula T = 1 / (1 + F sin^2 delta), F = ((n^2 - 1) / 2n)^2,
 delta = n w L, and R = 1 - T."""
+import json
 import math
+import pathlib
 
 import numpy as np
 import pytest
-from scipy.signal import find_peaks
 
 from oracle import closed_forms as cf
 from test_oracle_tmm import paper_cavity
 
-NU0, GAMMA_L, SIGMA_SLAB = 1.0, 0.04, 5e-3
+# the paper's printed parameters (tests/golden/paper_fig2_parameters.json, with citations)
+GOLD = json.loads((pathlib.Path(__file__).parent / "golden" / "paper_fig2_parameters.json").read_text())
+NU0, GAMMA_L, SIGMA_SLAB = (GOLD["lorentz"][k] for k in ("frequency", "gamma", "sigma"))
+LB = GOLD["lorentz_bath"]
+CAV = GOLD["cavity"]
+RES = 1.0 / GOLD["grid"]["dx"]
 
 
 def slab(m):
-    return dict(resolution=100.0, materials=[dict(m, z=(0, 100))])
+    return dict(resolution=RES, materials=[dict(m, z=(0, int(round(CAV["gap"] * RES))))])
 
 
 def lorentz(gamma=GAMMA_L, sigma=SIGMA_SLAB):
@@ -32,8 +38,9 @@ def lorentz(gamma=GAMMA_L, sigma=SIGMA_SLAB):
 
 
 def bath(form, sigma=SIGMA_SLAB):
-    f, g, k = cf.bath_form(form, NU0, 4e-4, 100, 0.4, 4e-4, 0.0396)
-    return dict(kind="lorentz_bath", eps_inf=1.0, frequency=NU0, gamma=4e-4, sigma=sigma,
+    width = 2.0 * LB["half_span_in_gamma"] * GAMMA_L
+    f, g, k = cf.bath_form(form, NU0, LB["gamma0"], LB["num_bath"], width, LB["bath_gamma"], LB["dephasing"])
+    return dict(kind="lorentz_bath", eps_inf=1.0, frequency=NU0, gamma=LB["gamma0"], sigma=sigma,
                 bath_frequencies=f, bath_gammas=g, bath_couplings=k)
 
 
@@ -83,16 +90,18 @@ def test_p8_bath_polaritons_least_damped():
     transmits the polaritons most, the uniform bath less, the Lorentz medium of the same total
     width (gamma = 0.04) least."""
     nu = np.linspace(0.85, 1.15, 15001)
+    sig = CAV["sigma"][1]
     peaks = {}
     for name in ("lorentz", "uniform", "lorentzian"):
-        p = paper_cavity(2e-2, gamma=0.04) if name == "lorentz" else paper_cavity(2e-2, gamma=4e-4, kind="lorentz_bath")
+        p = (paper_cavity(sig, gamma=GAMMA_L) if name == "lorentz"
+             else paper_cavity(sig, gamma=LB["gamma0"], kind="lorentz_bath"))
         if name != "lorentz":
-            b = bath(name, 2e-2)
+            b = bath(name, sig)
             p["materials"][1].update({k: b[k] for k in ("bath_frequencies", "bath_gammas", "bath_couplings")})
         T = cf.transmission_continuum(nu, p)
         lp, up = T[nu < NU0], T[nu >= NU0]
         nlp, nup = nu[nu < NU0][np.argmax(lp)], nu[nu >= NU0][np.argmax(up)]
-        assert nup - nlp == pytest.approx(math.sqrt(2e-2), rel=0.1), name
+        assert nup - nlp == pytest.approx(math.sqrt(sig), rel=0.1), name
         peaks[name] = (lp.max(), up.max())
     for side in (0, 1):
         assert peaks["lorentzian"][side] > 1.5 * peaks["uniform"][side] > 1.5 * peaks["lorentz"][side]

@@ -9,7 +9,9 @@
   d = 1, slab filling the cavity) the transfer-matrix polariton splitting equals the
   closed form w0 sqrt(sigma) that follows from Eq. chi_L for a resonant, filled cavity.
 """
+import json
 import math
+import pathlib
 
 import numpy as np
 import pytest
@@ -18,6 +20,9 @@ from scipy.signal import find_peaks
 from oracle import closed_forms as cf
 from oracle import oracle as O
 from paper_2505_23963_gb300 import workloads as wl
+
+# the paper's cavity (tests/golden/paper_fig2_parameters.json, with citations)
+CAV = json.loads((pathlib.Path(__file__).parent / "golden" / "paper_fig2_parameters.json").read_text())["cavity"]
 
 
 def leaky_cavity():
@@ -32,14 +37,17 @@ def leaky_cavity():
 def paper_cavity(sigma, gamma=0.004, kind="lorentz"):
     """Sec. IV.B / appendix geometry at resolution 100: mirrors n = 10 (eps 100), 2 cells;
     1-unit gap filled by the slab; CPML 16; 200 vacuum cells on each side."""
-    pml, vac, gap = 16, 200, 100
+    res = 100.0
+    pml, vac = 16, 200
+    gap, mir = int(round(CAV["gap"] * res)), int(round(CAV["mirror_thickness"] * res))
+    eps_m = CAV["mirror_index"] ** 2
     z0 = pml + vac
-    mats = [dict(kind="vacuum", z=(z0, z0 + 2), eps_inf=100.0),
-            dict(kind="vacuum", z=(z0 + 2 + gap, z0 + 4 + gap), eps_inf=100.0)]
+    mats = [dict(kind="vacuum", z=(z0, z0 + mir), eps_inf=eps_m),
+            dict(kind="vacuum", z=(z0 + mir + gap, z0 + 2 * mir + gap), eps_inf=eps_m)]
     if sigma > 0:
-        mats.insert(1, dict(kind=kind, z=(z0 + 2, z0 + 2 + gap), eps_inf=1.0, frequency=1.0,
+        mats.insert(1, dict(kind=kind, z=(z0 + mir, z0 + mir + gap), eps_inf=1.0, frequency=1.0,
                             gamma=gamma, sigma=sigma))
-    return dict(n=(1, 1, 2 * pml + 2 * vac + gap + 4), resolution=100.0, courant=0.5, pml=pml,
+    return dict(n=(1, 1, 2 * pml + 2 * vac + gap + 2 * mir), resolution=res, courant=0.5, pml=pml,
                 materials=mats, sources=[], monitors=[])
 
 
@@ -93,8 +101,8 @@ def test_p4_paper_cavity_modes():
     T = cf.transmission_discrete(nu, paper_cavity(2e-2, gamma=0.04))
     idx, _ = find_peaks(T)
     strong = [nu[i] for i in idx if T[i] > 0.3]
-    assert any(abs(x - 0.5) < 0.06 for x in strong)
-    assert any(abs(x - 1.5) < 0.06 for x in strong)
+    for mode in CAV["uncoupled_modes"]:
+        assert any(abs(x - mode) < 0.06 for x in strong)
     # with the paper's Lorentz damping the polaritons transmit only weakly (Fig. 2b, top)
     pol = [nu[i] for i in idx if 0.85 < nu[i] < 1.15 and T[i] > 0.005]
     assert len(pol) == 2 and pol[1] - pol[0] == pytest.approx(math.sqrt(2e-2), rel=0.05)
