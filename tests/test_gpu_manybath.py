@@ -131,3 +131,24 @@ def test_many_bath_modes_bf16_storage():
     assert rel(g, r) < 1e-3, rel(g, r)
     assert rel(s.dft(0), o.dft(0)) < 1e-3
     s.close()
+
+
+@pytest.mark.parametrize("precision", [64, 32])
+def test_zero_coupling_is_lorentz_bitwise_streamed(precision):
+    """Pin P2 on the streamed path: N_b = 100 bath modes with every coupling zero give the plain
+    Lorentz medium bit for bit (E, H, P)."""
+    prob, mat = ragged_3d(60)
+    lb = prob["materials"][mat]
+    lb0 = dict(lb, bath_couplings=np.zeros_like(lb["bath_couplings"]))
+    lor = dict(kind="lorentz", z=lb["z"], eps_inf=1.0, frequency=lb["frequency"], gamma=lb["gamma"],
+               sigma=lb["sigma"])
+    mats = list(prob["materials"])
+    sa = fb.Simulation(dict(prob, materials=mats[:mat] + [lb0] + mats[mat + 1:]), precision=precision)
+    sb = fb.Simulation(dict(prob, materials=mats[:mat] + [lor] + mats[mat + 1:]), precision=precision)
+    sa.step(60)
+    sb.step(60)
+    for name in ("E", "H", "P", "Pm"):
+        for c in range(3):
+            assert np.array_equal(sa.get(name, comp=c), sb.get(name, comp=c)), (name, c)
+    sa.close()
+    sb.close()
