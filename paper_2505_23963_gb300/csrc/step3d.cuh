@@ -201,8 +201,9 @@ struct BathStore<float, true> {
 template <typename T, int NBMAX, int TY, int TXW = kTX>
 struct StepBounds {
   static constexpr int threads = TXW * TY;
-  // wide single-row tiles (the TE form): four CTAs of TXW threads per SM
-  static constexpr int min_blocks = TXW > kTX ? 4
+  // wide single-row tiles (the TE form, 9 KB of frames per CTA): eight CTAs of TXW threads per SM
+  // for the bath-free kernel, five with up to 8 bath modes, four otherwise
+  static constexpr int min_blocks = TXW > kTX ? (NBMAX == 0 ? 8 : (NBMAX <= 8 ? 5 : 4))
       : (TY == 8 ? (NBMAX == 0 ? (sizeof(T) == 4 ? 4 : 2) : ((sizeof(T) == 8 && NBMAX >= 16) ? 1 : 2)) : 8);
 };
 
