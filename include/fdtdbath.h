@@ -325,14 +325,16 @@ const char *fdtdbath_batch_last_error(const fdtdbath_batch *batch);
 
 void fdtdbath_batch_destroy(fdtdbath_batch *batch);
 
-/* Host-only planning (no GPU needed): pack the cavities for cluster_ctas CTAs per cluster,
- * at most nclusters clusters and smem_per_cta bytes of dynamic shared memory per CTA.  Returns
- * the number of CTAs (nclusters_used * cluster_ctas, cluster-major) or a negative error; the
- * optional outputs receive per CTA its work units, cells and shared-memory bytes, and per cavity
- * its cluster. */
+/* Host-only planning (no GPU needed): pack the cavities for cluster_ctas CTAs of block_threads
+ * threads (1..1024) per cluster, at most nclusters clusters and smem_per_cta bytes of dynamic
+ * shared memory per CTA.  The packer bounds the work of the busiest thread (cell l of a CTA is
+ * thread l mod block_threads's); block_threads = 1 balances whole CTAs.  Returns the number of
+ * CTAs (nclusters_used * cluster_ctas, cluster-major) or a negative error; the optional outputs
+ * receive per CTA its work units, cells and shared-memory bytes, and per cavity its cluster. */
 int fdtdbath_batch_plan(const fdtdbath_cavity *cavities, int32_t ncav, double resolution, double courant,
-                        int32_t precision, int32_t cluster_ctas, int32_t nclusters, int32_t smem_per_cta,
-                        int64_t *cta_work, int32_t *cta_ncell, int32_t *cta_smem, int32_t *cav_cluster);
+                        int32_t precision, int32_t cluster_ctas, int32_t block_threads, int32_t nclusters,
+                        int32_t smem_per_cta, int64_t *cta_work, int32_t *cta_ncell, int32_t *cta_smem,
+                        int32_t *cav_cluster);
 
 #ifdef __cplusplus
 }

@@ -6,9 +6,11 @@
 // material, CPML status and energy-box status, so every cell of a piece has the same cost in work
 // units and shared-memory bytes.  Cavities are assigned to clusters longest-processing-time first
 // (each to the least-loaded cluster with shared memory to spare); the cavities of a cluster are
-// laid end to end and cut into at most C contiguous CTA ranges by a greedy fill under a per-CTA
-// work bound, the smallest feasible bound being found by bisection.  A fill also respects the
-// shared-memory budget and the descriptor limits of a CTA.
+// laid end to end and cut into at most C contiguous CTA ranges by a greedy fill under a bound on
+// the work of one thread (the kernel deals a CTA's cells round-robin over its threads, so a
+// Lorentz-Bath run's remainder falls on some threads only), the smallest feasible bound being
+// found by bisection.  A fill also respects the shared-memory budget and the descriptor limits
+// of a CTA.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -212,6 +214,11 @@ struct FillState {
   int nseg = 0, nrun = 0, nmat = 0;
   int mats[kBatchMaxMat];
   int last_cav = -1;
+  // per-thread work: cell l of a CTA belongs to thread l mod T (every phase deals the cells
+  // round-robin and continues the deal across runs), so thread t carries the work of its cells;
+  // stored as base + rel[t], the common part added in whole rounds of T cells
+  int64_t ncell = 0, base = 0, relmax = 0;
+  std::vector<int64_t> rel;
 };
 
 // Shared-memory bytes a CTA needs beyond its per-cell costs: alignment of its arrays and runs
@@ -219,21 +226,57 @@ struct FillState {
 int64_t cta_fixed_bytes() { return 6 * 16; }
 int64_t run_fixed_bytes() { return 2 * 32; }
 
-// Greedy fill of the cavities `ids` (in order) into CTAs under work bound W and byte budget
-// cap.  Returns the number of CTAs used (> maxc: infeasible) and, if out != null, the cut list
-// (cavity index in ids, z) where each CTA starts.
+// Largest k <= kmax such that placing the next k cells, each of work w, keeps every thread of
+// the CTA at or below W; applies the placement when apply is set.
+int64_t thread_fit(FillState& f, int T, int64_t w, int64_t kmax, int64_t W, bool apply) {
+  if (kmax <= 0) return 0;
+  const int64_t curmax = f.base + f.relmax;
+  if (w == 0) {
+    if (apply) f.ncell += kmax;
+    return kmax;
+  }
+  // whole rounds: every thread gets q cells; the q-th round must keep the fullest thread in bounds
+  const int64_t qfit = W >= curmax ? (W - curmax) / w : 0;
+  const int64_t q = std::min<int64_t>(qfit, kmax / T);
+  // the partial round: the next r threads of the deal, while each stays in bounds
+  const int64_t rlim = std::min<int64_t>(kmax - q * T, T - 1);
+  const int s = (int)(f.ncell % T);
+  int64_t r = 0;
+  while (r < rlim && f.base + f.rel[(size_t)((s + r) % T)] + (q + 1) * w <= W) ++r;
+  const int64_t k = q * T + r;
+  if (apply && k > 0) {
+    f.base += q * w;
+    for (int64_t i = 0; i < r; ++i) {
+      int64_t& v = f.rel[(size_t)((s + i) % T)];
+      v += w;
+      f.relmax = std::max(f.relmax, v);
+    }
+    f.ncell += k;
+  }
+  return k;
+}
+
+// Greedy fill of the cavities `ids` (in order) into CTAs of T threads under a per-thread work
+// bound W and byte budget cap.  Returns the number of CTAs used (> maxc: infeasible) and, if
+// out != null, the cut list (cavity index in ids, z) where each CTA starts.  T = 1 bounds the
+// whole CTA's work.
 int greedy_fill(const std::vector<BCav>& cavs, const std::vector<HostMat>& mats, const std::vector<int>& ids,
-                int64_t W, int64_t cap, size_t esz, int maxc, std::vector<std::pair<int, int64_t>>* out) {
+                int64_t W, int64_t cap, size_t esz, int T, int maxc, std::vector<std::pair<int, int64_t>>* out) {
   FillState f;
   int used = 1;
   f.bytes = cta_fixed_bytes();
+  f.rel.assign((size_t)T, 0);
   if (out) {
     out->clear();
     if (!ids.empty()) out->push_back({0, 0});
   }
   auto new_cta = [&](int ci, int64_t z) {
     ++used;
+    std::vector<int64_t> rel;
+    rel.swap(f.rel);
     f = FillState();
+    f.rel.swap(rel);
+    std::fill(f.rel.begin(), f.rel.end(), 0);
     f.bytes = cta_fixed_bytes();
     if (out) out->push_back({ci, z});
   };
@@ -257,13 +300,13 @@ int greedy_fill(const std::vector<BCav>& cavs, const std::vector<HostMat>& mats,
                           f.nmat + (newmat ? 1 : 0) <= kBatchMaxMat;
         int64_t k = p.z1 - z;
         if (room) {
-          if (p.work > 0) k = std::min(k, (W - f.work) / p.work);
           if (p.bytes > 0) k = std::min(k, (cap - f.bytes - extra) / p.bytes);
+          k = thread_fit(f, T, p.work, k, W, true);
         } else {
           k = 0;
         }
         if (k <= 0) {
-          if (f.work == 0 && f.nseg == 0) return maxc + 1;   // one cell does not fit an empty CTA
+          if (f.ncell == 0 && f.nseg == 0) return maxc + 1;   // one cell does not fit an empty CTA
           new_cta(ci, z);
           continue;
         }
@@ -283,7 +326,7 @@ int greedy_fill(const std::vector<BCav>& cavs, const std::vector<HostMat>& mats,
 }
 
 // Pack the batch for shape (C, nclusters) under a per-CTA dynamic shared-memory budget.
-int pack(const std::vector<BCav>& cavs, const std::vector<HostMat>& mats, size_t esz, bool inc, int C,
+int pack(const std::vector<BCav>& cavs, const std::vector<HostMat>& mats, size_t esz, bool inc, int C, int T,
          int nclusters, int64_t cap, Plan& plan, std::string& why) {
   const int ncav = (int)cavs.size();
   plan = Plan();
@@ -323,16 +366,17 @@ int pack(const std::vector<BCav>& cavs, const std::vector<HostMat>& mats, size_t
       tot += cavs[(size_t)i].work;
       for (const Piece& p : cavs[(size_t)i].pieces) maxw = std::max(maxw, p.work);
     }
-    int64_t lo = std::max<int64_t>((tot + C - 1) / C, maxw), hi = std::max<int64_t>(tot, lo);
-    if (greedy_fill(cavs, mats, ids, hi, cap, esz, C, nullptr) > C)
+    // bound on the work of one thread: at least an even share of the cluster and one cell
+    int64_t lo = std::max<int64_t>((tot + (int64_t)C * T - 1) / ((int64_t)C * T), maxw), hi = std::max<int64_t>(tot, lo);
+    if (greedy_fill(cavs, mats, ids, hi, cap, esz, T, C, nullptr) > C)
       return why = "a cluster's cavities do not fit its CTAs' shared memory", FDTDBATH_ERR_UNSUPPORTED;
     while (lo < hi) {
       const int64_t mid = lo + (hi - lo) / 2;
-      if (greedy_fill(cavs, mats, ids, mid, cap, esz, C, nullptr) <= C) hi = mid;
+      if (greedy_fill(cavs, mats, ids, mid, cap, esz, T, C, nullptr) <= C) hi = mid;
       else lo = mid + 1;
     }
     std::vector<std::pair<int, int64_t>> starts;
-    greedy_fill(cavs, mats, ids, lo, cap, esz, C, &starts);
+    greedy_fill(cavs, mats, ids, lo, cap, esz, T, C, &starts);
     // build the CTAs: CTA r holds cells from starts[r] up to starts[r+1]
     for (int r = 0; r < C; ++r) {
       PlanCta& pc = plan.ctas[(size_t)k * C + r];
@@ -663,7 +707,7 @@ int plan_shape(fdtdbath_batch* b, int C, int T, int ctas_per_sm, Plan& out, std:
   rc = batch1d_occupancy(b->prec, C, T, (int)cap, &maxc, &stat);
   if (rc) return why = cudaGetErrorString((cudaError_t)rc), FDTDBATH_ERR_CUDA;
   if (maxc <= 0) return why = "launch shape cannot be resident", FDTDBATH_ERR_UNSUPPORTED;
-  rc = pack(b->cavs, b->mats, b->esz, b->prec == 32, C, maxc, cap, out, why);
+  rc = pack(b->cavs, b->mats, b->esz, b->prec == 32, C, T, maxc, cap, out, why);
   if (rc) return rc;
   out.T = T;
   return 0;
@@ -1068,11 +1112,13 @@ void fdtdbath_batch_destroy(fdtdbath_batch* b) {
 }
 
 int fdtdbath_batch_plan(const fdtdbath_cavity* cavities, int32_t ncav, double resolution, double courant,
-                        int32_t precision, int32_t cluster_ctas, int32_t nclusters, int32_t smem_per_cta,
-                        int64_t* cta_work, int32_t* cta_ncell, int32_t* cta_smem, int32_t* cav_cluster) {
+                        int32_t precision, int32_t cluster_ctas, int32_t block_threads, int32_t nclusters,
+                        int32_t smem_per_cta, int64_t* cta_work, int32_t* cta_ncell, int32_t* cta_smem,
+                        int32_t* cav_cluster) {
   g_batch_create_error.clear();
   if (precision != 32 && precision != 64) return bfail(nullptr, FDTDBATH_ERR_ARG, "precision must be 32 or 64");
-  if (cluster_ctas < 1 || cluster_ctas > kBatchMaxCluster || nclusters < 1 || smem_per_cta < 1024 || !(resolution > 0))
+  if (cluster_ctas < 1 || cluster_ctas > kBatchMaxCluster || block_threads < 1 || block_threads > 1024 || nclusters < 1 ||
+      smem_per_cta < 1024 || !(resolution > 0))
     return bfail(nullptr, FDTDBATH_ERR_ARG, "bad plan shape");
   fdtdbath_batch tmp;
   tmp.prec = precision;
@@ -1084,7 +1130,7 @@ int fdtdbath_batch_plan(const fdtdbath_cavity* cavities, int32_t ncav, double re
   int rc = build_cavities(&tmp, cavities, ncav, why);
   if (rc) return bfail(nullptr, rc, why);
   Plan P;
-  rc = pack(tmp.cavs, tmp.mats, tmp.esz, precision == 32, cluster_ctas, nclusters, smem_per_cta, P, why);
+  rc = pack(tmp.cavs, tmp.mats, tmp.esz, precision == 32, cluster_ctas, block_threads, nclusters, smem_per_cta, P, why);
   if (rc) return bfail(nullptr, rc, why);
   for (size_t r = 0; r < P.ctas.size(); ++r) {
     if (cta_work) cta_work[r] = P.ctas[r].work;

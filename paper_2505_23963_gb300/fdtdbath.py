@@ -156,7 +156,7 @@ def lib(build_if_missing: bool = True):
         L.fdtdbath_batch_destroy.argtypes = [vp]
         L.fdtdbath_batch_plan.restype = i32
         L.fdtdbath_batch_plan.argtypes = [C.POINTER(Cavity), i32, C.c_double, C.c_double, i32,
-                                          i32, i32, i32, i64p, i32p, i32p, i32p]
+                                          i32, i32, i32, i32, i64p, i32p, i32p, i32p]
         _lib = L
     return _lib
 
@@ -449,9 +449,10 @@ def _cavities(probs, energy: bool, keep):
     return cav, res, cour
 
 
-def batch_plan(probs, precision: int, cluster_ctas: int, nclusters: int, smem_per_cta: int):
+def batch_plan(probs, precision: int, cluster_ctas: int, nclusters: int, smem_per_cta: int,
+               block_threads: int = 1):
     """fdtdbath_batch_plan (host only): per-CTA work / cells / shared-memory bytes and the
-    cluster of every cavity."""
+    cluster of every cavity, balanced for CTAs of block_threads threads."""
     keep = []
     cav, res, cour = _cavities(probs, True, keep)
     nmax = cluster_ctas * nclusters
@@ -460,8 +461,8 @@ def batch_plan(probs, precision: int, cluster_ctas: int, nclusters: int, smem_pe
     smem = np.zeros(nmax, np.int32)
     clus = np.zeros(len(probs), np.int32)
     rc = lib(build_if_missing=True).fdtdbath_batch_plan(
-        cav, len(probs), res, cour, int(precision), int(cluster_ctas), int(nclusters),
-        int(smem_per_cta), work.ctypes.data_as(C.POINTER(C.c_int64)),
+        cav, len(probs), res, cour, int(precision), int(cluster_ctas), int(block_threads),
+        int(nclusters), int(smem_per_cta), work.ctypes.data_as(C.POINTER(C.c_int64)),
         cells.ctypes.data_as(C.POINTER(C.c_int32)), smem.ctypes.data_as(C.POINTER(C.c_int32)),
         clus.ctypes.data_as(C.POINTER(C.c_int32)))
     _bcheck(rc, None)

@@ -60,3 +60,62 @@ def test_bad_cavities_are_named():
     with pytest.raises(fb.FdtdBathError) as e:
         fb.batch_plan([hot], 32, cluster_ctas=1, nclusters=1, smem_per_cta=100000)
     assert e.value.code == fb.ERR_CFL
+
+
+def _cell_work(p):
+    """Work units of every cell of a batch cavity, the packer's calibration: 4 per cell, 2 per
+    CPML memory (E: the first and last npml cells, H: one more on the right), 8 per Lorentz /
+    Drude cell, 8 + 4 N_b per Lorentz-Bath cell."""
+    L = p["n"][2]
+    w = np.full(L, 4, np.int64)
+    pml = int(p["pml"])
+    w[:pml] += 4
+    w[L - pml:] += 4
+    w[L - pml - 1] += 2
+    for m in p["materials"]:
+        z0, z1 = m["z"]
+        nb = len(m.get("bath_frequencies", ()))
+        w[z0:z1] += 8 + 4 * nb if nb else (8 if m["kind"] != "vacuum" else 0)
+    return w
+
+
+def _busiest_thread(probs, r, C, T):
+    """Largest per-thread work of a plan: the cells of a cluster's cavities (in index order) cut
+    into its CTAs by their cell counts, cell l of a CTA on thread l mod T."""
+    worst = 0
+    for k in range(r["work"].size // C):
+        ids = np.nonzero(r["cluster"] == k)[0]
+        if ids.size == 0:
+            continue
+        w = np.concatenate([_cell_work(probs[i]) for i in sorted(ids)])
+        off = 0
+        for c in range(C):
+            n = int(r["cells"][k * C + c])
+            pad = np.zeros(-(-max(n, 1) // T) * T, np.int64)
+            pad[:n] = w[off:off + n]
+            off += n
+            worst = max(worst, int(pad.reshape(-1, T).sum(0).max()))
+        assert off == w.size
+    return worst
+
+
+@pytest.mark.parametrize("C,T", [(4, 768), (8, 512)])
+def test_plan_bounds_the_busiest_thread(C, T):
+    """Cells are dealt round-robin over a CTA's threads, so a Lorentz-Bath run's remainder lands
+    on some threads only; the plan for T threads bounds the busiest thread, which the whole-CTA
+    balance (block_threads = 1) leaves up to twice the mean on the sweep."""
+    probs = wl.batch_sweep(steps=10)
+    cap = 220 * 1024
+    kw = dict(cluster_ctas=C, nclusters=152 // C, smem_per_cta=cap)
+    flat = fb.batch_plan(probs, 32, **kw)
+    aware = fb.batch_plan(probs, 32, block_threads=T, **kw)
+    L = np.array([p["n"][2] for p in probs])
+    assert int(aware["cells"].sum()) == int(L.sum())
+    assert np.all(aware["smem"] <= cap)
+    b_flat = _busiest_thread(probs, flat, C, T)
+    b_aware = _busiest_thread(probs, aware, C, T)
+    one_cell = 4 + 8 + 4 * 32          # an N_b = 32 bath cell: no thread can carry less
+    mean = int(aware["work"].sum()) / (aware["work"].size * T)
+    print(f"\nC={C} T={T}: busiest thread {b_flat} (whole-CTA balance) -> {b_aware}; mean {mean:.0f}")
+    assert b_aware <= 0.75 * b_flat
+    assert b_aware <= max(2 * mean, 1.25 * one_cell)
