@@ -131,6 +131,26 @@ def dist_env():
     return ws, rank, local
 
 
+def max_over_ranks(x: float, device=None) -> float:
+    """The largest of the ranks' values of x (the slowest replica sets the job's time); x itself
+    without a process group.  The reduction runs on the rank's GPU under NCCL, on the host under
+    gloo."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    dev = device if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_rate(units_per_rank: float, world_size: int, seconds: float) -> float:
+    """Whole-job throughput of independent replicas: the units every rank processed over the
+    slowest rank's time."""
+    return world_size * units_per_rank / seconds
+
+
 def oracle_sample(prob: dict, ny_sample: int) -> dict:
     """A bounded sample of the workload for the CPU oracle: the full x and z extent (every
     plane type in its true proportion) over the first ny_sample rows of y."""
@@ -433,14 +453,6 @@ def run_ours(args):
             import torch.distributed as dist
             dist.barrier()
 
-    def max_over_ranks(x: float) -> float:
-        if ws == 1:
-            return x
-        import torch.distributed as dist
-        t = torch.tensor([x], dtype=torch.float64, device=f"cuda:{dev}")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
-
     def timed_run(precision: int, steps: int, warmup: int, sample_clocks: bool):
         with torch.cuda.stream(stream):
             sim = fb.Simulation(prob, precision=precision, stream=stream,
@@ -482,8 +494,8 @@ def run_ours(args):
 
     # ---- FP32 headline ----
     ms32, launches, kms32, ok32, clocks = timed_run(32, args.steps, args.warmup, not args.quick)
-    ms32 = max_over_ranks(ms32)
-    value = ws * cells * args.steps / (ms32 * 1e-3)
+    ms32 = max_over_ranks(ms32, f"cuda:{dev}")
+    value = replica_rate(cells * args.steps, ws, ms32 * 1e-3)
     if args.quick:
         # profiling mode: the FP32 step only, no FP64 / end-to-end / CPU legs
         if rank == 0:
@@ -494,8 +506,8 @@ def run_ours(args):
     # ---- FP64 beside it (fewer steps: FP64 arithmetic is slow on this part) ----
     k64 = max(3, min(args.steps, 20))
     ms64, _, kms64, ok64, _ = timed_run(64, k64, 3, False)
-    ms64 = max_over_ranks(ms64)
-    value64 = ws * cells * k64 / (ms64 * 1e-3)
+    ms64 = max_over_ranks(ms64, f"cuda:{dev}")
+    value64 = replica_rate(cells * k64, ws, ms64 * 1e-3)
 
     # ---- end to end through the C ABI with host buffers (create .. dft/energy .. destroy) ----
     torch.cuda.synchronize()
@@ -506,8 +518,8 @@ def run_ours(args):
     tr = sim.trace()
     sim.close()
     torch.cuda.synchronize()
-    e2e_s = max_over_ranks(time.perf_counter() - t0)
-    e2e_value = ws * cells * args.steps / e2e_s
+    e2e_s = max_over_ranks(time.perf_counter() - t0, f"cuda:{dev}")
+    e2e_value = replica_rate(cells * args.steps, ws, e2e_s)
     h2d = (prob["sources"][0]["phase"].size * 8 + prob["monitors"][0]["freqs"].size * 8
            + sum(3 * 8 * len(m.get("bath_frequencies", [])) for m in prob["materials"]))
     d2h = spec.size * 16 + tr.size * 8
