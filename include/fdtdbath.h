@@ -50,7 +50,7 @@ enum fdtdbath_status {
   FDTDBATH_ERR_CUDA = -4,        /* a CUDA call failed; see fdtdbath_last_error */
   FDTDBATH_ERR_NONFINITE = -5,   /* a NaN/Inf appeared in the state */
   FDTDBATH_ERR_TIMEOUT = -6,     /* a bounded device wait gave up */
-  FDTDBATH_ERR_UNSUPPORTED = -7  /* valid request this build does not implement */
+  FDTDBATH_ERR_UNSUPPORTED = -7  /* valid request the library does not implement */
 };
 
 enum fdtdbath_kind {
