@@ -390,8 +390,8 @@ def form_adjoint(fb, torch):
 
 
 def profile_form(name: str) -> int:
-    """Short runs of one form for profiler captures: the 64-cavity batch for 64 steps in a fixed
-    launch shape (C = 8, 256 threads), 16 steps of the 2048^2 differentiation form forward and
+    """Short runs of one form for profiler captures: the 64-cavity batch for 64 steps in the shape
+    the autotuner picks for it (C = 4, 896 threads), 16 steps of the 2048^2 differentiation form forward and
     reverse (checkpoints every 8 steps: about 2 GB of device memory), or 8 steps of the N_b = 100
     slab at 128 x 128 (about 1.5 GB)."""
     import torch
@@ -405,8 +405,8 @@ def profile_form(name: str) -> int:
         sim.close()
         return 0
     if name == "batch":
-        b = fb.Batch(wl.batch_sweep(steps=64), precision=32, energy_every=10, cluster_ctas=8,
-                     block_threads=256, use_graph=False)
+        b = fb.Batch(wl.batch_sweep(steps=64), precision=32, energy_every=10, cluster_ctas=4,
+                     block_threads=896, use_graph=False)
         b.step(64)
         b.sync()
         print(json.dumps({"form": "batch", "steps": 64, **b.shape()}), flush=True)
