@@ -382,6 +382,9 @@ __global__ void __launch_bounds__(kBatchMaxThreads) batch1d_kernel(const BatchPa
         T a0 = T(0), a1 = T(0);
         int cur = -1, l = t;
         for (int r = 0; r < nrun; ++r) {
+          // off the energy steps a thread skips the runs that hold none of its cells (l is its
+          // next cell; on energy steps every lane walks every run for the per-segment warp sums)
+          if (!en && l >= srun[r].l1) continue;
           const BatchRun R = srun[r];
           if (en && R.seg != cur) {
             if (cur >= 0) {
@@ -423,6 +426,9 @@ __global__ void __launch_bounds__(kBatchMaxThreads) batch1d_kernel(const BatchPa
         T a1 = T(0), a2 = T(0), a3 = T(0);
         int cur = -1, l = t;
         for (int r = 0; r < nrun; ++r) {
+          // off the energy steps a thread skips the runs that hold none of its cells (l is its
+          // next cell; on energy steps every lane walks every run for the per-segment warp sums)
+          if (!en && l >= srun[r].l1) continue;
           const BatchRun R = srun[r];
           if (en && R.seg != cur) {
             if (cur >= 0) {
