@@ -82,8 +82,8 @@ typedef struct {
  * keywords).  For FDTDBATH_LORENTZ_BATH, gamma is gamma0 and the three bath arrays give
  * {w_j}, {gamma_j}, {k_j} (host pointers, num_bath entries each, 1 <= num_bath <= 128; the
  * paper's Fig. 2 baths have 100).  Up to 32 modes the step kernel keeps a cell's modes in
- * registers, above it streams them from memory; the batch form and the adjoint take at most 32
- * (FDTDBATH_ERR_ARG / FDTDBATH_ERR_UNSUPPORTED). */
+ * registers, above it streams them from memory; the batch form keeps every mode in shared
+ * memory (up to 128 as well); the adjoint takes at most 32 (FDTDBATH_ERR_UNSUPPORTED). */
 typedef struct {
   int32_t kind;
   int64_t z_lo, z_hi;
@@ -253,7 +253,7 @@ int fdtdbath_adjoint_backward(fdtdbath_sim *sim, int32_t monitor, const double *
 typedef struct fdtdbath_batch fdtdbath_batch; /* opaque, owned by the library */
 
 /* One cavity: nz cells (64 <= nz <= 2^24) with a CPML of pml_cells cells at each end, its layers
- * (z in the cavity's own cells, the same rules as fdtdbath_create, at most 32 bath modes per
+ * (z in the cavity's own cells, the same rules as fdtdbath_create, at most 128 bath modes per
  * layer), an optional soft source on
  * component 0 (E_x; phase NULL or one value) and an optional energy box [energy_lo, energy_hi)
  * (energy_hi <= energy_lo: none).  Host pointers, copied by fdtdbath_batch_create. */

@@ -544,7 +544,7 @@ int build_cavities(fdtdbath_batch* b, const fdtdbath_cavity* cavities, int ncav,
       std::string w;
       const int rc = build_material(M, 1, b->dt, b->courant, 1, h, w);
       if (rc) return why = pre + w, rc;
-      if (h.nb > kMaxBath) return why = pre + "the batch holds at most 32 bath modes per material", FDTDBATH_ERR_ARG;
+      if (h.nb > kMaxBathStep) return why = pre + "the batch holds at most 128 bath modes per material", FDTDBATH_ERR_ARG;
       h.base = 0;
       h.ybase = yb;
       yb += (int64_t)h.nb * h.ncell;

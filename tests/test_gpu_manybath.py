@@ -7,7 +7,8 @@ FP64 1e-12 for E, H, the layer's P and bath modes, spectra and energy traces; FP
 E, H and spectra, 1e-4 for the layer's P and bath modes.  Cases: a ragged 3D cavity (tiles cut
 in x and y) and the paper's free-space slab of Fig. 2a in 1D (600 cells at dx = 0.01, 50-cell
 CPML, a 1-unit slab), which runs on the step kernel (the register-resident 1D kernel holds at
-most 32 modes).  The bath arrays come from the oracle's Table I expansion (pinned by P7)."""
+most 32 modes); the slab again beside a Drude-mirror cavity in one batched launch.  The bath
+arrays come from the oracle's Table I expansion (pinned by P7)."""
 import numpy as np
 import pytest
 
@@ -89,17 +90,56 @@ def test_paper_slab_fig2a_1d(precision):
     compare(prob, mat, precision, 1500)
 
 
-def test_forms_limited_to_32_modes():
-    """The batch and the adjoint hold at most 32 bath modes per material."""
+def test_mode_limits_of_the_forms():
+    """The adjoint holds at most 32 bath modes per material, the batch (like the step kernel)
+    at most 128."""
     prob, _ = paper_slab_1d(10)
-    with pytest.raises(fb.FdtdBathError) as e:
-        fb.Batch([prob])
-    assert e.value.code == fb.ERR_ARG
     s = fb.Simulation(prob, precision=32)
     with pytest.raises(fb.FdtdBathError) as e:
         s.adjoint_forward(10, 4)
     assert e.value.code == fb.ERR_UNSUPPORTED
     s.close()
+    f, g, k = cf.bath_form("lorentzian", 1.0, 4e-4, 129, 0.4, 4e-4, 0.0396)
+    m0 = dict(prob["materials"][0], bath_frequencies=f, bath_gammas=g, bath_couplings=k)
+    with pytest.raises(fb.FdtdBathError) as e:
+        fb.Batch([dict(prob, materials=[m0])])
+    assert e.value.code == fb.ERR_ARG
+
+
+@pytest.mark.parametrize("precision", [64, 32])
+def test_batch_with_paper_baths(precision):
+    """The batched form with N_b = 100: the paper's Fig. 2a slab and a Drude-mirror cavity whose
+    360-cell bath layer (800 B of bath state per cell in FP32) spans the CTAs of a cluster, each
+    cavity against the FP64 oracle: E_x, H_y, the layer's P and bath modes 0 / 37 / 99 and the
+    energy traces."""
+    steps = 600
+    slab, _ = paper_slab_1d(steps)
+    cav = with_paper_bath(wl.batch_cavity(900, rabi=0.1, num_bath=8, steps=steps), 1, 1e-2)
+    probs = [slab, cav]
+    b = fb.Batch(probs, precision=precision, cluster_ctas=4, block_threads=256,
+                 energy_capacity=steps + 16)
+    b.step(steps)
+    for i, (p, mat) in enumerate(((slab, 0), (cav, 1))):
+        o = O.OracleSim(p, trace_cap=steps + 16)
+        o.step(steps)
+        lo, hi = p["materials"][mat]["z"]
+        assert rel(b.get(i, "E"), o.get("E", comp=0)[:, 0, 0]) < TOL[precision], (i, "E")
+        assert rel(b.get(i, "H"), o.get("H", comp=1)[:, 0, 0]) < TOL[precision], (i, "H")
+        for name in ("P", "Pm"):
+            e = rel(b.get(i, name)[lo:hi], o.get(name, comp=0)[lo:hi, 0, 0])
+            assert e < TOL_Y[precision], (i, name, e)
+        for j in (0, 37, NB - 1):
+            for lvl in (0, 1):
+                e = rel(b.get(i, "Y", mode=j, level=lvl)[lo:hi],
+                        o.get("Y", comp=0, mode=j, level=lvl)[lo:hi, 0, 0])
+                assert e < TOL_Y[precision], (i, j, lvl, e)
+        tg, to = b.trace(i), o.trace()
+        n = min(len(tg), len(to))
+        assert n == steps
+        for col in range(3):
+            if np.any(to[:n, col]):
+                assert rel(tg[:n, col], to[:n, col]) < 2 * TOL[precision], (i, col)
+    b.close()
 
 
 def test_many_bath_modes_2d_te_form():
