@@ -3,7 +3,7 @@
 Compiles ``fdtd_oracle.c`` with gcc, ``-O2 -ffp-contract=off`` (no fused
 multiply-add: every operation rounds on its own, as written) and OpenMP when
 available, into ``oracle/_build/liboracle.so``.  Only the tests, the smoke check
-and the benchmark's CPU-baseline leg use it.
+and the benchmark's CPU-baseline leg and reference arm use it.
 """
 from __future__ import annotations
 

@@ -2,7 +2,7 @@
  * fdtd_oracle.c -- plain FP64 CPU oracle of the FDTD-Bath time step.
  *
  * TEST INFRASTRUCTURE ONLY.  Only the tests, the smoke check and the
- * benchmark's CPU-baseline leg load this file.  It shares no code, header,
+ * benchmark's CPU-baseline leg and reference arm load this file.  It shares no code, header,
  * table or constant generator with the CUDA library; it reads the same seeded
  * inputs and nothing else.
  *

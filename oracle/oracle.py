@@ -3,7 +3,7 @@
 The time stepping lives in ``fdtd_oracle.c``; this module only marshals a
 problem description (the plain dict the seeded workload generators produce)
 into it and reads state back as numpy arrays.  Only tests, the smoke check and
-the benchmark's CPU-baseline leg import it.
+the benchmark's CPU-baseline leg and reference arm import it.
 
 Field ids follow the C file: 0..2 E, 3..5 H, 6..8 D, 9..11 P^{n+1/2},
 12..14 P^{n-1/2}; bath mode j of component c at level l (0: Y^{n+1/2},
