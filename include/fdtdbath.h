@@ -48,8 +48,8 @@ enum fdtdbath_status {
   FDTDBATH_ERR_CFL = -2,         /* unstable time step (Courant or oscillator update) */
   FDTDBATH_ERR_OOM = -3,         /* device allocation failed */
   FDTDBATH_ERR_CUDA = -4,        /* a CUDA call failed; see fdtdbath_last_error */
-  FDTDBATH_ERR_NONFINITE = -5,   /* a NaN/Inf appeared in the state */
-  FDTDBATH_ERR_TIMEOUT = -6,     /* a bounded device wait gave up */
+  FDTDBATH_ERR_NONFINITE = -5,   /* a NaN/Inf in the spectra or energy trace read out */
+  FDTDBATH_ERR_TIMEOUT = -6,     /* reserved: no kernel of the library waits on a flag */
   FDTDBATH_ERR_UNSUPPORTED = -7  /* valid request the library does not implement */
 };
 
@@ -163,7 +163,8 @@ int fdtdbath_read_fields(fdtdbath_sim *sim, int32_t field, void *dst, size_t dst
 int fdtdbath_write_fields(fdtdbath_sim *sim, int32_t field, const void *src, size_t src_bytes,
                           int32_t src_on_device);
 
-/* Spectra of monitor `monitor`: host out[nfreq][4][2] = (re, im) of (Ex, Ey, Hx, Hy). */
+/* Spectra of monitor `monitor`: host out[nfreq][4][2] = (re, im) of (Ex, Ey, Hx, Hy).
+ * FDTDBATH_ERR_NONFINITE (out filled all the same) when a value is NaN or Inf. */
 int fdtdbath_dft(fdtdbath_sim *sim, int32_t monitor, double *out);
 
 /* Energy trace per step (per unit transverse area, inside the energy box), host
@@ -171,7 +172,8 @@ int fdtdbath_dft(fdtdbath_sim *sim, int32_t monitor, double *out);
  *   U_EM = sum dx/(nx ny) 1/2 (eps_inf E.E + H.H) with E^{n+1/2}, H^{n+1};
  *   U_P = sum dx/(nx ny) rho/2 (((P - PM)/dt)^2 + w0^2 P^2), rho = 1/(sigma w0^2), w0 -> 0 in
  *   the potential for Drude;  U_bath = sum dx/(nx ny) sum_j rho/2 (((Y_j - Y_j')/dt)^2 + w_j^2 Y_j^2)
- * (the energy density of Eq. H_full with P and Y_j as coordinates).  *len = steps written. */
+ * (the energy density of Eq. H_full with P and Y_j as coordinates).  *len = steps written.
+ * FDTDBATH_ERR_NONFINITE (trace and *len filled all the same) when a record is NaN or Inf. */
 int fdtdbath_energy(fdtdbath_sim *sim, double *trace, int64_t maxlen, int64_t *len);
 
 /* Completed steps. */

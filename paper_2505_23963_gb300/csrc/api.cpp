@@ -630,6 +630,15 @@ int store_bf16_levels(fdtdbath_sim* s, int64_t off, const std::vector<float>& y0
   return h2d(s, elem_ptr(s->Yslot[0], off, 4), ab.data(), ab.size() * 2);
 }
 
+// FDTDBATH_ERR_NONFINITE when any of the n values copied out is a NaN or an Inf.
+int check_finite(fdtdbath_sim* s, const double* v, size_t n, const char* what) {
+  for (size_t i = 0; i < n; ++i)
+    if (!std::isfinite(v[i]))
+      return fail(s, FDTDBATH_ERR_NONFINITE,
+                  std::string(what) + " holds NaN or Inf: the state diverged or was given non-finite values");
+  return FDTDBATH_OK;
+}
+
 }  // namespace
 
 int fdtdbath_internal_view(fdtdbath_sim* s, SimView* v) {
@@ -1168,7 +1177,10 @@ int fdtdbath_dft(fdtdbath_sim* s, int32_t monitor, double* out) {
   cudaSetDevice(s->device);
   int rc = flush_all(s);
   if (rc) return rc;
-  return d2h(s, out, s->mons[monitor].dacc, (size_t)s->mons[monitor].nfreq * 8 * 8);
+  const size_t nval = (size_t)s->mons[monitor].nfreq * 8;
+  rc = d2h(s, out, s->mons[monitor].dacc, nval * 8);
+  if (rc) return rc;
+  return check_finite(s, out, nval, "the spectrum");
 }
 
 int fdtdbath_energy(fdtdbath_sim* s, double* trace, int64_t maxlen, int64_t* len) {
@@ -1183,6 +1195,7 @@ int fdtdbath_energy(fdtdbath_sim* s, double* trace, int64_t maxlen, int64_t* len
   if (n > maxlen) n = maxlen;
   if (n > 0) rc = d2h(s, trace, s->trace, (size_t)n * 4 * 8);
   *len = n;
+  if (!rc && n > 0) rc = check_finite(s, trace, (size_t)n * 4, "the energy trace");
   return rc;
 }
 
