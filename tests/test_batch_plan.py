@@ -119,3 +119,39 @@ def test_plan_bounds_the_busiest_thread(C, T):
     print(f"\nC={C} T={T}: busiest thread {b_flat} (whole-CTA balance) -> {b_aware}; mean {mean:.0f}")
     assert b_aware <= 0.75 * b_flat
     assert b_aware <= max(2 * mean, 1.25 * one_cell)
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+@pytest.mark.parametrize("C,T", [(1, 128), (2, 384), (4, 896), (16, 1024)])
+def test_random_batches_are_covered(seed, C, T):
+    """Seeded random batches (lengths 200..3000, N_b in {0, 4, 32, 100}; a cavity is at most as
+    long as its bath state, 8 N_b B per layer cell in FP32, lets it fit 80% of a cluster's shared
+    memory) in several launch shapes: every cavity in one cluster, every cell in exactly one CTA,
+    no CTA above its budget."""
+    cap = 200 * 1024
+    rng = np.random.default_rng(seed)
+    probs = []
+    for i in range(int(rng.integers(3, 20))):
+        nb = int(rng.choice([0, 4, 32, 100]))
+        lmax = min(3000, int(0.8 * C * cap / (0.4 * 8 * nb + 40)))
+        L = int(rng.integers(200, lmax + 1))
+        p = wl.batch_cavity(L, rabi=float(rng.uniform(0.01, 0.2)), num_bath=4, steps=10)
+        m = dict(p["materials"][1])
+        if nb == 0:   # plain Lorentz layer
+            m["kind"] = "lorentz"
+            for k in ("bath_frequencies", "bath_gammas", "bath_couplings"):
+                m.pop(k, None)
+        elif nb > 4:
+            m["bath_frequencies"] = np.linspace(0.8, 1.2, nb)
+            m["bath_gammas"] = np.full(nb, 4e-4)
+            m["bath_couplings"] = np.full(nb, 0.002)
+        p["materials"] = [p["materials"][0], m, p["materials"][2]]
+        probs.append(p)
+    ncl = max(1, 152 // C)
+    r = fb.batch_plan(probs, 32, cluster_ctas=C, nclusters=ncl, smem_per_cta=cap, block_threads=T)
+    L = np.array([p["n"][2] for p in probs])
+    assert r["work"].size % C == 0
+    assert np.all(r["cells"] >= 0) and np.all(r["smem"] <= cap)
+    for k in range(r["work"].size // C):
+        assert int(r["cells"][C * k:C * k + C].sum()) == int(L[r["cluster"] == k].sum())
+    assert int(r["cells"].sum()) == int(L.sum())
