@@ -226,13 +226,13 @@ struct FillState {
 int64_t cta_fixed_bytes() { return 6 * 16; }
 int64_t run_fixed_bytes() { return 2 * 32; }
 
-// Largest k <= kmax such that placing the next k cells, each of work w, keeps every thread of
-// the CTA at or below W; applies the placement when apply is set.
-int64_t thread_fit(FillState& f, int T, int64_t w, int64_t kmax, int64_t W, bool apply) {
+// Places the largest k <= kmax of the next cells, each of work w, that keeps every thread of the
+// CTA at or below W, and returns k.
+int64_t thread_fit(FillState& f, int T, int64_t w, int64_t kmax, int64_t W) {
   if (kmax <= 0) return 0;
   const int64_t curmax = f.base + f.relmax;
   if (w == 0) {
-    if (apply) f.ncell += kmax;
+    f.ncell += kmax;
     return kmax;
   }
   // whole rounds: every thread gets q cells; the q-th round must keep the fullest thread in bounds
@@ -244,7 +244,7 @@ int64_t thread_fit(FillState& f, int T, int64_t w, int64_t kmax, int64_t W, bool
   int64_t r = 0;
   while (r < rlim && f.base + f.rel[(size_t)((s + r) % T)] + (q + 1) * w <= W) ++r;
   const int64_t k = q * T + r;
-  if (apply && k > 0) {
+  if (k > 0) {
     f.base += q * w;
     for (int64_t i = 0; i < r; ++i) {
       int64_t& v = f.rel[(size_t)((s + i) % T)];
@@ -301,7 +301,7 @@ int greedy_fill(const std::vector<BCav>& cavs, const std::vector<HostMat>& mats,
         int64_t k = p.z1 - z;
         if (room) {
           if (p.bytes > 0) k = std::min(k, (cap - f.bytes - extra) / p.bytes);
-          k = thread_fit(f, T, p.work, k, W, true);
+          k = thread_fit(f, T, p.work, k, W);
         } else {
           k = 0;
         }
