@@ -315,6 +315,30 @@ def form_many_bath(fb, stream, torch):
             "finite": finite}
 
 
+# FP32 ALU peak derived from the part's unit counts: 152 SMs x 128 FP32 lanes x 2 flops per FMA
+# x 2.07 GHz maximum SM clock (no measured FP32 figure exists for this machine)
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+
+
+def batch_flops_per_step(probs) -> float:
+    """Algorithmic flops of one step of a batch of 1D cavities (an FMA counts 2): per cell 6 for
+    the E and H half-steps, +8 in CPML cells (both memories), +8 for a Lorentz / Drude
+    polarization, +10 N_b + 8 for a Lorentz-Bath polarization with its N_b bath modes.  Energy
+    sums are not counted."""
+    total = 0.0
+    for p in probs:
+        nz, pml = p["n"][2], int(p.get("pml", 0))
+        total += 6.0 * nz + 8.0 * 2 * pml
+        for m in p["materials"]:
+            n = m["z"][1] - m["z"][0]
+            nb = len(m.get("bath_frequencies", ()))
+            if m["kind"] == "lorentz_bath" and nb > 0:
+                total += (10.0 * nb + 8.0) * n
+            elif m["kind"] in ("lorentz", "drude", "lorentz_bath"):
+                total += 8.0 * n
+    return total
+
+
 def form_batch(fb, torch):
     """Batching form: 64 independent 1D cavities (lengths 1000-8000, Rabi 0.01-0.2, N_b in
     {4, 8, 16, 32}), 50000 FP32 steps in persistent launches replayed from CUDA graphs, energy every
@@ -353,6 +377,7 @@ def form_batch(fb, torch):
     rate64 = ref["n"][2] * 2000 / (time.perf_counter() - t0)
     sim.close()
     g = np.asarray(gam)
+    flops = batch_flops_per_step(probs)
     return {"workload": "batch sweep: 64 cavities x 50000 steps", "value": cells * steps / secs,
             "unit": UNIT, "seconds": secs, "steps": steps, "cells": cells,
             "launch_shape": {"cluster_ctas": C, "threads": T, **shape}, "autotune_s": tune_s,
@@ -361,7 +386,14 @@ def form_batch(fb, torch):
             "bath_share": {"min": float(np.nanmin(share)), "median": float(np.nanmedian(share)),
                            "max": float(np.nanmax(share))},
             "plain_fp64_path": {"value": rate64, "unit": UNIT,
-                                "seconds_for_same_work": cells * steps / rate64}}
+                                "seconds_for_same_work": cells * steps / rate64},
+            # on-chip and bound by issue and latency, not by arithmetic: the FP32 rate against
+            # the derived ALU peak shows how far
+            "roofline": {"bound": "alu", "achieved": flops * steps / secs / 1e12,
+                         "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                         "frac": flops * steps / secs / 1e12 / FP32_PEAK_TFLOPS,
+                         "peak_kind": "derived (152 SMs x 128 FP32 lanes x 2 x 2.07 GHz)",
+                         "flops_per_step": flops}}
 
 
 def form_adjoint(fb, torch):
