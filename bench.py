@@ -315,6 +315,32 @@ def form_many_bath(fb, stream, torch):
             "finite": finite}
 
 
+def form_cavity_1d(fb, stream, torch):
+    """The plain method on the 1D Fabry-Perot cavity (Nz = 2000, N_b = 16, 500 DFT frequencies,
+    energy every step), 20000 steps on the persistent 1D kernel in FP64 and FP32: steps/s and
+    cell-updates/s.  On-chip and latency-bound: the state stays in registers for a whole call."""
+    steps = 20000
+    prob = wl.cavity_1d(steps=steps)
+    nz = prob["n"][2]
+    out = {"workload": prob["name"], "steps": steps}
+    for prec in (64, 32):
+        with torch.cuda.stream(stream):
+            sim = fb.Simulation(prob, precision=prec, stream=stream, energy_capacity=steps + 208)
+        sim.step(200)
+        sim.sync()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        ev[0].record(stream)
+        sim.step(steps)
+        ev[1].record(stream)
+        torch.cuda.synchronize()
+        ms = ev[0].elapsed_time(ev[1])
+        out[f"fp{prec}"] = {"value": nz * steps / (ms * 1e-3), "unit": UNIT,
+                            "steps_per_s": steps / (ms * 1e-3), "us_per_step": 1e3 * ms / steps,
+                            "finite": spectrum_is_finite(fb, sim)}
+        sim.close()
+    return out
+
+
 # FP32 ALU peak derived from the part's unit counts: 152 SMs x 128 FP32 lanes x 2 flops per FMA
 # x 2.07 GHz maximum SM clock (no measured FP32 figure exists for this pool)
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
@@ -624,7 +650,8 @@ def run_ours(args):
         for name, fn in (("precision", lambda: form_precision(fb, stream, torch)),
                          ("many_bath", lambda: form_many_bath(fb, stream, torch)),
                          ("batch", lambda: form_batch(fb, torch)),
-                         ("adjoint", lambda: form_adjoint(fb, torch))):
+                         ("adjoint", lambda: form_adjoint(fb, torch)),
+                         ("cavity_1d", lambda: form_cavity_1d(fb, stream, torch))):
             try:
                 forms[name] = fn()
             except Exception as exc:   # reported, not hidden: the line says which form failed
