@@ -40,7 +40,7 @@
 extern "C" {
 #endif
 
-#define FDTDBATH_ABI_VERSION 1
+#define FDTDBATH_ABI_VERSION 2   /* 2: fdtdbath_batch_plan takes block_threads */
 
 enum fdtdbath_status {
   FDTDBATH_OK = 0,
