@@ -49,7 +49,8 @@ enum fdtdbath_status {
   FDTDBATH_ERR_OOM = -3,         /* device allocation failed */
   FDTDBATH_ERR_CUDA = -4,        /* a CUDA call failed; see fdtdbath_last_error */
   FDTDBATH_ERR_NONFINITE = -5,   /* a NaN/Inf in the spectra or energy trace read out */
-  FDTDBATH_ERR_TIMEOUT = -6,     /* reserved: no kernel of the library waits on a flag */
+  FDTDBATH_ERR_TIMEOUT = -6,     /* a kernel's bounded (1 s) wait for its staged planes ran out;
+                                  * returned by fdtdbath_sync / dft / energy, results invalid */
   FDTDBATH_ERR_UNSUPPORTED = -7  /* valid request the library does not implement */
 };
 

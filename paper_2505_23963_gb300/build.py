@@ -26,6 +26,8 @@ UNITS = [
     ("api.cpp", []),
     ("step3d_f32.cu", []),
     ("step3d_f64.cu", ["--fmad=false"]),
+    ("plain3d_f32.cu", []),
+    ("plain3d_f64.cu", ["--fmad=false"]),
     ("reduce.cu", ["--fmad=false"]),
     ("noalloc.cu", ["--fmad=false"]),
     ("cavity1d_f32.cu", []),

@@ -131,6 +131,11 @@ struct fdtdbath_sim {
   // write could make one of them nonzero
   bool te = false;
   bool adj_te = false;      // the last reverse sweep ran the TE form
+  // plain-plane kernel (plain3d.cuh) for the chunks without bath planes: grids of at least 8 rows,
+  // nx a multiple of 4, every source plane outside the layers; planes staged ahead by it
+  bool plain_ok = false;
+  int plain_minb = 0;       // FP32 tile / pipeline variant of the plain-plane kernel
+  void* errflag = nullptr;  // device int: a bounded wait of a kernel ran out (FDTDBATH_ERR_TIMEOUT)
   AdjState adj;
   std::string err;
 };
@@ -206,7 +211,7 @@ bool chunk_has_bath(const fdtdbath_sim* s, int64_t lo, int64_t hi) {
 // Between those cuts, a range of L planes is split into chunks of zc planes (uniform plan), or
 // (balanced plan) into a head chunk of ceil(3L/4) planes and a tail chunk of the rest: dispatched
 // longest first, the tail chunks of a launch fill its last partial wave of CTAs.
-int plan_chunks(fdtdbath_sim* s, int zc, bool balanced, std::vector<int>& starts) {
+int plan_chunks(fdtdbath_sim* s, int zc, bool balanced, int plain_zc, std::vector<int>& starts) {
   starts.clear();
   starts.push_back(0);
   const int64_t lo_ok = s->npml + 1, hi_ok = s->nz - 1 - s->npml;
@@ -222,6 +227,21 @@ int plan_chunks(fdtdbath_sim* s, int zc, bool balanced, std::vector<int>& starts
   for (size_t b = 0; b + 1 < bounds.size(); ++b) {
     const int64_t a = bounds[b], e = bounds[b + 1];
     if (z >= e) continue;   // already covered by a chunk the boundary rule extended
+    if (plain_zc > 0 && !chunk_has_bath(s, z, e)) {
+      // ranges without bath planes (the plain-plane kernel): near-equal chunks of about plain_zc
+      const int64_t z0 = z, L = e - z0;
+      const int64_t n = std::max<int64_t>(1, (L + plain_zc / 2) / plain_zc);
+      for (int64_t i = 1; i <= n && z < e; ++i) {
+        int64_t nx = z0 + (L * i) / n;
+        if (nx < lo_ok) nx = lo_ok;
+        if (nx > hi_ok) nx = s->nz;
+        if (nx > s->nz) nx = s->nz;
+        if (nx <= z) continue;
+        starts.push_back((int)nx);
+        z = nx;
+      }
+      continue;
+    }
     const int64_t step = balanced ? std::max<int64_t>(1, (3 * (e - a) + 3) / 4) : zc;
     while (z < e) {
       int64_t nx = std::min(z + step, e);
@@ -318,6 +338,7 @@ Step3DParams<T> make_params(fdtdbath_sim* s, int doH, int doE) {
   p.nchunks_total = s->nchunks;
   p.nbxy = s->nbx * s->nby;
   p.vec16 = (s->nx % (int64_t)(16 / sizeof(T)) == 0) ? 1 : 0;
+  p.err = (int*)s->errflag;
   return p;
 }
 
@@ -337,6 +358,23 @@ int launch_chunks(fdtdbath_sim* s, Step3DParams<T> p, int nbmax, int id_off, int
   return launch_typed(p, nbmax, s->ty, s->nbx, s->nby, n, s->ybf, s->te && s->ty == 1, st);
 }
 
+int launch_plain_typed(const Step3DParams<float>& p, int n, int minb, cudaStream_t st) {
+  return launch_plain3d_f32(p, n, minb, st);
+}
+int launch_plain_typed(const Step3DParams<double>& p, int n, int minb, cudaStream_t st) {
+  return launch_plain3d_f64(p, n, minb, st);
+}
+
+// Chunks without bath planes: the plain-plane kernel when it applies (both half-steps of a step),
+// otherwise the general kernel's bath-free instantiation.
+template <typename T>
+int launch_plain_chunks(fdtdbath_sim* s, Step3DParams<T> p, int id_off, int n, cudaStream_t st) {
+  if (!(s->plain_ok && p.doH && p.doE)) return launch_chunks<T>(s, p, 0, id_off, n, st);
+  p.chunk_ids = (const int*)s->chunk_ids + id_off;
+  s->launches++;
+  return launch_plain_typed(p, n, s->plain_minb, st);
+}
+
 // One step's launches: without a pending E half-step, or without bath chunks, one launch over
 // all chunks (the bath-free kernel when no bath update runs); otherwise the bath-free kernel
 // over the plain chunks on the side stream, concurrently with the bath kernel over the bath
@@ -344,13 +382,14 @@ int launch_chunks(fdtdbath_sim* s, Step3DParams<T> p, int nbmax, int id_off, int
 template <typename T>
 int launch_all(fdtdbath_sim* s, int doH, int doE) {
   Step3DParams<T> p = make_params<T>(s, doH, doE);
-  if (!doE || s->nbmax == 0 || s->nbath == 0)
-    return launch_chunks<T>(s, p, doE ? s->nbmax : 0, 0, s->nchunks, s->stream);
+  if (!doE) return launch_chunks<T>(s, p, 0, 0, s->nchunks, s->stream);
+  if (s->nbmax == 0) return launch_plain_chunks<T>(s, p, 0, s->nchunks, s->stream);
+  if (s->nbath == 0) return launch_chunks<T>(s, p, s->nbmax, 0, s->nchunks, s->stream);
   if (s->nplain == 0) return launch_chunks<T>(s, p, s->nbmax, s->nchunks, s->nbath, s->stream);
   cudaError_t e = cudaEventRecord(s->ev_fork, s->stream);
   if (e == cudaSuccess) e = cudaStreamWaitEvent(s->side, s->ev_fork, 0);
   if (e != cudaSuccess) return (int)e;
-  int rc = launch_chunks<T>(s, p, 0, s->nchunks, s->nplain, s->side);
+  int rc = launch_plain_chunks<T>(s, p, s->nchunks, s->nplain, s->side);
   if (rc) return rc;
   rc = launch_chunks<T>(s, p, s->nbmax, s->nchunks + s->nplain, s->nbath, s->stream);
   if (rc) return rc;
@@ -639,6 +678,18 @@ int check_finite(fdtdbath_sim* s, const double* v, size_t n, const char* what) {
   return FDTDBATH_OK;
 }
 
+// FDTDBATH_ERR_TIMEOUT when a kernel's bounded wait for staged data ran out since the simulation
+// was created (its results are then not valid).  Call after the stream has been synchronized.
+int check_timeout(fdtdbath_sim* s) {
+  int flag = 0;
+  cudaError_t e = cudaMemcpy(&flag, s->errflag, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(s, e, "error flag");
+  if (flag)
+    return fail(s, FDTDBATH_ERR_TIMEOUT,
+                "a step kernel's bounded wait for its staged planes ran out (the results are not valid)");
+  return FDTDBATH_OK;
+}
+
 }  // namespace
 
 int fdtdbath_internal_view(fdtdbath_sim* s, SimView* v) {
@@ -821,19 +872,38 @@ int fdtdbath_create(const fdtdbath_grid* grid, double resolution, double courant
     zc = std::min(64, std::max(1, std::atoi(e)));
     balanced = false;
   }
+  // the plain-plane kernel may take the chunks without bath planes (plain3d.cuh: at least 8 rows, nx
+  // a multiple of 4 for its 16-byte vectors and bulk copies and at least 16, source planes outside
+  // the layers; FDTDBATH_PLAIN=1 selects it); those ranges are then cut into near-equal chunks of
+  // about plain_zc planes (FDTDBATH_PLAIN_ZCHUNK)
+  s->plain_ok = s->ty == 8 && nx % 4 == 0 && nx >= 16;
+  {
+    const char* e = std::getenv("FDTDBATH_PLAIN");   // off unless FDTDBATH_PLAIN=1
+    s->plain_ok = s->plain_ok && e && std::atoi(e) != 0;
+  }
+  for (auto& q : s->srcs)
+    for (auto& m : s->mats)
+      if (q.z >= m.zlo && q.z < m.zhi) s->plain_ok = false;
+  int plain_zc = 0;
+  if (s->plain_ok) {
+    plain_zc = 16;
+    if (const char* e = std::getenv("FDTDBATH_PLAIN_ZCHUNK")) plain_zc = std::min(64, std::max(1, std::atoi(e)));
+    if (const char* e = std::getenv("FDTDBATH_PLAIN_SHAPE")) s->plain_minb = std::atoi(e);
+  }
   std::vector<int> starts;
   if (balanced) {
     int sms = 0;
     balanced = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s->device) == cudaSuccess && sms > 0;
     if (balanced) {
-      const int n = plan_chunks(s, zc, true, starts);
+      const int n = plan_chunks(s, zc, true, plain_zc, starts);
       int64_t nplain = 0, nbath = 0;
       for (int c = 0; c < n; ++c) {
         if (starts[c + 1] - starts[c] > 128) balanced = false;
         (chunk_has_bath(s, starts[c], starts[c + 1]) ? nbath : nplain) += 1;
       }
       const int64_t tiles = (int64_t)s->nbx * s->nby;
-      if ((nplain > 0 && nplain * tiles < 4LL * sms) || (nbath > 0 && nbath * tiles < 2LL * sms)) balanced = false;
+      if ((!s->plain_ok && nplain > 0 && nplain * tiles < 4LL * sms) || (nbath > 0 && nbath * tiles < 2LL * sms))
+        balanced = false;
     }
   }
   // uniform plan on grids with few tiles per plane (the 2D cavities: one row of 32-wide tiles, or
@@ -845,7 +915,9 @@ int fdtdbath_create(const fdtdbath_grid* grid, double resolution, double courant
     const int64_t ktiles = te0 ? (nx + 4 * kTX - 1) / (4 * kTX) : (int64_t)s->nbx * s->nby;
     if (ktiles < 64) zc = 16;
   }
-  s->nchunks = plan_chunks(s, zc, balanced, starts);
+  s->nchunks = plan_chunks(s, zc, balanced, plain_zc, starts);
+  for (int c = 0; c < s->nchunks; ++c)   // the plain-plane kernel takes chunks of at most 64 planes
+    if (!chunk_has_bath(s, starts[c], starts[c + 1]) && starts[c + 1] - starts[c] > 64) s->plain_ok = false;
   for (size_t c = 0; c + 1 < starts.size(); ++c)
     if (starts[c + 1] - starts[c] > 128) return bail(FDTDBATH_ERR_ARG, "z-chunk longer than 128 planes");
   if ((int64_t)s->nbx * s->nby > 65535 * 64) return bail(FDTDBATH_ERR_ARG, "grid too large for the launch plan");
@@ -872,8 +944,9 @@ int fdtdbath_create(const fdtdbath_grid* grid, double resolution, double courant
   for (auto& m : s->mats) nmodes += m.nb;
   s->coef = dalloc(s, (size_t)std::max(1, nmodes) * kCoefStride * esz);
   s->zstart = dalloc(s, starts.size() * sizeof(int));
+  s->errflag = dalloc(s, 16);
   s->chunk_ids = dalloc(s, 2 * (size_t)s->nchunks * sizeof(int));
-  if (!s->psiE || !s->pmlE || !s->pmlH || !s->D || !s->coef || !s->zstart || !s->chunk_ids)
+  if (!s->psiE || !s->pmlE || !s->pmlH || !s->D || !s->coef || !s->zstart || !s->chunk_ids || !s->errflag)
     return bail(FDTDBATH_ERR_OOM, "device allocation failed");
   std::vector<int> ids;
   for (int c = 0; c < s->nchunks; ++c) ids.push_back(c);
@@ -1030,7 +1103,7 @@ int fdtdbath_sync(fdtdbath_sim* s) {
   if (e != cudaSuccess) return cuda_fail(s, e, "stream");
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(s, e, "deferred");
-  return FDTDBATH_OK;
+  return check_timeout(s);
 }
 
 int fdtdbath_read_fields(fdtdbath_sim* s, int32_t field, void* dst, size_t dst_bytes, int32_t dst_on_device) {
@@ -1180,6 +1253,8 @@ int fdtdbath_dft(fdtdbath_sim* s, int32_t monitor, double* out) {
   const size_t nval = (size_t)s->mons[monitor].nfreq * 8;
   rc = d2h(s, out, s->mons[monitor].dacc, nval * 8);
   if (rc) return rc;
+  rc = check_timeout(s);
+  if (rc) return rc;
   return check_finite(s, out, nval, "the spectrum");
 }
 
@@ -1195,6 +1270,7 @@ int fdtdbath_energy(fdtdbath_sim* s, double* trace, int64_t maxlen, int64_t* len
   if (n > maxlen) n = maxlen;
   if (n > 0) rc = d2h(s, trace, s->trace, (size_t)n * 4 * 8);
   *len = n;
+  if (!rc) rc = check_timeout(s);
   if (!rc && n > 0) rc = check_finite(s, trace, (size_t)n * 4, "the energy trace");
   return rc;
 }

@@ -25,6 +25,7 @@ constexpr int kMaxBath = 32;       // bath modes per material: 1D cavity kernel,
 constexpr int kMaxBathStep = 128;  // bath modes per material: the 3D / 2D step kernel (streamed above 32)
 constexpr int kTX = 32;
 constexpr int kCoefStride = 8;  // coefficient row per bath mode
+constexpr int kMaxChunk = 128;  // planes per z-chunk (the per-plane table in shared memory)
 
 enum Kind { kVacuum = 0, kLorentz = 1, kDrude = 2, kLorentzBath = 3 };
 
@@ -103,6 +104,7 @@ struct Step3DParams {
   int nchunks_total;
   int nbxy;               // partial-sum slots per z-chunk (the (x, y) tiles of the 32 x 8 tiling)
   int vec16;              // nx is a multiple of 16 bytes' worth of elements: 16-byte staging
+  int* err;               // device flag set when a bounded wait for an asynchronous copy ran out
 };
 
 // Persistent 1D cavity kernel (nx = ny = 1, x polarization): all steps of a call in one launch,
@@ -149,6 +151,11 @@ int launch_step3d_f32(const Step3DParams<float>& p, int nbmax, int ty, int nbx, 
                       int nchunks, int bath_bf16, int te, void* stream);
 int launch_step3d_f64(const Step3DParams<double>& p, int nbmax, int ty, int nbx, int nby,
                       int nchunks, int te, void* stream);
+// The plain-plane step (plain3d.cuh): chunks without bath modes, grids of at least 8 rows with nx a
+// multiple of 4 and at least 16, chunks of at most 64 planes, H and E half-steps together; shape:
+// the FP32 tile / pipeline variant (see plain3d_f32.cu).
+int launch_plain3d_f32(const Step3DParams<float>& p, int nchunks, int shape, void* stream);
+int launch_plain3d_f64(const Step3DParams<double>& p, int nchunks, int shape, void* stream);
 
 // ---- discrete adjoint (adjoint.cu) ----
 // One reverse step of the exact transpose of the forward step (D-free form), applied to the

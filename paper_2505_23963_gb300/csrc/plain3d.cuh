@@ -1,0 +1,744 @@
+// plain3d.cuh -- the fused step of the z-planes without bath modes (vacuum, CPML, Lorentz and
+// Drude layers), general 3D form on grids of at least 8 rows.
+//
+// It computes what step3d_kernel<T, INC, 0, 8> computes for such planes -- the H half-step of
+// the previous step (H^n from E^{n-1/2}, Eq. 1b, with the CPML memories of the z-derivative
+// terms), this step's D/E half-step (Eq. 1a, D = E + P, soft plane sources) and the Lorentz /
+// Drude polarization update (Eq. Pz_1D_Lorentz, one P per component) -- with the same
+// expressions in the same order, so that FP64 runs (compiled without FMA contraction) agree bit
+// for bit with it.  It exists because the general kernel, one cell per thread with ~1000
+// per-thread 16-byte copies and two barriers per plane, spends ~130 integer instructions per cell
+// and plane and is issue-bound at half of the memory bandwidth on these planes.  Here:
+//
+//   * a CTA owns a (32 VX) x TY column tile and marches along a z-chunk; compute warp w owns row
+//     y0 + w, lane l the VX = 16 / sizeof(T) adjacent cells x0 + VX l ..., so every shared-memory
+//     and global access of a thread is one 16-byte vector and the per-plane bookkeeping is paid
+//     once per VX cells; plain vacuum planes run a code path without the CPML, layer, source and
+//     monitor branches;
+//   * one more warp (the helper) stages the planes ahead: the E_in frame (the tile and one cell of
+//     halo on each side, padded to 16-byte boundaries) and the H_in frame (the tile and its -x / -y
+//     halo) by the bulk-copy engine (cp.async.bulk, one copy per frame row and periodic piece),
+//     A planes ahead, completing on one mbarrier per stage in flight (waits bounded in time); it
+//     also recomputes H^n on the halo row y0-1, so the compute warps carry equal work;
+//   * the halo cell x0-1 of each row is recomputed by lane 0 of the row's warp; x-neighbours of H^n
+//     pass between lanes by shuffles, y-neighbours (H_x, H_z only) through shared memory;
+//   * one CTA barrier per plane: H^n of plane k goes to one of two shared buffers, so the E update
+//     of plane k and the H update of plane k+1 never touch the same buffer.
+//
+// Shared-memory ring: E frames in A+1 slots, H_in frames in A slots, H^n (x and z) in two
+// buffers.  Stage g of a chunk (plane k = zb + g) brings E_in(k+1) and H_in(k), stage 0 also
+// E_in(zb); it is issued after the barrier of plane k-A, when the slots it overwrites
+// (E_in(k-A), H_in(k-A)) have been read for the last time.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <type_traits>
+
+#include "internal.h"
+
+namespace fdtdbath {
+
+namespace plain {
+
+constexpr int TY = 8;                          // rows of a tile = compute warps (one more: the helper)
+constexpr int kMaxPieces = 12;                 // periodic pieces of one frame row (nx >= 16)
+constexpr int kMaxPlanes = 64;                 // planes per z-chunk of this kernel
+constexpr uint64_t kWaitLimitNs = 1000000000;  // a stage not complete after 1 s is an error
+// per-plane table bits (material index + 1 in the low four bits)
+enum : int { kBox = 0x10, kMonE = 0x20, kMonH = 0x40, kSrc = 0x80, kPmlE = 0x100, kPmlH = 0x200, kTop = 0x400 };
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* b, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(b)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* b, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(b)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ unsigned mbar_try_wait(uint64_t* b, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(b)), "r"(parity)
+      : "memory");
+  return ok;
+}
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;\n" : "=l"(t));
+  return t;
+}
+// Wait for the phase of the given parity to complete; false after kWaitLimitNs without it.
+__device__ __forceinline__ bool mbar_wait(uint64_t* b, unsigned parity) {
+  if (mbar_try_wait(b, parity)) return true;
+  const uint64_t t0 = global_ns();
+  for (;;) {
+    for (int r = 0; r < 32; ++r)
+      if (mbar_try_wait(b, parity)) return true;
+    if (global_ns() - t0 > kWaitLimitNs) return false;
+  }
+}
+// Bulk copy global -> this CTA's shared memory (shared-space address sdst), completing `bytes` on
+// mbarrier b.  Both addresses and the size are multiples of 16 bytes.
+__device__ __forceinline__ void bulk_g2s(unsigned sdst, const void* gsrc, unsigned bytes, uint64_t* b) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(sdst),
+      "l"(gsrc), "r"(bytes), "r"(smem_u32(b))
+      : "memory");
+}
+
+// VX-cell vectors (8 or 16 bytes, naturally aligned)
+template <typename T, int VX>
+struct Vec;
+template <>
+struct Vec<float, 4> {
+  static __device__ __forceinline__ void ld(const void* p, float* o) {
+    const float4 v = *reinterpret_cast<const float4*>(p);
+    o[0] = v.x;
+    o[1] = v.y;
+    o[2] = v.z;
+    o[3] = v.w;
+  }
+  static __device__ __forceinline__ void st(void* p, const float* v) {
+    *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+  }
+};
+template <>
+struct Vec<float, 2> {
+  static __device__ __forceinline__ void ld(const void* p, float* o) {
+    const float2 v = *reinterpret_cast<const float2*>(p);
+    o[0] = v.x;
+    o[1] = v.y;
+  }
+  static __device__ __forceinline__ void st(void* p, const float* v) {
+    *reinterpret_cast<float2*>(p) = make_float2(v[0], v[1]);
+  }
+};
+template <>
+struct Vec<double, 2> {
+  static __device__ __forceinline__ void ld(const void* p, double* o) {
+    const double2 v = *reinterpret_cast<const double2*>(p);
+    o[0] = v.x;
+    o[1] = v.y;
+  }
+  static __device__ __forceinline__ void st(void* p, const double* v) {
+    *reinterpret_cast<double2*>(p) = make_double2(v[0], v[1]);
+  }
+};
+
+__device__ __forceinline__ int wrap(int v, int n) {
+  v %= n;
+  return v < 0 ? v + n : v;
+}
+
+// H update (Eq. 1b, mu0 = 1) of one cell from the six E differences, in the form of the general
+// kernel's h_update: psi <- b psi + c dE|z inside the CPML.
+template <typename T>
+__device__ __forceinline__ void h_cell(T& hx, T& hy, T& hz, T& psx, T& psy, T dyEz, T dzEy, T dzEx, T dxEz,
+                                       T dxEy, T dyEx, bool pml, T b, T c, T S) {
+  if (pml) {
+    psx = b * psx + c * dzEy;
+    psy = b * psy + c * dzEx;
+    hx = hx - S * (dyEz - (dzEy + psx));
+    hy = hy - S * ((dzEx + psy) - dxEz);
+  } else {
+    hx = hx - S * (dyEz - dzEy);
+    hy = hy - S * (dzEx - dxEz);
+  }
+  hz = hz - S * (dxEy - dyEx);
+}
+
+}  // namespace plain
+
+// Per 32 x 8 partial-sum slot (a tile's rows are its slot's rows): each slot column h (VX per
+// block) collects 32/VX lanes per row.  block_slot_sums: the sum of v[q] over each slot's
+// lanes (shuffles in V's precision) lands in red[q][row][h] (FP64), written by the compute warps;
+// a barrier follows, so slot_total reads it.  Fixed order throughout.
+template <int TY, int VX, int NQ, typename V>
+__device__ __forceinline__ void block_slot_sums(V (&v)[NQ], double* red, int w, int lane) {
+  constexpr int LPS = 32 / VX;
+#pragma unroll
+  for (int q = 0; q < NQ; ++q)
+#pragma unroll
+    for (int o = LPS / 2; o > 0; o >>= 1) v[q] += __shfl_down_sync(0xffffffffu, v[q], o, LPS);
+  if (w < TY && (lane % LPS) == 0)
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) red[(q * TY + w) * VX + lane / LPS] = (double)v[q];
+  __syncthreads();
+}
+// the slot's total over the TY rows (0.0 + the sum in row order)
+template <int TY, int VX>
+__device__ __forceinline__ double slot_total(const double* red, int q, int h) {
+  double s = 0.0;
+  for (int ww = 0; ww < TY; ++ww) s += red[(q * TY + ww) * VX + h];
+  return s;
+}
+
+template <typename T, int VX_, int A>
+struct Plain3DLayout {
+  static constexpr int VX = VX_, TY = plain::TY;
+  static constexpr int TX = 32 * VX, FX = TX + 8, HX = TX + 4, FY = TY + 2, HY = TY + 1;
+  static constexpr int FE = FY * FX, FH = HY * HX;   // elements per component of an E / H frame
+  static constexpr int NE = A + 1, NH = A;            // E and H_in frame slots
+  static constexpr int threads = 32 * (TY + 1);
+  // byte offsets: E slots [NE][3][FE], H_in slots [NH][3][FH], H^n buffers [2][Hx, Hz][HY][TX],
+  // mbarriers [A], plane table [kMaxPlanes], row pieces [2][4][kMaxPieces]
+  static constexpr unsigned ES = 3u * FE * sizeof(T), HS = 3u * FH * sizeof(T), XS = 2u * HY * TX * sizeof(T);
+  static constexpr unsigned OFF_E = 0, OFF_HIN = NE * ES, OFF_SH = OFF_HIN + NH * HS, OFF_MBAR = OFF_SH + 2 * XS;
+  static constexpr unsigned OFF_INFO = OFF_MBAR + ((8 * A + 15) / 16) * 16, OFF_PIECE = OFF_INFO + plain::kMaxPlanes * 4;
+  static constexpr unsigned bytes = OFF_PIECE + 2 * 4 * plain::kMaxPieces * 4;
+  // CTAs per SM that the shared memory admits (228 KB per SM, 1 KB reserved per CTA, static 128 B)
+  static constexpr int per_sm = 233472 / (bytes + 1024 + 128) > 8 ? 8 : 233472 / (bytes + 1024 + 128);
+  static_assert(OFF_MBAR % 16 == 0, "mbarrier alignment");
+  static_assert(ES % 16 == 0 && HS % 16 == 0 && XS % 16 == 0, "16-byte aligned frames");
+  // the slot sums of the monitors / energy use the H^n buffer not in use (4 x TY x VX doubles)
+  static_assert(4 * TY * VX * 8 <= XS, "reduction scratch fits an H buffer");
+};
+
+template <typename T, bool INC, int VX, int A>
+__global__ void __launch_bounds__(Plain3DLayout<T, VX, A>::threads, Plain3DLayout<T, VX, A>::per_sm)
+plain3d_kernel(const Step3DParams<T> p) {
+  using namespace plain;
+  using L = Plain3DLayout<T, VX, A>;
+  using VV = Vec<T, VX>;
+  constexpr int TY = L::TY;
+  constexpr int TX = L::TX, FX = L::FX, HX = L::HX, FY = L::FY, HY = L::HY, NE = L::NE, NH = L::NH;
+  constexpr unsigned SZ = sizeof(T), ES = L::ES, HS = L::HS, XS = L::XS;
+  constexpr unsigned CE = L::FE * SZ, CH = L::FH * SZ;   // component strides (bytes)
+  constexpr unsigned RE = FX * SZ, RH = HX * SZ;         // row strides (bytes)
+  constexpr unsigned RX = TX * SZ, CX = HY * RX;         // H^n buffer: row and component strides
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(smem_raw + L::OFF_MBAR);
+  int* sInfo = reinterpret_cast<int*>(smem_raw + L::OFF_INFO);
+  int* sPiece = reinterpret_cast<int*>(smem_raw + L::OFF_PIECE);   // [2][4][kMaxPieces]
+  __shared__ int s_abort;
+  auto at = [&](unsigned off) -> unsigned char* { return smem_raw + off; };
+
+  const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
+  const bool helper = w == TY;
+  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+  const int i0 = x0 + VX * lane, j = y0 + w;
+  const bool own = !helper && (i0 < p.nx) && (j < p.ny);   // nx is a multiple of VX: all VX cells or none
+  const int chunk = p.chunk_ids[blockIdx.z];
+  const int zb = p.zstart[chunk], ze = p.zstart[chunk + 1];
+  const int np = ze - zb;
+  const int plane = (int)p.plane, ncell = (int)p.ncell;
+  const int qxy = own ? j * p.nx + i0 : 0;
+  const T dt = p.dt, S = p.S;
+  const int nmc = (int)p.nmatcell;
+  const int nbx32 = (p.nx + 31) / 32;
+  const int slot_row = blockIdx.y;   // 32 x 8 partial-sum slots: the tile's rows
+  // frame byte offsets of this thread's first cell: compute warps their row w + 1, the helper the
+  // halo row 0 (E frame column of x is x - x0 + 4); H^n buffer offset (column of x is x - x0)
+  const int frow = helper ? 0 : w + 1;
+  const unsigned oE = (unsigned)(frow * FX + 4 + VX * lane) * SZ;
+  const unsigned oH = (unsigned)(frow * HX + 4 + VX * lane) * SZ;
+  const unsigned oX = (unsigned)frow * RX + (unsigned)(VX * lane) * SZ;
+
+  // ---- set-up: mbarriers, periodic pieces of the frame rows, per-plane table ----
+  if (tid == 0) {
+    s_abort = 0;
+    for (int a = 0; a < A; ++a) plain::mbar_init(&mbar[a], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    // pieces of an E row (frame cols 0..FX-1 <-> x0-4 .. x0+TX+3) and of an H row (0..HX-1)
+    for (int f = 0; f < 2; ++f) {
+      const int W = f == 0 ? FX : HX;
+      int* tab = sPiece + f * 4 * kMaxPieces;
+      int n = 0, col = 0;
+      while (col < W && n < kMaxPieces) {
+        const int x = wrap(x0 - 4 + col, p.nx);
+        const int len = min(W - col, p.nx - x);
+        tab[n] = col;
+        tab[kMaxPieces + n] = x;
+        tab[2 * kMaxPieces + n] = len;
+        col += len;
+        ++n;
+      }
+      tab[3 * kMaxPieces] = n;
+      if (col != W) s_abort = 1;   // cannot happen for nx >= 16 (checked on the host)
+    }
+    if (np > kMaxPlanes) s_abort = 1;   // the host plans chunks of at most kMaxPlanes planes
+  }
+  for (int t = tid; t < np && t < kMaxPlanes; t += L::threads) {
+    const int k = zb + t;
+    int info = 0;
+    for (int m = 0; m < p.nmat; ++m)
+      if (k >= p.mat[m].zlo && k < p.mat[m].zhi) info = m + 1;
+    if (k >= p.ebox_lo && k < p.ebox_hi) info |= kBox;
+    for (int m = 0; m < p.nmon; ++m) {
+      if (k == p.mon_z[m]) info |= kMonE;
+      if (k == p.mon_z[m] || k == p.mon_z[m] - 1) info |= kMonH;
+    }
+    for (int q = 0; q < p.nsrc; ++q)
+      if (k == p.src_z[q]) info |= kSrc;
+    if (k < p.npml || k >= p.nz - p.npml) info |= kPmlE;
+    if (p.npml > 0 && (k < p.npml || k >= p.nz - p.npml - 1)) info |= kPmlH;
+    if (k + 1 >= p.nz) info |= kTop;
+    sInfo[t] = info;
+  }
+  __syncthreads();
+  if (s_abort) {
+    if (tid == 0) atomicExch(p.err, 1);
+    return;
+  }
+
+  // ---- helper: stage g brings E_in(zb+g+1) (unless past the grid) and H_in(zb+g), stage 0 also
+  // E_in(zb); one frame row (component c, row r) per lane and pass, copied piece by piece ----
+  const int nrowE = 3 * FY, nrowH = 3 * HY;
+  auto stage_bytes = [&](int g) -> unsigned {
+    const int nE = (zb + g + 1 < p.nz ? 1 : 0) + (g == 0 ? 1 : 0);
+    return (unsigned)(nE * nrowE * FX + nrowH * HX) * SZ;
+  };
+  auto issue_stage = [&](int g) {
+    const int k = zb + g;
+    const bool nextE = k + 1 < p.nz;
+    const int nrow = (nextE ? nrowE : 0) + (g == 0 ? nrowE : 0) + nrowH;
+    uint64_t* bar = &mbar[g % A];
+    for (int row = lane; row < nrow; row += 32) {
+      int rr = row, kk, frame;   // frame 0: an E frame of plane kk, 1: the H_in frame of plane k
+      if (nextE && rr < nrowE) {
+        kk = k + 1;
+        frame = 0;
+      } else {
+        if (nextE) rr -= nrowE;
+        if (g == 0 && rr < nrowE) {
+          kk = zb;
+          frame = 0;
+        } else {
+          if (g == 0) rr -= nrowE;
+          kk = k;
+          frame = 1;
+        }
+      }
+      const int rows = frame == 0 ? FY : HY;
+      const int c = rr / rows, r = rr - c * rows;
+      int y = y0 - 1 + r;   // y0 - 1 <= y <= y0 + TY < 2 ny
+      y = y < 0 ? y + p.ny : (y >= p.ny ? y - p.ny : y);
+      const T* src = (frame == 0 ? p.Ein : p.Hin) + (int64_t)kk * plane + (int64_t)c * ncell + (int64_t)y * p.nx;
+      const unsigned dst = smem_u32(smem_raw) +
+                           (frame == 0 ? L::OFF_E + ((kk - zb) % NE) * ES + c * CE + r * RE
+                                       : L::OFF_HIN + ((kk - zb) % NH) * HS + c * CH + r * RH);
+      const int* tab = sPiece + frame * 4 * kMaxPieces;
+      const int npc = tab[3 * kMaxPieces];
+      for (int pc = 0; pc < npc; ++pc)
+        plain::bulk_g2s(dst + tab[pc] * SZ, src + tab[kMaxPieces + pc], (unsigned)tab[2 * kMaxPieces + pc] * SZ,
+                        bar);
+    }
+  };
+  if (helper) {
+    for (int g = 0; g < A && g < np; ++g) {
+      if (lane == 0) plain::mbar_arrive_expect_tx(&mbar[g], stage_bytes(g));
+      __syncwarp();
+      issue_stage(g);
+    }
+  }
+
+  // ---- prologue: H^n of plane zb-1 at the own cells (z-difference of the E update at zb);
+  // zb-1 is never inside the CPML (chunk starts are planned that way) ----
+  T hxm[VX], hym[VX];
+#pragma unroll
+  for (int v = 0; v < VX; ++v) hxm[v] = hym[v] = T(0);
+  if (zb > 0 && own) {
+#pragma unroll
+    for (int v = 0; v < VX; ++v) {
+      const int i = i0 + v;
+      const int q = (zb - 1) * plane + j * p.nx + i;
+      const int qj1 = (zb - 1) * plane + ((j + 1) % p.ny) * p.nx + i;
+      const int qi1 = (zb - 1) * plane + j * p.nx + (i + 1) % p.nx;
+      T hx = p.Hin[q], hy = p.Hin[ncell + q];
+      const T dyEz = p.Ein[2 * ncell + qj1] - p.Ein[2 * ncell + q];
+      const T dzEy = p.Ein[ncell + q + plane] - p.Ein[ncell + q];
+      const T dzEx = p.Ein[q + plane] - p.Ein[q];
+      const T dxEz = p.Ein[2 * ncell + qi1] - p.Ein[2 * ncell + q];
+      hx = hx - S * (dyEz - dzEy);
+      hy = hy - S * (dzEx - dxEz);
+      hxm[v] = hx;
+      hym[v] = hy;
+    }
+  }
+
+  T uE = T(0), uP = T(0), uH = T(0);
+  const int pstrE = 2 * p.npml * plane, pstrH = (2 * p.npml + 1) * plane;
+  int g_last = 0;        // the plane of the last wait
+  bool wait_ok = true;   // that wait succeeded
+  auto wait_stage = [&](int g) {
+    g_last = g;
+    wait_ok = plain::mbar_wait(&mbar[g % A], (unsigned)((g / A) & 1));
+    if (!wait_ok) {
+      s_abort = 1;
+      atomicExch(p.err, 1);
+    }
+  };
+  // H^n of plane k at the thread's VX cells from the staged frames (offsets oE / oH / oX: the own
+  // row of a compute warp, the halo row y0-1 for the helper); writes H_x, H_z to the H^n buffer
+  // and returns the cells' E_in(k) and H^n.  PML: the plane lies in the CPML of the H update.
+  auto h_cells = [&](bool PML, bool top, unsigned e0, unsigned e1, unsigned hin, unsigned xb, T bH, T cH,
+                     T* psHx, T* psHy, T* ex0, T* ey0, T* ez0, T* Hx, T* Hy, T* Hz) {
+    VV::ld(at(e0 + oE), ex0);
+    VV::ld(at(e0 + CE + oE), ey0);
+    VV::ld(at(e0 + 2 * CE + oE), ez0);
+    T ex1[VX], ey1[VX], ez1[VX], exj[VX], ezj[VX];
+    if (!top) {
+      VV::ld(at(e1 + oE), ex1);
+      VV::ld(at(e1 + CE + oE), ey1);
+      VV::ld(at(e1 + 2 * CE + oE), ez1);
+    } else {
+#pragma unroll
+      for (int v = 0; v < VX; ++v) ex1[v] = ey1[v] = ez1[v] = T(0);
+    }
+    VV::ld(at(e0 + oE + RE), exj);
+    VV::ld(at(e0 + 2 * CE + oE + RE), ezj);
+    const T eyi = *reinterpret_cast<const T*>(at(e0 + CE + oE + VX * SZ));
+    const T ezi = *reinterpret_cast<const T*>(at(e0 + 2 * CE + oE + VX * SZ));
+    VV::ld(at(hin + oH), Hx);
+    VV::ld(at(hin + CH + oH), Hy);
+    VV::ld(at(hin + 2 * CH + oH), Hz);
+#pragma unroll
+    for (int v = 0; v < VX; ++v) {
+      const T ey_i1 = v + 1 < VX ? ey0[v + 1 < VX ? v + 1 : 0] : eyi;
+      const T ez_i1 = v + 1 < VX ? ez0[v + 1 < VX ? v + 1 : 0] : ezi;
+      plain::h_cell(Hx[v], Hy[v], Hz[v], psHx[v], psHy[v], ezj[v] - ez0[v], ey1[v] - ey0[v], ex1[v] - ex0[v],
+                    ez_i1 - ez0[v], ey_i1 - ey0[v], exj[v] - ex0[v], PML, bH, cH, S);
+    }
+    VV::st(at(xb + oX), Hx);
+    VV::st(at(xb + CX + oX), Hz);
+  };
+
+  if (helper) {
+    // ======== helper warp: the halo row y0-1 of H^n, the staging of the planes ahead, and its part
+    // in the barriers of the compute warps' reductions ========
+    const int gxy = wrap(y0 - 1, p.ny) * p.nx + i0 % p.nx;   // grid column of the halo-row cells
+    for (int g = 0; g < np; ++g) {
+      const int k = zb + g;
+      const int info = sInfo[g];
+      const bool top = (info & kTop) != 0, pmlH = (info & kPmlH) != 0;
+      const int ipH = k < p.npml ? k : k - p.nz + 1 + 2 * p.npml;
+      const unsigned e0 = L::OFF_E + (g % NE) * ES, e1 = L::OFF_E + ((g + 1) % NE) * ES;
+      const unsigned hin = L::OFF_HIN + (g % NH) * HS, xb = L::OFF_SH + (g & 1) * XS;
+      double* red = reinterpret_cast<double*>(at(L::OFF_SH + ((g + 1) & 1) * XS));
+      T psHx[VX], psHy[VX], ex0[VX], ey0[VX], ez0[VX], Hx[VX], Hy[VX], Hz[VX];
+#pragma unroll
+      for (int v = 0; v < VX; ++v) psHx[v] = psHy[v] = T(0);
+      if (pmlH) {
+        VV::ld(p.psiHin + ipH * plane + gxy, psHx);
+        VV::ld(p.psiHin + pstrH + ipH * plane + gxy, psHy);
+      }
+      wait_stage(g);
+      if (pmlH)
+        h_cells(true, top, e0, e1, hin, xb, p.pmlH[2 * k], p.pmlH[2 * k + 1], psHx, psHy, ex0, ey0, ez0, Hx, Hy, Hz);
+      else
+        h_cells(false, top, e0, e1, hin, xb, T(1), T(0), psHx, psHy, ex0, ey0, ez0, Hx, Hy, Hz);
+      // arm the mbarrier of stage g+A (the one of stage g) before the barrier, once stage g's phase
+      // has completed: the new phase cannot complete before its copies, issued after the barrier
+      if (lane == 0 && wait_ok && g + A < np) plain::mbar_arrive_expect_tx(&mbar[g % A], stage_bytes(g + A));
+      __syncthreads();   // H^n(k) of the tile and its halo complete; E_in(k), H_in(k) slots free
+      if (s_abort) break;
+      if (g + A < np) {
+        __syncwarp();
+        issue_stage(g + A);
+      }
+      if (info & (kMonH | kMonE)) {
+        for (int m = 0; m < p.nmon; ++m) {
+          const int zm = p.mon_z[m];
+          if ((info & kMonH) && (k == zm - 1 || k == zm)) {
+            double v2[2] = {0.0, 0.0};
+            block_slot_sums<TY, VX>(v2, red, w, lane);
+            __syncthreads();
+          }
+        }
+        for (int m = 0; m < p.nmon; ++m)
+          if ((info & kMonE) && k == p.mon_z[m]) {
+            double v2[2] = {0.0, 0.0};
+            block_slot_sums<TY, VX>(v2, red, w, lane);
+            __syncthreads();
+          }
+      }
+    }
+  } else {
+    // ======== compute warps: plane k of the own row.  GEN = false is a plain vacuum plane (no
+    // layer, CPML, source, monitor or energy box, not the top plane) ========
+    auto body = [&](auto gen_t, int g, int info) -> bool {
+      constexpr bool GEN = decltype(gen_t)::value;
+      const int k = zb + g;
+      const int mi = GEN ? (info & 0xF) - 1 : -1;
+      const bool in_box = GEN && (info & kBox) != 0;
+      const bool top = GEN && (info & kTop) != 0;
+      const bool pmlE = GEN && (info & kPmlE) != 0, pmlH = GEN && (info & kPmlH) != 0;
+      const int ipE = k < p.npml ? k : k - p.nz + 2 * p.npml;
+      const int ipH = k < p.npml ? k : k - p.nz + 1 + 2 * p.npml;
+      const unsigned e0 = L::OFF_E + (g % NE) * ES, e1 = L::OFF_E + ((g + 1) % NE) * ES;
+      const unsigned hin = L::OFF_HIN + (g % NH) * HS, xb = L::OFF_SH + (g & 1) * XS;
+      double* red = reinterpret_cast<double*>(at(L::OFF_SH + ((g + 1) & 1) * XS));   // the other H^n buffer
+      T psHx[VX], psHy[VX];
+#pragma unroll
+      for (int v = 0; v < VX; ++v) psHx[v] = psHy[v] = T(0);
+      if (pmlH && own) {
+        VV::ld(p.psiHin + ipH * plane + qxy, psHx);
+        VV::ld(p.psiHin + pstrH + ipH * plane + qxy, psHy);
+      }
+      wait_stage(g);
+
+      // ---- H^n of plane k at the own cells ----
+      T ex0[VX], ey0[VX], ez0[VX], Hx[VX], Hy[VX], Hz[VX];
+      const T bH = pmlH ? p.pmlH[2 * k] : T(1), cH = pmlH ? p.pmlH[2 * k + 1] : T(0);
+      if (pmlH)
+        h_cells(true, top, e0, e1, hin, xb, bH, cH, psHx, psHy, ex0, ey0, ez0, Hx, Hy, Hz);
+      else
+        h_cells(false, top, e0, e1, hin, xb, bH, cH, psHx, psHy, ex0, ey0, ez0, Hx, Hy, Hz);
+      if (own) {
+        const int q = k * plane + qxy;
+        VV::st(p.Hout + q, Hx);
+        VV::st(p.Hout + ncell + q, Hy);
+        VV::st(p.Hout + 2 * ncell + q, Hz);
+        if (pmlH) {
+          VV::st(p.psiHout + ipH * plane + qxy, psHx);
+          VV::st(p.psiHout + pstrH + ipH * plane + qxy, psHy);
+        }
+      }
+      // ---- H_y, H_z at x-1 of the thread's first cell: from the lane to the left, or on lane 0
+      // recomputed for the halo cell x0-1 of this row ----
+      T hyx0 = __shfl_up_sync(0xffffffffu, Hy[VX - 1], 1), hzx0 = __shfl_up_sync(0xffffffffu, Hz[VX - 1], 1);
+      if (lane == 0) {
+        const unsigned fe = (unsigned)((w + 1) * FX + 3) * SZ, fh = (unsigned)((w + 1) * HX + 3) * SZ;
+        auto ldf = [&](unsigned off) { return *reinterpret_cast<const T*>(at(off)); };
+        const T ax = ldf(e0 + fe), ay = ldf(e0 + CE + fe), az = ldf(e0 + 2 * CE + fe);
+        const T bx = top ? T(0) : ldf(e1 + fe), by = top ? T(0) : ldf(e1 + CE + fe);
+        const T jx = ldf(e0 + fe + RE), jz = ldf(e0 + 2 * CE + fe + RE);
+        T hx = ldf(hin + fh), hy = ldf(hin + CH + fh), hz = ldf(hin + 2 * CH + fh);
+        T qx = T(0), qy = T(0);
+        if (pmlH) {
+          const int gq = wrap(j, p.ny) * p.nx + wrap(x0 - 1, p.nx);
+          qx = p.psiHin[ipH * plane + gq];
+          qy = p.psiHin[pstrH + ipH * plane + gq];
+        }
+        // the cell's x+1 neighbour is this lane's first cell (ey0[0], ez0[0])
+        plain::h_cell(hx, hy, hz, qx, qy, jz - az, by - ay, bx - ax, ez0[0] - az, ey0[0] - ay, jx - ax, pmlH, bH,
+                      cH, S);
+        hyx0 = hy;
+        hzx0 = hz;
+      }
+      __syncthreads();   // H^n(k) of the tile and its halo complete; E_in(k), H_in(k) slots free
+      if (s_abort) return false;
+
+      // ---- E-side CPML memories ----
+      T psEx[VX], psEy[VX];
+#pragma unroll
+      for (int v = 0; v < VX; ++v) psEx[v] = psEy[v] = T(0);
+      if (pmlE && own) {
+        VV::ld(p.psiE + ipE * plane + qxy, psEx);
+        VV::ld(p.psiE + pstrE + ipE * plane + qxy, psEy);
+      }
+      // ---- H-side monitor partials (planes zm-1 and zm) and the H energy ----
+      if (GEN && (info & kMonH)) {
+        for (int m = 0; m < p.nmon; ++m) {
+          const int zm = p.mon_z[m];
+          if (k != zm - 1 && k != zm) continue;
+          const int off = (k == zm) ? 1 : 0;
+          double v2[2] = {0.0, 0.0};
+          if (own)
+#pragma unroll
+            for (int v = 0; v < VX; ++v) {
+              v2[0] += (double)Hx[v];
+              v2[1] += (double)Hy[v];
+            }
+          block_slot_sums<TY, VX>(v2, red, w, lane);
+          if (tid < 2 * VX && p.mon_partial_H) {
+            const int qn = tid / VX, h = tid - qn * VX;
+            if (blockIdx.x * VX + h < nbx32)
+              p.mon_partial_H[(int64_t)(4 * m + 2 * qn + off) * p.nbxy + slot_row * nbx32 + blockIdx.x * VX + h] =
+                  slot_total<TY, VX>(red, qn, h);
+          }
+          __syncthreads();   // red read before it is rewritten
+        }
+      }
+      if (GEN && p.eH_on && own && in_box) {
+#pragma unroll
+        for (int v = 0; v < VX; ++v) uH += Hx[v] * Hx[v] + Hy[v] * Hy[v] + Hz[v] * Hz[v];
+      }
+
+      // ---- D/E (Eq. 1a) and P (Eq. Pz_1D_Lorentz) of plane k at the own cells, one component at
+      // a time (the material state of a component is loaded, used and stored before the next) ----
+      double monE[2] = {0.0, 0.0};   // sums of E_x and E_y over the thread's cells (E monitors)
+      if (own) {
+        T hxy[VX], hzy[VX];   // H_x, H_z at y-1
+        VV::ld(at(xb + oX - RX), hxy);
+        VV::ld(at(xb + CX + oX - RX), hzy);
+        const T bE = pmlE ? p.pmlE[2 * k] : T(1), cE_ = pmlE ? p.pmlE[2 * k + 1] : T(0);
+        const int q = k * plane + qxy;
+        const MatK<T>* M = mi >= 0 ? &p.mat[mi] : nullptr;
+        const int r = mi >= 0 ? (int)M->base + (k - M->zlo) * plane + qxy : 0;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          // the curl differences of component c (Eq. FDTD-1D form, CPML memory on the z term)
+          T curl[VX];
+#pragma unroll
+          for (int v = 0; v < VX; ++v) {
+            if (c == 0) {
+              const T dyHz = Hz[v] - hzy[v];
+              const T dzHy = Hy[v] - hym[v];
+              if (pmlE) {
+                psEx[v] = bE * psEx[v] + cE_ * dzHy;
+                curl[v] = dyHz - (dzHy + psEx[v]);
+              } else {
+                curl[v] = dyHz - dzHy;
+              }
+            } else if (c == 1) {
+              const T dzHx = Hx[v] - hxm[v];
+              const T dxHz = Hz[v] - (v > 0 ? Hz[v > 0 ? v - 1 : 0] : hzx0);
+              if (pmlE) {
+                psEy[v] = bE * psEy[v] + cE_ * dzHx;
+                curl[v] = (dzHx + psEy[v]) - dxHz;
+              } else {
+                curl[v] = dzHx - dxHz;
+              }
+            } else {
+              const T dxHy = Hy[v] - (v > 0 ? Hy[v > 0 ? v - 1 : 0] : hyx0);
+              const T dyHx = Hx[v] - hxy[v];
+              curl[v] = dxHy - dyHx;
+            }
+          }
+          const T* e0c = c == 0 ? ex0 : (c == 1 ? ey0 : ez0);
+          T Ec[VX];
+          if (mi < 0) {
+            // outside the layers, with the soft sources of this plane on component c (the host runs
+            // this kernel only for simulations whose source planes all lie outside the layers)
+            T J[VX];
+            bool hasJ = false;
+#pragma unroll
+            for (int v = 0; v < VX; ++v) J[v] = T(0);
+            if (GEN && (info & kSrc)) {
+              for (int s = 0; s < p.nsrc; ++s) {
+                if (p.src_z[s] != k || p.src_comp[s] != c) continue;
+                hasJ = true;
+                if (p.src_cos[s]) {
+                  T cs[VX], sn[VX];
+                  VV::ld(p.src_cos[s] + qxy, cs);
+                  VV::ld(p.src_sin[s] + qxy, sn);
+#pragma unroll
+                  for (int v = 0; v < VX; ++v) J[v] += p.src_a[s] * cs[v] + p.src_b[s] * sn[v];
+                } else {
+#pragma unroll
+                  for (int v = 0; v < VX; ++v) J[v] += p.src_a[s];
+                }
+              }
+            }
+#pragma unroll
+            for (int v = 0; v < VX; ++v) {
+              T e = e0c[v] + S * curl[v];
+              if (hasJ) e = e + dt * J[v];
+              Ec[v] = e;
+            }
+            if (GEN && p.eE_on && in_box)
+#pragma unroll
+              for (int v = 0; v < VX; ++v) uE += Ec[v] * Ec[v];
+          } else {
+            T Pa[VX], Pb[VX], D[VX];
+            VV::ld(p.Pa + c * nmc + r, Pa);
+            VV::ld(p.Pb + c * nmc + r, Pb);
+            if (!INC) VV::ld(p.D + c * nmc + r, D);
+#pragma unroll
+            for (int v = 0; v < VX; ++v) {
+              if (!INC) {
+                // D^{n+1/2} = D^{n-1/2} + S [curl differences];  E = (1/eps_inf)(D - P^{n+1/2})
+                D[v] = D[v] + S * curl[v];
+                Ec[v] = M->inv_eps * (D[v] - Pa[v]);
+              } else {
+                // D-free: E += (dt curl H - (P^{n+1/2} - P^{n-1/2})) / eps_inf
+                Ec[v] = e0c[v] + (S * curl[v] - (Pa[v] - Pb[v])) * M->inv_eps;
+              }
+            }
+            if (!INC) VV::st(p.D + c * nmc + r, D);
+            if (M->kind != kVacuum) {
+              // Eq. Pz_1D_Lorentz (Drude: w0^2 dropped from the restoring term); the new level
+              // overwrites P^{n-1}
+              T Pn[VX];
+#pragma unroll
+              for (int v = 0; v < VX; ++v) {
+                T Vn;
+                if (!INC) {
+                  const T num = M->cE * Ec[v] - M->c1m * Pa[v] - M->c2 * Pb[v];
+                  Pn[v] = M->inv_A * num;
+                  Vn = Pn[v] - Pa[v];
+                } else {
+                  const T V0 = Pa[v] - Pb[v];
+                  const T num = M->cE * Ec[v] - M->W * Pa[v] + M->c2 * V0;
+                  Vn = num * M->inv_A;
+                  Pn[v] = Pa[v] + Vn;
+                }
+                if (p.eE_on && in_box) uP += M->rho_idt2 * (Vn * Vn + M->w0r2dt2 * Pn[v] * Pn[v]);
+              }
+              VV::st(p.Pb + c * nmc + r, Pn);
+            }
+            if (p.eE_on && in_box)
+#pragma unroll
+              for (int v = 0; v < VX; ++v) uE += M->eps * (Ec[v] * Ec[v]);
+          }
+          VV::st(p.Eout + c * ncell + q, Ec);
+          if (GEN && c < 2)
+#pragma unroll
+            for (int v = 0; v < VX; ++v) monE[c] += (double)Ec[v];
+        }
+        if (pmlE) {
+          VV::st(p.psiE + ipE * plane + qxy, psEx);
+          VV::st(p.psiE + pstrE + ipE * plane + qxy, psEy);
+        }
+      }
+      // ---- E-side monitor partials ----
+      if (GEN && (info & kMonE)) {
+        for (int m = 0; m < p.nmon; ++m) {
+          if (k != p.mon_z[m]) continue;
+          double v2[2] = {monE[0], monE[1]};
+          block_slot_sums<TY, VX>(v2, red, w, lane);
+          if (tid < 2 * VX && p.mon_partial_E) {
+            const int qn = tid / VX, h = tid - qn * VX;
+            if (blockIdx.x * VX + h < nbx32)
+              p.mon_partial_E[(int64_t)(2 * m + qn) * p.nbxy + slot_row * nbx32 + blockIdx.x * VX + h] =
+                  slot_total<TY, VX>(red, qn, h);
+          }
+          __syncthreads();   // red read before it is rewritten
+        }
+      }
+      // ---- H^n(k) of the own cells: the next plane's z-difference ----
+#pragma unroll
+      for (int v = 0; v < VX; ++v) {
+        hxm[v] = Hx[v];
+        hym[v] = Hy[v];
+      }
+      return true;
+    };
+    for (int g = 0; g < np; ++g) {
+      const int info = sInfo[g];
+      const bool ok = info == 0 ? body(std::false_type{}, g, info) : body(std::true_type{}, g, info);
+      if (!ok) break;
+    }
+  }
+  // after an abort: when the helper's own wait ran out, a bounded wait for that stage and the
+  // stages issued after it, so that no copy is in flight into this CTA's shared memory when it
+  // exits (a stage armed but not issued has no copies)
+  if (s_abort && helper && lane == 0) {
+    for (int g = wait_ok ? g_last + 1 : g_last; g < np && g < g_last + A; ++g)
+      plain::mbar_wait(&mbar[g % A], (unsigned)((g / A) & 1));
+  }
+  // ---- energy partials of this block, one per 32 x 8 slot (zero outside the box) ----
+  if (p.eE_on || p.eH_on) {
+    __syncthreads();
+    double* red = reinterpret_cast<double*>(at(L::OFF_SH));
+    T u4[4] = {uE, uP, T(0), uH};
+    block_slot_sums<TY, VX>(u4, red, w, lane);
+    if (tid < 4 * VX) {
+      const int qn = tid / VX, h = tid - qn * VX;
+      const int64_t slot = (int64_t)chunk * p.nbxy + slot_row * nbx32 + blockIdx.x * VX + h;
+      if (blockIdx.x * VX + h < nbx32) {
+        const double s = slot_total<TY, VX>(red, qn, h);
+        if (qn < 3 && p.eE_on) p.en_partial_E[(int64_t)qn * p.nbxy * p.nchunks_total + slot] = s;
+        if (qn == 3 && p.eH_on) p.en_partial_H[slot] = s;
+      }
+    }
+  }
+}
+
+}  // namespace fdtdbath

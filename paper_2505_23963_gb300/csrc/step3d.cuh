@@ -131,7 +131,6 @@ __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_gr
 constexpr int kAheadE = 4;
 constexpr int kRingE = 6;   // E frames: k-1 (still read by the E update of k-1), k .. k+kAheadE
 constexpr int kRingH = 4;   // H frames: k .. k+kAheadE-1
-constexpr int kMaxChunk = 128;   // planes per z-chunk (the per-plane table in shared memory)
 
 // plane-info bits of the per-chunk table
 enum : int { kPlaneMat = 0xF, kPlaneEbox = 0x10, kPlaneMonE = 0x20, kPlaneMonH = 0x40, kPlaneSrc = 0x80 };
