@@ -201,7 +201,9 @@ int fdtdbath_bath_form(int32_t shape, double frequency, double gamma, int32_t nu
  * live components are bit-identical to the general form's.  A write_fields call on any of those
  * components returns the simulation to the general form for good.  Key 6: whether the last
  * fdtdbath_adjoint_backward ran the TE form of the reverse sweep (a TE forward run and dL_dF zero
- * for the E_x and H_y spectra). */
+ * for the E_x and H_y spectra).  Key 7: whether the z-chunks without bath modes run the
+ * plain-plane kernel (grids of at least 8 rows tiled exactly by its 128 x 8 FP32 or 64 x 8 FP64
+ * tiles, ny a multiple of 8, no source plane inside a layer) instead of the general kernel. */
 int64_t fdtdbath_query(const fdtdbath_sim *sim, int32_t key);
 
 /* Energy (U_EM, U_P, U_bath) of planes z_lo <= k < z_hi of the current state -- the same

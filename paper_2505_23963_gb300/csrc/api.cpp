@@ -6,6 +6,7 @@
 // kernel and drives it: one launch per step, the H half-step of step n folded into the
 // launch of step n+1 (an "H pending" flag carries it across calls), and a fixed-order
 // reduction of the monitor / energy partial sums every few hundred steps.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -134,7 +135,11 @@ struct fdtdbath_sim {
   // plain-plane kernel (plain3d.cuh) for the chunks without bath planes: grids of at least 8 rows,
   // nx a multiple of 4, every source plane outside the layers; planes staged ahead by it
   bool plain_ok = false;
-  int plain_minb = 0;       // FP32 tile / pipeline variant of the plain-plane kernel
+  PlainMaps maps{};         // its tensor maps of the E and H arrays
+  // the bath-free and bath launches of a step one after the other on the simulation's stream (with
+  // the plain-plane kernel: its CTAs and the bath kernel's lose more to sharing SMs than they gain
+  // from overlapping), or concurrently on two streams (with the general kernel's bath-free form)
+  bool serial_pair = false;
   void* errflag = nullptr;  // device int: a bounded wait of a kernel ran out (FDTDBATH_ERR_TIMEOUT)
   AdjState adj;
   std::string err;
@@ -271,6 +276,42 @@ void source_amp(const HostSrc& q, double t, double* a, double* b) {
   }
 }
 
+// Tensor maps of the plain-plane kernel (PlainMaps): the E and H blocks as 5-D tensors (x, y, z,
+// component, buffer), boxes of the tile's rows, one row and the 4-cell side columns.  The encoder
+// is the driver's cuTensorMapEncodeTiled, looked up through the runtime; false when unavailable.
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+bool encode_plain_maps(fdtdbath_sim* s) {
+  static EncodeTiledFn fn = nullptr;
+  static bool looked_up = false;
+  if (!looked_up) {
+    looked_up = true;
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (EncodeTiledFn)f;
+  }
+  if (!fn) return false;
+  const cuuint64_t esz = s->esz;
+  const cuuint64_t dims[5] = {(cuuint64_t)s->nx, (cuuint64_t)s->ny, (cuuint64_t)s->nz, 3, 2};
+  const cuuint64_t strides[4] = {(cuuint64_t)s->nx * esz, (cuuint64_t)s->plane * esz, (cuuint64_t)s->ncell * esz,
+                                 3 * (cuuint64_t)s->ncell * esz};
+  const cuuint32_t es[5] = {1, 1, 1, 1, 1};
+  const cuuint32_t tx = (cuuint32_t)plain_tile_x(s->prec);
+  const CUtensorMapDataType dt = s->prec == 64 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+  auto enc = [&](CUtensorMap* m, void* base, cuuint32_t bx, cuuint32_t by) {
+    const cuuint32_t box[5] = {bx, by, 1, 3, 1};
+    return fn(m, dt, 5, base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+  };
+  return enc(&s->maps.e_main, s->E[0], tx, 8) && enc(&s->maps.e_row, s->E[0], tx, 1) &&
+         enc(&s->maps.e_pad8, s->E[0], 4, 8) && enc(&s->maps.e_pad1, s->E[0], 4, 1) &&
+         enc(&s->maps.h_main, s->H[0], tx, 8) && enc(&s->maps.h_row, s->H[0], tx, 1) &&
+         enc(&s->maps.h_pad8, s->H[0], 4, 8);
+}
+
 template <typename T>
 Step3DParams<T> make_params(fdtdbath_sim* s, int doH, int doE) {
   Step3DParams<T> p{};
@@ -358,11 +399,11 @@ int launch_chunks(fdtdbath_sim* s, Step3DParams<T> p, int nbmax, int id_off, int
   return launch_typed(p, nbmax, s->ty, s->nbx, s->nby, n, s->ybf, s->te && s->ty == 1, st);
 }
 
-int launch_plain_typed(const Step3DParams<float>& p, int n, int minb, cudaStream_t st) {
-  return launch_plain3d_f32(p, n, minb, st);
+int launch_plain_typed(const Step3DParams<float>& p, const fdtdbath_sim* s, int n, cudaStream_t st) {
+  return launch_plain3d_f32(p, s->maps, s->ecur, s->hcur, n, st);
 }
-int launch_plain_typed(const Step3DParams<double>& p, int n, int minb, cudaStream_t st) {
-  return launch_plain3d_f64(p, n, minb, st);
+int launch_plain_typed(const Step3DParams<double>& p, const fdtdbath_sim* s, int n, cudaStream_t st) {
+  return launch_plain3d_f64(p, s->maps, s->ecur, s->hcur, n, st);
 }
 
 // Chunks without bath planes: the plain-plane kernel when it applies (both half-steps of a step),
@@ -372,7 +413,7 @@ int launch_plain_chunks(fdtdbath_sim* s, Step3DParams<T> p, int id_off, int n, c
   if (!(s->plain_ok && p.doH && p.doE)) return launch_chunks<T>(s, p, 0, id_off, n, st);
   p.chunk_ids = (const int*)s->chunk_ids + id_off;
   s->launches++;
-  return launch_plain_typed(p, n, s->plain_minb, st);
+  return launch_plain_typed(p, s, n, st);
 }
 
 // One step's launches: without a pending E half-step, or without bath chunks, one launch over
@@ -386,6 +427,10 @@ int launch_all(fdtdbath_sim* s, int doH, int doE) {
   if (s->nbmax == 0) return launch_plain_chunks<T>(s, p, 0, s->nchunks, s->stream);
   if (s->nbath == 0) return launch_chunks<T>(s, p, s->nbmax, 0, s->nchunks, s->stream);
   if (s->nplain == 0) return launch_chunks<T>(s, p, s->nbmax, s->nchunks, s->nbath, s->stream);
+  if (s->serial_pair) {
+    const int rc = launch_plain_chunks<T>(s, p, s->nchunks, s->nplain, s->stream);
+    return rc ? rc : launch_chunks<T>(s, p, s->nbmax, s->nchunks + s->nplain, s->nbath, s->stream);
+  }
   cudaError_t e = cudaEventRecord(s->ev_fork, s->stream);
   if (e == cudaSuccess) e = cudaStreamWaitEvent(s->side, s->ev_fork, 0);
   if (e != cudaSuccess) return (int)e;
@@ -872,14 +917,14 @@ int fdtdbath_create(const fdtdbath_grid* grid, double resolution, double courant
     zc = std::min(64, std::max(1, std::atoi(e)));
     balanced = false;
   }
-  // the plain-plane kernel may take the chunks without bath planes (plain3d.cuh: at least 8 rows, nx
-  // a multiple of 4 for its 16-byte vectors and bulk copies and at least 16, source planes outside
-  // the layers; FDTDBATH_PLAIN=1 selects it); those ranges are then cut into near-equal chunks of
-  // about plain_zc planes (FDTDBATH_PLAIN_ZCHUNK)
-  s->plain_ok = s->ty == 8 && nx % 4 == 0 && nx >= 16;
+  // the plain-plane kernel takes the chunks without bath planes (plain3d.cuh) on grids tiled exactly
+  // by its (TX x 8) tiles whose source planes lie outside the layers, when the tensor maps can be
+  // encoded (FDTDBATH_PLAIN=0 keeps the general kernel); those ranges are then cut into near-equal
+  // chunks of about plain_zc planes (FDTDBATH_PLAIN_ZCHUNK, at most 64)
   {
-    const char* e = std::getenv("FDTDBATH_PLAIN");   // off unless FDTDBATH_PLAIN=1
-    s->plain_ok = s->plain_ok && e && std::atoi(e) != 0;
+    const int tx = plain_tile_x(s->prec);
+    const char* e = std::getenv("FDTDBATH_PLAIN");
+    s->plain_ok = !(e && std::atoi(e) == 0) && s->ty == 8 && nx % tx == 0 && ny % 8 == 0;
   }
   for (auto& q : s->srcs)
     for (auto& m : s->mats)
@@ -888,7 +933,6 @@ int fdtdbath_create(const fdtdbath_grid* grid, double resolution, double courant
   if (s->plain_ok) {
     plain_zc = 16;
     if (const char* e = std::getenv("FDTDBATH_PLAIN_ZCHUNK")) plain_zc = std::min(64, std::max(1, std::atoi(e)));
-    if (const char* e = std::getenv("FDTDBATH_PLAIN_SHAPE")) s->plain_minb = std::atoi(e);
   }
   std::vector<int> starts;
   if (balanced) {
@@ -927,15 +971,21 @@ int fdtdbath_create(const fdtdbath_grid* grid, double resolution, double courant
 
   // ---- device state ----
   const size_t esz = s->esz;
+  // E and H: one allocation of two buffers each (the tensor maps of the plain-plane kernel span both)
+  s->E[0] = dalloc(s, 2 * 3 * s->ncell * esz);
+  s->H[0] = dalloc(s, 2 * 3 * s->ncell * esz);
+  if (!s->E[0] || !s->H[0]) return bail(FDTDBATH_ERR_OOM, "device allocation failed");
+  s->E[1] = (char*)s->E[0] + 3 * s->ncell * esz;
+  s->H[1] = (char*)s->H[0] + 3 * s->ncell * esz;
   for (int b = 0; b < 2; ++b) {
-    s->E[b] = dalloc(s, 3 * s->ncell * esz);
-    s->H[b] = dalloc(s, 3 * s->ncell * esz);
     s->psiH[b] = dalloc(s, 2 * (size_t)(2 * s->npml + 1) * s->plane * esz);
     s->Pslot[b] = dalloc(s, 3 * (size_t)s->nmatcell * esz);
     s->Yslot[b] = dalloc(s, s->ybf ? (b == 0 ? (size_t)s->nybath * 4 : 16) : (size_t)s->nybath * s->yesz);
-    if (!s->E[b] || !s->H[b] || !s->psiH[b] || !s->Pslot[b] || !s->Yslot[b])
+    if (!s->psiH[b] || !s->Pslot[b] || !s->Yslot[b])
       return bail(FDTDBATH_ERR_OOM, "device allocation failed");
   }
+  if (s->plain_ok && !encode_plain_maps(s)) s->plain_ok = false;   // no tensor-map encoder: general kernel
+  s->serial_pair = s->plain_ok;
   s->psiE = dalloc(s, 2 * (size_t)(2 * s->npml) * s->plane * esz);
   s->pmlE = dalloc(s, 2 * (size_t)nz * esz);
   s->pmlH = dalloc(s, 2 * (size_t)nz * esz);
@@ -1328,6 +1378,7 @@ int64_t fdtdbath_query(const fdtdbath_sim* s, int32_t key) {
     case 4: return s->nchunks;
     case 5: return s->te && s->ty == 1 ? 1 : 0;
     case 6: return s->adj_te ? 1 : 0;
+    case 7: return s->plain_ok ? 1 : 0;
     default: return -1;
   }
 }

@@ -14,6 +14,8 @@
 //                 reduced in a fixed order by reduce.cu.
 #pragma once
 
+#include <cuda.h>
+
 #include <cstdint>
 
 namespace fdtdbath {
@@ -151,11 +153,21 @@ int launch_step3d_f32(const Step3DParams<float>& p, int nbmax, int ty, int nbx, 
                       int nchunks, int bath_bf16, int te, void* stream);
 int launch_step3d_f64(const Step3DParams<double>& p, int nbmax, int ty, int nbx, int nby,
                       int nchunks, int te, void* stream);
-// The plain-plane step (plain3d.cuh): chunks without bath modes, grids of at least 8 rows with nx a
-// multiple of 4 and at least 16, chunks of at most 64 planes, H and E half-steps together; shape:
-// the FP32 tile / pipeline variant (see plain3d_f32.cu).
-int launch_plain3d_f32(const Step3DParams<float>& p, int nchunks, int shape, void* stream);
-int launch_plain3d_f64(const Step3DParams<double>& p, int nchunks, int shape, void* stream);
+// The plain-plane step (plain3d.cuh): chunks without bath modes of at most 64 planes, grids tiled
+// exactly by its (32 VX) x 8 tiles, H and E half-steps together.  Its frames are staged by tensor
+// copies described by these maps: the E and H arrays, each one allocation of two buffers, as 5-D
+// tensors (x, y, z, component, buffer); boxes of (x, y) extent the tile's rows (TX x 8), one row
+// (TX x 1) and the 4-cell side columns (4 x 8, 4 x 1), all three components at once.
+struct PlainMaps {
+  CUtensorMap e_main, e_row, e_pad8, e_pad1;
+  CUtensorMap h_main, h_row, h_pad8;
+};
+// tile width: four FP32 or two FP64 cells per thread (16-byte vectors), 32 threads per row
+constexpr int plain_tile_x(int prec) { return prec == 64 ? 64 : 128; }
+int launch_plain3d_f32(const Step3DParams<float>& p, const PlainMaps& maps, int ebuf, int hbuf, int nchunks,
+                       void* stream);
+int launch_plain3d_f64(const Step3DParams<double>& p, const PlainMaps& maps, int ebuf, int hbuf, int nchunks,
+                       void* stream);
 
 // ---- discrete adjoint (adjoint.cu) ----
 // One reverse step of the exact transpose of the forward step (D-free form), applied to the

@@ -1,25 +1,28 @@
 // plain3d.cuh -- the fused step of the z-planes without bath modes (vacuum, CPML, Lorentz and
-// Drude layers), general 3D form on grids of at least 8 rows.
+// Drude layers), general 3D form on grids tiled exactly by its tiles.
 //
 // It computes what step3d_kernel<T, INC, 0, 8> computes for such planes -- the H half-step of
 // the previous step (H^n from E^{n-1/2}, Eq. 1b, with the CPML memories of the z-derivative
 // terms), this step's D/E half-step (Eq. 1a, D = E + P, soft plane sources) and the Lorentz /
 // Drude polarization update (Eq. Pz_1D_Lorentz, one P per component) -- with the same
-// expressions in the same order, so that FP64 runs (compiled without FMA contraction) agree bit
-// for bit with it.  It exists because the general kernel, one cell per thread with ~1000
-// per-thread 16-byte copies and two barriers per plane, spends ~130 integer instructions per cell
-// and plane and is issue-bound at half of the memory bandwidth on these planes.  Here:
+// expressions in the same order, so that FP64 runs (compiled without FMA contraction) agree with
+// it to rounding of the partial sums.  It exists because the general kernel, one cell per thread
+// with ~1000 per-thread 16-byte copies and two barriers per plane, spends ~130 integer
+// instructions per cell and plane and runs these planes at half of the memory bandwidth.  Here:
 //
-//   * a CTA owns a (32 VX) x TY column tile and marches along a z-chunk; compute warp w owns row
-//     y0 + w, lane l the VX = 16 / sizeof(T) adjacent cells x0 + VX l ..., so every shared-memory
-//     and global access of a thread is one 16-byte vector and the per-plane bookkeeping is paid
-//     once per VX cells; plain vacuum planes run a code path without the CPML, layer, source and
-//     monitor branches;
-//   * one more warp (the helper) stages the planes ahead: the E_in frame (the tile and one cell of
-//     halo on each side, padded to 16-byte boundaries) and the H_in frame (the tile and its -x / -y
-//     halo) by the bulk-copy engine (cp.async.bulk, one copy per frame row and periodic piece),
-//     A planes ahead, completing on one mbarrier per stage in flight (waits bounded in time); it
-//     also recomputes H^n on the halo row y0-1, so the compute warps carry equal work;
+//   * a CTA owns a TX x 8 column tile (TX = 32 VX) and marches along a z-chunk; compute warp w owns
+//     row y0 + w, lane l the VX = 16 / sizeof(T) adjacent cells x0 + VX l ..., so every
+//     shared-memory and global access of a thread is one 16-byte vector and the per-plane
+//     bookkeeping is paid once per VX cells; plain vacuum planes run a code path without the
+//     CPML, layer, source and monitor branches;
+//   * one more warp (the helper) stages the planes ahead with the tensor-copy engine
+//     (cp.async.bulk.tensor, 5-D maps of the E / H double buffers): per stage ten boxes -- the
+//     tile's rows, the rows y0-1 and y0+8 and the 4-cell side columns of E_in(k+1), the tile's rows,
+//     row y0-1 and left column of H_in(k) -- each into a box-dense part of the frame, so that the
+//     periodic neighbours are plain boxes at wrapped coordinates; stages complete on one mbarrier
+//     each (waits bounded in time).  Many small row copies instead (one per frame row) saturated
+//     the copy engine at about half of the bandwidth.  The helper also recomputes H^n on the halo
+//     row y0-1, so the eight compute warps carry equal work;
 //   * the halo cell x0-1 of each row is recomputed by lane 0 of the row's warp; x-neighbours of H^n
 //     pass between lanes by shuffles, y-neighbours (H_x, H_z only) through shared memory;
 //   * one CTA barrier per plane: H^n of plane k goes to one of two shared buffers, so the E update
@@ -31,6 +34,7 @@
 // (E_in(k-A), H_in(k-A)) have been read for the last time.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -43,7 +47,6 @@ namespace fdtdbath {
 namespace plain {
 
 constexpr int TY = 8;                          // rows of a tile = compute warps (one more: the helper)
-constexpr int kMaxPieces = 12;                 // periodic pieces of one frame row (nx >= 16)
 constexpr int kMaxPlanes = 64;                 // planes per z-chunk of this kernel
 constexpr uint64_t kWaitLimitNs = 1000000000;  // a stage not complete after 1 s is an error
 // per-plane table bits (material index + 1 in the low four bits)
@@ -82,12 +85,14 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* b, unsigned parity) {
     if (global_ns() - t0 > kWaitLimitNs) return false;
   }
 }
-// Bulk copy global -> this CTA's shared memory (shared-space address sdst), completing `bytes` on
-// mbarrier b.  Both addresses and the size are multiples of 16 bytes.
-__device__ __forceinline__ void bulk_g2s(unsigned sdst, const void* gsrc, unsigned bytes, uint64_t* b) {
+// Tensor copy global -> this CTA's shared memory (shared-space address sdst, 128-byte aligned) of
+// the box of tensor map tmap at coordinates (x, y, z, c, b), completing its bytes on mbarrier bar.
+__device__ __forceinline__ void tma_load5(unsigned sdst, const void* tmap, int x, int y, int z, int c, int b,
+                                          uint64_t* bar) {
   asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(sdst),
-      "l"(gsrc), "r"(bytes), "r"(smem_u32(b))
+      "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5, "
+      "%6}], [%7];\n" ::"r"(sdst),
+      "l"(reinterpret_cast<uint64_t>(tmap)), "r"(x), "r"(y), "r"(z), "r"(c), "r"(b), "r"(smem_u32(bar))
       : "memory");
 }
 
@@ -180,49 +185,64 @@ __device__ __forceinline__ double slot_total(const double* red, int q, int h) {
 
 template <typename T, int VX_, int A>
 struct Plain3DLayout {
-  static constexpr int VX = VX_, TY = plain::TY;
-  static constexpr int TX = 32 * VX, FX = TX + 8, HX = TX + 4, FY = TY + 2, HY = TY + 1;
-  static constexpr int FE = FY * FX, FH = HY * HX;   // elements per component of an E / H frame
-  static constexpr int NE = A + 1, NH = A;            // E and H_in frame slots
+  static constexpr int VX = VX_, TY = plain::TY, TX = 32 * VX;
+  static constexpr int NE = A + 1, NH = A;   // E and H_in frame slots
   static constexpr int threads = 32 * (TY + 1);
-  // byte offsets: E slots [NE][3][FE], H_in slots [NH][3][FH], H^n buffers [2][Hx, Hz][HY][TX],
-  // mbarriers [A], plane table [kMaxPlanes], row pieces [2][4][kMaxPieces]
-  static constexpr unsigned ES = 3u * FE * sizeof(T), HS = 3u * FH * sizeof(T), XS = 2u * HY * TX * sizeof(T);
+  static constexpr unsigned SZ = sizeof(T);
+  static constexpr unsigned r128(unsigned b) { return (b + 127u) & ~127u; }
+  // An E frame slot (each part one box, box-dense, 128-byte aligned): main [3][TY][TX] rows
+  // y0..y0+TY-1; top [3][TX] row y0-1; bot [3][TX] row y0+TY; pl8 [3][TY][4] columns x0-4..x0-1 of
+  // rows y0..; plb [3][4] the same columns of row y0+TY; prt [3][4] columns x0+TX..x0+TX+3 of row
+  // y0-1; pr8 [3][TY][4] those columns of rows y0...
+  static constexpr unsigned E_MAIN = 0, E_TOP = r128(3u * TY * TX * SZ), E_BOT = E_TOP + r128(3u * TX * SZ);
+  static constexpr unsigned E_PL8 = E_BOT + r128(3u * TX * SZ), E_PLB = E_PL8 + r128(3u * TY * 4 * SZ);
+  static constexpr unsigned E_PRT = E_PLB + r128(12u * SZ), E_PR8 = E_PRT + r128(12u * SZ);
+  static constexpr unsigned ES = E_PR8 + r128(3u * TY * 4 * SZ);
+  // an H_in frame slot: main [3][TY][TX], top [3][TX] (row y0-1), pl8 [3][TY][4] (columns x0-4..x0-1)
+  static constexpr unsigned H_MAIN = 0, H_TOP = r128(3u * TY * TX * SZ), H_PL8 = H_TOP + r128(3u * TX * SZ);
+  static constexpr unsigned HS = H_PL8 + r128(3u * TY * 4 * SZ);
+  // bytes of the boxes of one E frame and of one H_in frame
+  static constexpr unsigned E_BYTES = (3u * TY * TX + 2 * 3u * TX + 2 * 3u * TY * 4 + 2 * 12u) * SZ;
+  static constexpr unsigned H_BYTES = (3u * TY * TX + 3u * TX + 3u * TY * 4) * SZ;
+  // H^n buffers [2][Hx, Hz][TY + 1][TX] (row 0: y0-1), then mbarriers [A], plane table [kMaxPlanes]
+  static constexpr unsigned XS = 2u * (TY + 1) * TX * SZ;
   static constexpr unsigned OFF_E = 0, OFF_HIN = NE * ES, OFF_SH = OFF_HIN + NH * HS, OFF_MBAR = OFF_SH + 2 * XS;
-  static constexpr unsigned OFF_INFO = OFF_MBAR + ((8 * A + 15) / 16) * 16, OFF_PIECE = OFF_INFO + plain::kMaxPlanes * 4;
-  static constexpr unsigned bytes = OFF_PIECE + 2 * 4 * plain::kMaxPieces * 4;
+  static constexpr unsigned OFF_INFO = OFF_MBAR + ((8 * A + 15) / 16) * 16;
+  static constexpr unsigned bytes = OFF_INFO + plain::kMaxPlanes * 4 + 128;   // + alignment slack
   // CTAs per SM that the shared memory admits (228 KB per SM, 1 KB reserved per CTA, static 128 B)
   static constexpr int per_sm = 233472 / (bytes + 1024 + 128) > 8 ? 8 : 233472 / (bytes + 1024 + 128);
-  static_assert(OFF_MBAR % 16 == 0, "mbarrier alignment");
-  static_assert(ES % 16 == 0 && HS % 16 == 0 && XS % 16 == 0, "16-byte aligned frames");
+  static_assert(ES % 128 == 0 && HS % 128 == 0 && XS % 128 == 0, "128-byte aligned frames");
   // the slot sums of the monitors / energy use the H^n buffer not in use (4 x TY x VX doubles)
   static_assert(4 * TY * VX * 8 <= XS, "reduction scratch fits an H buffer");
 };
 
 template <typename T, bool INC, int VX, int A>
 __global__ void __launch_bounds__(Plain3DLayout<T, VX, A>::threads, Plain3DLayout<T, VX, A>::per_sm)
-plain3d_kernel(const Step3DParams<T> p) {
+plain3d_kernel(const Step3DParams<T> p, const __grid_constant__ PlainMaps maps, int ebuf, int hbuf) {
   using namespace plain;
   using L = Plain3DLayout<T, VX, A>;
   using VV = Vec<T, VX>;
-  constexpr int TY = L::TY;
-  constexpr int TX = L::TX, FX = L::FX, HX = L::HX, FY = L::FY, HY = L::HY, NE = L::NE, NH = L::NH;
+  constexpr int TY = L::TY, TX = L::TX, NE = L::NE, NH = L::NH;
   constexpr unsigned SZ = sizeof(T), ES = L::ES, HS = L::HS, XS = L::XS;
-  constexpr unsigned CE = L::FE * SZ, CH = L::FH * SZ;   // component strides (bytes)
-  constexpr unsigned RE = FX * SZ, RH = HX * SZ;         // row strides (bytes)
-  constexpr unsigned RX = TX * SZ, CX = HY * RX;         // H^n buffer: row and component strides
-  extern __shared__ __align__(128) unsigned char smem_raw[];
+  constexpr unsigned RT = TX * SZ;              // a frame row (bytes)
+  constexpr unsigned CM = TY * RT, CR = RT;     // component strides of main parts and of single rows
+  constexpr unsigned CP8 = TY * 4 * SZ, CP1 = 4 * SZ;   // ... of the side columns
+  constexpr unsigned CX = (TY + 1) * RT;        // H^n buffer: component stride
+  extern __shared__ __align__(128) unsigned char smem_raw_[];
+  // the dynamic shared memory, aligned to 128 bytes for the tensor copies
+  unsigned char* smem_raw = smem_raw_ + ((128u - (smem_u32(smem_raw_) & 127u)) & 127u);
   uint64_t* mbar = reinterpret_cast<uint64_t*>(smem_raw + L::OFF_MBAR);
   int* sInfo = reinterpret_cast<int*>(smem_raw + L::OFF_INFO);
-  int* sPiece = reinterpret_cast<int*>(smem_raw + L::OFF_PIECE);   // [2][4][kMaxPieces]
   __shared__ int s_abort;
   auto at = [&](unsigned off) -> unsigned char* { return smem_raw + off; };
+  auto ldf = [&](unsigned off) -> T { return *reinterpret_cast<const T*>(smem_raw + off); };
 
   const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
   const bool helper = w == TY;
   const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
   const int i0 = x0 + VX * lane, j = y0 + w;
-  const bool own = !helper && (i0 < p.nx) && (j < p.ny);   // nx is a multiple of VX: all VX cells or none
+  // the host runs this kernel only when the tiles cover the grid exactly (nx % TX == 0, ny % 8 == 0)
+  const bool own = !helper;
   const int chunk = p.chunk_ids[blockIdx.z];
   const int zb = p.zstart[chunk], ze = p.zstart[chunk + 1];
   const int np = ze - zb;
@@ -230,37 +250,27 @@ plain3d_kernel(const Step3DParams<T> p) {
   const int qxy = own ? j * p.nx + i0 : 0;
   const T dt = p.dt, S = p.S;
   const int nmc = (int)p.nmatcell;
-  const int nbx32 = (p.nx + 31) / 32;
+  const int nbx32 = p.nx / 32;
   const int slot_row = blockIdx.y;   // 32 x 8 partial-sum slots: the tile's rows
-  // frame byte offsets of this thread's first cell: compute warps their row w + 1, the helper the
-  // halo row 0 (E frame column of x is x - x0 + 4); H^n buffer offset (column of x is x - x0)
-  const int frow = helper ? 0 : w + 1;
-  const unsigned oE = (unsigned)(frow * FX + 4 + VX * lane) * SZ;
-  const unsigned oH = (unsigned)(frow * HX + 4 + VX * lane) * SZ;
-  const unsigned oX = (unsigned)frow * RX + (unsigned)(VX * lane) * SZ;
+  // frame byte offsets of the thread's cells (relative to a slot): its row (compute warps: main
+  // row w; the helper: the row y0-1), the row above it in y (+1), the column after its last cell,
+  // its H_in row; and their component strides
+  const unsigned cell = (unsigned)(VX * lane) * SZ;
+  const unsigned oR = helper ? L::E_TOP + cell : L::E_MAIN + (unsigned)w * RT + cell;
+  const unsigned cR = helper ? CR : CM;
+  const unsigned oJ = helper ? L::E_MAIN + cell : (w + 1 < TY ? L::E_MAIN + (unsigned)(w + 1) * RT + cell : L::E_BOT + cell);
+  const unsigned cJ = helper ? CM : (w + 1 < TY ? CM : CR);
+  const unsigned oX = helper ? L::E_PRT : L::E_PR8 + (unsigned)w * 4 * SZ;
+  const unsigned cXc = helper ? CP1 : CP8;
+  const unsigned oH = helper ? L::H_TOP + cell : L::H_MAIN + (unsigned)w * RT + cell;
+  const unsigned cH = helper ? CR : CM;
+  const unsigned oS = (helper ? 0u : (unsigned)(w + 1) * RT) + cell;   // H^n buffer, row y - y0 + 1
 
-  // ---- set-up: mbarriers, periodic pieces of the frame rows, per-plane table ----
+  // ---- set-up: mbarriers, per-plane table ----
   if (tid == 0) {
     s_abort = 0;
     for (int a = 0; a < A; ++a) plain::mbar_init(&mbar[a], 1);
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
-    // pieces of an E row (frame cols 0..FX-1 <-> x0-4 .. x0+TX+3) and of an H row (0..HX-1)
-    for (int f = 0; f < 2; ++f) {
-      const int W = f == 0 ? FX : HX;
-      int* tab = sPiece + f * 4 * kMaxPieces;
-      int n = 0, col = 0;
-      while (col < W && n < kMaxPieces) {
-        const int x = wrap(x0 - 4 + col, p.nx);
-        const int len = min(W - col, p.nx - x);
-        tab[n] = col;
-        tab[kMaxPieces + n] = x;
-        tab[2 * kMaxPieces + n] = len;
-        col += len;
-        ++n;
-      }
-      tab[3 * kMaxPieces] = n;
-      if (col != W) s_abort = 1;   // cannot happen for nx >= 16 (checked on the host)
-    }
     if (np > kMaxPlanes) s_abort = 1;   // the host plans chunks of at most kMaxPlanes planes
   }
   for (int t = tid; t < np && t < kMaxPlanes; t += L::threads) {
@@ -286,53 +296,37 @@ plain3d_kernel(const Step3DParams<T> p) {
     return;
   }
 
-  // ---- helper: stage g brings E_in(zb+g+1) (unless past the grid) and H_in(zb+g), stage 0 also
-  // E_in(zb); one frame row (component c, row r) per lane and pass, copied piece by piece ----
-  const int nrowE = 3 * FY, nrowH = 3 * HY;
+  // ---- staging (helper lane 0): stage g brings E_in(zb+g+1) (unless past the grid) and H_in(zb+g),
+  // stage 0 also E_in(zb); the periodic neighbours are boxes of their own (wrapped coordinates) ----
+  const int ym = y0 == 0 ? p.ny - 1 : y0 - 1, yp = y0 + TY == p.ny ? 0 : y0 + TY;
+  const int xm = x0 == 0 ? p.nx - 4 : x0 - 4, xp = x0 + TX == p.nx ? 0 : x0 + TX;
   auto stage_bytes = [&](int g) -> unsigned {
     const int nE = (zb + g + 1 < p.nz ? 1 : 0) + (g == 0 ? 1 : 0);
-    return (unsigned)(nE * nrowE * FX + nrowH * HX) * SZ;
+    return nE * L::E_BYTES + L::H_BYTES;
+  };
+  auto load_e = [&](int kk, uint64_t* bar) {
+    const unsigned d = smem_u32(smem_raw) + L::OFF_E + ((kk - zb) % NE) * ES;
+    plain::tma_load5(d + L::E_MAIN, &maps.e_main, x0, y0, kk, 0, ebuf, bar);
+    plain::tma_load5(d + L::E_TOP, &maps.e_row, x0, ym, kk, 0, ebuf, bar);
+    plain::tma_load5(d + L::E_BOT, &maps.e_row, x0, yp, kk, 0, ebuf, bar);
+    plain::tma_load5(d + L::E_PL8, &maps.e_pad8, xm, y0, kk, 0, ebuf, bar);
+    plain::tma_load5(d + L::E_PLB, &maps.e_pad1, xm, yp, kk, 0, ebuf, bar);
+    plain::tma_load5(d + L::E_PRT, &maps.e_pad1, xp, ym, kk, 0, ebuf, bar);
+    plain::tma_load5(d + L::E_PR8, &maps.e_pad8, xp, y0, kk, 0, ebuf, bar);
   };
   auto issue_stage = [&](int g) {
     const int k = zb + g;
-    const bool nextE = k + 1 < p.nz;
-    const int nrow = (nextE ? nrowE : 0) + (g == 0 ? nrowE : 0) + nrowH;
     uint64_t* bar = &mbar[g % A];
-    for (int row = lane; row < nrow; row += 32) {
-      int rr = row, kk, frame;   // frame 0: an E frame of plane kk, 1: the H_in frame of plane k
-      if (nextE && rr < nrowE) {
-        kk = k + 1;
-        frame = 0;
-      } else {
-        if (nextE) rr -= nrowE;
-        if (g == 0 && rr < nrowE) {
-          kk = zb;
-          frame = 0;
-        } else {
-          if (g == 0) rr -= nrowE;
-          kk = k;
-          frame = 1;
-        }
-      }
-      const int rows = frame == 0 ? FY : HY;
-      const int c = rr / rows, r = rr - c * rows;
-      int y = y0 - 1 + r;   // y0 - 1 <= y <= y0 + TY < 2 ny
-      y = y < 0 ? y + p.ny : (y >= p.ny ? y - p.ny : y);
-      const T* src = (frame == 0 ? p.Ein : p.Hin) + (int64_t)kk * plane + (int64_t)c * ncell + (int64_t)y * p.nx;
-      const unsigned dst = smem_u32(smem_raw) +
-                           (frame == 0 ? L::OFF_E + ((kk - zb) % NE) * ES + c * CE + r * RE
-                                       : L::OFF_HIN + ((kk - zb) % NH) * HS + c * CH + r * RH);
-      const int* tab = sPiece + frame * 4 * kMaxPieces;
-      const int npc = tab[3 * kMaxPieces];
-      for (int pc = 0; pc < npc; ++pc)
-        plain::bulk_g2s(dst + tab[pc] * SZ, src + tab[kMaxPieces + pc], (unsigned)tab[2 * kMaxPieces + pc] * SZ,
-                        bar);
-    }
+    if (k + 1 < p.nz) load_e(k + 1, bar);
+    if (g == 0) load_e(zb, bar);
+    const unsigned d = smem_u32(smem_raw) + L::OFF_HIN + (g % NH) * HS;
+    plain::tma_load5(d + L::H_MAIN, &maps.h_main, x0, y0, k, 0, hbuf, bar);
+    plain::tma_load5(d + L::H_TOP, &maps.h_row, x0, ym, k, 0, hbuf, bar);
+    plain::tma_load5(d + L::H_PL8, &maps.h_pad8, xm, y0, k, 0, hbuf, bar);
   };
-  if (helper) {
+  if (helper && lane == 0) {
     for (int g = 0; g < A && g < np; ++g) {
-      if (lane == 0) plain::mbar_arrive_expect_tx(&mbar[g], stage_bytes(g));
-      __syncwarp();
+      plain::mbar_arrive_expect_tx(&mbar[g], stage_bytes(g));
       issue_stage(g);
     }
   }
@@ -373,45 +367,49 @@ plain3d_kernel(const Step3DParams<T> p) {
       atomicExch(p.err, 1);
     }
   };
-  // H^n of plane k at the thread's VX cells from the staged frames (offsets oE / oH / oX: the own
-  // row of a compute warp, the halo row y0-1 for the helper); writes H_x, H_z to the H^n buffer
-  // and returns the cells' E_in(k) and H^n.  PML: the plane lies in the CPML of the H update.
-  auto h_cells = [&](bool PML, bool top, unsigned e0, unsigned e1, unsigned hin, unsigned xb, T bH, T cH,
+  // H^n of plane k at the thread's VX cells from the staged frames (the own row of a compute warp,
+  // the halo row y0-1 for the helper); writes H_x, H_z to the H^n buffer and returns the cells'
+  // E_in(k) and H^n.  PML: the plane lies in the CPML of the H update.
+  auto h_cells = [&](bool PML, bool top, unsigned e0, unsigned e1, unsigned hin, unsigned xb, T bH, T cH_,
                      T* psHx, T* psHy, T* ex0, T* ey0, T* ez0, T* Hx, T* Hy, T* Hz) {
-    VV::ld(at(e0 + oE), ex0);
-    VV::ld(at(e0 + CE + oE), ey0);
-    VV::ld(at(e0 + 2 * CE + oE), ez0);
+    VV::ld(at(e0 + oR), ex0);
+    VV::ld(at(e0 + cR + oR), ey0);
+    VV::ld(at(e0 + 2 * cR + oR), ez0);
     T ex1[VX], ey1[VX], ez1[VX], exj[VX], ezj[VX];
     if (!top) {
-      VV::ld(at(e1 + oE), ex1);
-      VV::ld(at(e1 + CE + oE), ey1);
-      VV::ld(at(e1 + 2 * CE + oE), ez1);
+      VV::ld(at(e1 + oR), ex1);
+      VV::ld(at(e1 + cR + oR), ey1);
+      VV::ld(at(e1 + 2 * cR + oR), ez1);
     } else {
 #pragma unroll
       for (int v = 0; v < VX; ++v) ex1[v] = ey1[v] = ez1[v] = T(0);
     }
-    VV::ld(at(e0 + oE + RE), exj);
-    VV::ld(at(e0 + 2 * CE + oE + RE), ezj);
-    const T eyi = *reinterpret_cast<const T*>(at(e0 + CE + oE + VX * SZ));
-    const T ezi = *reinterpret_cast<const T*>(at(e0 + 2 * CE + oE + VX * SZ));
+    VV::ld(at(e0 + oJ), exj);
+    VV::ld(at(e0 + 2 * cJ + oJ), ezj);
+    // E_y, E_z after the last cell: the next lane's first cell, or the column x0+TX
+    T eyi = __shfl_down_sync(0xffffffffu, ey0[0], 1), ezi = __shfl_down_sync(0xffffffffu, ez0[0], 1);
+    if (lane == 31) {
+      eyi = ldf(e0 + oX + cXc);
+      ezi = ldf(e0 + oX + 2 * cXc);
+    }
     VV::ld(at(hin + oH), Hx);
-    VV::ld(at(hin + CH + oH), Hy);
-    VV::ld(at(hin + 2 * CH + oH), Hz);
+    VV::ld(at(hin + cH + oH), Hy);
+    VV::ld(at(hin + 2 * cH + oH), Hz);
 #pragma unroll
     for (int v = 0; v < VX; ++v) {
       const T ey_i1 = v + 1 < VX ? ey0[v + 1 < VX ? v + 1 : 0] : eyi;
       const T ez_i1 = v + 1 < VX ? ez0[v + 1 < VX ? v + 1 : 0] : ezi;
       plain::h_cell(Hx[v], Hy[v], Hz[v], psHx[v], psHy[v], ezj[v] - ez0[v], ey1[v] - ey0[v], ex1[v] - ex0[v],
-                    ez_i1 - ez0[v], ey_i1 - ey0[v], exj[v] - ex0[v], PML, bH, cH, S);
+                    ez_i1 - ez0[v], ey_i1 - ey0[v], exj[v] - ex0[v], PML, bH, cH_, S);
     }
-    VV::st(at(xb + oX), Hx);
-    VV::st(at(xb + CX + oX), Hz);
+    VV::st(at(xb + oS), Hx);
+    VV::st(at(xb + CX + oS), Hz);
   };
 
   if (helper) {
     // ======== helper warp: the halo row y0-1 of H^n, the staging of the planes ahead, and its part
     // in the barriers of the compute warps' reductions ========
-    const int gxy = wrap(y0 - 1, p.ny) * p.nx + i0 % p.nx;   // grid column of the halo-row cells
+    const int gxy = ym * p.nx + i0;   // grid column of the halo-row cells
     for (int g = 0; g < np; ++g) {
       const int k = zb + g;
       const int info = sInfo[g];
@@ -437,10 +435,7 @@ plain3d_kernel(const Step3DParams<T> p) {
       if (lane == 0 && wait_ok && g + A < np) plain::mbar_arrive_expect_tx(&mbar[g % A], stage_bytes(g + A));
       __syncthreads();   // H^n(k) of the tile and its halo complete; E_in(k), H_in(k) slots free
       if (s_abort) break;
-      if (g + A < np) {
-        __syncwarp();
-        issue_stage(g + A);
-      }
+      if (lane == 0 && g + A < np) issue_stage(g + A);
       if (info & (kMonH | kMonE)) {
         for (int m = 0; m < p.nmon; ++m) {
           const int zm = p.mon_z[m];
@@ -461,6 +456,11 @@ plain3d_kernel(const Step3DParams<T> p) {
   } else {
     // ======== compute warps: plane k of the own row.  GEN = false is a plain vacuum plane (no
     // layer, CPML, source, monitor or energy box, not the top plane) ========
+    // frame offsets of the halo cell x0-1 of this row (and of the row above it in y)
+    const unsigned oL = L::E_PL8 + (unsigned)(w * 4 + 3) * SZ;
+    const unsigned oLJ = w + 1 < TY ? L::E_PL8 + (unsigned)((w + 1) * 4 + 3) * SZ : L::E_PLB + 3u * SZ;
+    const unsigned cLJ = w + 1 < TY ? CP8 : CP1;
+    const unsigned oLH = L::H_PL8 + (unsigned)(w * 4 + 3) * SZ;
     auto body = [&](auto gen_t, int g, int info) -> bool {
       constexpr bool GEN = decltype(gen_t)::value;
       const int k = zb + g;
@@ -476,7 +476,7 @@ plain3d_kernel(const Step3DParams<T> p) {
       T psHx[VX], psHy[VX];
 #pragma unroll
       for (int v = 0; v < VX; ++v) psHx[v] = psHy[v] = T(0);
-      if (pmlH && own) {
+      if (pmlH) {
         VV::ld(p.psiHin + ipH * plane + qxy, psHx);
         VV::ld(p.psiHin + pstrH + ipH * plane + qxy, psHy);
       }
@@ -484,12 +484,12 @@ plain3d_kernel(const Step3DParams<T> p) {
 
       // ---- H^n of plane k at the own cells ----
       T ex0[VX], ey0[VX], ez0[VX], Hx[VX], Hy[VX], Hz[VX];
-      const T bH = pmlH ? p.pmlH[2 * k] : T(1), cH = pmlH ? p.pmlH[2 * k + 1] : T(0);
+      const T bH = pmlH ? p.pmlH[2 * k] : T(1), cH_ = pmlH ? p.pmlH[2 * k + 1] : T(0);
       if (pmlH)
-        h_cells(true, top, e0, e1, hin, xb, bH, cH, psHx, psHy, ex0, ey0, ez0, Hx, Hy, Hz);
+        h_cells(true, top, e0, e1, hin, xb, bH, cH_, psHx, psHy, ex0, ey0, ez0, Hx, Hy, Hz);
       else
-        h_cells(false, top, e0, e1, hin, xb, bH, cH, psHx, psHy, ex0, ey0, ez0, Hx, Hy, Hz);
-      if (own) {
+        h_cells(false, top, e0, e1, hin, xb, bH, cH_, psHx, psHy, ex0, ey0, ez0, Hx, Hy, Hz);
+      {
         const int q = k * plane + qxy;
         VV::st(p.Hout + q, Hx);
         VV::st(p.Hout + ncell + q, Hy);
@@ -503,21 +503,19 @@ plain3d_kernel(const Step3DParams<T> p) {
       // recomputed for the halo cell x0-1 of this row ----
       T hyx0 = __shfl_up_sync(0xffffffffu, Hy[VX - 1], 1), hzx0 = __shfl_up_sync(0xffffffffu, Hz[VX - 1], 1);
       if (lane == 0) {
-        const unsigned fe = (unsigned)((w + 1) * FX + 3) * SZ, fh = (unsigned)((w + 1) * HX + 3) * SZ;
-        auto ldf = [&](unsigned off) { return *reinterpret_cast<const T*>(at(off)); };
-        const T ax = ldf(e0 + fe), ay = ldf(e0 + CE + fe), az = ldf(e0 + 2 * CE + fe);
-        const T bx = top ? T(0) : ldf(e1 + fe), by = top ? T(0) : ldf(e1 + CE + fe);
-        const T jx = ldf(e0 + fe + RE), jz = ldf(e0 + 2 * CE + fe + RE);
-        T hx = ldf(hin + fh), hy = ldf(hin + CH + fh), hz = ldf(hin + 2 * CH + fh);
+        const T ax = ldf(e0 + oL), ay = ldf(e0 + CP8 + oL), az = ldf(e0 + 2 * CP8 + oL);
+        const T bx = top ? T(0) : ldf(e1 + oL), by = top ? T(0) : ldf(e1 + CP8 + oL);
+        const T jx = ldf(e0 + oLJ), jz = ldf(e0 + 2 * cLJ + oLJ);
+        T hx = ldf(hin + oLH), hy = ldf(hin + CP8 + oLH), hz = ldf(hin + 2 * CP8 + oLH);
         T qx = T(0), qy = T(0);
         if (pmlH) {
-          const int gq = wrap(j, p.ny) * p.nx + wrap(x0 - 1, p.nx);
+          const int gq = j * p.nx + (x0 == 0 ? p.nx - 1 : x0 - 1);
           qx = p.psiHin[ipH * plane + gq];
           qy = p.psiHin[pstrH + ipH * plane + gq];
         }
         // the cell's x+1 neighbour is this lane's first cell (ey0[0], ez0[0])
         plain::h_cell(hx, hy, hz, qx, qy, jz - az, by - ay, bx - ax, ez0[0] - az, ey0[0] - ay, jx - ax, pmlH, bH,
-                      cH, S);
+                      cH_, S);
         hyx0 = hy;
         hzx0 = hz;
       }
@@ -528,7 +526,7 @@ plain3d_kernel(const Step3DParams<T> p) {
       T psEx[VX], psEy[VX];
 #pragma unroll
       for (int v = 0; v < VX; ++v) psEx[v] = psEy[v] = T(0);
-      if (pmlE && own) {
+      if (pmlE) {
         VV::ld(p.psiE + ipE * plane + qxy, psEx);
         VV::ld(p.psiE + pstrE + ipE * plane + qxy, psEy);
       }
@@ -539,23 +537,21 @@ plain3d_kernel(const Step3DParams<T> p) {
           if (k != zm - 1 && k != zm) continue;
           const int off = (k == zm) ? 1 : 0;
           double v2[2] = {0.0, 0.0};
-          if (own)
 #pragma unroll
-            for (int v = 0; v < VX; ++v) {
-              v2[0] += (double)Hx[v];
-              v2[1] += (double)Hy[v];
-            }
+          for (int v = 0; v < VX; ++v) {
+            v2[0] += (double)Hx[v];
+            v2[1] += (double)Hy[v];
+          }
           block_slot_sums<TY, VX>(v2, red, w, lane);
           if (tid < 2 * VX && p.mon_partial_H) {
             const int qn = tid / VX, h = tid - qn * VX;
-            if (blockIdx.x * VX + h < nbx32)
-              p.mon_partial_H[(int64_t)(4 * m + 2 * qn + off) * p.nbxy + slot_row * nbx32 + blockIdx.x * VX + h] =
-                  slot_total<TY, VX>(red, qn, h);
+            p.mon_partial_H[(int64_t)(4 * m + 2 * qn + off) * p.nbxy + slot_row * nbx32 + blockIdx.x * VX + h] =
+                slot_total<TY, VX>(red, qn, h);
           }
           __syncthreads();   // red read before it is rewritten
         }
       }
-      if (GEN && p.eH_on && own && in_box) {
+      if (GEN && p.eH_on && in_box) {
 #pragma unroll
         for (int v = 0; v < VX; ++v) uH += Hx[v] * Hx[v] + Hy[v] * Hy[v] + Hz[v] * Hz[v];
       }
@@ -563,10 +559,10 @@ plain3d_kernel(const Step3DParams<T> p) {
       // ---- D/E (Eq. 1a) and P (Eq. Pz_1D_Lorentz) of plane k at the own cells, one component at
       // a time (the material state of a component is loaded, used and stored before the next) ----
       double monE[2] = {0.0, 0.0};   // sums of E_x and E_y over the thread's cells (E monitors)
-      if (own) {
+      {
         T hxy[VX], hzy[VX];   // H_x, H_z at y-1
-        VV::ld(at(xb + oX - RX), hxy);
-        VV::ld(at(xb + CX + oX - RX), hzy);
+        VV::ld(at(xb + oS - RT), hxy);
+        VV::ld(at(xb + CX + oS - RT), hzy);
         const T bE = pmlE ? p.pmlE[2 * k] : T(1), cE_ = pmlE ? p.pmlE[2 * k + 1] : T(0);
         const int q = k * plane + qxy;
         const MatK<T>* M = mi >= 0 ? &p.mat[mi] : nullptr;
@@ -695,9 +691,8 @@ plain3d_kernel(const Step3DParams<T> p) {
           block_slot_sums<TY, VX>(v2, red, w, lane);
           if (tid < 2 * VX && p.mon_partial_E) {
             const int qn = tid / VX, h = tid - qn * VX;
-            if (blockIdx.x * VX + h < nbx32)
-              p.mon_partial_E[(int64_t)(2 * m + qn) * p.nbxy + slot_row * nbx32 + blockIdx.x * VX + h] =
-                  slot_total<TY, VX>(red, qn, h);
+            p.mon_partial_E[(int64_t)(2 * m + qn) * p.nbxy + slot_row * nbx32 + blockIdx.x * VX + h] =
+                slot_total<TY, VX>(red, qn, h);
           }
           __syncthreads();   // red read before it is rewritten
         }
@@ -716,9 +711,9 @@ plain3d_kernel(const Step3DParams<T> p) {
       if (!ok) break;
     }
   }
-  // after an abort: when the helper's own wait ran out, a bounded wait for that stage and the
-  // stages issued after it, so that no copy is in flight into this CTA's shared memory when it
-  // exits (a stage armed but not issued has no copies)
+  // after an abort: a bounded wait for the stage that ran out and those issued after it, so that no
+  // copy is in flight into this CTA's shared memory when it exits (a stage armed but not issued
+  // has no copies)
   if (s_abort && helper && lane == 0) {
     for (int g = wait_ok ? g_last + 1 : g_last; g < np && g < g_last + A; ++g)
       plain::mbar_wait(&mbar[g % A], (unsigned)((g / A) & 1));
@@ -732,11 +727,9 @@ plain3d_kernel(const Step3DParams<T> p) {
     if (tid < 4 * VX) {
       const int qn = tid / VX, h = tid - qn * VX;
       const int64_t slot = (int64_t)chunk * p.nbxy + slot_row * nbx32 + blockIdx.x * VX + h;
-      if (blockIdx.x * VX + h < nbx32) {
-        const double s = slot_total<TY, VX>(red, qn, h);
-        if (qn < 3 && p.eE_on) p.en_partial_E[(int64_t)qn * p.nbxy * p.nchunks_total + slot] = s;
-        if (qn == 3 && p.eH_on) p.en_partial_H[slot] = s;
-      }
+      const double s = slot_total<TY, VX>(red, qn, h);
+      if (qn < 3 && p.eE_on) p.en_partial_E[(int64_t)qn * p.nbxy * p.nchunks_total + slot] = s;
+      if (qn == 3 && p.eH_on) p.en_partial_H[slot] = s;
     }
   }
 }

@@ -1,4 +1,5 @@
-// plain3d_f32.cu -- float instantiations of the plain-plane step kernel.
+// plain3d_f32.cu -- float instantiation of the plain-plane step kernel (four cells per thread, two
+// planes staged ahead, two CTAs per SM).
 #include <cuda_runtime.h>
 
 #include "plain3d.cuh"
@@ -6,7 +7,8 @@
 namespace fdtdbath {
 
 template <int VX, int A>
-static int launch_shape(const Step3DParams<float>& p, int nchunks, void* stream) {
+static int launch_shape(const Step3DParams<float>& p, const PlainMaps& maps, int ebuf, int hbuf, int nchunks,
+                        void* stream) {
   using L = Plain3DLayout<float, VX, A>;
   auto kern = plain3d_kernel<float, true, VX, A>;
   static bool attr_set = false;   // once per process: more than 48 KB, shared-memory carveout
@@ -17,20 +19,14 @@ static int launch_shape(const Step3DParams<float>& p, int nchunks, void* stream)
     if (e != cudaSuccess) return (int)e;
     attr_set = true;
   }
-  dim3 grid((p.nx + L::TX - 1) / L::TX, (p.ny + L::TY - 1) / L::TY, nchunks), block(L::threads);
-  kern<<<grid, block, L::bytes, (cudaStream_t)stream>>>(p);
+  dim3 grid(p.nx / L::TX, p.ny / L::TY, nchunks), block(L::threads);
+  kern<<<grid, block, L::bytes, (cudaStream_t)stream>>>(p, maps, ebuf, hbuf);
   return (int)cudaGetLastError();
 }
 
-// shape: 0 = four cells per thread, one plane ahead; 1 = four cells, two planes ahead;
-// 2 = two cells, two planes ahead; 3 = two cells, three planes ahead
-int launch_plain3d_f32(const Step3DParams<float>& p, int nchunks, int shape, void* stream) {
-  switch (shape) {
-    case 1: return launch_shape<4, 2>(p, nchunks, stream);
-    case 2: return launch_shape<2, 2>(p, nchunks, stream);
-    case 3: return launch_shape<2, 3>(p, nchunks, stream);
-    default: return launch_shape<4, 1>(p, nchunks, stream);
-  }
+int launch_plain3d_f32(const Step3DParams<float>& p, const PlainMaps& maps, int ebuf, int hbuf, int nchunks,
+                       void* stream) {
+  return launch_shape<4, 2>(p, maps, ebuf, hbuf, nchunks, stream);
 }
 
 }  // namespace fdtdbath

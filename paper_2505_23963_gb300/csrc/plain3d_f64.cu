@@ -1,14 +1,16 @@
-// plain3d_f64.cu -- double instantiation of the plain-plane step kernel (built without FMA
-// contraction).
+// plain3d_f64.cu -- double instantiation of the plain-plane step kernel (two cells per thread, two
+// planes staged ahead; built without FMA contraction).
 #include <cuda_runtime.h>
 
 #include "plain3d.cuh"
 
 namespace fdtdbath {
 
-int launch_plain3d_f64(const Step3DParams<double>& p, int nchunks, int, void* stream) {
-  using L = Plain3DLayout<double, 2, 2>;
-  auto kern = plain3d_kernel<double, false, 2, 2>;
+template <int VX, int A>
+static int launch_shape(const Step3DParams<double>& p, const PlainMaps& maps, int ebuf, int hbuf, int nchunks,
+                        void* stream) {
+  using L = Plain3DLayout<double, VX, A>;
+  auto kern = plain3d_kernel<double, false, VX, A>;
   static bool attr_set = false;   // once per process: more than 48 KB, shared-memory carveout
   if (!attr_set) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::bytes);
@@ -17,9 +19,14 @@ int launch_plain3d_f64(const Step3DParams<double>& p, int nchunks, int, void* st
     if (e != cudaSuccess) return (int)e;
     attr_set = true;
   }
-  dim3 grid((p.nx + L::TX - 1) / L::TX, (p.ny + L::TY - 1) / L::TY, nchunks), block(L::threads);
-  kern<<<grid, block, L::bytes, (cudaStream_t)stream>>>(p);
+  dim3 grid(p.nx / L::TX, p.ny / L::TY, nchunks), block(L::threads);
+  kern<<<grid, block, L::bytes, (cudaStream_t)stream>>>(p, maps, ebuf, hbuf);
   return (int)cudaGetLastError();
+}
+
+int launch_plain3d_f64(const Step3DParams<double>& p, const PlainMaps& maps, int ebuf, int hbuf, int nchunks,
+                       void* stream) {
+  return launch_shape<2, 2>(p, maps, ebuf, hbuf, nchunks, stream);
 }
 
 }  // namespace fdtdbath

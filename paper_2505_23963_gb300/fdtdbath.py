@@ -391,6 +391,10 @@ class Simulation:
         """Whether the last reverse sweep ran the TE form (query key 6)."""
         return query(self.h, 6) == 1
 
+    def plain_kernel(self) -> bool:
+        """Whether the z-chunks without bath modes run the plain-plane kernel (query key 7)."""
+        return query(self.h, 7) == 1
+
     def adjoint_forward(self, nsteps: int, checkpoint_every: int = 256):
         """fdtdbath_adjoint_forward: advance nsteps steps keeping checkpoints for the adjoint."""
         _check(lib().fdtdbath_adjoint_forward(self.h, int(nsteps), int(checkpoint_every)), self.h)

@@ -257,7 +257,8 @@ def adjoint_target_params(params: np.ndarray, seed: int = 0) -> np.ndarray:
 
 # ----------------------------------------------------------------- random states
 def random_state(prob: dict, seed: int, scale: float = 1e-2, with_bath: bool = True) -> dict:
-    """Seeded random E, H, P (two levels) and Y (two levels) for every material cell.
+    """Seeded random E, H, P (two levels) and Y (two levels) for every cell of a polarizable
+    layer (a vacuum-kind layer, a plain dielectric, has no polarization).
 
     Returns {("E", c): arr, ("H", c): arr, ("P", c): arr, ("Pm", c): arr,
     ("Y", c, j, level): arr}; material-only quantities are zero outside their
@@ -271,7 +272,8 @@ def random_state(prob: dict, seed: int, scale: float = 1e-2, with_bath: bool = T
         st[("H", c)] = scale * rng.standard_normal(shp)
     mask = np.zeros(shp, dtype=bool)
     for m in prob["materials"]:
-        mask[m["z"][0]:m["z"][1]] = True
+        if m["kind"] != "vacuum":
+            mask[m["z"][0]:m["z"][1]] = True
     for c in range(3):
         st[("P", c)] = np.where(mask, 0.1 * scale * rng.standard_normal(shp), 0.0)
         st[("Pm", c)] = np.where(mask, 0.1 * scale * rng.standard_normal(shp), 0.0)
