@@ -67,6 +67,32 @@ def algorithmic_bytes(prob: dict, esz: int, bath_bytes: float | None = None) -> 
     return float(words.sum()) * nx * ny * esz
 
 
+def algorithmic_flops_fp64(prob: dict) -> float:
+    """Floating-point operations per step of the FP64 path, which evaluates the literal updates
+    (Eq. FDTD-1D with Eq. 1a,b in 3D, Eq. Pz_1D_Lorentz / Pz_update-LB, Eq. Yzj_finite_difference)
+    without FMA contraction, one operation per multiply or add, counted per cell from those
+    expressions: the H update 15 (six differences, three scaled subtractions), the E update 15
+    (six differences, three curl subtractions, three scaled additions), +8 per CPML memory pair
+    on each side; Drude / Lorentz planes +8 per component (D, E = (D - P)/eps, P update); a
+    Lorentz-Bath plane with N_b modes 51 N_b + 112 (per component 5 N_b for the bath sum, 12 N_b
+    for the mode updates and their energy, 27 for D, E, P and the P energy), energy-box planes
+    +7 for the field energy."""
+    nx, ny, nz = prob["n"]
+    pml = prob.get("pml", 0)
+    f = np.full(nz, 30.0)
+    f[:pml] += 16
+    f[nz - pml:] += 16
+    lo_b, hi_b = prob.get("energy_box", (0, 0))
+    for m in prob["materials"]:
+        lo, hi = m["z"]
+        if m["kind"] in ("lorentz", "drude"):
+            f[lo:hi] += 24
+        elif m["kind"] == "lorentz_bath":
+            f[lo:hi] = 51 * len(m["bath_frequencies"]) + 112
+    f[lo_b:hi_b] += 7
+    return float(f.sum()) * nx * ny
+
+
 class ClockSampler:
     """nvidia-smi clocks / throttle reasons sampled every 200 ms while active."""
 
@@ -577,6 +603,21 @@ def run_ours(args):
     ms64 = max_over_ranks(ms64, f"cuda:{dev}")
     value64 = replica_rate(cells * k64, ws, ms64 * 1e-3)
 
+    # ---- FP64 roofline: the measured FP64 FMA rate halved (no contraction: one flop per
+    # instruction) against the memory roofline of the same step ----
+    fma64 = fb.measure_fma_rate(64, dev, 5)
+    flops64 = algorithmic_flops_fp64(prob)
+    step64 = ms64 / k64 * 1e-3
+    hbm_gbs, _ = peaks()
+    alu_frac = flops64 / step64 / (fma64 / 2.0)
+    hbm_frac64 = algorithmic_bytes(prob, 8) / step64 / 1e9 / hbm_gbs
+    roof64 = {"bound": "alu" if alu_frac >= hbm_frac64 else "hbm",
+              "achieved": flops64 / step64 / 1e12, "peak": fma64 / 2.0 / 1e12, "unit": "TFLOP/s",
+              "frac": alu_frac, "flops_per_step": flops64, "fma_rate_tflops": fma64 / 1e12,
+              "peak_kind": "measured FP64 FMA rate / 2 (the FP64 path is compiled without FMA "
+                           "contraction: one flop per instruction)",
+              "hbm_frac": hbm_frac64}
+
     # ---- end to end through the C ABI with host buffers (create .. dft/energy .. destroy) ----
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -632,7 +673,7 @@ def run_ours(args):
                    "precision": 32, "l2": "state 1.6 GB > 129 MB L2 (no flush needed)",
                    "parallelism": f"replicas x{ws}"},
         "fp64": {"value": value64, "unit": UNIT, "steps": k64, "ms_per_step": ms64 / k64,
-                 "kernel_ms": kms64, "finite": ok64},
+                 "kernel_ms": kms64, "finite": ok64, "roofline": roof64},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": achieved / hbm, "traffic": traffic, "peak_kind": peak_kind,
                      "kernel": "step3d_kernel<float> (launch pair of one step)", "kernel_ms": step_ms,

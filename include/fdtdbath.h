@@ -40,7 +40,7 @@
 extern "C" {
 #endif
 
-#define FDTDBATH_ABI_VERSION 2   /* 2: fdtdbath_batch_plan takes block_threads */
+#define FDTDBATH_ABI_VERSION 3   /* 3: snapshot / restore, FMA-rate measurement; 2: batch_plan takes block_threads */
 
 enum fdtdbath_status {
   FDTDBATH_OK = 0,
@@ -180,6 +180,24 @@ int fdtdbath_energy(fdtdbath_sim *sim, double *trace, int64_t maxlen, int64_t *l
 /* Completed steps. */
 int64_t fdtdbath_steps_done(const fdtdbath_sim *sim);
 
+/* Checkpoint / resume of the whole state: every quantity the following steps read (E^{n-1/2},
+ * H, the CPML memories of both half-steps, D in FP64, both time levels of P and of every bath
+ * mode of Eq. Pz_update-LB / Yzj_finite_difference), the running DFT accumulators of every
+ * monitor, the energy trace and the step count.  The H half-step of the last step, which the
+ * library computes in the launch of the next step, stays pending: the snapshot holds H^{n-1} and
+ * the partial sums of step n-1, so a simulation restored from it -- the same one later, or a fresh
+ * one created with the same arguments -- runs the very launches the original would have and
+ * continues bit for bit (on the same device and library).
+ * The snapshot is an opaque byte string of fdtdbath_snapshot_size bytes (a header, then the
+ * device state), written to dst in host or device memory.  fdtdbath_restore checks that the
+ * snapshot comes from a simulation of the same layout (grid, CPML, precision, bath storage,
+ * material cells and modes, monitors, energy capacity; FDTDBATH_ERR_ARG otherwise) and replaces
+ * this simulation's state; a recorded adjoint forward run is discarded.  Both synchronize the
+ * simulation's stream. */
+int fdtdbath_snapshot_size(fdtdbath_sim *sim, size_t *bytes);
+int fdtdbath_snapshot(fdtdbath_sim *sim, void *dst, size_t dst_bytes, int32_t dst_on_device);
+int fdtdbath_restore(fdtdbath_sim *sim, const void *src, size_t src_bytes, int32_t src_on_device);
+
 /* Text of the last error of sim (or of the last failed create when sim is NULL). */
 const char *fdtdbath_last_error(const fdtdbath_sim *sim);
 
@@ -208,17 +226,29 @@ int64_t fdtdbath_query(const fdtdbath_sim *sim, int32_t key);
 
 /* Energy (U_EM, U_P, U_bath) of planes z_lo <= k < z_hi of the current state -- the same
  * quantities and weights as one fdtdbath_energy() entry -- computed WITHOUT allocating memory.
- * The paper has no counterpart: this entry point exists for callers that cannot allocate device
- * memory when they need the result (code running inside a stream capture, a real-time loop that
- * forbids allocation, a host framework that owns the whole memory pool).  Its scratch space is a
- * static device array of this library holding one partial sum per plane: boxes deeper than 4096
- * planes are rejected with FDTDBATH_ERR_ARG.  out receives 3 doubles, in device memory when
- * out_on_device is nonzero, else in host memory; the call waits for the simulation's stream.
- * The first call on a device looks the array's address up (a host-side runtime call), so make
- * it before any stream capture on that device.  All calls on a device share the array: calls
- * that overlap on the GPU (e.g. from two streams) race and must be serialized by the caller. */
+ * The paper has no counterpart.  It serves callers that may not allocate device memory at the
+ * moment they need the result: a real-time or latency-bound loop (a cudaMalloc can synchronize
+ * the device and take unbounded time), a host framework that owns the whole device memory pool
+ * and gives this library only the simulation's own buffers, or a process held to a fixed
+ * device-memory budget.  Its scratch space is a static device array of this library holding one
+ * partial sum per plane: boxes deeper than 4096 planes are rejected with FDTDBATH_ERR_ARG.  out
+ * receives 3 doubles, in device memory when out_on_device is nonzero, else in host memory.  The
+ * call may first launch the simulation's pending H half-step, and it waits for the simulation's
+ * stream before returning.  The first call on a device looks the array's address up (a
+ * host-side runtime call, then cached for that device for the life of the process, so the entry
+ * point must not be used on a device after cudaDeviceReset); make that first call before any
+ * stream capture on the device.  All calls on a device share the array, which keeps the last
+ * call's contents: calls that overlap on the GPU (e.g. from two streams) race and must be
+ * serialized by the caller. */
 int fdtdbath_box_energy_noalloc(fdtdbath_sim *sim, int64_t z_lo, int64_t z_hi, double *out,
                                 int32_t out_on_device);
+
+/* Measured fused-multiply-add throughput of the device (flops per second, 2 per FMA) in FP32 or
+ * FP64: the best of reps timed launches of independent FMA chains on every SM (CUDA events; no
+ * clock or power setting is touched).  The paper has no counterpart: it is the arithmetic ceiling
+ * of the step kernels' roofline (the FP64 step is bound by FP64 arithmetic on this part).
+ * Allocates a few KB of device memory for the duration of the call. */
+int fdtdbath_measure_fma_rate(int32_t precision, int32_t device, int32_t reps, double *flops_per_s);
 
 /* ---------------------------------------------------------------------------------------------
  * Discrete adjoint (differentiation form).  The gradient of a scalar loss L of one monitor's

@@ -30,6 +30,7 @@ UNITS = [
     ("plain3d_f64.cu", ["--fmad=false"]),
     ("reduce.cu", ["--fmad=false"]),
     ("noalloc.cu", ["--fmad=false"]),
+    ("peak.cu", []),
     ("cavity1d_f32.cu", []),
     ("cavity1d_f64.cu", ["--fmad=false"]),
     ("batch.cpp", []),

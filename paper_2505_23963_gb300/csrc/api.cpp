@@ -1754,3 +1754,161 @@ int fdtdbath_adjoint_backward(fdtdbath_sim* s, int32_t monitor, const double* dL
   for (size_t j = 2; j < g.size(); ++j) grad[j] = 2.0 * M_PI * g[j];
   return FDTDBATH_OK;
 }
+
+// ---- snapshot / restore of the whole state -------------------------------------------
+namespace {
+
+// Header of a snapshot: the layout it was taken from (checked on restore) and the progress.
+struct SnapHeader {
+  char magic[8];
+  int32_t version, prec, ybf, nmon;
+  int64_t nx, ny, nz, npml, nmatcell, nybath, e_cap;
+  int32_t nfreq[kMaxMon];
+  int64_t n;
+  int32_t pcur, te, ncomp1d, hpend;
+  int64_t state_bytes, dft_bytes, trace_bytes, ring_bytes;
+};
+constexpr char kSnapMagic[8] = {'F', 'D', 'T', 'D', 'B', 'S', 'N', '1'};
+constexpr size_t kSnapHead = 256;
+static_assert(sizeof(SnapHeader) <= kSnapHead, "snapshot header");
+
+SnapHeader snap_header(const fdtdbath_sim* s) {
+  SnapHeader h{};
+  std::memcpy(h.magic, kSnapMagic, 8);
+  h.version = 1;
+  h.prec = s->prec;
+  h.ybf = s->ybf ? 1 : 0;
+  h.nmon = (int32_t)s->mons.size();
+  h.nx = s->nx;
+  h.ny = s->ny;
+  h.nz = s->nz;
+  h.npml = s->npml;
+  h.nmatcell = s->nmatcell;
+  h.nybath = s->nybath;
+  h.e_cap = s->energy_on ? s->e_cap : 0;
+  for (size_t m = 0; m < s->mons.size(); ++m) h.nfreq[m] = s->mons[m].nfreq;
+  h.n = s->n;
+  h.pcur = s->pcur;
+  h.te = s->te ? 1 : 0;
+  h.ncomp1d = s->ncomp1d;
+  h.state_bytes = (int64_t)checkpoint_bytes(const_cast<fdtdbath_sim*>(s));
+  for (auto& mo : s->mons) h.dft_bytes += (int64_t)mo.nfreq * 8 * 8;
+  h.trace_bytes = h.e_cap * 4 * 8;
+  h.hpend = s->h_pending ? 1 : 0;
+  h.ring_bytes = s->ring_stride * 8;
+  return h;
+}
+
+// Copy every piece of a snapshot between the simulation and buf (host or device), in order:
+// header, device state (the checkpoint layout), DFT accumulators, energy trace, and -- while the
+// H half-step of the last step is pending -- the partial sums of that step (its E half).
+int snap_io(fdtdbath_sim* s, char* buf, bool save, bool on_device, bool hpend) {
+  const cudaMemcpyKind to_buf = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  const cudaMemcpyKind from_buf = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  size_t off = kSnapHead;
+  auto piece = [&](void* dev, size_t bytes) -> int {
+    if (bytes) {
+      cudaError_t e = save ? cudaMemcpyAsync(buf + off, dev, bytes, to_buf, s->stream)
+                           : cudaMemcpyAsync(dev, buf + off, bytes, from_buf, s->stream);
+      if (e != cudaSuccess) return cuda_fail(s, e, save ? "snapshot copy" : "restore copy");
+    }
+    off += (bytes + 255) & ~size_t(255);
+    return 0;
+  };
+  for (const StateRef& r : state_refs(s)) {
+    const int rc = piece(r.p, r.bytes);
+    if (rc) return rc;
+  }
+  for (auto& mo : s->mons) {
+    const int rc = piece(mo.dacc, (size_t)mo.nfreq * 8 * 8);
+    if (rc) return rc;
+  }
+  if (s->energy_on) {
+    const int rc = piece(s->trace, (size_t)s->e_cap * 4 * 8);
+    if (rc) return rc;
+  }
+  if (hpend) {
+    const int64_t slot = (s->n - 1) % s->ring_cap;
+    const int rc = piece((double*)s->partial + slot * s->ring_stride, (size_t)s->ring_stride * 8);
+    if (rc) return rc;
+  }
+  const cudaError_t e = cudaStreamSynchronize(s->stream);
+  if (e != cudaSuccess) return cuda_fail(s, e, "snapshot stream");
+  return 0;
+}
+
+// Bytes of a snapshot (with room for the pending step's partial sums, whether pending or not).
+size_t snap_bytes(fdtdbath_sim* s) {
+  size_t n = kSnapHead + checkpoint_bytes(s);
+  for (auto& mo : s->mons) n += ((size_t)mo.nfreq * 64 + 255) & ~size_t(255);
+  if (s->energy_on) n += ((size_t)s->e_cap * 32 + 255) & ~size_t(255);
+  n += ((size_t)s->ring_stride * 8 + 255) & ~size_t(255);
+  return n;
+}
+
+}  // namespace
+
+extern "C" {
+
+int fdtdbath_snapshot_size(fdtdbath_sim* s, size_t* bytes) {
+  if (!s || !bytes) return fail(s, FDTDBATH_ERR_ARG, "NULL argument");
+  *bytes = snap_bytes(s);
+  return FDTDBATH_OK;
+}
+
+int fdtdbath_snapshot(fdtdbath_sim* s, void* dst, size_t dst_bytes, int32_t dst_on_device) {
+  if (!s || !dst) return fail(s, FDTDBATH_ERR_ARG, "NULL argument");
+  if (dst_bytes < snap_bytes(s)) return fail(s, FDTDBATH_ERR_ARG, "snapshot buffer smaller than fdtdbath_snapshot_size");
+  cudaSetDevice(s->device);
+  // the partial sums of every complete step folded into the spectra and the trace; a pending H
+  // half-step stays pending (the resumed run computes it in the launch the original would have)
+  int rc = reduce_upto(s, s->h_pending ? s->n - 1 : s->n);
+  if (rc) return rc;
+  const SnapHeader h = snap_header(s);
+  if (dst_on_device) {
+    cudaError_t e = cudaMemcpyAsync(dst, &h, sizeof(h), cudaMemcpyHostToDevice, s->stream);
+    if (e != cudaSuccess) return cuda_fail(s, e, "snapshot header");
+  } else {
+    std::memcpy(dst, &h, sizeof(h));
+  }
+  return snap_io(s, (char*)dst, true, dst_on_device != 0, h.hpend != 0);
+}
+
+int fdtdbath_restore(fdtdbath_sim* s, const void* src, size_t src_bytes, int32_t src_on_device) {
+  if (!s || !src) return fail(s, FDTDBATH_ERR_ARG, "NULL argument");
+  cudaSetDevice(s->device);
+  if (src_bytes < snap_bytes(s)) return fail(s, FDTDBATH_ERR_ARG, "snapshot smaller than this simulation's state");
+  SnapHeader h{};
+  if (src_on_device) {
+    cudaError_t e = cudaMemcpy(&h, src, sizeof(h), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(s, e, "restore header");
+  } else {
+    std::memcpy(&h, src, sizeof(h));
+  }
+  SnapHeader mine = snap_header(s);
+  const bool same = std::memcmp(h.magic, kSnapMagic, 8) == 0 && h.version == 1 && h.prec == mine.prec &&
+                    h.ybf == mine.ybf && h.nmon == mine.nmon && h.nx == mine.nx && h.ny == mine.ny &&
+                    h.nz == mine.nz && h.npml == mine.npml && h.nmatcell == mine.nmatcell &&
+                    h.nybath == mine.nybath && h.e_cap == mine.e_cap &&
+                    std::memcmp(h.nfreq, mine.nfreq, sizeof(h.nfreq)) == 0 && h.state_bytes == mine.state_bytes &&
+                    h.ring_bytes == mine.ring_bytes && h.n >= 0 && (h.pcur == 0 || h.pcur == 1) &&
+                    (h.ncomp1d == 1 || h.ncomp1d == 3) && (h.hpend == 0 || (h.hpend == 1 && h.n > 0));
+  if (!same) return fail(s, FDTDBATH_ERR_ARG, "the snapshot was taken from a simulation of another layout");
+  int rc = flush_all(s);   // nothing of this simulation's own queue may land after the restore
+  if (rc) return rc;
+  if (s->ncomp1d == 1 && h.ncomp1d == 3) {
+    rc = switch_to_3d(s);   // the snapshot's 1D simulation had left the persistent 1D kernel
+    if (rc) return rc;
+  }
+  s->n = h.n;   // the ring slot of a pending step is addressed through n
+  rc = snap_io(s, (char*)const_cast<void*>(src), false, src_on_device != 0, h.hpend != 0);
+  if (rc) return rc;
+  s->h_pending = h.hpend != 0;
+  s->reduced = s->h_pending ? h.n - 1 : h.n;
+  s->pcur = h.pcur;
+  if (!h.te) s->te = false;
+  s->adj.recorded = false;
+  return FDTDBATH_OK;
+}
+
+}  // extern "C"

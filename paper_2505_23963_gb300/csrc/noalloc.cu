@@ -1,10 +1,12 @@
 // noalloc.cu -- energy of a z-box of the current state, computed without allocating memory.
 //
-// Some callers cannot allocate device memory at the moment they need a result: a caller
-// that only runs inside a stream capture, a real-time loop that forbids allocation after
-// start-up, or a host framework that owns the whole device memory pool and hands this
-// library nothing beyond the simulation's own buffers.  fdtdbath_box_energy_noalloc serves
-// them: its scratch space is the file-scope device array below, not an allocation.
+// Some callers may not allocate device memory at the moment they need a result: a real-time
+// or latency-bound loop (an allocation can synchronize the device and take unbounded time), a
+// host framework that owns the whole device memory pool and hands this library nothing beyond
+// the simulation's own buffers, or a process held to a fixed device-memory budget.
+// fdtdbath_box_energy_noalloc serves them: its scratch space is the file-scope device array
+// below, not an allocation.  The call may launch the simulation's pending H half-step and waits
+// for the simulation's stream.
 //
 // The array holds one FP64 partial sum per plane and quantity for at most
 // kNoAllocMaxPlanes planes (about 96 KB), and every GPU that loads this library keeps it
@@ -100,9 +102,10 @@ __global__ void box_energy_sum_kernel(double* scratch, int nplanes, double ew) {
   scratch[3 * kNoAllocMaxPlanes + threadIdx.x] = 0.5 * ew * s;
 }
 
-// Device address of the scratch array on the current device, looked up once per device.
-// The lookup is a host call (cudaGetSymbolAddress): the first call on a device should come
-// before any stream capture on it.
+// Device address of the scratch array on the current device, looked up once per device and
+// cached for the life of the process (an address of the device's primary context: not valid
+// after cudaDeviceReset).  The lookup is a host call (cudaGetSymbolAddress): the first call on a
+// device should come before any stream capture on it.
 double* scratch_address(int device, cudaError_t* err) {
   static std::mutex mu;
   static double* addr[kNoAllocMaxDevices] = {};

@@ -123,6 +123,14 @@ def lib(build_if_missing: bool = True):
         L.fdtdbath_last_error.argtypes = [vp]
         L.fdtdbath_destroy.restype = None
         L.fdtdbath_destroy.argtypes = [vp]
+        L.fdtdbath_snapshot_size.restype = i32
+        L.fdtdbath_snapshot_size.argtypes = [vp, C.POINTER(C.c_size_t)]
+        L.fdtdbath_snapshot.restype = i32
+        L.fdtdbath_snapshot.argtypes = [vp, vp, C.c_size_t, i32]
+        L.fdtdbath_restore.restype = i32
+        L.fdtdbath_restore.argtypes = [vp, vp, C.c_size_t, i32]
+        L.fdtdbath_measure_fma_rate.restype = i32
+        L.fdtdbath_measure_fma_rate.argtypes = [i32, i32, i32, dp]
         L.fdtdbath_bath_form.restype = i32
         L.fdtdbath_bath_form.argtypes = [i32, C.c_double, C.c_double, i32, C.c_double,
                                          C.c_double, C.c_double, dp, dp, dp]
@@ -182,6 +190,13 @@ def _f64(a) -> np.ndarray:
 
 
 # ------------------------------------------------------------------ C-named wrappers
+def measure_fma_rate(precision: int, device: int = 0, reps: int = 5) -> float:
+    """fdtdbath_measure_fma_rate: the device's measured FMA throughput in flops per second."""
+    out = C.c_double(0.0)
+    _check(lib().fdtdbath_measure_fma_rate(int(precision), int(device), int(reps), C.byref(out)))
+    return float(out.value)
+
+
 def bath_form(shape: str, frequency: float, gamma: float, num_bath: int, width: float,
               bath_gamma: float, dephasing: float):
     """Table I expansion (fdtdbath_bath_form): returns (frequencies, gammas, couplings)."""
@@ -390,6 +405,19 @@ class Simulation:
     def adjoint_te_form(self) -> bool:
         """Whether the last reverse sweep ran the TE form (query key 6)."""
         return query(self.h, 6) == 1
+
+    def snapshot(self) -> np.ndarray:
+        """fdtdbath_snapshot into host memory: the whole state as an opaque byte array."""
+        n = C.c_size_t(0)
+        _check(lib().fdtdbath_snapshot_size(self.h, C.byref(n)), self.h)
+        buf = np.empty(n.value, dtype=np.uint8)
+        _check(lib().fdtdbath_snapshot(self.h, buf.ctypes.data, buf.nbytes, 0), self.h)
+        return buf
+
+    def restore(self, buf: np.ndarray):
+        """fdtdbath_restore from a host snapshot taken by snapshot()."""
+        buf = np.ascontiguousarray(buf, dtype=np.uint8)
+        _check(lib().fdtdbath_restore(self.h, buf.ctypes.data, buf.nbytes, 0), self.h)
 
     def plain_kernel(self) -> bool:
         """Whether the z-chunks without bath modes run the plain-plane kernel (query key 7)."""

@@ -41,3 +41,14 @@ def test_spectrum_is_finite_reads_the_error_code():
     assert not bench.spectrum_is_finite(fb, Sim(fb.ERR_NONFINITE))
     with pytest.raises(fb.FdtdBathError):
         bench.spectrum_is_finite(fb, Sim(fb.ERR_CUDA))
+
+
+def test_fp64_flop_count():
+    """FP64 literal path: vacuum 30 per cell, +16 in the CPML, Drude +24, a Lorentz-Bath plane
+    51 N_b + 112, +7 inside the energy box.  256^3, N_b = 8: (144 x 30 + 32 x 46 + 16 x 54 +
+    64 x (520 + 7)) per column."""
+    p = wl.slab_3d(steps=10)
+    col = 144 * 30 + 32 * 46 + 16 * 54 + 64 * (51 * 8 + 112 + 7)
+    assert bench.algorithmic_flops_fp64(p) == col * 256 * 256
+    q = dict(p, materials=[], energy_box=(0, 0))
+    assert bench.algorithmic_flops_fp64(q) == (224 * 30 + 32 * 46) * 256 * 256
