@@ -221,7 +221,9 @@ int fdtdbath_bath_form(int32_t shape, double frequency, double gamma, int32_t nu
  * fdtdbath_adjoint_backward ran the TE form of the reverse sweep (a TE forward run and dL_dF zero
  * for the E_x and H_y spectra).  Key 7: whether the z-chunks without bath modes run the
  * plain-plane kernel (grids of at least 8 rows tiled exactly by its 128 x 8 FP32 or 64 x 8 FP64
- * tiles, ny a multiple of 8, no source plane inside a layer) instead of the general kernel. */
+ * tiles, ny a multiple of 8, no source plane inside a layer) instead of the general kernel.
+ * Key 8: whether the steps run on the persistent 1D cavity kernel (nx = ny = 1, at most one
+ * source and one monitor, at most 32 bath modes per material, x polarization only). */
 int64_t fdtdbath_query(const fdtdbath_sim *sim, int32_t key);
 
 /* Energy (U_EM, U_P, U_bath) of planes z_lo <= k < z_hi of the current state -- the same

@@ -1379,6 +1379,7 @@ int64_t fdtdbath_query(const fdtdbath_sim* s, int32_t key) {
     case 5: return s->te && s->ty == 1 ? 1 : 0;
     case 6: return s->adj_te ? 1 : 0;
     case 7: return s->plain_ok ? 1 : 0;
+    case 8: return s->path1d && s->ncomp1d == 1 ? 1 : 0;
     default: return -1;
   }
 }

@@ -419,6 +419,10 @@ class Simulation:
         buf = np.ascontiguousarray(buf, dtype=np.uint8)
         _check(lib().fdtdbath_restore(self.h, buf.ctypes.data, buf.nbytes, 0), self.h)
 
+    def cavity_1d_kernel(self) -> bool:
+        """Whether the steps run on the persistent 1D cavity kernel (query key 8)."""
+        return query(self.h, 8) == 1
+
     def plain_kernel(self) -> bool:
         """Whether the z-chunks without bath modes run the plain-plane kernel (query key 7)."""
         return query(self.h, 7) == 1

@@ -132,3 +132,20 @@ def test_plain_kernel_step_calls_compose_bitwise():
     for name in ("E", "H", "P", "Pm"):
         for c in range(3):
             assert np.array_equal(a.get(name, comp=c), b.get(name, comp=c)), (name, c)
+
+
+@pytest.mark.parametrize("precision", [64, 32])
+def test_eps_layers_on_ragged_tiles_match_oracle(precision):
+    """The same cavity (eps_inf = 2.25 spacer, 1.5 Drude mirrors, 2.0 Lorentz-Bath layer) on a
+    grid its tiles do not cover: every plane runs the general kernel with ragged x / y tiles."""
+    prob = plain_cavity(nx=40, ny=12, steps=120)
+    g = fb.Simulation(prob, precision=precision, energy_capacity=200)
+    assert not g.plain_kernel()
+    o = O.OracleSim(prob, trace_cap=200)
+    g.step(120)
+    o.step(120)
+    assert_errs(compare(g, o, prob, precision), precision, sens=oracle_sensitivity(prob, 120))
+    assert rel(g.dft(0), o.dft(0)) < TOL[precision]
+    tg, to = g.trace(), o.trace()
+    for col in range(3):
+        assert rel(tg[:, col], to[:, col]) < TOL[precision], col
