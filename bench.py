@@ -636,19 +636,20 @@ def run_ours(args):
     # ---- roofline of the step kernel ----
     hbm, peak_kind = peaks()
     bytes32 = algorithmic_bytes(prob, 4)
-    # one step = the launch pair of the step kernel (bath-free chunks on a side stream joined
-    # back into the simulation's stream, bath chunks on it); its average duration over the timed
-    # region comes from the events on the simulation's stream (plus one reduce + DFT per 256 steps)
+    # one step = the launch pair of the plain-plane kernel (the bath-free chunks on a side stream
+    # beside its Lorentz-Bath form over the bath chunks on the simulation's stream, joined back into
+    # it); its average duration over the timed region comes from the events on the simulation's
+    # stream (plus one reduce + DFT per 256 steps)
     step_ms = ms32 / args.steps
     achieved = bytes32 / (step_ms * 1e-3) / 1e9
     traffic = None
-    prof = os.path.join(ROOT, "profiles", "step3d_f32_slab3d_traffic.json")
+    prof = os.path.join(ROOT, "profiles", "plain3d_f32_slab3d_traffic.json")
     if os.path.exists(prof) and not args.grid:
         try:
             import hashlib
             with open(prof) as f:
                 rec = json.load(f)
-            with open(os.path.join(ROOT, "paper_2505_23963_gb300", "csrc", "step3d.cuh"), "rb") as f:
+            with open(os.path.join(ROOT, "paper_2505_23963_gb300", "csrc", "plain3d.cuh"), "rb") as f:
                 cur = hashlib.sha256(f.read()).hexdigest()[:16]
             # counters describe the kernel they were taken on: none once it has changed
             traffic = rec.get("dram_bytes_per_step") if rec.get("source_sha256_16") == cur else None
@@ -676,7 +677,8 @@ def run_ours(args):
                  "kernel_ms": kms64, "finite": ok64, "roofline": roof64},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": achieved / hbm, "traffic": traffic, "peak_kind": peak_kind,
-                     "kernel": "step3d_kernel<float> (launch pair of one step)", "kernel_ms": step_ms,
+                     "kernel": "plain3d_kernel<float> (launch pair of one step: bath-free chunks, "
+                               "Lorentz-Bath form)", "kernel_ms": step_ms,
                      "kernel_ms_single_call": kms32,
                      "algorithmic_bytes_per_launch": bytes32},
         "cpu_baseline": cpu,

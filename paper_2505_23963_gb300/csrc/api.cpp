@@ -132,13 +132,18 @@ struct fdtdbath_sim {
   // write could make one of them nonzero
   bool te = false;
   bool adj_te = false;      // the last reverse sweep ran the TE form
-  // plain-plane kernel (plain3d.cuh) for the chunks without bath planes: grids of at least 8 rows,
-  // nx a multiple of 4, every source plane outside the layers; planes staged ahead by it
+  // plain-plane kernel (plain3d.cuh) for the chunks without bath planes: grids tiled exactly by
+  // its TX x 8 tiles (TX = 128 FP32, 64 FP64 cells), every source plane outside the layers
   bool plain_ok = false;
   PlainMaps maps{};         // its tensor maps of the E and H arrays
-  // the bath-free and bath launches of a step one after the other on the simulation's stream (with
-  // the plain-plane kernel: its CTAs and the bath kernel's lose more to sharing SMs than they gain
-  // from overlapping), or concurrently on two streams (with the general kernel's bath-free form)
+  // its one-cell-per-thread form for the Lorentz-Bath chunks: FP32 with FP32 bath storage, at most
+  // 8 bath modes per material, 32 x 8 tiles; chunks of at most 64 planes
+  bool bath_plain = false;
+  PlainMaps bmaps{};        // tensor maps of 32-cell-wide boxes
+  BathMaps bath_maps{};     // tensor maps of its polarization and bath-mode arrays
+  // the bath-free and bath launches of a step one after the other on the simulation's stream (the
+  // plain-plane kernel beside the general kernel's bath instantiation: their CTAs lose more to
+  // sharing SMs than they gain from overlapping), or concurrently on two streams (otherwise)
   bool serial_pair = false;
   void* errflag = nullptr;  // device int: a bounded wait of a kernel ran out (FDTDBATH_ERR_TIMEOUT)
   AdjState adj;
@@ -216,7 +221,8 @@ bool chunk_has_bath(const fdtdbath_sim* s, int64_t lo, int64_t hi) {
 // Between those cuts, a range of L planes is split into chunks of zc planes (uniform plan), or
 // (balanced plan) into a head chunk of ceil(3L/4) planes and a tail chunk of the rest: dispatched
 // longest first, the tail chunks of a launch fill its last partial wave of CTAs.
-int plan_chunks(fdtdbath_sim* s, int zc, bool balanced, int plain_zc, std::vector<int>& starts) {
+int plan_chunks(fdtdbath_sim* s, int zc, bool balanced, int plain_zc, int bath_zc, int bath_nmin,
+                std::vector<int>& starts) {
   starts.clear();
   starts.push_back(0);
   const int64_t lo_ok = s->npml + 1, hi_ok = s->nz - 1 - s->npml;
@@ -232,10 +238,14 @@ int plan_chunks(fdtdbath_sim* s, int zc, bool balanced, int plain_zc, std::vecto
   for (size_t b = 0; b + 1 < bounds.size(); ++b) {
     const int64_t a = bounds[b], e = bounds[b + 1];
     if (z >= e) continue;   // already covered by a chunk the boundary rule extended
-    if (plain_zc > 0 && !chunk_has_bath(s, z, e)) {
-      // ranges without bath planes (the plain-plane kernel): near-equal chunks of about plain_zc
+    const bool bath = chunk_has_bath(s, z, e);
+    const int nzc = bath ? bath_zc : plain_zc;
+    if (nzc > 0) {
+      // ranges of the plain-plane kernel (without bath planes): near-equal chunks of about nzc
+      // planes; of its bath form: near-equal chunks of at most nzc planes, at least bath_nmin
       const int64_t z0 = z, L = e - z0;
-      const int64_t n = std::max<int64_t>(1, (L + plain_zc / 2) / plain_zc);
+      const int64_t n = bath ? std::max<int64_t>((L + nzc - 1) / nzc, std::min<int64_t>(L, bath_nmin))
+                             : std::max<int64_t>(1, (L + nzc / 2) / nzc);
       for (int64_t i = 1; i <= n && z < e; ++i) {
         int64_t nx = z0 + (L * i) / n;
         if (nx < lo_ok) nx = lo_ok;
@@ -282,7 +292,7 @@ void source_amp(const HostSrc& q, double t, double* a, double* b) {
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-bool encode_plain_maps(fdtdbath_sim* s) {
+EncodeTiledFn tensor_map_encoder() {
   static EncodeTiledFn fn = nullptr;
   static bool looked_up = false;
   if (!looked_up) {
@@ -293,23 +303,66 @@ bool encode_plain_maps(fdtdbath_sim* s) {
         q == cudaDriverEntryPointSuccess)
       fn = (EncodeTiledFn)f;
   }
+  return fn;
+}
+
+bool encode_plain_maps(fdtdbath_sim* s, int tile_x, PlainMaps* out) {
+  const EncodeTiledFn fn = tensor_map_encoder();
   if (!fn) return false;
   const cuuint64_t esz = s->esz;
   const cuuint64_t dims[5] = {(cuuint64_t)s->nx, (cuuint64_t)s->ny, (cuuint64_t)s->nz, 3, 2};
   const cuuint64_t strides[4] = {(cuuint64_t)s->nx * esz, (cuuint64_t)s->plane * esz, (cuuint64_t)s->ncell * esz,
                                  3 * (cuuint64_t)s->ncell * esz};
   const cuuint32_t es[5] = {1, 1, 1, 1, 1};
-  const cuuint32_t tx = (cuuint32_t)plain_tile_x(s->prec);
+  const cuuint32_t tx = (cuuint32_t)tile_x;
   const CUtensorMapDataType dt = s->prec == 64 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
   auto enc = [&](CUtensorMap* m, void* base, cuuint32_t bx, cuuint32_t by) {
     const cuuint32_t box[5] = {bx, by, 1, 3, 1};
     return fn(m, dt, 5, base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
   };
-  return enc(&s->maps.e_main, s->E[0], tx, 8) && enc(&s->maps.e_row, s->E[0], tx, 1) &&
-         enc(&s->maps.e_pad8, s->E[0], 4, 8) && enc(&s->maps.e_pad1, s->E[0], 4, 1) &&
-         enc(&s->maps.h_main, s->H[0], tx, 8) && enc(&s->maps.h_row, s->H[0], tx, 1) &&
-         enc(&s->maps.h_pad8, s->H[0], 4, 8);
+  return enc(&out->e_main, s->E[0], tx, 8) && enc(&out->e_row, s->E[0], tx, 1) &&
+         enc(&out->e_pad8, s->E[0], 4, 8) && enc(&out->e_pad1, s->E[0], 4, 1) &&
+         enc(&out->h_main, s->H[0], tx, 8) && enc(&out->h_row, s->H[0], tx, 1) &&
+         enc(&out->h_pad8, s->H[0], 4, 8);
+}
+
+// Tensor maps of the bath form's state staging (BathMaps): for each Lorentz-Bath material with
+// modes (at most kBathPlainMaxMats) and each of the two state slots, P (x, y, z in the layer,
+// component) and the bath modes (x, y, z in the layer, component * nb + mode), FP32, boxes of one
+// kBathTileX x 8 tile of one plane.
+bool encode_bath_maps(fdtdbath_sim* s, BathMaps* out) {
+  const EncodeTiledFn fn = tensor_map_encoder();
+  if (!fn || s->prec != 32) return false;
+  *out = BathMaps{};
+  for (size_t m = 0; m < s->mats.size(); ++m) {
+    const HostMat& M = s->mats[m];
+    if (M.kind != FDTDBATH_LORENTZ_BATH || M.nb == 0) continue;
+    if (out->nmat == kBathPlainMaxMats) return false;
+    const int i = out->nmat++;
+    out->mat[i] = (int)m;
+    const cuuint64_t nzm = (cuuint64_t)(M.zhi - M.zlo);
+    const cuuint32_t es[4] = {1, 1, 1, 1};
+    for (int b = 0; b < 2; ++b) {
+      const cuuint64_t ydims[4] = {(cuuint64_t)s->nx, (cuuint64_t)s->ny, nzm, 3 * (cuuint64_t)M.nb};
+      const cuuint64_t ystr[3] = {(cuuint64_t)s->nx * 4, (cuuint64_t)s->plane * 4, (cuuint64_t)M.ncell * 4};
+      const cuuint32_t ybox[4] = {(cuuint32_t)kBathTileX, 8, 1, 3 * (cuuint32_t)M.nb};
+      const cuuint64_t pdims[4] = {(cuuint64_t)s->nx, (cuuint64_t)s->ny, nzm, 3};
+      const cuuint64_t pstr[3] = {(cuuint64_t)s->nx * 4, (cuuint64_t)s->plane * 4, (cuuint64_t)s->nmatcell * 4};
+      const cuuint32_t pbox[4] = {(cuuint32_t)kBathTileX, 8, 1, 3};
+      void* yb = (char*)s->Yslot[b] + M.ybase * 4;
+      void* pb = (char*)s->Pslot[b] + M.base * 4;
+      if (fn(&out->y[i][b], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, yb, ydims, ystr, ybox, es,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return false;
+      if (fn(&out->pp[i][b], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, pb, pdims, pstr, pbox, es,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return false;
+    }
+  }
+  return out->nmat > 0;
 }
 
 template <typename T>
@@ -406,6 +459,23 @@ int launch_plain_typed(const Step3DParams<double>& p, const fdtdbath_sim* s, int
   return launch_plain3d_f64(p, s->maps, s->ecur, s->hcur, n, st);
 }
 
+int launch_bath_typed(const Step3DParams<float>& p, const fdtdbath_sim* s, int n, cudaStream_t st) {
+  return launch_bath3d_f32(p, s->bmaps, s->bath_maps, s->pcur, s->ecur, s->hcur, n, s->nbmax, st);
+}
+int launch_bath_typed(const Step3DParams<double>&, const fdtdbath_sim*, int, cudaStream_t) {
+  return (int)cudaErrorInvalidValue;   // FP64 runs the general kernel (bath_plain is never set)
+}
+
+// Chunks with bath planes: the plain-plane kernel's bath form when it applies (both half-steps of
+// a step), otherwise the general kernel with the simulation's bath-mode bound.
+template <typename T>
+int launch_bath_chunks(fdtdbath_sim* s, Step3DParams<T> p, int id_off, int n, cudaStream_t st) {
+  if (!(s->bath_plain && p.doH && p.doE)) return launch_chunks<T>(s, p, s->nbmax, id_off, n, st);
+  p.chunk_ids = (const int*)s->chunk_ids + id_off;
+  s->launches++;
+  return launch_bath_typed(p, s, n, st);
+}
+
 // Chunks without bath planes: the plain-plane kernel when it applies (both half-steps of a step),
 // otherwise the general kernel's bath-free instantiation.
 template <typename T>
@@ -426,17 +496,17 @@ int launch_all(fdtdbath_sim* s, int doH, int doE) {
   if (!doE) return launch_chunks<T>(s, p, 0, 0, s->nchunks, s->stream);
   if (s->nbmax == 0) return launch_plain_chunks<T>(s, p, 0, s->nchunks, s->stream);
   if (s->nbath == 0) return launch_chunks<T>(s, p, s->nbmax, 0, s->nchunks, s->stream);
-  if (s->nplain == 0) return launch_chunks<T>(s, p, s->nbmax, s->nchunks, s->nbath, s->stream);
+  if (s->nplain == 0) return launch_bath_chunks<T>(s, p, s->nchunks, s->nbath, s->stream);
   if (s->serial_pair) {
     const int rc = launch_plain_chunks<T>(s, p, s->nchunks, s->nplain, s->stream);
-    return rc ? rc : launch_chunks<T>(s, p, s->nbmax, s->nchunks + s->nplain, s->nbath, s->stream);
+    return rc ? rc : launch_bath_chunks<T>(s, p, s->nchunks + s->nplain, s->nbath, s->stream);
   }
   cudaError_t e = cudaEventRecord(s->ev_fork, s->stream);
   if (e == cudaSuccess) e = cudaStreamWaitEvent(s->side, s->ev_fork, 0);
   if (e != cudaSuccess) return (int)e;
   int rc = launch_plain_chunks<T>(s, p, s->nchunks, s->nplain, s->side);
   if (rc) return rc;
-  rc = launch_chunks<T>(s, p, s->nbmax, s->nchunks + s->nplain, s->nbath, s->stream);
+  rc = launch_bath_chunks<T>(s, p, s->nchunks + s->nplain, s->nbath, s->stream);
   if (rc) return rc;
   e = cudaEventRecord(s->ev_join, s->side);
   if (e == cudaSuccess) e = cudaStreamWaitEvent(s->stream, s->ev_join, 0);
@@ -921,25 +991,48 @@ int fdtdbath_create(const fdtdbath_grid* grid, double resolution, double courant
   // by its (TX x 8) tiles whose source planes lie outside the layers, when the tensor maps can be
   // encoded (FDTDBATH_PLAIN=0 keeps the general kernel); those ranges are then cut into near-equal
   // chunks of about plain_zc planes (FDTDBATH_PLAIN_ZCHUNK, at most 64)
+  // Its bath form (FP32 with FP32 bath storage, at most 8 modes per material in at most two
+  // Lorentz-Bath materials, 32 x 8 tiles) takes the Lorentz-Bath ranges, cut into near-equal
+  // chunks of about bath_zc planes (FDTDBATH_BATH_ZCHUNK, at most 64; FDTDBATH_BATHPLAIN=0 keeps
+  // the general kernel there).  One chunk per layer of up to 64 planes measured fastest on the
+  // 256^3 slab: each chunk start pays the prologue and the first stages' latency.
   {
+    bool src_in_layer = false;
+    for (auto& q : s->srcs)
+      for (auto& m : s->mats)
+        if (q.z >= m.zlo && q.z < m.zhi) src_in_layer = true;
     const int tx = plain_tile_x(s->prec);
     const char* e = std::getenv("FDTDBATH_PLAIN");
-    s->plain_ok = !(e && std::atoi(e) == 0) && s->ty == 8 && nx % tx == 0 && ny % 8 == 0;
+    s->plain_ok = !(e && std::atoi(e) == 0) && s->ty == 8 && nx % tx == 0 && ny % 8 == 0 && !src_in_layer;
+    const char* eb = std::getenv("FDTDBATH_BATHPLAIN");
+    s->bath_plain = !(eb && std::atoi(eb) == 0) && s->prec == 32 && !s->ybf && s->nbmax > 0 &&
+                    s->nbmax <= kBathPlainMaxModes && s->ty == 8 && nx % kBathTileX == 0 && ny % 8 == 0 &&
+                    !src_in_layer;
   }
-  for (auto& q : s->srcs)
-    for (auto& m : s->mats)
-      if (q.z >= m.zlo && q.z < m.zhi) s->plain_ok = false;
-  int plain_zc = 0;
+  int plain_zc = 0, bath_zc = 0, bath_nmin = 1;
   if (s->plain_ok) {
     plain_zc = 16;
     if (const char* e = std::getenv("FDTDBATH_PLAIN_ZCHUNK")) plain_zc = std::min(64, std::max(1, std::atoi(e)));
+  }
+  if (s->bath_plain) {
+    // chunks of at most 64 planes, and enough of them for a CTA on every SM
+    bath_zc = 64;
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s->device) == cudaSuccess && sms > 0) {
+      const int64_t tiles = (nx / kBathTileX) * (ny / 8);
+      bath_nmin = (int)((sms + tiles - 1) / tiles);
+    }
+    if (const char* e = std::getenv("FDTDBATH_BATH_ZCHUNK")) {
+      bath_zc = std::min(64, std::max(1, std::atoi(e)));
+      bath_nmin = 1;
+    }
   }
   std::vector<int> starts;
   if (balanced) {
     int sms = 0;
     balanced = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s->device) == cudaSuccess && sms > 0;
     if (balanced) {
-      const int n = plan_chunks(s, zc, true, plain_zc, starts);
+      const int n = plan_chunks(s, zc, true, plain_zc, bath_zc, bath_nmin, starts);
       int64_t nplain = 0, nbath = 0;
       for (int c = 0; c < n; ++c) {
         if (starts[c + 1] - starts[c] > 128) balanced = false;
@@ -959,9 +1052,9 @@ int fdtdbath_create(const fdtdbath_grid* grid, double resolution, double courant
     const int64_t ktiles = te0 ? (nx + 4 * kTX - 1) / (4 * kTX) : (int64_t)s->nbx * s->nby;
     if (ktiles < 64) zc = 16;
   }
-  s->nchunks = plan_chunks(s, zc, balanced, plain_zc, starts);
+  s->nchunks = plan_chunks(s, zc, balanced, plain_zc, bath_zc, bath_nmin, starts);
   for (int c = 0; c < s->nchunks; ++c)   // the plain-plane kernel takes chunks of at most 64 planes
-    if (!chunk_has_bath(s, starts[c], starts[c + 1]) && starts[c + 1] - starts[c] > 64) s->plain_ok = false;
+    if (starts[c + 1] - starts[c] > 64) (chunk_has_bath(s, starts[c], starts[c + 1]) ? s->bath_plain : s->plain_ok) = false;
   for (size_t c = 0; c + 1 < starts.size(); ++c)
     if (starts[c + 1] - starts[c] > 128) return bail(FDTDBATH_ERR_ARG, "z-chunk longer than 128 planes");
   if ((int64_t)s->nbx * s->nby > 65535 * 64) return bail(FDTDBATH_ERR_ARG, "grid too large for the launch plan");
@@ -984,8 +1077,13 @@ int fdtdbath_create(const fdtdbath_grid* grid, double resolution, double courant
     if (!s->psiH[b] || !s->Pslot[b] || !s->Yslot[b])
       return bail(FDTDBATH_ERR_OOM, "device allocation failed");
   }
-  if (s->plain_ok && !encode_plain_maps(s)) s->plain_ok = false;   // no tensor-map encoder: general kernel
-  s->serial_pair = s->plain_ok;
+  // no tensor-map encoder: the general kernel
+  if (s->plain_ok && !encode_plain_maps(s, plain_tile_x(s->prec), &s->maps)) s->plain_ok = false;
+  if (s->bath_plain && !(encode_plain_maps(s, kBathTileX, &s->bmaps) && encode_bath_maps(s, &s->bath_maps)))
+    s->bath_plain = false;
+  // the plain-plane kernel beside the general kernel's bath form: one after the other; beside its
+  // own bath form: concurrently (the two kinds of CTAs fit on one SM together)
+  s->serial_pair = s->plain_ok && !s->bath_plain;
   s->psiE = dalloc(s, 2 * (size_t)(2 * s->npml) * s->plane * esz);
   s->pmlE = dalloc(s, 2 * (size_t)nz * esz);
   s->pmlH = dalloc(s, 2 * (size_t)nz * esz);
@@ -1380,6 +1478,7 @@ int64_t fdtdbath_query(const fdtdbath_sim* s, int32_t key) {
     case 6: return s->adj_te ? 1 : 0;
     case 7: return s->plain_ok ? 1 : 0;
     case 8: return s->path1d && s->ncomp1d == 1 ? 1 : 0;
+    case 9: return s->bath_plain ? 1 : 0;
     default: return -1;
   }
 }

@@ -50,7 +50,10 @@ constexpr int TY = 8;                          // rows of a tile = compute warps
 constexpr int kMaxPlanes = 64;                 // planes per z-chunk of this kernel
 constexpr uint64_t kWaitLimitNs = 1000000000;  // a stage not complete after 1 s is an error
 // per-plane table bits (material index + 1 in the low four bits)
-enum : int { kBox = 0x10, kMonE = 0x20, kMonH = 0x40, kSrc = 0x80, kPmlE = 0x100, kPmlH = 0x200, kTop = 0x400 };
+enum : int {
+  kBox = 0x10, kMonE = 0x20, kMonH = 0x40, kSrc = 0x80, kPmlE = 0x100, kPmlH = 0x200, kTop = 0x400,
+  kBath = 0x800   // a Lorentz-Bath plane with bath modes
+};
 
 __device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
 
@@ -96,6 +99,15 @@ __device__ __forceinline__ void tma_load5(unsigned sdst, const void* tmap, int x
       : "memory");
 }
 
+// Tensor copy of a 4-D box (coordinates x, y, z, m), as tma_load5.
+__device__ __forceinline__ void tma_load4(unsigned sdst, const void* tmap, int x, int y, int z, int m, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
+      "[%6];\n" ::"r"(sdst),
+      "l"(reinterpret_cast<uint64_t>(tmap)), "r"(x), "r"(y), "r"(z), "r"(m), "r"(smem_u32(bar))
+      : "memory");
+}
+
 // VX-cell vectors (8 or 16 bytes, naturally aligned)
 template <typename T, int VX>
 struct Vec;
@@ -122,6 +134,11 @@ struct Vec<float, 2> {
   static __device__ __forceinline__ void st(void* p, const float* v) {
     *reinterpret_cast<float2*>(p) = make_float2(v[0], v[1]);
   }
+};
+template <typename T>
+struct Vec<T, 1> {
+  static __device__ __forceinline__ void ld(const void* p, T* o) { o[0] = *reinterpret_cast<const T*>(p); }
+  static __device__ __forceinline__ void st(void* p, const T* v) { *reinterpret_cast<T*>(p) = v[0]; }
 };
 template <>
 struct Vec<double, 2> {
@@ -183,11 +200,13 @@ __device__ __forceinline__ double slot_total(const double* red, int q, int h) {
   return s;
 }
 
-template <typename T, int VX_, int A>
+template <typename T, int VX_, int A, int NB = 0>
 struct Plain3DLayout {
   static constexpr int VX = VX_, TY = plain::TY, TX = 32 * VX;
   static constexpr int NE = A + 1, NH = A;   // E and H_in frame slots
-  static constexpr int threads = 32 * (TY + 1);
+  // the helper warp (NB = 0); the bath form runs without it, its 8 warps sized for 128 registers
+  static constexpr bool HELPER = NB == 0;
+  static constexpr int threads = 32 * (TY + (HELPER ? 1 : 0));
   static constexpr unsigned SZ = sizeof(T);
   static constexpr unsigned r128(unsigned b) { return (b + 127u) & ~127u; }
   // An E frame slot (each part one box, box-dense, 128-byte aligned): main [3][TY][TX] rows
@@ -207,20 +226,39 @@ struct Plain3DLayout {
   // H^n buffers [2][Hx, Hz][TY + 1][TX] (row 0: y0-1), then mbarriers [A], plane table [kMaxPlanes]
   static constexpr unsigned XS = 2u * (TY + 1) * TX * SZ;
   static constexpr unsigned OFF_E = 0, OFF_HIN = NE * ES, OFF_SH = OFF_HIN + NH * HS, OFF_MBAR = OFF_SH + 2 * XS;
-  static constexpr unsigned OFF_INFO = OFF_MBAR + ((8 * A + 15) / 16) * 16;
-  static constexpr unsigned bytes = OFF_INFO + plain::kMaxPlanes * 4 + 128;   // + alignment slack
+  // mbarriers: one per frame stage, one for the bath state
+  static constexpr unsigned OFF_INFO = OFF_MBAR + ((8 * (A + 1) + 15) / 16) * 16;
+  // bath-mode coefficient rows of every material ([modes][kCoefStride], at most kMaxMat NB rows)
+  static constexpr unsigned OFF_COEF = OFF_INFO + plain::kMaxPlanes * 4;
+  static constexpr unsigned COEF_BYTES = NB > 0 ? (unsigned)kMaxMat * NB * kCoefStride * SZ : 0u;
+  // bath state of one plane tile (bath form): per level (P^{n+1/2}, Y^n, then P^{n-1/2}, Y^{n-1})
+  // the modes [3 nb][TY][TX] (box order), then P [3][TY][TX]
+  static constexpr unsigned BT = TY * TX * SZ;   // one component / mode of the tile
+  static constexpr unsigned B_P = 3u * (NB > 0 ? NB : 0) * BT, B_LVL = B_P + 3u * BT;
+  static constexpr unsigned OFF_BATH = r128(OFF_COEF + COEF_BYTES);
+  static constexpr unsigned BATH_BYTES = NB > 0 ? 2u * B_LVL : 0u;
+  static constexpr unsigned bytes = OFF_BATH + BATH_BYTES + 128;   // + alignment slack
   // CTAs per SM that the shared memory admits (228 KB per SM, 1 KB reserved per CTA, static 128 B)
   static constexpr int per_sm = 233472 / (bytes + 1024 + 128) > 8 ? 8 : 233472 / (bytes + 1024 + 128);
+  // CTAs per SM the registers are sized for: as the shared memory admits, or two with bath modes
+  // (a cell's whole bath state is held in registers)
+  static constexpr int min_blocks = NB > 0 ? 2 : per_sm;
   static_assert(ES % 128 == 0 && HS % 128 == 0 && XS % 128 == 0, "128-byte aligned frames");
   // the slot sums of the monitors / energy use the H^n buffer not in use (4 x TY x VX doubles)
   static_assert(4 * TY * VX * 8 <= XS, "reduction scratch fits an H buffer");
 };
 
-template <typename T, bool INC, int VX, int A>
-__global__ void __launch_bounds__(Plain3DLayout<T, VX, A>::threads, Plain3DLayout<T, VX, A>::per_sm)
-plain3d_kernel(const Step3DParams<T> p, const __grid_constant__ PlainMaps maps, int ebuf, int hbuf) {
+// NB = 0: the plain-plane kernel; NB > 0 (one cell per thread, FP32 increment form): the same
+// kernel for z-chunks with Lorentz-Bath planes of at most NB bath modes per material, whose
+// polarization and bath state (both levels) is loaded into registers at the start of the plane
+template <typename T, bool INC, int VX, int A, int NB = 0>
+__global__ void __launch_bounds__(Plain3DLayout<T, VX, A, NB>::threads, Plain3DLayout<T, VX, A, NB>::min_blocks)
+plain3d_kernel(const Step3DParams<T> p, const __grid_constant__ PlainMaps maps, const __grid_constant__ BathMaps bm,
+               int pcur, int ebuf, int hbuf) {
   using namespace plain;
-  using L = Plain3DLayout<T, VX, A>;
+  using L = Plain3DLayout<T, VX, A, NB>;
+  static_assert(NB == 0 || (INC && VX == 1), "bath planes: FP32 increment form, one cell per thread");
+  constexpr int NBA = NB > 0 ? NB : 1;
   using VV = Vec<T, VX>;
   constexpr int TY = L::TY, TX = L::TX, NE = L::NE, NH = L::NH;
   constexpr unsigned SZ = sizeof(T), ES = L::ES, HS = L::HS, XS = L::XS;
@@ -238,7 +276,10 @@ plain3d_kernel(const Step3DParams<T> p, const __grid_constant__ PlainMaps maps, 
   auto ldf = [&](unsigned off) -> T { return *reinterpret_cast<const T*>(smem_raw + off); };
 
   const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
-  const bool helper = w == TY;
+  constexpr bool HELPER = L::HELPER;
+  const bool helper = HELPER && w == TY;
+  // the thread that issues the tensor copies: the helper's lane 0, else lane 0 of warp 0
+  const bool issuer = (HELPER ? w == TY : w == 0) && lane == 0;
   const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
   const int i0 = x0 + VX * lane, j = y0 + w;
   // the host runs this kernel only when the tiles cover the grid exactly (nx % TX == 0, ny % 8 == 0)
@@ -252,24 +293,30 @@ plain3d_kernel(const Step3DParams<T> p, const __grid_constant__ PlainMaps maps, 
   const int nmc = (int)p.nmatcell;
   const int nbx32 = p.nx / 32;
   const int slot_row = blockIdx.y;   // 32 x 8 partial-sum slots: the tile's rows
-  // frame byte offsets of the thread's cells (relative to a slot): its row (compute warps: main
-  // row w; the helper: the row y0-1), the row above it in y (+1), the column after its last cell,
-  // its H_in row; and their component strides
+  // frame byte offsets of a row's cells of this lane (relative to a slot): the row (main row w, or
+  // the halo row y0-1), the row above it in y (+1), the column after the tile, the H_in row; their
+  // component strides; the H^n buffer row (y - y0 + 1)
+  struct RowOffs {
+    unsigned oR, cR, oJ, cJ, oX, cXc, oH, cH, oS;
+  };
   const unsigned cell = (unsigned)(VX * lane) * SZ;
-  const unsigned oR = helper ? L::E_TOP + cell : L::E_MAIN + (unsigned)w * RT + cell;
-  const unsigned cR = helper ? CR : CM;
-  const unsigned oJ = helper ? L::E_MAIN + cell : (w + 1 < TY ? L::E_MAIN + (unsigned)(w + 1) * RT + cell : L::E_BOT + cell);
-  const unsigned cJ = helper ? CM : (w + 1 < TY ? CM : CR);
-  const unsigned oX = helper ? L::E_PRT : L::E_PR8 + (unsigned)w * 4 * SZ;
-  const unsigned cXc = helper ? CP1 : CP8;
-  const unsigned oH = helper ? L::H_TOP + cell : L::H_MAIN + (unsigned)w * RT + cell;
-  const unsigned cH = helper ? CR : CM;
-  const unsigned oS = (helper ? 0u : (unsigned)(w + 1) * RT) + cell;   // H^n buffer, row y - y0 + 1
+  const RowOffs halo_row{L::E_TOP + cell, CR, L::E_MAIN + cell, CM, L::E_PRT, CP1, L::H_TOP + cell, CR, cell};
+  const int wr = w < TY ? w : 0;
+  const RowOffs main_row{L::E_MAIN + (unsigned)wr * RT + cell,
+                         CM,
+                         wr + 1 < TY ? L::E_MAIN + (unsigned)(wr + 1) * RT + cell : L::E_BOT + cell,
+                         wr + 1 < TY ? CM : CR,
+                         L::E_PR8 + (unsigned)wr * 4 * SZ,
+                         CP8,
+                         L::H_MAIN + (unsigned)wr * RT + cell,
+                         CM,
+                         (unsigned)(wr + 1) * RT + cell};
+  const unsigned oS = main_row.oS;
 
   // ---- set-up: mbarriers, per-plane table ----
   if (tid == 0) {
     s_abort = 0;
-    for (int a = 0; a < A; ++a) plain::mbar_init(&mbar[a], 1);
+    for (int a = 0; a <= A; ++a) plain::mbar_init(&mbar[a], 1);
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     if (np > kMaxPlanes) s_abort = 1;   // the host plans chunks of at most kMaxPlanes planes
   }
@@ -288,15 +335,20 @@ plain3d_kernel(const Step3DParams<T> p, const __grid_constant__ PlainMaps maps, 
     if (k < p.npml || k >= p.nz - p.npml) info |= kPmlE;
     if (p.npml > 0 && (k < p.npml || k >= p.nz - p.npml - 1)) info |= kPmlH;
     if (k + 1 >= p.nz) info |= kTop;
+    if ((info & 0xF) && p.mat[(info & 0xF) - 1].kind == kLorentzBath && p.mat[(info & 0xF) - 1].nb > 0)
+      info |= kBath;
     sInfo[t] = info;
   }
+  T* sCoef = reinterpret_cast<T*>(smem_raw + L::OFF_COEF);   // [modes][kCoefStride]
+  if (NB > 0)
+    for (int q = tid; q < kCoefStride * p.nmodes; q += L::threads) sCoef[q] = p.coef[q];
   __syncthreads();
   if (s_abort) {
     if (tid == 0) atomicExch(p.err, 1);
     return;
   }
 
-  // ---- staging (helper lane 0): stage g brings E_in(zb+g+1) (unless past the grid) and H_in(zb+g),
+  // ---- staging (the issuer): stage g brings E_in(zb+g+1) (unless past the grid) and H_in(zb+g),
   // stage 0 also E_in(zb); the periodic neighbours are boxes of their own (wrapped coordinates) ----
   const int ym = y0 == 0 ? p.ny - 1 : y0 - 1, yp = y0 + TY == p.ny ? 0 : y0 + TY;
   const int xm = x0 == 0 ? p.nx - 4 : x0 - 4, xp = x0 + TX == p.nx ? 0 : x0 + TX;
@@ -324,11 +376,32 @@ plain3d_kernel(const Step3DParams<T> p, const __grid_constant__ PlainMaps maps, 
     plain::tma_load5(d + L::H_TOP, &maps.h_row, x0, ym, k, 0, hbuf, bar);
     plain::tma_load5(d + L::H_PL8, &maps.h_pad8, xm, y0, k, 0, hbuf, bar);
   };
-  if (helper && lane == 0) {
+  // bath form: the bath state of plane zb+g (P^{n+1/2}, Y^n, P^{n-1/2}, Y^{n-1} of the tile) into the
+  // bath buffer, completing on mbarrier A; issued after the barrier of the plane before, when the
+  // buffer has been read into registers
+  unsigned bpar = 0;           // parity of the next bath-state wait
+  bool bath_pending = false;   // (issuer) a bath-state copy not yet waited for
+  auto issue_bath = [&](int g) {
+    const int mi_ = (sInfo[g] & 0xF) - 1;
+    const int i = bm.mat[0] == mi_ ? 0 : 1;
+    const MatK<T>& M = p.mat[mi_];
+    const int z = zb + g - M.zlo;
+    uint64_t* bar = &mbar[A];
+    plain::mbar_arrive_expect_tx(bar, 2u * (3u * M.nb + 3u) * L::BT);
+    const unsigned d = smem_u32(smem_raw) + L::OFF_BATH;
+    plain::tma_load4(d, &bm.y[i][pcur], x0, y0, z, 0, bar);
+    plain::tma_load4(d + L::B_P, &bm.pp[i][pcur], x0, y0, z, 0, bar);
+    plain::tma_load4(d + L::B_LVL, &bm.y[i][1 - pcur], x0, y0, z, 0, bar);
+    plain::tma_load4(d + L::B_LVL + L::B_P, &bm.pp[i][1 - pcur], x0, y0, z, 0, bar);
+    bath_pending = true;
+  };
+  if (issuer) {
     for (int g = 0; g < A && g < np; ++g) {
       plain::mbar_arrive_expect_tx(&mbar[g], stage_bytes(g));
       issue_stage(g);
     }
+    if constexpr (NB > 0)
+      if (np > 0 && (sInfo[0] & kBath)) issue_bath(0);
   }
 
   // ---- prologue: H^n of plane zb-1 at the own cells (z-difference of the E update at zb);
@@ -355,7 +428,7 @@ plain3d_kernel(const Step3DParams<T> p, const __grid_constant__ PlainMaps maps, 
     }
   }
 
-  T uE = T(0), uP = T(0), uH = T(0);
+  T uE = T(0), uP = T(0), uB = T(0), uH = T(0);
   const int pstrE = 2 * p.npml * plane, pstrH = (2 * p.npml + 1) * plane;
   int g_last = 0;        // the plane of the last wait
   bool wait_ok = true;   // that wait succeeded
@@ -370,8 +443,9 @@ plain3d_kernel(const Step3DParams<T> p, const __grid_constant__ PlainMaps maps, 
   // H^n of plane k at the thread's VX cells from the staged frames (the own row of a compute warp,
   // the halo row y0-1 for the helper); writes H_x, H_z to the H^n buffer and returns the cells'
   // E_in(k) and H^n.  PML: the plane lies in the CPML of the H update.
-  auto h_cells = [&](bool PML, bool top, unsigned e0, unsigned e1, unsigned hin, unsigned xb, T bH, T cH_,
-                     T* psHx, T* psHy, T* ex0, T* ey0, T* ez0, T* Hx, T* Hy, T* Hz) {
+  auto h_cells = [&](const RowOffs& o, bool PML, bool top, unsigned e0, unsigned e1, unsigned hin, unsigned xb,
+                     T bH, T cH_, T* psHx, T* psHy, T* ex0, T* ey0, T* ez0, T* Hx, T* Hy, T* Hz) {
+    const unsigned oR = o.oR, cR = o.cR, oJ = o.oJ, cJ = o.cJ, oX = o.oX, cXc = o.cXc, oH = o.oH, cH = o.cH;
     VV::ld(at(e0 + oR), ex0);
     VV::ld(at(e0 + cR + oR), ey0);
     VV::ld(at(e0 + 2 * cR + oR), ez0);
@@ -402,8 +476,8 @@ plain3d_kernel(const Step3DParams<T> p, const __grid_constant__ PlainMaps maps, 
       plain::h_cell(Hx[v], Hy[v], Hz[v], psHx[v], psHy[v], ezj[v] - ez0[v], ey1[v] - ey0[v], ex1[v] - ex0[v],
                     ez_i1 - ez0[v], ey_i1 - ey0[v], exj[v] - ex0[v], PML, bH, cH_, S);
     }
-    VV::st(at(xb + oS), Hx);
-    VV::st(at(xb + CX + oS), Hz);
+    VV::st(at(xb + o.oS), Hx);
+    VV::st(at(xb + CX + o.oS), Hz);
   };
 
   if (helper) {
@@ -427,9 +501,10 @@ plain3d_kernel(const Step3DParams<T> p, const __grid_constant__ PlainMaps maps, 
       }
       wait_stage(g);
       if (pmlH)
-        h_cells(true, top, e0, e1, hin, xb, p.pmlH[2 * k], p.pmlH[2 * k + 1], psHx, psHy, ex0, ey0, ez0, Hx, Hy, Hz);
+        h_cells(halo_row, true, top, e0, e1, hin, xb, p.pmlH[2 * k], p.pmlH[2 * k + 1], psHx, psHy, ex0, ey0, ez0,
+                Hx, Hy, Hz);
       else
-        h_cells(false, top, e0, e1, hin, xb, T(1), T(0), psHx, psHy, ex0, ey0, ez0, Hx, Hy, Hz);
+        h_cells(halo_row, false, top, e0, e1, hin, xb, T(1), T(0), psHx, psHy, ex0, ey0, ez0, Hx, Hy, Hz);
       // arm the mbarrier of stage g+A (the one of stage g) before the barrier, once stage g's phase
       // has completed: the new phase cannot complete before its copies, issued after the barrier
       if (lane == 0 && wait_ok && g + A < np) plain::mbar_arrive_expect_tx(&mbar[g % A], stage_bytes(g + A));
@@ -461,8 +536,9 @@ plain3d_kernel(const Step3DParams<T> p, const __grid_constant__ PlainMaps maps, 
     const unsigned oLJ = w + 1 < TY ? L::E_PL8 + (unsigned)((w + 1) * 4 + 3) * SZ : L::E_PLB + 3u * SZ;
     const unsigned cLJ = w + 1 < TY ? CP8 : CP1;
     const unsigned oLH = L::H_PL8 + (unsigned)(w * 4 + 3) * SZ;
-    auto body = [&](auto gen_t, int g, int info) -> bool {
+    auto body = [&](auto gen_t, auto bath_t, int g, int info) -> bool {
       constexpr bool GEN = decltype(gen_t)::value;
+      constexpr bool BATH = NB > 0 && decltype(bath_t)::value;   // a Lorentz-Bath plane with modes
       const int k = zb + g;
       const int mi = GEN ? (info & 0xF) - 1 : -1;
       const bool in_box = GEN && (info & kBox) != 0;
@@ -480,15 +556,39 @@ plain3d_kernel(const Step3DParams<T> p, const __grid_constant__ PlainMaps maps, 
         VV::ld(p.psiHin + ipH * plane + qxy, psHx);
         VV::ld(p.psiHin + pstrH + ipH * plane + qxy, psHy);
       }
+      // bath planes: P^{n+1/2}, P^{n-1/2} and both levels of the bath modes of the cell, read from
+      // the staged bath buffer before the plane's barrier (Y^n in bY; Y^{n-1} in bV, which becomes
+      // V = Y^n - Y^{n-1} below)
+      T bPa[3], bPb[3], bY[3][NBA], bV[3][NBA];
+      int rB = 0, yB = 0, mstr = 0, nbm = 0;
+      if constexpr (BATH) {
+        const MatK<T>& M = p.mat[mi];
+        const int rl = (k - M.zlo) * plane + qxy;
+        rB = (int)M.base + rl;
+        yB = (int)M.ybase + rl;
+        mstr = (int)M.ncell;
+        nbm = M.nb;
+      }
+      // without the helper: warp 0 also computes the halo row y0-1 (its CPML memories loaded here)
+      [[maybe_unused]] T hpsx[VX], hpsy[VX];
+      if constexpr (!HELPER) {
+#pragma unroll
+        for (int v = 0; v < VX; ++v) hpsx[v] = hpsy[v] = T(0);
+        if (pmlH && w == 0) {
+          const int gxy = ym * p.nx + i0;
+          VV::ld(p.psiHin + ipH * plane + gxy, hpsx);
+          VV::ld(p.psiHin + pstrH + ipH * plane + gxy, hpsy);
+        }
+      }
       wait_stage(g);
 
       // ---- H^n of plane k at the own cells ----
       T ex0[VX], ey0[VX], ez0[VX], Hx[VX], Hy[VX], Hz[VX];
       const T bH = pmlH ? p.pmlH[2 * k] : T(1), cH_ = pmlH ? p.pmlH[2 * k + 1] : T(0);
       if (pmlH)
-        h_cells(true, top, e0, e1, hin, xb, bH, cH_, psHx, psHy, ex0, ey0, ez0, Hx, Hy, Hz);
+        h_cells(main_row, true, top, e0, e1, hin, xb, bH, cH_, psHx, psHy, ex0, ey0, ez0, Hx, Hy, Hz);
       else
-        h_cells(false, top, e0, e1, hin, xb, bH, cH_, psHx, psHy, ex0, ey0, ez0, Hx, Hy, Hz);
+        h_cells(main_row, false, top, e0, e1, hin, xb, bH, cH_, psHx, psHy, ex0, ey0, ez0, Hx, Hy, Hz);
       {
         const int q = k * plane + qxy;
         VV::st(p.Hout + q, Hx);
@@ -498,6 +598,17 @@ plain3d_kernel(const Step3DParams<T> p, const __grid_constant__ PlainMaps maps, 
           VV::st(p.psiHout + ipH * plane + qxy, psHx);
           VV::st(p.psiHout + pstrH + ipH * plane + qxy, psHy);
         }
+      }
+      if constexpr (!HELPER) {
+        if (w == 0) {
+          T hx0[VX], hy0[VX], hz0[VX], hHx[VX], hHy[VX], hHz[VX];
+          if (pmlH)
+            h_cells(halo_row, true, top, e0, e1, hin, xb, bH, cH_, hpsx, hpsy, hx0, hy0, hz0, hHx, hHy, hHz);
+          else
+            h_cells(halo_row, false, top, e0, e1, hin, xb, bH, cH_, hpsx, hpsy, hx0, hy0, hz0, hHx, hHy, hHz);
+        }
+        // arm the mbarrier of stage g+A once stage g's phase has completed (as the helper does)
+        if (issuer && wait_ok && g + A < np) plain::mbar_arrive_expect_tx(&mbar[g % A], stage_bytes(g + A));
       }
       // ---- H_y, H_z at x-1 of the thread's first cell: from the lane to the left, or on lane 0
       // recomputed for the halo cell x0-1 of this row ----
@@ -519,8 +630,35 @@ plain3d_kernel(const Step3DParams<T> p, const __grid_constant__ PlainMaps maps, 
         hyx0 = hy;
         hzx0 = hz;
       }
+      if constexpr (BATH) {
+        if (plain::mbar_wait(&mbar[A], bpar)) {
+          if (issuer) bath_pending = false;
+        } else {
+          s_abort = 1;
+          atomicExch(p.err, 1);
+        }
+        bpar ^= 1u;
+        const unsigned cofs = L::OFF_BATH + (unsigned)(w * TX + lane) * SZ;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          bPa[c] = ldf(cofs + L::B_P + c * L::BT);
+          bPb[c] = ldf(cofs + L::B_LVL + L::B_P + c * L::BT);
+        }
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+#pragma unroll
+          for (int jj = 0; jj < NBA; ++jj)
+            if (jj < nbm) {
+              bY[c][jj] = ldf(cofs + (unsigned)(c * nbm + jj) * L::BT);
+              bV[c][jj] = ldf(cofs + L::B_LVL + (unsigned)(c * nbm + jj) * L::BT);
+            }
+      }
       __syncthreads();   // H^n(k) of the tile and its halo complete; E_in(k), H_in(k) slots free
       if (s_abort) return false;
+      if constexpr (!HELPER)
+        if (issuer && g + A < np) issue_stage(g + A);
+      if constexpr (NB > 0)
+        if (issuer && g + 1 < np && (sInfo[g + 1] & kBath)) issue_bath(g + 1);
 
       // ---- E-side CPML memories ----
       T psEx[VX], psEy[VX];
@@ -559,6 +697,7 @@ plain3d_kernel(const Step3DParams<T> p, const __grid_constant__ PlainMaps maps, 
       // ---- D/E (Eq. 1a) and P (Eq. Pz_1D_Lorentz) of plane k at the own cells, one component at
       // a time (the material state of a component is loaded, used and stored before the next) ----
       double monE[2] = {0.0, 0.0};   // sums of E_x and E_y over the thread's cells (E monitors)
+      T Ev[3];                       // bath planes: E^{n+1/2} of the cell
       {
         T hxy[VX], hzy[VX];   // H_x, H_z at y-1
         VV::ld(at(xb + oS - RT), hxy);
@@ -631,6 +770,12 @@ plain3d_kernel(const Step3DParams<T> p, const __grid_constant__ PlainMaps maps, 
             if (GEN && p.eE_on && in_box)
 #pragma unroll
               for (int v = 0; v < VX; ++v) uE += Ec[v] * Ec[v];
+          } else if (BATH) {
+            // D-free form as below, from the P levels in registers; P and the bath modes of the three
+            // components are updated together after the loop
+            Ec[0] = e0c[0] + (S * curl[0] - (bPa[c] - bPb[c])) * M->inv_eps;
+            Ev[c] = Ec[0];
+            if (p.eE_on && in_box) uE += M->eps * (Ec[0] * Ec[0]);
           } else {
             T Pa[VX], Pb[VX], D[VX];
             VV::ld(p.Pa + c * nmc + r, Pa);
@@ -683,6 +828,60 @@ plain3d_kernel(const Step3DParams<T> p, const __grid_constant__ PlainMaps maps, 
           VV::st(p.psiE + pstrE + ipE * plane + qxy, psEy);
         }
       }
+      if constexpr (BATH) {
+        // ---- Eq. Pz_update-LB and Eq. Yzj_finite_difference (increment form) for the three
+        // components, modes outer: each mode's coefficient row
+        // {k(a+b), -k b, a+b, -(b+1), c, (w dt)^2} is read once; per component the sums run over
+        // ascending j ----
+        const MatK<T>& M = p.mat[mi];
+        const T* cfm = sCoef + M.coef_off * kCoefStride;
+        T bsum[3] = {T(0), T(0), T(0)};
+#pragma unroll
+        for (int jj = 0; jj < NBA; ++jj) {
+          if (jj < nbm) {
+            const float4 ca = *reinterpret_cast<const float4*>(cfm + jj * kCoefStride);
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+              bV[c][jj] = bY[c][jj] - bV[c][jj];   // V_j = Y^n - Y^{n-1}
+              bsum[c] = bsum[c] + (ca.x * bY[c][jj] + ca.y * bV[c][jj]);
+            }
+          }
+        }
+        T Pn[3], Vn[3], dP[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          const T V0 = bPa[c] - bPb[c];
+          T num = M.cE * Ev[c] - M.W * bPa[c] + M.c2 * V0;
+          num = num - T(0.5) * dt * bsum[c];
+          Vn[c] = num * M.inv_A;
+          Pn[c] = bPa[c] + Vn[c];
+          p.Pb[c * nmc + rB] = Pn[c];   // overwrites P^{n-1/2}
+          dP[c] = Vn[c] + V0;           // P^{n+3/2} - P^{n-1/2}
+        }
+        T ub[3] = {T(0), T(0), T(0)};
+#pragma unroll
+        for (int jj = 0; jj < NBA; ++jj) {
+          if (jj < nbm) {
+            const float4 ca = *reinterpret_cast<const float4*>(cfm + jj * kCoefStride);
+            const float2 cb = *reinterpret_cast<const float2*>(cfm + jj * kCoefStride + 4);
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+              const T y = bY[c][jj];
+              const T Vy = ca.z * y + ca.w * bV[c][jj] + cb.x * dP[c];
+              const T Ynew = y + Vy;
+              p.Yb[yB + (c * nbm + jj) * mstr] = Ynew;   // overwrites Y^{n-1}
+              if (p.eE_on) ub[c] += Vy * Vy + cb.y * Ynew * Ynew;
+            }
+          }
+        }
+        if (p.eE_on && in_box) {
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            uP += M.rho_idt2 * (Vn[c] * Vn[c] + M.w0r2dt2 * Pn[c] * Pn[c]);
+            uB += M.rho_idt2 * ub[c];
+          }
+        }
+      }
       // ---- E-side monitor partials ----
       if (GEN && (info & kMonE)) {
         for (int m = 0; m < p.nmon; ++m) {
@@ -707,22 +906,29 @@ plain3d_kernel(const Step3DParams<T> p, const __grid_constant__ PlainMaps maps, 
     };
     for (int g = 0; g < np; ++g) {
       const int info = sInfo[g];
-      const bool ok = info == 0 ? body(std::false_type{}, g, info) : body(std::true_type{}, g, info);
+      bool ok;
+      if (info == 0)
+        ok = body(std::false_type{}, std::false_type{}, g, info);
+      else if (NB > 0 && (info & kBath))
+        ok = body(std::true_type{}, std::true_type{}, g, info);
+      else
+        ok = body(std::true_type{}, std::false_type{}, g, info);
       if (!ok) break;
     }
   }
   // after an abort: a bounded wait for the stage that ran out and those issued after it, so that no
   // copy is in flight into this CTA's shared memory when it exits (a stage armed but not issued
   // has no copies)
-  if (s_abort && helper && lane == 0) {
+  if (s_abort && issuer) {
     for (int g = wait_ok ? g_last + 1 : g_last; g < np && g < g_last + A; ++g)
       plain::mbar_wait(&mbar[g % A], (unsigned)((g / A) & 1));
+    if (NB > 0 && bath_pending) plain::mbar_wait(&mbar[A], bpar);
   }
   // ---- energy partials of this block, one per 32 x 8 slot (zero outside the box) ----
   if (p.eE_on || p.eH_on) {
     __syncthreads();
     double* red = reinterpret_cast<double*>(at(L::OFF_SH));
-    T u4[4] = {uE, uP, T(0), uH};
+    T u4[4] = {uE, uP, uB, uH};
     block_slot_sums<TY, VX>(u4, red, w, lane);
     if (tid < 4 * VX) {
       const int qn = tid / VX, h = tid - qn * VX;

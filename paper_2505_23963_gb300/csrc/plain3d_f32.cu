@@ -1,16 +1,17 @@
-// plain3d_f32.cu -- float instantiation of the plain-plane step kernel (four cells per thread, two
-// planes staged ahead, two CTAs per SM).
+// plain3d_f32.cu -- float instantiations of the plain-plane step kernel: four cells per thread for
+// the chunks without bath planes, one cell per thread (bath state in registers, at most 4 or 8
+// modes per material) for the Lorentz-Bath chunks; two planes staged ahead, two CTAs per SM.
 #include <cuda_runtime.h>
 
 #include "plain3d.cuh"
 
 namespace fdtdbath {
 
-template <int VX, int A>
-static int launch_shape(const Step3DParams<float>& p, const PlainMaps& maps, int ebuf, int hbuf, int nchunks,
-                        void* stream) {
-  using L = Plain3DLayout<float, VX, A>;
-  auto kern = plain3d_kernel<float, true, VX, A>;
+template <int VX, int A, int NB = 0>
+static int launch_shape(const Step3DParams<float>& p, const PlainMaps& maps, const BathMaps& bmaps, int pcur, int ebuf,
+                        int hbuf, int nchunks, void* stream) {
+  using L = Plain3DLayout<float, VX, A, NB>;
+  auto kern = plain3d_kernel<float, true, VX, A, NB>;
   static bool attr_set = false;   // once per process: more than 48 KB, shared-memory carveout
   if (!attr_set) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::bytes);
@@ -20,13 +21,21 @@ static int launch_shape(const Step3DParams<float>& p, const PlainMaps& maps, int
     attr_set = true;
   }
   dim3 grid(p.nx / L::TX, p.ny / L::TY, nchunks), block(L::threads);
-  kern<<<grid, block, L::bytes, (cudaStream_t)stream>>>(p, maps, ebuf, hbuf);
+  kern<<<grid, block, L::bytes, (cudaStream_t)stream>>>(p, maps, bmaps, pcur, ebuf, hbuf);
   return (int)cudaGetLastError();
 }
 
 int launch_plain3d_f32(const Step3DParams<float>& p, const PlainMaps& maps, int ebuf, int hbuf, int nchunks,
                        void* stream) {
-  return launch_shape<4, 2>(p, maps, ebuf, hbuf, nchunks, stream);
+  static const BathMaps none{};   // no bath planes in these chunks
+  return launch_shape<4, 2>(p, maps, none, 0, ebuf, hbuf, nchunks, stream);
+}
+
+int launch_bath3d_f32(const Step3DParams<float>& p, const PlainMaps& maps, const BathMaps& bmaps, int pcur, int ebuf,
+                      int hbuf, int nchunks, int nb, void* stream) {
+  if (nb <= 4) return launch_shape<1, 2, 4>(p, maps, bmaps, pcur, ebuf, hbuf, nchunks, stream);
+  if (nb <= 8) return launch_shape<1, 2, 8>(p, maps, bmaps, pcur, ebuf, hbuf, nchunks, stream);
+  return (int)cudaErrorInvalidValue;
 }
 
 }  // namespace fdtdbath

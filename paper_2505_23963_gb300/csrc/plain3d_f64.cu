@@ -20,7 +20,8 @@ static int launch_shape(const Step3DParams<double>& p, const PlainMaps& maps, in
     attr_set = true;
   }
   dim3 grid(p.nx / L::TX, p.ny / L::TY, nchunks), block(L::threads);
-  kern<<<grid, block, L::bytes, (cudaStream_t)stream>>>(p, maps, ebuf, hbuf);
+  static const BathMaps none{};   // no bath planes in these chunks
+  kern<<<grid, block, L::bytes, (cudaStream_t)stream>>>(p, maps, none, 0, ebuf, hbuf);
   return (int)cudaGetLastError();
 }
 

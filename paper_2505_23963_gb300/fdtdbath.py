@@ -427,6 +427,11 @@ class Simulation:
         """Whether the z-chunks without bath modes run the plain-plane kernel (query key 7)."""
         return query(self.h, 7) == 1
 
+    def bath_plain_kernel(self) -> bool:
+        """Whether the z-chunks with bath modes run the plain-plane kernel's Lorentz-Bath form
+        (query key 9)."""
+        return query(self.h, 9) == 1
+
     def adjoint_forward(self, nsteps: int, checkpoint_every: int = 256):
         """fdtdbath_adjoint_forward: advance nsteps steps keeping checkpoints for the adjoint."""
         _check(lib().fdtdbath_adjoint_forward(self.h, int(nsteps), int(checkpoint_every)), self.h)
