@@ -1133,12 +1133,13 @@ int fdtdbath_create(const fdtdbath_grid* grid, double resolution, double courant
     s->ring_cap = 4096;
   }
   // partial-sum ring: the 3D kernel's layout (nbxy per monitor quantity, nblk3d per energy
-  // quantity), or the 1D kernel's (one per CTA of its cluster); space for the larger of the two,
+  // quantity), or the 1D kernel's (one per warp of its cluster); space for the larger of the two,
   // since a 1D simulation moves to the 3D kernel once a y/z component is set (switch_to_3d)
   s->nblk3d = s->nbx * s->nby * s->nchunks;
   s->red_nbxy = s->nbx * s->nby;
-  s->red_nblocks = (s->path1d && s->ncomp1d == 1) ? s->c1d : s->nblk3d;
-  const int64_t nbxy = s->red_nbxy, nblocks = std::max(s->nblk3d, s->path1d ? s->c1d : 1);
+  const int nblk1d = s->c1d * (kCav1DThreads / 32);
+  s->red_nblocks = (s->path1d && s->ncomp1d == 1) ? nblk1d : s->nblk3d;
+  const int64_t nbxy = s->red_nbxy, nblocks = std::max(s->nblk3d, s->path1d ? nblk1d : 1);
   s->monE_off = 0;
   s->monH_off = 2 * (int64_t)s->mons.size() * nbxy;
   s->enE_off = s->monH_off + 4 * (int64_t)s->mons.size() * nbxy;

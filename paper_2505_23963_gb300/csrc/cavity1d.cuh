@@ -45,11 +45,12 @@ __global__ void __launch_bounds__(kCav1DThreads) cavity1d_kernel(const Cav1DPara
   cg::cluster_group cluster = cg::this_cluster();
   __shared__ T sE[kCav1DThreads];
   __shared__ T sH[kCav1DThreads];
-  __shared__ double sred[kCav1DThreads / 32][4];
   constexpr int NBA = NBMAX > 0 ? NBMAX : 1;
   const int C = (int)cluster.num_blocks();
   const int rank = (int)cluster.block_rank();
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5, nwarp = blockDim.x >> 5;
+  // energy partials: one per warp of the cluster and quantity (NW per quantity)
+  const int NW = C * nwarp, wslot = rank * nwarp + warp;
   const int nz = p.nz;
   const int lo = p.bounds[rank], hi = p.bounds[rank + 1];
   const int cnt = hi - lo;
@@ -126,7 +127,9 @@ __global__ void __launch_bounds__(kCav1DThreads) cavity1d_kernel(const Cav1DPara
     const int64_t n = p.step0 + s;
     double* rec = p.partial + (int64_t)(n % p.ring_cap) * p.ring_stride;
     const bool en = p.energy_on && (n % p.every) == 0;
-    double uE = 0.0, uP = 0.0, uB = 0.0, uH = 0.0;
+    // energy terms of the cell and their warp sums in the state precision (FP64 arithmetic is
+    // slow on this part: in the FP32 path it would dominate the step), FP64 from the warp sums on
+    T uE = T(0), uP = T(0), uB = T(0), uH = T(0);
     // ---------------- D/E half-step, polarization and bath ----------------
     if (own) {
       T hm;   // H_y(z-1)
@@ -205,11 +208,11 @@ __global__ void __launch_bounds__(kCav1DThreads) cavity1d_kernel(const Cav1DPara
         Pb = Pa;
         Pa = Pn;
         if (en && in_box) {
-          uP = (double)(rho_idt2 * (Vn * Vn + w0r2dt2 * Pn * Pn));
-          uB = (double)(rho_idt2 * ub);
+          uP = rho_idt2 * (Vn * Vn + w0r2dt2 * Pn * Pn);
+          uB = rho_idt2 * ub;
         }
       }
-      if (en && in_box) uE = (double)eps * ((double)e * (double)e);
+      if (en && in_box) uE = eps * (e * e);
       if (p.nmon > 0 && z == p.mon_z) {
         rec[p.monE_off + 0] = (double)e;
         rec[p.monE_off + 1] = 0.0;
@@ -217,6 +220,8 @@ __global__ void __launch_bounds__(kCav1DThreads) cavity1d_kernel(const Cav1DPara
     }
     sE[t] = e;
     if (en) {
+      // one partial per warp and quantity into the ring (summed there in fixed order later, so
+      // no serial FP64 sum sits between the half-steps)
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) {
         uE += __shfl_down_sync(0xffffffffu, uE, o);
@@ -224,23 +229,12 @@ __global__ void __launch_bounds__(kCav1DThreads) cavity1d_kernel(const Cav1DPara
         uB += __shfl_down_sync(0xffffffffu, uB, o);
       }
       if (lane == 0) {
-        sred[warp][0] = uE;
-        sred[warp][1] = uP;
-        sred[warp][2] = uB;
+        rec[p.enE_off + wslot] = (double)uE;
+        rec[p.enE_off + NW + wslot] = (double)uP;
+        rec[p.enE_off + 2 * NW + wslot] = (double)uB;
       }
     }
     cluster.sync();
-    if (en && t == 0) {
-      double a = 0.0, b = 0.0, c = 0.0;
-      for (int w = 0; w < nwarp; ++w) {
-        a += sred[w][0];
-        b += sred[w][1];
-        c += sred[w][2];
-      }
-      rec[p.enE_off + rank] = a;
-      rec[p.enE_off + C + rank] = b;
-      rec[p.enE_off + 2 * C + rank] = c;
-    }
     // ---------------- H half-step ----------------
     if (own) {
       T ep;   // E_x(z+1)
@@ -253,7 +247,7 @@ __global__ void __launch_bounds__(kCav1DThreads) cavity1d_kernel(const Cav1DPara
       } else {
         h = h - S * (dzEx - T(0));
       }
-      if (en && in_box) uH = (double)h * (double)h;
+      if (en && in_box) uH = h * h;
       if (p.nmon > 0 && (z == p.mon_z - 1 || z == p.mon_z)) {
         const int off = z == p.mon_z ? 1 : 0;
         rec[p.monH_off + off] = 0.0;
@@ -264,14 +258,9 @@ __global__ void __launch_bounds__(kCav1DThreads) cavity1d_kernel(const Cav1DPara
     if (en) {
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) uH += __shfl_down_sync(0xffffffffu, uH, o);
-      if (lane == 0) sred[warp][3] = uH;
+      if (lane == 0) rec[p.enH_off + wslot] = (double)uH;
     }
     cluster.sync();
-    if (en && t == 0) {
-      double a = 0.0;
-      for (int w = 0; w < nwarp; ++w) a += sred[w][3];
-      rec[p.enH_off + rank] = a;
-    }
   }
 
   // ---- write the state back ----

@@ -1,5 +1,6 @@
 // plain3d.cuh -- the fused step of the z-planes without bath modes (vacuum, CPML, Lorentz and
-// Drude layers), general 3D form on grids tiled exactly by its tiles.
+// Drude layers), general 3D form on grids tiled exactly by its tiles; and its Lorentz-Bath form
+// for the layers with at most 8 bath modes (FP32).
 //
 // It computes what step3d_kernel<T, INC, 0, 8> computes for such planes -- the H half-step of
 // the previous step (H^n from E^{n-1/2}, Eq. 1b, with the CPML memories of the z-derivative
@@ -32,6 +33,22 @@
 // buffers.  Stage g of a chunk (plane k = zb + g) brings E_in(k+1) and H_in(k), stage 0 also
 // E_in(zb); it is issued after the barrier of plane k-A, when the slots it overwrites
 // (E_in(k-A), H_in(k-A)) have been read for the last time.
+//
+// The Lorentz-Bath form (NB > 0: FP32 increment form, one cell per thread, 32 x 8 tiles) runs the
+// z-chunks of the Lorentz-Bath layers with at most NB modes per material, with what
+// step3d_kernel<float, true, NB, 8> computes there: the polarization update of Eq.
+// Pz_update-LB and the bath-mode update of Eq. Yzj_finite_difference, three components together
+// with the modes outer, sums over ascending j.  Per cell and step it reads and writes P (two
+// levels) and 2 x 3 NB bath-mode words, far more than the fields, so:
+//   * the CTA has the eight compute warps only (no helper: a ninth warp caps the registers at 96
+//     for two CTAs per SM, and the 54 state words of a cell then spill); warp 0 also recomputes the
+//     halo row y0-1 and lane 0 of warp 0 issues the copies;
+//   * the state of plane k of the tile -- P^{n+1/2}, Y^n, P^{n-1/2}, Y^{n-1} -- arrives in a
+//     shared buffer by four 4-D tensor copies (one box each, from maps of the two state slots),
+//     issued after the barrier of plane k-1, read into registers before the barrier of plane k, so
+//     a whole plane of work covers each copy's latency.  Loading it from global memory straight
+//     into registers at the start of the plane instead left the loads' latency exposed (long
+//     scoreboard stalls 2.6 per issue) and ran the layer at 0.55 of the bandwidth.
 #pragma once
 
 #include <cuda.h>
