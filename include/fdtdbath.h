@@ -137,7 +137,10 @@ typedef struct {
 /* Build a simulation: validate (Courant <= 1/sqrt(number of axes with more than one cell),
  * 1 + gamma dt/2 > 0, layers inside the grid and disjoint, monitors and sources inside),
  * expand the per-material ADE coefficients of Eq. Pz_update-LB / Yzj_finite_difference,
- * build the CPML profiles, allocate and zero the device state.  *out receives the handle. */
+ * build the CPML profiles, allocate and zero the device state.  *out receives the handle.
+ * The kernels index the state with 32-bit offsets: a grid whose E / H arrays (3 nx ny nz), pooled
+ * polarization (3 x the layer cells), bath-mode array or CPML memories would exceed 2^31 - 1
+ * elements (e.g. 1024^3) is refused with FDTDBATH_ERR_ARG. */
 int fdtdbath_create(const fdtdbath_grid *grid, double resolution, double courant,
                     const fdtdbath_material *materials, int32_t nmat,
                     const fdtdbath_source *sources, int32_t nsrc,
