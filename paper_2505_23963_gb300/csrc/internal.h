@@ -166,14 +166,15 @@ struct PlainMaps {
 constexpr int plain_tile_x(int prec) { return prec == 64 ? 64 : 128; }
 int launch_plain3d_f32(const Step3DParams<float>& p, const PlainMaps& maps, int ebuf, int hbuf, int nchunks,
                        void* stream);
-// The Lorentz-Bath chunks (FP32, one cell per thread, tiles 32 x 8 with maps of that box width,
-// nb = the largest number of bath modes of a material: at most 8).  The polarization and bath
+// The Lorentz-Bath chunks (FP32, one cell per thread -- two with more than 8 modes --, tiles
+// 32 x 8 with maps of that box width, nb = the largest number of bath modes of a material: at
+// most 16).  The polarization and bath
 // modes of a plane (both levels) are staged by tensor copies too, from these maps: per
 // Lorentz-Bath material with modes (at most 2) and per state slot (the two P / Y buffers, whose
 // roles swap every step), P as a 4-D tensor (x, y, z in the layer, component) and the modes as
 // (x, y, z in the layer, component * nb + mode), boxes of one 32 x 8 plane tile.
 constexpr int kBathTileX = 32;
-constexpr int kBathPlainMaxModes = 8;
+constexpr int kBathPlainMaxModes = 16;
 constexpr int kBathPlainMaxMats = 2;
 struct BathMaps {
   int nmat;                                   // materials with maps

@@ -221,9 +221,12 @@ template <typename T, int VX_, int A, int NB = 0>
 struct Plain3DLayout {
   static constexpr int VX = VX_, TY = plain::TY, TX = 32 * VX;
   static constexpr int NE = A + 1, NH = A;   // E and H_in frame slots
-  // the helper warp (NB = 0); the bath form runs without it, its 8 warps sized for 128 registers
+  // the helper warp (NB = 0); the bath form runs without it, its warps sized for 128 registers.
+  // Above 8 modes (NB = 16) two threads share a cell, each with half of its modes (SPLIT warps
+  // per tile row: the first computes the fields, both the bath)
   static constexpr bool HELPER = NB == 0;
-  static constexpr int threads = 32 * (TY + (HELPER ? 1 : 0));
+  static constexpr int SPLIT = NB > 8 ? 2 : 1, NBH = NB > 0 ? NB / SPLIT : 1;
+  static constexpr int threads = 32 * (TY * SPLIT + (HELPER ? 1 : 0));
   static constexpr unsigned SZ = sizeof(T);
   static constexpr unsigned r128(unsigned b) { return (b + 127u) & ~127u; }
   // An E frame slot (each part one box, box-dense, 128-byte aligned): main [3][TY][TX] rows
@@ -254,12 +257,16 @@ struct Plain3DLayout {
   static constexpr unsigned B_P = 3u * (NB > 0 ? NB : 0) * BT, B_LVL = B_P + 3u * BT;
   static constexpr unsigned OFF_BATH = r128(OFF_COEF + COEF_BYTES);
   static constexpr unsigned BATH_BYTES = NB > 0 ? 2u * B_LVL : 0u;
-  static constexpr unsigned bytes = OFF_BATH + BATH_BYTES + 128;   // + alignment slack
+  // the two halves' exchange (SPLIT = 2): E^{n+1/2} and the bath sums of each half, [9][TY][TX]
+  static constexpr unsigned OFF_XCH = r128(OFF_BATH + BATH_BYTES);
+  static constexpr unsigned XCH_BYTES = SPLIT > 1 ? 9u * BT : 0u;
+  static constexpr unsigned bytes = OFF_XCH + XCH_BYTES + 128;   // + alignment slack
   // CTAs per SM that the shared memory admits (228 KB per SM, 1 KB reserved per CTA, static 128 B)
   static constexpr int per_sm = 233472 / (bytes + 1024 + 128) > 8 ? 8 : 233472 / (bytes + 1024 + 128);
   // CTAs per SM the registers are sized for: as the shared memory admits, or two with bath modes
   // (a cell's whole bath state is held in registers)
-  static constexpr int min_blocks = NB > 0 ? 2 : per_sm;
+  static constexpr int min_blocks = NB > 0 ? (SPLIT > 1 ? 1 : 2) : per_sm;
+  static_assert(NB == 0 || NB == 4 || NB == 8 || NB == 16, "bath form: 4, 8 or 16 modes");
   static_assert(ES % 128 == 0 && HS % 128 == 0 && XS % 128 == 0, "128-byte aligned frames");
   // the slot sums of the monitors / energy use the H^n buffer not in use (4 x TY x VX doubles)
   static_assert(4 * TY * VX * 8 <= XS, "reduction scratch fits an H buffer");
@@ -275,7 +282,6 @@ plain3d_kernel(const Step3DParams<T> p, const __grid_constant__ PlainMaps maps, 
   using namespace plain;
   using L = Plain3DLayout<T, VX, A, NB>;
   static_assert(NB == 0 || (INC && VX == 1), "bath planes: FP32 increment form, one cell per thread");
-  constexpr int NBA = NB > 0 ? NB : 1;
   using VV = Vec<T, VX>;
   constexpr int TY = L::TY, TX = L::TX, NE = L::NE, NH = L::NH;
   constexpr unsigned SZ = sizeof(T), ES = L::ES, HS = L::HS, XS = L::XS;
@@ -295,17 +301,21 @@ plain3d_kernel(const Step3DParams<T> p, const __grid_constant__ PlainMaps maps, 
   const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
   constexpr bool HELPER = L::HELPER;
   const bool helper = HELPER && w == TY;
+  // the bath form's second thread of a cell (modes NBH.. of the cells of tile row w - TY)
+  constexpr int SPLIT = L::SPLIT, NBH = L::NBH;
+  const bool secondary = SPLIT > 1 && w >= TY;
+  const int wrow = NB > 0 ? w % TY : w;   // the tile row of the thread's cells
   // the thread that issues the tensor copies: the helper's lane 0, else lane 0 of warp 0
   const bool issuer = (HELPER ? w == TY : w == 0) && lane == 0;
   const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
-  const int i0 = x0 + VX * lane, j = y0 + w;
+  const int i0 = x0 + VX * lane, j = y0 + wrow;
   // the host runs this kernel only when the tiles cover the grid exactly (nx % TX == 0, ny % 8 == 0)
-  const bool own = !helper;
+  const bool own = !helper && !secondary;
   const int chunk = p.chunk_ids[blockIdx.z];
   const int zb = p.zstart[chunk], ze = p.zstart[chunk + 1];
   const int np = ze - zb;
   const int plane = (int)p.plane, ncell = (int)p.ncell;
-  const int qxy = own ? j * p.nx + i0 : 0;
+  const int qxy = own || secondary ? j * p.nx + i0 : 0;
   const T dt = p.dt, S = p.S;
   const int nmc = (int)p.nmatcell;
   const int nbx32 = p.nx / 32;
@@ -497,6 +507,78 @@ plain3d_kernel(const Step3DParams<T> p, const __grid_constant__ PlainMaps maps, 
     VV::st(at(xb + CX + o.oS), Hz);
   };
 
+  // ---- bath form: a thread's modes [j0, j0 + NBH) of a cell's nbm modes ----
+  const int cellx = wrow * TX + lane;   // the cell's index in the tile (bath form: VX = 1)
+  // P^{n+1/2}, P^{n-1/2}, Y^n (into bY) and Y^{n-1} (into bV) from the staged bath buffer
+  auto bath_read = [&](int j0, int nbm, T (&bPa)[3], T (&bPb)[3], T (&bY)[3][NBH], T (&bV)[3][NBH]) {
+    const unsigned cofs = L::OFF_BATH + (unsigned)cellx * SZ;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      bPa[c] = ldf(cofs + L::B_P + c * L::BT);
+      bPb[c] = ldf(cofs + L::B_LVL + L::B_P + c * L::BT);
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+      for (int jj = 0; jj < NBH; ++jj)
+        if (j0 + jj < nbm) {
+          bY[c][jj] = ldf(cofs + (unsigned)(c * nbm + j0 + jj) * L::BT);
+          bV[c][jj] = ldf(cofs + L::B_LVL + (unsigned)(c * nbm + j0 + jj) * L::BT);
+        }
+  };
+  // Eq. Pz_update-LB's bath sum over the thread's modes, three components, modes outer (each
+  // coefficient row {k(a+b), -k b, a+b, -(b+1), c, (w dt)^2} read once; ascending j); bV becomes
+  // V = Y^n - Y^{n-1}
+  auto bath_sum = [&](const T* cfm, int j0, int nbm, T (&bY)[3][NBH], T (&bV)[3][NBH], T (&bsum)[3]) {
+#pragma unroll
+    for (int jj = 0; jj < NBH; ++jj) {
+      if (j0 + jj < nbm) {
+        const float4 ca = *reinterpret_cast<const float4*>(cfm + (j0 + jj) * kCoefStride);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          bV[c][jj] = bY[c][jj] - bV[c][jj];
+          bsum[c] = bsum[c] + (ca.x * bY[c][jj] + ca.y * bV[c][jj]);
+        }
+      }
+    }
+  };
+  // Eq. Pz_update-LB (increment form): P^{n+3/2}, its increment, and P^{n+3/2} - P^{n-1/2}
+  auto p_update = [&](const MatK<T>& M, const T (&bPa)[3], const T (&bPb)[3], const T (&Ev)[3],
+                      const T (&bsum)[3], T (&Pn)[3], T (&Vn)[3], T (&dP)[3]) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const T V0 = bPa[c] - bPb[c];
+      T num = M.cE * Ev[c] - M.W * bPa[c] + M.c2 * V0;
+      num = num - T(0.5) * dt * bsum[c];
+      Vn[c] = num * M.inv_A;
+      Pn[c] = bPa[c] + Vn[c];
+      dP[c] = Vn[c] + V0;
+    }
+  };
+  // Eq. Yzj_finite_difference (increment form) for the thread's modes; Y^{n+3/2} overwrites
+  // Y^{n-1/2}; ub collects (Y^{n+3/2} - Y^{n+1/2})^2 + (w dt)^2 (Y^{n+3/2})^2 per component
+  auto bath_modes = [&](const T* cfm, int j0, int nbm, int yB, int mstr, const T (&bY)[3][NBH],
+                        const T (&bV)[3][NBH], const T (&dP)[3], T (&ub)[3]) {
+#pragma unroll
+    for (int jj = 0; jj < NBH; ++jj) {
+      if (j0 + jj < nbm) {
+        const float4 ca = *reinterpret_cast<const float4*>(cfm + (j0 + jj) * kCoefStride);
+        const float2 cb = *reinterpret_cast<const float2*>(cfm + (j0 + jj) * kCoefStride + 4);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          const T y = bY[c][jj];
+          const T Vy = ca.z * y + ca.w * bV[c][jj] + cb.x * dP[c];
+          const T Ynew = y + Vy;
+          p.Yb[yB + (c * nbm + j0 + jj) * mstr] = Ynew;
+          if (p.eE_on) ub[c] += Vy * Vy + cb.y * Ynew * Ynew;
+        }
+      }
+    }
+  };
+  // the two halves' exchange buffer: [0..2] E, [3..5] the first half's bath sums, [6..8] the second's
+  T* sX = reinterpret_cast<T*>(smem_raw + L::OFF_XCH);
+  constexpr int XT = TY * TX;
+
   if (helper) {
     // ======== helper warp: the halo row y0-1 of H^n, the staging of the planes ahead, and its part
     // in the barriers of the compute warps' reductions ========
@@ -545,6 +627,72 @@ plain3d_kernel(const Step3DParams<T> p, const __grid_constant__ PlainMaps maps, 
           }
       }
     }
+  } else if (secondary) {
+    // ======== the bath form's second thread of each cell (SPLIT = 2): modes NBH.. of the cells of
+    // tile row wrow; the same barriers as the first threads' planes ========
+    for (int g = 0; g < np; ++g) {
+      const int k = zb + g;
+      const int info = sInfo[g];
+      const bool bathp = (info & kBath) != 0;
+      double* red = reinterpret_cast<double*>(at(L::OFF_SH + ((g + 1) & 1) * XS));
+      T bPa[3], bPb[3], bY[3][NBH], bV[3][NBH];
+      const int mi2 = (info & 0xF) - 1;
+      int nbm = 0, yB = 0, mstr = 0;
+      if (bathp) {
+        const MatK<T>& M = p.mat[mi2];
+        nbm = M.nb;
+        yB = (int)M.ybase + (k - M.zlo) * plane + qxy;
+        mstr = (int)M.ncell;
+        if (!plain::mbar_wait(&mbar[A], bpar)) {
+          s_abort = 1;
+          atomicExch(p.err, 1);
+        }
+        bpar ^= 1u;
+        bath_read(NBH, nbm, bPa, bPb, bY, bV);
+      }
+      __syncthreads();   // the plane's barrier
+      if (s_abort) break;
+      if (info & kMonH) {
+        for (int m = 0; m < p.nmon; ++m) {
+          const int zm = p.mon_z[m];
+          if (k != zm - 1 && k != zm) continue;
+          double v2[2] = {0.0, 0.0};
+          block_slot_sums<TY, VX>(v2, red, w, lane);
+          __syncthreads();
+        }
+      }
+      if (bathp) {
+        const MatK<T>& M = p.mat[mi2];
+        const T* cfm = sCoef + M.coef_off * kCoefStride;
+        T bsum[3] = {T(0), T(0), T(0)};
+        bath_sum(cfm, NBH, nbm, bY, bV, bsum);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) sX[(6 + c) * XT + cellx] = bsum[c];
+        __syncthreads();   // E and both halves' bath sums exchanged
+        T Ev[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          Ev[c] = sX[c * XT + cellx];
+          bsum[c] = sX[(3 + c) * XT + cellx] + bsum[c];   // the first half's sum first, as there
+        }
+        T Pn[3], Vn[3], dP[3];
+        p_update(M, bPa, bPb, Ev, bsum, Pn, Vn, dP);
+        T ub[3] = {T(0), T(0), T(0)};
+        bath_modes(cfm, NBH, nbm, yB, mstr, bY, bV, dP, ub);
+        if (p.eE_on && (info & kBox)) {
+#pragma unroll
+          for (int c = 0; c < 3; ++c) uB += M.rho_idt2 * ub[c];
+        }
+      }
+      if (info & kMonE) {
+        for (int m = 0; m < p.nmon; ++m) {
+          if (k != p.mon_z[m]) continue;
+          double v2[2] = {0.0, 0.0};
+          block_slot_sums<TY, VX>(v2, red, w, lane);
+          __syncthreads();
+        }
+      }
+    }
   } else {
     // ======== compute warps: plane k of the own row.  GEN = false is a plain vacuum plane (no
     // layer, CPML, source, monitor or energy box, not the top plane) ========
@@ -576,7 +724,7 @@ plain3d_kernel(const Step3DParams<T> p, const __grid_constant__ PlainMaps maps, 
       // bath planes: P^{n+1/2}, P^{n-1/2} and both levels of the bath modes of the cell, read from
       // the staged bath buffer before the plane's barrier (Y^n in bY; Y^{n-1} in bV, which becomes
       // V = Y^n - Y^{n-1} below)
-      T bPa[3], bPb[3], bY[3][NBA], bV[3][NBA];
+      T bPa[3], bPb[3], bY[3][NBH], bV[3][NBH];
       int rB = 0, yB = 0, mstr = 0, nbm = 0;
       if constexpr (BATH) {
         const MatK<T>& M = p.mat[mi];
@@ -655,20 +803,7 @@ plain3d_kernel(const Step3DParams<T> p, const __grid_constant__ PlainMaps maps, 
           atomicExch(p.err, 1);
         }
         bpar ^= 1u;
-        const unsigned cofs = L::OFF_BATH + (unsigned)(w * TX + lane) * SZ;
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-          bPa[c] = ldf(cofs + L::B_P + c * L::BT);
-          bPb[c] = ldf(cofs + L::B_LVL + L::B_P + c * L::BT);
-        }
-#pragma unroll
-        for (int c = 0; c < 3; ++c)
-#pragma unroll
-          for (int jj = 0; jj < NBA; ++jj)
-            if (jj < nbm) {
-              bY[c][jj] = ldf(cofs + (unsigned)(c * nbm + jj) * L::BT);
-              bV[c][jj] = ldf(cofs + L::B_LVL + (unsigned)(c * nbm + jj) * L::BT);
-            }
+        bath_read(0, nbm, bPa, bPb, bY, bV);
       }
       __syncthreads();   // H^n(k) of the tile and its halo complete; E_in(k), H_in(k) slots free
       if (s_abort) return false;
@@ -847,50 +982,28 @@ plain3d_kernel(const Step3DParams<T> p, const __grid_constant__ PlainMaps maps, 
       }
       if constexpr (BATH) {
         // ---- Eq. Pz_update-LB and Eq. Yzj_finite_difference (increment form) for the three
-        // components, modes outer: each mode's coefficient row
-        // {k(a+b), -k b, a+b, -(b+1), c, (w dt)^2} is read once; per component the sums run over
-        // ascending j ----
+        // components, modes outer (with SPLIT = 2 this thread's half of the modes; the halves
+        // exchange their bath sums and both form the same P^{n+3/2}) ----
         const MatK<T>& M = p.mat[mi];
         const T* cfm = sCoef + M.coef_off * kCoefStride;
         T bsum[3] = {T(0), T(0), T(0)};
+        bath_sum(cfm, 0, nbm, bY, bV, bsum);
+        if constexpr (SPLIT > 1) {
 #pragma unroll
-        for (int jj = 0; jj < NBA; ++jj) {
-          if (jj < nbm) {
-            const float4 ca = *reinterpret_cast<const float4*>(cfm + jj * kCoefStride);
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-              bV[c][jj] = bY[c][jj] - bV[c][jj];   // V_j = Y^n - Y^{n-1}
-              bsum[c] = bsum[c] + (ca.x * bY[c][jj] + ca.y * bV[c][jj]);
-            }
+          for (int c = 0; c < 3; ++c) {
+            sX[c * XT + cellx] = Ev[c];
+            sX[(3 + c) * XT + cellx] = bsum[c];
           }
+          __syncthreads();   // E and both halves' bath sums exchanged
+#pragma unroll
+          for (int c = 0; c < 3; ++c) bsum[c] = bsum[c] + sX[(6 + c) * XT + cellx];
         }
         T Pn[3], Vn[3], dP[3];
+        p_update(M, bPa, bPb, Ev, bsum, Pn, Vn, dP);
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
-          const T V0 = bPa[c] - bPb[c];
-          T num = M.cE * Ev[c] - M.W * bPa[c] + M.c2 * V0;
-          num = num - T(0.5) * dt * bsum[c];
-          Vn[c] = num * M.inv_A;
-          Pn[c] = bPa[c] + Vn[c];
-          p.Pb[c * nmc + rB] = Pn[c];   // overwrites P^{n-1/2}
-          dP[c] = Vn[c] + V0;           // P^{n+3/2} - P^{n-1/2}
-        }
+        for (int c = 0; c < 3; ++c) p.Pb[c * nmc + rB] = Pn[c];   // overwrites P^{n-1/2}
         T ub[3] = {T(0), T(0), T(0)};
-#pragma unroll
-        for (int jj = 0; jj < NBA; ++jj) {
-          if (jj < nbm) {
-            const float4 ca = *reinterpret_cast<const float4*>(cfm + jj * kCoefStride);
-            const float2 cb = *reinterpret_cast<const float2*>(cfm + jj * kCoefStride + 4);
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-              const T y = bY[c][jj];
-              const T Vy = ca.z * y + ca.w * bV[c][jj] + cb.x * dP[c];
-              const T Ynew = y + Vy;
-              p.Yb[yB + (c * nbm + jj) * mstr] = Ynew;   // overwrites Y^{n-1}
-              if (p.eE_on) ub[c] += Vy * Vy + cb.y * Ynew * Ynew;
-            }
-          }
-        }
+        bath_modes(cfm, 0, nbm, yB, mstr, bY, bV, dP, ub);
         if (p.eE_on && in_box) {
 #pragma unroll
           for (int c = 0; c < 3; ++c) {
@@ -942,6 +1055,15 @@ plain3d_kernel(const Step3DParams<T> p, const __grid_constant__ PlainMaps maps, 
     if (NB > 0 && bath_pending) plain::mbar_wait(&mbar[A], bpar);
   }
   // ---- energy partials of this block, one per 32 x 8 slot (zero outside the box) ----
+  if constexpr (SPLIT > 1) {
+    // the second threads' bath energy joins the first threads' before the block sums
+    if (p.eE_on) {
+      __syncthreads();
+      if (secondary) sX[cellx] = uB;
+      __syncthreads();
+      if (!secondary) uB += sX[cellx];
+    }
+  }
   if (p.eE_on || p.eH_on) {
     __syncthreads();
     double* red = reinterpret_cast<double*>(at(L::OFF_SH));

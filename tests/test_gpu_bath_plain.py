@@ -1,6 +1,6 @@
-"""GPU parity of the plain-plane kernel's Lorentz-Bath form (FP32, one cell per thread, at most
-8 bath modes per material, 32 x 8 tiles) against the FP64 CPU oracle and against the general
-step kernel.
+"""GPU parity of the plain-plane kernel's Lorentz-Bath form (FP32, 32 x 8 tiles; one cell per
+thread with at most 8 bath modes per material, two threads per cell with 9 to 16) against the
+FP64 CPU oracle and against the general step kernel.
 
 The cavities are those of test_gpu_plain.py (CPML, vacuum with a phased source, an
 eps_inf = 2.25 spacer, eps_inf = 1.5 Drude mirrors, an eps_inf = 2 Lorentz-Bath layer, the energy
@@ -52,7 +52,7 @@ def bath_cavity(nx=64, ny=16, steps=120, seed=3, nb=8, layer=10):
     return p
 
 
-@pytest.mark.parametrize("nb", [8, 4, 3])
+@pytest.mark.parametrize("nb", [8, 4, 3, 16, 11])
 def test_bath_form_from_rest_matches_oracle(nb):
     prob = bath_cavity(nb=nb)
     g = fb.Simulation(prob, precision=32, energy_capacity=200)
@@ -69,11 +69,11 @@ def test_bath_form_from_rest_matches_oracle(nb):
     assert np.max(np.abs(to[:, 2])) > 0
 
 
-@pytest.mark.parametrize("shape", [(64, 16), (32, 8), (96, 24)])
-def test_bath_form_random_state_matches_oracle(shape):
+@pytest.mark.parametrize("shape,nb", [((64, 16), 8), ((32, 8), 8), ((96, 24), 8), ((64, 16), 16), ((32, 8), 13)])
+def test_bath_form_random_state_matches_oracle(shape, nb):
     """Every field, polarization and bath-mode component nonzero; one tile per plane (32 x 8:
-    every halo is the tile's own wrapped column / row) and several."""
-    prob = bath_cavity(nx=shape[0], ny=shape[1], steps=7, seed=5)
+    every halo is the tile's own wrapped column / row) and several; one and two threads per cell."""
+    prob = bath_cavity(nx=shape[0], ny=shape[1], steps=7, seed=5, nb=nb)
     st = wl.random_state(prob, seed=11)
     g = fb.Simulation(prob, precision=32, energy_capacity=16)
     assert g.bath_plain_kernel()
@@ -87,12 +87,12 @@ def test_bath_form_random_state_matches_oracle(shape):
         assert rel(tg[:, col], to[:, col]) < TOL[32], col
 
 
-@pytest.mark.parametrize("zchunk", ["16", "5", "64"])
-def test_bath_form_equals_general_kernel(zchunk):
+@pytest.mark.parametrize("zchunk,nb", [("16", 8), ("5", 8), ("64", 8), ("16", 16), ("64", 16)])
+def test_bath_form_equals_general_kernel(zchunk, nb):
     """The same run with the bath form and with the general kernel's bath instantiation: fields,
     polarizations and every bath mode to FP32 rounding; the layer cut into chunks of about 5, 16
     and 64 (one chunk) planes."""
-    prob = bath_cavity(nx=64, ny=16, steps=60, layer=40)
+    prob = bath_cavity(nx=64, ny=16, steps=60, layer=40, nb=nb)
     sims = []
     for flag in ("1", "0"):
         with env(FDTDBATH_BATHPLAIN=flag, FDTDBATH_BATH_ZCHUNK=zchunk):
@@ -104,7 +104,7 @@ def test_bath_form_equals_general_kernel(zchunk):
     for name in ("E", "H", "P", "Pm"):
         assert rel(stack(a, name), stack(b, name)) < 1e-6, name
     lo, hi = prob["materials"][2]["z"]
-    for j in range(8):
+    for j in range(nb):
         for lvl in (0, 1):
             assert rel(stack(a, "Y", mode=j, level=lvl)[:, lo:hi],
                        stack(b, "Y", mode=j, level=lvl)[:, lo:hi]) < 1e-6, (j, lvl)
@@ -135,10 +135,10 @@ def test_bath_form_zero_coupling_is_lorentz():
 
 
 def test_bath_form_not_used_outside_its_range():
-    """FP64, more than 8 modes, bf16 bath storage, x not a multiple of 32, y not of 8, a source
+    """FP64, more than 16 modes, bf16 bath storage, x not a multiple of 32, y not of 8, a source
     plane inside the layer: the general kernel."""
     cases = [(bath_cavity(steps=1), dict(precision=64)),
-             (bath_cavity(steps=1, nb=16), dict(precision=32)),
+             (bath_cavity(steps=1, nb=17), dict(precision=32)),
              (bath_cavity(steps=1), dict(precision=32, bath_storage=1)),
              (bath_cavity(nx=48, steps=1), dict(precision=32)),
              (bath_cavity(ny=12, steps=1), dict(precision=32))]
@@ -155,10 +155,11 @@ def test_bath_form_not_used_outside_its_range():
     g.close()
 
 
-def test_bath_form_snapshot_resume_bitwise():
+@pytest.mark.parametrize("nb", [8, 16])
+def test_bath_form_snapshot_resume_bitwise(nb):
     """A snapshot taken between steps and restored into a fresh simulation continues bit for bit
     with the bath form (its pending H half-step stays pending across the snapshot)."""
-    prob = bath_cavity(steps=40)
+    prob = bath_cavity(steps=40, nb=nb)
     a = fb.Simulation(prob, precision=32, energy_capacity=64)
     a.step(17)
     buf = a.snapshot()
