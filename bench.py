@@ -279,7 +279,15 @@ def form_precision(fb, stream, torch):
         byts = algorithmic_bytes(prob, 4, None if bs == 0 else 8.0)
         out[tag] = {"value": cells / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms,
                     "bytes_per_cell": byts / cells, "achieved_GBs": byts / (ms * 1e-3) / 1e9,
-                    "frac_hbm": byts / (ms * 1e-3) / 1e9 / hbm}
+                    "frac_hbm": byts / (ms * 1e-3) / 1e9 / hbm,
+                    "bath_kernel": "plain3d Lorentz-Bath form" if sim.bath_plain_kernel() else "step3d"}
+        if bs:
+            # against 6 B per mode and component (a bf16 value of each of two levels read, one
+            # written): the bf16 pair layout moves 8 (value and increment read and written)
+            b6 = algorithmic_bytes(prob, 4, 6.0)
+            out[tag].update({"bytes_per_cell_6B_per_mode": b6 / cells,
+                             "frac_hbm_6B_per_mode": b6 / (ms * 1e-3) / 1e9 / hbm,
+                             "pair_layout_extra_bytes_per_cell": (byts - b6) / cells})
         sim.close()
     crop = wl.precision_crop()
     runs = {}

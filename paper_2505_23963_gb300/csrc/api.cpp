@@ -136,8 +136,8 @@ struct fdtdbath_sim {
   // its TX x 8 tiles (TX = 128 FP32, 64 FP64 cells), every source plane outside the layers
   bool plain_ok = false;
   PlainMaps maps{};         // its tensor maps of the E and H arrays
-  // its one-cell-per-thread form for the Lorentz-Bath chunks: FP32 with FP32 bath storage, at most
-  // 8 bath modes per material, 32 x 8 tiles; chunks of at most 64 planes
+  // its Lorentz-Bath form for the bath chunks: FP32 (FP32 or bf16 bath storage), at most 16 bath
+  // modes per material, 32 x 8 tiles; chunks of at most 64 planes
   bool bath_plain = false;
   PlainMaps bmaps{};        // tensor maps of 32-cell-wide boxes
   BathMaps bath_maps{};     // tensor maps of its polarization and bath-mode arrays
@@ -350,7 +350,8 @@ bool encode_bath_maps(fdtdbath_sim* s, BathMaps* out) {
       const cuuint64_t pdims[4] = {(cuuint64_t)s->nx, (cuuint64_t)s->ny, nzm, 3};
       const cuuint64_t pstr[3] = {(cuuint64_t)s->nx * 4, (cuuint64_t)s->plane * 4, (cuuint64_t)s->nmatcell * 4};
       const cuuint32_t pbox[4] = {(cuuint32_t)kBathTileX, 8, 1, 3};
-      void* yb = (char*)s->Yslot[b] + M.ybase * 4;
+      // (bf16 storage: one array of 4-byte (value, increment) pairs, the same for both slots)
+      void* yb = (char*)s->Yslot[s->ybf ? 0 : b] + M.ybase * 4;
       void* pb = (char*)s->Pslot[b] + M.base * 4;
       if (fn(&out->y[i][b], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, yb, ydims, ystr, ybox, es,
              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -460,7 +461,7 @@ int launch_plain_typed(const Step3DParams<double>& p, const fdtdbath_sim* s, int
 }
 
 int launch_bath_typed(const Step3DParams<float>& p, const fdtdbath_sim* s, int n, cudaStream_t st) {
-  return launch_bath3d_f32(p, s->bmaps, s->bath_maps, s->pcur, s->ecur, s->hcur, n, s->nbmax, st);
+  return launch_bath3d_f32(p, s->bmaps, s->bath_maps, s->pcur, s->ecur, s->hcur, n, s->nbmax, s->ybf ? 1 : 0, st);
 }
 int launch_bath_typed(const Step3DParams<double>&, const fdtdbath_sim*, int, cudaStream_t) {
   return (int)cudaErrorInvalidValue;   // FP64 runs the general kernel (bath_plain is never set)
@@ -991,7 +992,7 @@ int fdtdbath_create(const fdtdbath_grid* grid, double resolution, double courant
   // by its (TX x 8) tiles whose source planes lie outside the layers, when the tensor maps can be
   // encoded (FDTDBATH_PLAIN=0 keeps the general kernel); those ranges are then cut into near-equal
   // chunks of about plain_zc planes (FDTDBATH_PLAIN_ZCHUNK, at most 64)
-  // Its bath form (FP32 with FP32 bath storage, at most 8 modes per material in at most two
+  // Its bath form (FP32, FP32 or bf16 bath storage, at most 16 modes per material in at most two
   // Lorentz-Bath materials, 32 x 8 tiles) takes the Lorentz-Bath ranges, cut into near-equal
   // chunks of about bath_zc planes (FDTDBATH_BATH_ZCHUNK, at most 64; FDTDBATH_BATHPLAIN=0 keeps
   // the general kernel there).  One chunk per layer of up to 64 planes measured fastest on the
@@ -1005,7 +1006,7 @@ int fdtdbath_create(const fdtdbath_grid* grid, double resolution, double courant
     const char* e = std::getenv("FDTDBATH_PLAIN");
     s->plain_ok = !(e && std::atoi(e) == 0) && s->ty == 8 && nx % tx == 0 && ny % 8 == 0 && !src_in_layer;
     const char* eb = std::getenv("FDTDBATH_BATHPLAIN");
-    s->bath_plain = !(eb && std::atoi(eb) == 0) && s->prec == 32 && !s->ybf && s->nbmax > 0 &&
+    s->bath_plain = !(eb && std::atoi(eb) == 0) && s->prec == 32 && s->nbmax > 0 &&
                     s->nbmax <= kBathPlainMaxModes && s->ty == 8 && nx % kBathTileX == 0 && ny % 8 == 0 &&
                     !src_in_layer;
   }

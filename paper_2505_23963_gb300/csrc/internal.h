@@ -182,8 +182,10 @@ struct BathMaps {
   CUtensorMap y[kBathPlainMaxMats][2];        // [material][slot]
   CUtensorMap pp[kBathPlainMaxMats][2];       // [material][slot]
 };
+// ybf: bf16 bath storage (the modes as in-place (value, increment) pairs, maps y[i][0] = y[i][1]
+// over them; at most 16 modes)
 int launch_bath3d_f32(const Step3DParams<float>& p, const PlainMaps& maps, const BathMaps& bmaps, int pcur, int ebuf,
-                      int hbuf, int nchunks, int nb, void* stream);
+                      int hbuf, int nchunks, int nb, int ybf, void* stream);
 int launch_plain3d_f64(const Step3DParams<double>& p, const PlainMaps& maps, int ebuf, int hbuf, int nchunks,
                        void* stream);
 

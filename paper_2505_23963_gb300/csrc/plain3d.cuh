@@ -52,6 +52,7 @@
 #pragma once
 
 #include <cuda.h>
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -275,13 +276,18 @@ struct Plain3DLayout {
 // NB = 0: the plain-plane kernel; NB > 0 (one cell per thread, FP32 increment form): the same
 // kernel for z-chunks with Lorentz-Bath planes of at most NB bath modes per material, whose
 // polarization and bath state (both levels) is loaded into registers at the start of the plane
-template <typename T, bool INC, int VX, int A, int NB = 0>
+//
+// YB: bf16 bath storage -- one 32-bit word per mode, component and cell holding the value Y^n and
+// the increment V = Y^n - Y^{n-1} as a bf16 pair, updated in place (the general kernel's layout);
+// one level of words is staged instead of two.
+template <typename T, bool INC, int VX, int A, int NB = 0, bool YB = false>
 __global__ void __launch_bounds__(Plain3DLayout<T, VX, A, NB>::threads, Plain3DLayout<T, VX, A, NB>::min_blocks)
 plain3d_kernel(const Step3DParams<T> p, const __grid_constant__ PlainMaps maps, const __grid_constant__ BathMaps bm,
                int pcur, int ebuf, int hbuf) {
   using namespace plain;
   using L = Plain3DLayout<T, VX, A, NB>;
   static_assert(NB == 0 || (INC && VX == 1), "bath planes: FP32 increment form, one cell per thread");
+  static_assert(!YB || (NB > 0 && sizeof(T) == 4), "bf16 bath storage: the FP32 bath form");
   using VV = Vec<T, VX>;
   constexpr int TY = L::TY, TX = L::TX, NE = L::NE, NH = L::NH;
   constexpr unsigned SZ = sizeof(T), ES = L::ES, HS = L::HS, XS = L::XS;
@@ -414,11 +420,12 @@ plain3d_kernel(const Step3DParams<T> p, const __grid_constant__ PlainMaps maps, 
     const MatK<T>& M = p.mat[mi_];
     const int z = zb + g - M.zlo;
     uint64_t* bar = &mbar[A];
-    plain::mbar_arrive_expect_tx(bar, 2u * (3u * M.nb + 3u) * L::BT);
+    // (bf16 pairs: the words have the size of T, one level in place)
+    plain::mbar_arrive_expect_tx(bar, ((YB ? 1u : 2u) * 3u * M.nb + 6u) * L::BT);
     const unsigned d = smem_u32(smem_raw) + L::OFF_BATH;
     plain::tma_load4(d, &bm.y[i][pcur], x0, y0, z, 0, bar);
     plain::tma_load4(d + L::B_P, &bm.pp[i][pcur], x0, y0, z, 0, bar);
-    plain::tma_load4(d + L::B_LVL, &bm.y[i][1 - pcur], x0, y0, z, 0, bar);
+    if (!YB) plain::tma_load4(d + L::B_LVL, &bm.y[i][1 - pcur], x0, y0, z, 0, bar);
     plain::tma_load4(d + L::B_LVL + L::B_P, &bm.pp[i][1 - pcur], x0, y0, z, 0, bar);
     bath_pending = true;
   };
@@ -522,13 +529,20 @@ plain3d_kernel(const Step3DParams<T> p, const __grid_constant__ PlainMaps maps, 
 #pragma unroll
       for (int jj = 0; jj < NBH; ++jj)
         if (j0 + jj < nbm) {
-          bY[c][jj] = ldf(cofs + (unsigned)(c * nbm + j0 + jj) * L::BT);
-          bV[c][jj] = ldf(cofs + L::B_LVL + (unsigned)(c * nbm + j0 + jj) * L::BT);
+          if constexpr (YB) {
+            const __nv_bfloat162 q =
+                *reinterpret_cast<const __nv_bfloat162*>(at(cofs + (unsigned)(c * nbm + j0 + jj) * L::BT));
+            bY[c][jj] = __low2float(q);    // Y^n
+            bV[c][jj] = __high2float(q);   // V = Y^n - Y^{n-1}
+          } else {
+            bY[c][jj] = ldf(cofs + (unsigned)(c * nbm + j0 + jj) * L::BT);
+            bV[c][jj] = ldf(cofs + L::B_LVL + (unsigned)(c * nbm + j0 + jj) * L::BT);
+          }
         }
   };
   // Eq. Pz_update-LB's bath sum over the thread's modes, three components, modes outer (each
   // coefficient row {k(a+b), -k b, a+b, -(b+1), c, (w dt)^2} read once; ascending j); bV becomes
-  // V = Y^n - Y^{n-1}
+  // V = Y^n - Y^{n-1} (bf16 pairs: it holds V already)
   auto bath_sum = [&](const T* cfm, int j0, int nbm, T (&bY)[3][NBH], T (&bV)[3][NBH], T (&bsum)[3]) {
 #pragma unroll
     for (int jj = 0; jj < NBH; ++jj) {
@@ -536,7 +550,7 @@ plain3d_kernel(const Step3DParams<T> p, const __grid_constant__ PlainMaps maps, 
         const float4 ca = *reinterpret_cast<const float4*>(cfm + (j0 + jj) * kCoefStride);
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-          bV[c][jj] = bY[c][jj] - bV[c][jj];
+          if (!YB) bV[c][jj] = bY[c][jj] - bV[c][jj];
           bsum[c] = bsum[c] + (ca.x * bY[c][jj] + ca.y * bV[c][jj]);
         }
       }
@@ -556,7 +570,7 @@ plain3d_kernel(const Step3DParams<T> p, const __grid_constant__ PlainMaps maps, 
     }
   };
   // Eq. Yzj_finite_difference (increment form) for the thread's modes; Y^{n+3/2} overwrites
-  // Y^{n-1/2}; ub collects (Y^{n+3/2} - Y^{n+1/2})^2 + (w dt)^2 (Y^{n+3/2})^2 per component
+  // Y^{n-1/2} (bf16 pairs: the pair (Y^{n+3/2}, its increment) overwrites the word); ub collects (Y^{n+3/2} - Y^{n+1/2})^2 + (w dt)^2 (Y^{n+3/2})^2 per component
   auto bath_modes = [&](const T* cfm, int j0, int nbm, int yB, int mstr, const T (&bY)[3][NBH],
                         const T (&bV)[3][NBH], const T (&dP)[3], T (&ub)[3]) {
 #pragma unroll
@@ -569,7 +583,12 @@ plain3d_kernel(const Step3DParams<T> p, const __grid_constant__ PlainMaps maps, 
           const T y = bY[c][jj];
           const T Vy = ca.z * y + ca.w * bV[c][jj] + cb.x * dP[c];
           const T Ynew = y + Vy;
-          p.Yb[yB + (c * nbm + j0 + jj) * mstr] = Ynew;
+          const int q = yB + (c * nbm + j0 + jj) * mstr;
+          if constexpr (YB)
+            reinterpret_cast<__nv_bfloat162*>(p.Ya)[q] =
+                __halves2bfloat162(__float2bfloat16_rn(Ynew), __float2bfloat16_rn(Vy));
+          else
+            p.Yb[q] = Ynew;
           if (p.eE_on) ub[c] += Vy * Vy + cb.y * Ynew * Ynew;
         }
       }

@@ -8,11 +8,11 @@
 
 namespace fdtdbath {
 
-template <int VX, int A, int NB = 0>
+template <int VX, int A, int NB = 0, bool YB = false>
 static int launch_shape(const Step3DParams<float>& p, const PlainMaps& maps, const BathMaps& bmaps, int pcur, int ebuf,
                         int hbuf, int nchunks, void* stream) {
   using L = Plain3DLayout<float, VX, A, NB>;
-  auto kern = plain3d_kernel<float, true, VX, A, NB>;
+  auto kern = plain3d_kernel<float, true, VX, A, NB, YB>;
   static bool attr_set = false;   // once per process: more than 48 KB, shared-memory carveout
   if (!attr_set) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::bytes);
@@ -33,7 +33,12 @@ int launch_plain3d_f32(const Step3DParams<float>& p, const PlainMaps& maps, int 
 }
 
 int launch_bath3d_f32(const Step3DParams<float>& p, const PlainMaps& maps, const BathMaps& bmaps, int pcur, int ebuf,
-                      int hbuf, int nchunks, int nb, void* stream) {
+                      int hbuf, int nchunks, int nb, int ybf, void* stream) {
+  if (ybf) {
+    if (nb <= 8) return launch_shape<1, 2, 8, true>(p, maps, bmaps, pcur, ebuf, hbuf, nchunks, stream);
+    if (nb <= 16) return launch_shape<1, 2, 16, true>(p, maps, bmaps, pcur, ebuf, hbuf, nchunks, stream);
+    return (int)cudaErrorInvalidValue;
+  }
   if (nb <= 4) return launch_shape<1, 2, 4>(p, maps, bmaps, pcur, ebuf, hbuf, nchunks, stream);
   if (nb <= 8) return launch_shape<1, 2, 8>(p, maps, bmaps, pcur, ebuf, hbuf, nchunks, stream);
   if (nb <= 16) return launch_shape<1, 2, 16>(p, maps, bmaps, pcur, ebuf, hbuf, nchunks, stream);

@@ -135,11 +135,11 @@ def test_bath_form_zero_coupling_is_lorentz():
 
 
 def test_bath_form_not_used_outside_its_range():
-    """FP64, more than 16 modes, bf16 bath storage, x not a multiple of 32, y not of 8, a source
-    plane inside the layer: the general kernel."""
+    """FP64, more than 16 modes, x not a multiple of 32, y not of 8, a source plane inside the
+    layer: the general kernel."""
     cases = [(bath_cavity(steps=1), dict(precision=64)),
              (bath_cavity(steps=1, nb=17), dict(precision=32)),
-             (bath_cavity(steps=1), dict(precision=32, bath_storage=1)),
+             (bath_cavity(steps=1, nb=17), dict(precision=32, bath_storage=1)),
              (bath_cavity(nx=48, steps=1), dict(precision=32)),
              (bath_cavity(ny=12, steps=1), dict(precision=32))]
     src_in = bath_cavity(steps=1)
@@ -150,9 +150,10 @@ def test_bath_form_not_used_outside_its_range():
         g = fb.Simulation(prob, **kw)
         assert not g.bath_plain_kernel(), kw
         g.close()
-    g = fb.Simulation(bath_cavity(steps=1), precision=32)
-    assert g.bath_plain_kernel()
-    g.close()
+    for kw in (dict(precision=32), dict(precision=32, bath_storage=1)):
+        g = fb.Simulation(bath_cavity(steps=1), **kw)
+        assert g.bath_plain_kernel(), kw
+        g.close()
 
 
 @pytest.mark.parametrize("nb", [8, 16])
@@ -170,3 +171,30 @@ def test_bath_form_snapshot_resume_bitwise(nb):
     for name in ("E", "H", "P", "Pm"):
         assert np.array_equal(stack(a, name), stack(b, name)), name
     assert np.array_equal(a.dft(0), b.dft(0))
+
+
+@pytest.mark.parametrize("nb", [8, 16, 6])
+def test_bath_form_bf16_storage_equals_general_kernel(nb):
+    """bf16 bath storage (in-place (value, increment) pairs): the bath form against the general
+    kernel's bf16 instantiation on the same run.  Both do the same FP32 arithmetic and round the
+    same pairs, so the fields agree to FP32 rounding; a pair rounded to the other side of a bf16
+    step by a last-bit difference moves a mode by 2^-8 relative, so the modes get 1e-3."""
+    prob = bath_cavity(nx=64, ny=16, steps=60, layer=24, nb=nb)
+    sims = []
+    for flag in ("1", "0"):
+        with env(FDTDBATH_BATHPLAIN=flag):
+            s = fb.Simulation(prob, precision=32, bath_storage=1, energy_capacity=64)
+        assert s.bath_plain_kernel() == (flag == "1")
+        s.step(60)
+        sims.append(s)
+    a, b = sims
+    for name in ("E", "H", "P", "Pm"):
+        assert rel(stack(a, name), stack(b, name)) < 1e-5, name
+    lo, hi = prob["materials"][2]["z"]
+    for j in sorted({0, nb // 2, nb - 1}):
+        for lvl in (0, 1):
+            assert rel(stack(a, "Y", mode=j, level=lvl)[:, lo:hi],
+                       stack(b, "Y", mode=j, level=lvl)[:, lo:hi]) < 1e-3, (j, lvl)
+    ta, tb = a.trace(), b.trace()
+    for col in range(3):
+        assert rel(ta[:, col], tb[:, col]) < 1e-4, col
