@@ -227,9 +227,10 @@ int fdtdbath_bath_form(int32_t shape, double frequency, double gamma, int32_t nu
  * tiles, ny a multiple of 8, no source plane inside a layer) instead of the general kernel.
  * Key 8: whether the steps run on the persistent 1D cavity kernel (nx = ny = 1, at most one
  * source and one monitor, at most 32 bath modes per material, x polarization only).  Key 9:
- * whether the z-chunks with bath modes run the plain-plane kernel's Lorentz-Bath form (FP32,
- * FP32 or bf16 bath storage, at most 16 bath modes per material in at most two Lorentz-Bath
- * layers, nx a multiple of 32, ny of 8, no source plane inside a layer). */
+ * whether the z-chunks with bath modes run the plain-plane kernel's Lorentz-Bath form (FP32; at
+ * most 16 bath modes per material with FP32 or bf16 bath storage, or up to 128 with FP32
+ * storage; at most two Lorentz-Bath layers; nx a multiple of 32, ny of 8, no source plane inside a
+ * layer). */
 int64_t fdtdbath_query(const fdtdbath_sim *sim, int32_t key);
 
 /* Energy (U_EM, U_P, U_bath) of planes z_lo <= k < z_hi of the current state -- the same

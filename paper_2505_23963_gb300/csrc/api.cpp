@@ -136,8 +136,9 @@ struct fdtdbath_sim {
   // its TX x 8 tiles (TX = 128 FP32, 64 FP64 cells), every source plane outside the layers
   bool plain_ok = false;
   PlainMaps maps{};         // its tensor maps of the E and H arrays
-  // its Lorentz-Bath form for the bath chunks: FP32 (FP32 or bf16 bath storage), at most 16 bath
-  // modes per material, 32 x 8 tiles; chunks of at most 64 planes
+  // its Lorentz-Bath form for the bath chunks: FP32, at most 16 bath modes per material in
+  // registers (FP32 or bf16 bath storage) or up to 128 streamed (FP32 storage), 32 x 8 tiles;
+  // chunks of at most 64 planes
   bool bath_plain = false;
   PlainMaps bmaps{};        // tensor maps of 32-cell-wide boxes
   BathMaps bath_maps{};     // tensor maps of its polarization and bath-mode arrays
@@ -346,7 +347,9 @@ bool encode_bath_maps(fdtdbath_sim* s, BathMaps* out) {
     for (int b = 0; b < 2; ++b) {
       const cuuint64_t ydims[4] = {(cuuint64_t)s->nx, (cuuint64_t)s->ny, nzm, 3 * (cuuint64_t)M.nb};
       const cuuint64_t ystr[3] = {(cuuint64_t)s->nx * 4, (cuuint64_t)s->plane * 4, (cuuint64_t)M.ncell * 4};
-      const cuuint32_t ybox[4] = {(cuuint32_t)kBathTileX, 8, 1, 3 * (cuuint32_t)M.nb};
+      // boxes of the whole plane tile's modes, or (streamed form) of kStreamBatchModes modes
+      const cuuint32_t bm_ = s->nbmax > kBathPlainRegModes ? (cuuint32_t)kStreamBatchModes : 3 * (cuuint32_t)M.nb;
+      const cuuint32_t ybox[4] = {(cuuint32_t)kBathTileX, 8, 1, bm_};
       const cuuint64_t pdims[4] = {(cuuint64_t)s->nx, (cuuint64_t)s->ny, nzm, 3};
       const cuuint64_t pstr[3] = {(cuuint64_t)s->nx * 4, (cuuint64_t)s->plane * 4, (cuuint64_t)s->nmatcell * 4};
       const cuuint32_t pbox[4] = {(cuuint32_t)kBathTileX, 8, 1, 3};
@@ -992,8 +995,9 @@ int fdtdbath_create(const fdtdbath_grid* grid, double resolution, double courant
   // by its (TX x 8) tiles whose source planes lie outside the layers, when the tensor maps can be
   // encoded (FDTDBATH_PLAIN=0 keeps the general kernel); those ranges are then cut into near-equal
   // chunks of about plain_zc planes (FDTDBATH_PLAIN_ZCHUNK, at most 64)
-  // Its bath form (FP32, FP32 or bf16 bath storage, at most 16 modes per material in at most two
-  // Lorentz-Bath materials, 32 x 8 tiles) takes the Lorentz-Bath ranges, cut into near-equal
+  // Its bath form (FP32; at most 16 modes per material held in registers, with FP32 or bf16 bath
+  // storage, or up to 128 streamed, with FP32 storage; at most two Lorentz-Bath materials; 32 x 8
+  // tiles) takes the Lorentz-Bath ranges, cut into near-equal
   // chunks of about bath_zc planes (FDTDBATH_BATH_ZCHUNK, at most 64; FDTDBATH_BATHPLAIN=0 keeps
   // the general kernel there).  One chunk per layer of up to 64 planes measured fastest on the
   // 256^3 slab: each chunk start pays the prologue and the first stages' latency.
@@ -1006,9 +1010,13 @@ int fdtdbath_create(const fdtdbath_grid* grid, double resolution, double courant
     const char* e = std::getenv("FDTDBATH_PLAIN");
     s->plain_ok = !(e && std::atoi(e) == 0) && s->ty == 8 && nx % tx == 0 && ny % 8 == 0 && !src_in_layer;
     const char* eb = std::getenv("FDTDBATH_BATHPLAIN");
+    int nmodes_all = 0;
+    for (auto& m : s->mats) nmodes_all += m.nb;
     s->bath_plain = !(eb && std::atoi(eb) == 0) && s->prec == 32 && s->nbmax > 0 &&
                     s->nbmax <= kBathPlainMaxModes && s->ty == 8 && nx % kBathTileX == 0 && ny % 8 == 0 &&
-                    !src_in_layer;
+                    !src_in_layer &&
+                    // the streamed form (more than 16 modes): FP32 bath storage, its coefficient table
+                    (s->nbmax <= kBathPlainRegModes || (!s->ybf && nmodes_all <= kStreamCoefRows));
   }
   int plain_zc = 0, bath_zc = 0, bath_nmin = 1;
   if (s->plain_ok) {

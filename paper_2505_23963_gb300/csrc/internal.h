@@ -174,7 +174,10 @@ int launch_plain3d_f32(const Step3DParams<float>& p, const PlainMaps& maps, int 
 // roles swap every step), P as a 4-D tensor (x, y, z in the layer, component) and the modes as
 // (x, y, z in the layer, component * nb + mode), boxes of one 32 x 8 plane tile.
 constexpr int kBathTileX = 32;
-constexpr int kBathPlainMaxModes = 16;
+constexpr int kBathPlainMaxModes = 128;
+constexpr int kBathPlainRegModes = 16;   // above: the streamed form (FP32 bath storage only)
+constexpr int kStreamCoefRows = 256;     // the streamed form's coefficient rows (all materials)
+constexpr int kStreamBatchModes = 8;     // modes of one component per streamed batch
 constexpr int kBathPlainMaxMats = 2;
 struct BathMaps {
   int nmat;                                   // materials with maps

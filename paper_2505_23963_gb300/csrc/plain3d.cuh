@@ -82,6 +82,9 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* b, unsigned byte
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(b)), "r"(bytes)
                : "memory");
 }
+__device__ __forceinline__ void mbar_arrive(uint64_t* b) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_u32(b)) : "memory");
+}
 __device__ __forceinline__ unsigned mbar_try_wait(uint64_t* b, unsigned parity) {
   unsigned ok;
   asm volatile(
@@ -226,7 +229,13 @@ struct Plain3DLayout {
   // Above 8 modes (NB = 16) two threads share a cell, each with half of its modes (SPLIT warps
   // per tile row: the first computes the fields, both the bath)
   static constexpr bool HELPER = NB == 0;
-  static constexpr int SPLIT = NB > 8 ? 2 : 1, NBH = NB > 0 ? NB / SPLIT : 1;
+  // Above 16 (NB = 128, STREAM) the modes are streamed: batches of MB modes of one component (both
+  // levels) pass through an R-slot shared-memory ring filled by tensor copies, twice per component
+  // (bath sum, then the mode update)
+  static constexpr bool STREAM = NB > 16;
+  static constexpr int SPLIT = NB > 8 && !STREAM ? 2 : 1, NBH = NB > 0 && !STREAM ? NB / SPLIT : 1;
+  static constexpr int MB = kStreamBatchModes, R = 4;
+  static constexpr int NMBAR = A + 1 + (STREAM ? 2 * R : 0);   // frame stages, bath state, ring
   static constexpr int threads = 32 * (TY * SPLIT + (HELPER ? 1 : 0));
   static constexpr unsigned SZ = sizeof(T);
   static constexpr unsigned r128(unsigned b) { return (b + 127u) & ~127u; }
@@ -248,26 +257,31 @@ struct Plain3DLayout {
   static constexpr unsigned XS = 2u * (TY + 1) * TX * SZ;
   static constexpr unsigned OFF_E = 0, OFF_HIN = NE * ES, OFF_SH = OFF_HIN + NH * HS, OFF_MBAR = OFF_SH + 2 * XS;
   // mbarriers: one per frame stage, one for the bath state
-  static constexpr unsigned OFF_INFO = OFF_MBAR + ((8 * (A + 1) + 15) / 16) * 16;
+  static constexpr unsigned OFF_INFO = OFF_MBAR + ((8 * NMBAR + 15) / 16) * 16;
   // bath-mode coefficient rows of every material ([modes][kCoefStride], at most kMaxMat NB rows)
   static constexpr unsigned OFF_COEF = OFF_INFO + plain::kMaxPlanes * 4;
-  static constexpr unsigned COEF_BYTES = NB > 0 ? (unsigned)kMaxMat * NB * kCoefStride * SZ : 0u;
+  // (streamed: at most kStreamCoefRows rows in all, the host checks)
+  static constexpr unsigned COEF_BYTES =
+      NB > 0 ? (unsigned)(STREAM ? kStreamCoefRows : kMaxMat * NB) * kCoefStride * SZ : 0u;
   // bath state of one plane tile (bath form): per level (P^{n+1/2}, Y^n, then P^{n-1/2}, Y^{n-1})
   // the modes [3 nb][TY][TX] (box order), then P [3][TY][TX]
   static constexpr unsigned BT = TY * TX * SZ;   // one component / mode of the tile
-  static constexpr unsigned B_P = 3u * (NB > 0 ? NB : 0) * BT, B_LVL = B_P + 3u * BT;
+  static constexpr unsigned B_P = 3u * (NB > 0 && !STREAM ? NB : 0) * BT, B_LVL = B_P + 3u * BT;
   static constexpr unsigned OFF_BATH = r128(OFF_COEF + COEF_BYTES);
   static constexpr unsigned BATH_BYTES = NB > 0 ? 2u * B_LVL : 0u;
   // the two halves' exchange (SPLIT = 2): E^{n+1/2} and the bath sums of each half, [9][TY][TX]
   static constexpr unsigned OFF_XCH = r128(OFF_BATH + BATH_BYTES);
   static constexpr unsigned XCH_BYTES = SPLIT > 1 ? 9u * BT : 0u;
-  static constexpr unsigned bytes = OFF_XCH + XCH_BYTES + 128;   // + alignment slack
+  // the streamed modes' ring: R slots of [level a: MB][TY][TX], [level b: MB][TY][TX]
+  static constexpr unsigned RING_SLOT = STREAM ? 2u * MB * BT : 0u;
+  static constexpr unsigned OFF_RING = r128(OFF_XCH + XCH_BYTES);
+  static constexpr unsigned bytes = OFF_RING + R * RING_SLOT + 128;   // + alignment slack
   // CTAs per SM that the shared memory admits (228 KB per SM, 1 KB reserved per CTA, static 128 B)
   static constexpr int per_sm = 233472 / (bytes + 1024 + 128) > 8 ? 8 : 233472 / (bytes + 1024 + 128);
   // CTAs per SM the registers are sized for: as the shared memory admits, or two with bath modes
   // (a cell's whole bath state is held in registers)
   static constexpr int min_blocks = NB > 0 ? (SPLIT > 1 ? 1 : 2) : per_sm;
-  static_assert(NB == 0 || NB == 4 || NB == 8 || NB == 16, "bath form: 4, 8 or 16 modes");
+  static_assert(NB == 0 || NB == 4 || NB == 8 || NB == 16 || NB == 128, "bath form: 4, 8, 16 or 128 modes");
   static_assert(ES % 128 == 0 && HS % 128 == 0 && XS % 128 == 0, "128-byte aligned frames");
   // the slot sums of the monitors / energy use the H^n buffer not in use (4 x TY x VX doubles)
   static_assert(4 * TY * VX * 8 <= XS, "reduction scratch fits an H buffer");
@@ -350,6 +364,12 @@ plain3d_kernel(const Step3DParams<T> p, const __grid_constant__ PlainMaps maps, 
   if (tid == 0) {
     s_abort = 0;
     for (int a = 0; a <= A; ++a) plain::mbar_init(&mbar[a], 1);
+    // streamed modes: per ring slot a "full" barrier (the copies) and an "empty" one (one arrival
+    // per warp once it has read the slot)
+    for (int r = 0; r < (L::STREAM ? L::R : 0); ++r) {
+      plain::mbar_init(&mbar[A + 1 + r], 1);
+      plain::mbar_init(&mbar[A + 1 + L::R + r], TY);
+    }
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     if (np > kMaxPlanes) s_abort = 1;   // the host plans chunks of at most kMaxPlanes planes
   }
@@ -420,14 +440,54 @@ plain3d_kernel(const Step3DParams<T> p, const __grid_constant__ PlainMaps maps, 
     const MatK<T>& M = p.mat[mi_];
     const int z = zb + g - M.zlo;
     uint64_t* bar = &mbar[A];
-    // (bf16 pairs: the words have the size of T, one level in place)
-    plain::mbar_arrive_expect_tx(bar, ((YB ? 1u : 2u) * 3u * M.nb + 6u) * L::BT);
+    // (bf16 pairs: the words have the size of T, one level in place; streamed modes: P only)
+    plain::mbar_arrive_expect_tx(bar, ((L::STREAM ? 0u : (YB ? 1u : 2u) * 3u * M.nb) + 6u) * L::BT);
     const unsigned d = smem_u32(smem_raw) + L::OFF_BATH;
-    plain::tma_load4(d, &bm.y[i][pcur], x0, y0, z, 0, bar);
+    if (!L::STREAM) plain::tma_load4(d, &bm.y[i][pcur], x0, y0, z, 0, bar);
     plain::tma_load4(d + L::B_P, &bm.pp[i][pcur], x0, y0, z, 0, bar);
-    if (!YB) plain::tma_load4(d + L::B_LVL, &bm.y[i][1 - pcur], x0, y0, z, 0, bar);
+    if (!YB && !L::STREAM) plain::tma_load4(d + L::B_LVL, &bm.y[i][1 - pcur], x0, y0, z, 0, bar);
     plain::tma_load4(d + L::B_LVL + L::B_P, &bm.pp[i][1 - pcur], x0, y0, z, 0, bar);
     bath_pending = true;
+  };
+  // ---- streamed modes (STREAM): batches of MB modes of one component, both levels, in the order
+  // of use -- per bath plane of the chunk, per component, the bath-sum pass, then the update pass.
+  // The issuer's cursor: bath plane sg (np: none left), component sc, pass sp, batch sb ----
+  constexpr int MB = L::MB, R = L::R;
+  uint64_t* rfull = mbar + A + 1;
+  uint64_t* rempty = mbar + A + 1 + R;
+  int sg = np, sc = 0, sp = 0, sb = 0;
+  int q_issued = 0;   // (issuer) batches issued
+  int q_used = 0;     // batches consumed
+  int q_landed = 0;   // batches whose copies this thread saw complete (in order)
+  auto next_bath_plane = [&](int g) {
+    while (g < np && !(sInfo[g] & kBath)) ++g;
+    return g;
+  };
+  auto issue_batch = [&]() {
+    if (sg >= np) return;
+    const int mi_ = (sInfo[sg] & 0xF) - 1;
+    const int i = bm.mat[0] == mi_ ? 0 : 1;
+    const int nbm_ = p.mat[mi_].nb;
+    const int slot = q_issued % R;
+    uint64_t* bar = &rfull[slot];
+    plain::mbar_arrive_expect_tx(bar, 2u * MB * L::BT);
+    const unsigned d = smem_u32(smem_raw) + L::OFF_RING + slot * L::RING_SLOT;
+    // the box past the component's last mode reads the next component's (or, past the array, the
+    // zero fill); those values go unused
+    const int z = zb + sg - p.mat[mi_].zlo, m0 = sc * nbm_ + sb * MB;
+    plain::tma_load4(d, &bm.y[i][pcur], x0, y0, z, m0, bar);
+    plain::tma_load4(d + MB * L::BT, &bm.y[i][1 - pcur], x0, y0, z, m0, bar);
+    ++q_issued;
+    if (++sb * MB >= nbm_) {
+      sb = 0;
+      if (++sp == 2) {
+        sp = 0;
+        if (++sc == 3) {
+          sc = 0;
+          sg = next_bath_plane(sg + 1);
+        }
+      }
+    }
   };
   if (issuer) {
     for (int g = 0; g < A && g < np; ++g) {
@@ -436,6 +496,10 @@ plain3d_kernel(const Step3DParams<T> p, const __grid_constant__ PlainMaps maps, 
     }
     if constexpr (NB > 0)
       if (np > 0 && (sInfo[0] & kBath)) issue_bath(0);
+    if constexpr (L::STREAM) {
+      sg = next_bath_plane(0);
+      for (int r = 0; r < R; ++r) issue_batch();
+    }
   }
 
   // ---- prologue: H^n of plane zb-1 at the own cells (z-difference of the E update at zb);
@@ -822,7 +886,7 @@ plain3d_kernel(const Step3DParams<T> p, const __grid_constant__ PlainMaps maps, 
           atomicExch(p.err, 1);
         }
         bpar ^= 1u;
-        bath_read(0, nbm, bPa, bPb, bY, bV);
+        bath_read(0, L::STREAM ? 0 : nbm, bPa, bPb, bY, bV);   // streamed: P only
       }
       __syncthreads();   // H^n(k) of the tile and its halo complete; E_in(k), H_in(k) slots free
       if (s_abort) return false;
@@ -999,7 +1063,88 @@ plain3d_kernel(const Step3DParams<T> p, const __grid_constant__ PlainMaps maps, 
           VV::st(p.psiE + pstrE + ipE * plane + qxy, psEy);
         }
       }
-      if constexpr (BATH) {
+      if constexpr (BATH && L::STREAM) {
+        // ---- streamed modes: per component, the bath sum of Eq. Pz_update-LB over the batches
+        // as they arrive, P^{n+3/2}, then Eq. Yzj_finite_difference over the same batches again
+        // (the general kernel's arithmetic and order, ascending j) ----
+        const MatK<T>& M = p.mat[mi];
+        const T* cfm = sCoef + M.coef_off * kCoefStride;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          T bsum = T(0), ub = T(0), Pn = T(0), Vn = T(0), dP = T(0);
+#pragma unroll 1
+          for (int pass = 0; pass < 2; ++pass) {
+#pragma unroll 1
+            for (int j0 = 0; j0 < nbm; j0 += MB) {
+              const int slot = q_used % R;
+              const unsigned par = (unsigned)((q_used / R) & 1);
+              if (!s_abort) {
+                if (plain::mbar_wait(&rfull[slot], par)) {
+                  ++q_landed;
+                } else {
+                  s_abort = 1;
+                  atomicExch(p.err, 1);
+                }
+              }
+              const unsigned so = L::OFF_RING + slot * L::RING_SLOT + (unsigned)cellx * SZ;
+              T ys[MB], vs[MB];
+#pragma unroll
+              for (int u = 0; u < MB; ++u) {
+                ys[u] = ldf(so + u * L::BT);
+                vs[u] = ldf(so + (MB + u) * L::BT);
+              }
+              __syncwarp();
+              if (lane == 0) plain::mbar_arrive(&rempty[slot]);   // this warp has read the slot
+              if (pass == 0) {
+#pragma unroll
+                for (int u = 0; u < MB; ++u) {
+                  if (j0 + u < nbm) {
+                    const float2 ca = *reinterpret_cast<const float2*>(cfm + (j0 + u) * kCoefStride);
+                    const T v = ys[u] - vs[u];
+                    bsum = bsum + (ca.x * ys[u] + ca.y * v);
+                  }
+                }
+              } else {
+#pragma unroll
+                for (int u = 0; u < MB; ++u) {
+                  if (j0 + u < nbm) {
+                    const float4 ca = *reinterpret_cast<const float4*>(cfm + (j0 + u) * kCoefStride);
+                    const float2 cb = *reinterpret_cast<const float2*>(cfm + (j0 + u) * kCoefStride + 4);
+                    const T y = ys[u], v = y - vs[u];
+                    const T Vy = ca.z * y + ca.w * v + cb.x * dP;
+                    const T Ynew = y + Vy;
+                    p.Yb[yB + (c * nbm + j0 + u) * mstr] = Ynew;   // overwrites Y^{n-1}
+                    if (p.eE_on) ub += Vy * Vy + cb.y * Ynew * Ynew;
+                  }
+                }
+              }
+              // the issuer refills the slot once every warp has read it
+              if (issuer && !s_abort) {
+                if (plain::mbar_wait(&rempty[slot], par)) {
+                  issue_batch();
+                } else {
+                  s_abort = 1;
+                  atomicExch(p.err, 1);
+                }
+              }
+              ++q_used;
+            }
+            if (pass == 0) {
+              const T V0 = bPa[c] - bPb[c];
+              T num = M.cE * Ev[c] - M.W * bPa[c] + M.c2 * V0;
+              num = num - T(0.5) * dt * bsum;
+              Vn = num * M.inv_A;
+              Pn = bPa[c] + Vn;
+              p.Pb[c * nmc + rB] = Pn;   // overwrites P^{n-1/2}
+              dP = Vn + V0;              // P^{n+3/2} - P^{n-1/2}
+            }
+          }
+          if (p.eE_on && in_box) {
+            uP += M.rho_idt2 * (Vn * Vn + M.w0r2dt2 * Pn * Pn);
+            uB += M.rho_idt2 * ub;
+          }
+        }
+      } else if constexpr (BATH) {
         // ---- Eq. Pz_update-LB and Eq. Yzj_finite_difference (increment form) for the three
         // components, modes outer (with SPLIT = 2 this thread's half of the modes; the halves
         // exchange their bath sums and both form the same P^{n+3/2}) ----
@@ -1072,6 +1217,8 @@ plain3d_kernel(const Step3DParams<T> p, const __grid_constant__ PlainMaps maps, 
     for (int g = wait_ok ? g_last + 1 : g_last; g < np && g < g_last + A; ++g)
       plain::mbar_wait(&mbar[g % A], (unsigned)((g / A) & 1));
     if (NB > 0 && bath_pending) plain::mbar_wait(&mbar[A], bpar);
+    // streamed modes issued whose completion this thread has not seen
+    for (int q = q_landed; q < q_issued; ++q) plain::mbar_wait(&rfull[q % R], (unsigned)((q / R) & 1));
   }
   // ---- energy partials of this block, one per 32 x 8 slot (zero outside the box) ----
   if constexpr (SPLIT > 1) {

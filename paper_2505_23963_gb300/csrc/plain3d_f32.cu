@@ -1,7 +1,7 @@
 // plain3d_f32.cu -- float instantiations of the plain-plane step kernel: four cells per thread for
 // the chunks without bath planes, one cell per thread (bath state in registers, at most 4 or 8
-// modes per material; two threads per cell with 16) for the Lorentz-Bath chunks; two planes staged
-// ahead.
+// modes per material; two threads per cell with 16; up to 128 streamed through a shared-memory
+// ring) for the Lorentz-Bath chunks; two planes staged ahead.
 #include <cuda_runtime.h>
 
 #include "plain3d.cuh"
@@ -42,6 +42,7 @@ int launch_bath3d_f32(const Step3DParams<float>& p, const PlainMaps& maps, const
   if (nb <= 4) return launch_shape<1, 2, 4>(p, maps, bmaps, pcur, ebuf, hbuf, nchunks, stream);
   if (nb <= 8) return launch_shape<1, 2, 8>(p, maps, bmaps, pcur, ebuf, hbuf, nchunks, stream);
   if (nb <= 16) return launch_shape<1, 2, 16>(p, maps, bmaps, pcur, ebuf, hbuf, nchunks, stream);
+  if (nb <= 128) return launch_shape<1, 2, 128>(p, maps, bmaps, pcur, ebuf, hbuf, nchunks, stream);
   return (int)cudaErrorInvalidValue;
 }
 

@@ -1,6 +1,7 @@
 """GPU parity of the plain-plane kernel's Lorentz-Bath form (FP32, 32 x 8 tiles; one cell per
-thread with at most 8 bath modes per material, two threads per cell with 9 to 16) against the
-FP64 CPU oracle and against the general step kernel.
+thread with at most 8 bath modes per material, two threads per cell with 9 to 16, up to 128
+streamed through a shared-memory ring) against the FP64 CPU oracle and against the general step
+kernel.
 
 The cavities are those of test_gpu_plain.py (CPML, vacuum with a phased source, an
 eps_inf = 2.25 spacer, eps_inf = 1.5 Drude mirrors, an eps_inf = 2 Lorentz-Bath layer, the energy
@@ -52,7 +53,7 @@ def bath_cavity(nx=64, ny=16, steps=120, seed=3, nb=8, layer=10):
     return p
 
 
-@pytest.mark.parametrize("nb", [8, 4, 3, 16, 11])
+@pytest.mark.parametrize("nb", [8, 4, 3, 16, 11, 100, 20])
 def test_bath_form_from_rest_matches_oracle(nb):
     prob = bath_cavity(nb=nb)
     g = fb.Simulation(prob, precision=32, energy_capacity=200)
@@ -69,7 +70,8 @@ def test_bath_form_from_rest_matches_oracle(nb):
     assert np.max(np.abs(to[:, 2])) > 0
 
 
-@pytest.mark.parametrize("shape,nb", [((64, 16), 8), ((32, 8), 8), ((96, 24), 8), ((64, 16), 16), ((32, 8), 13)])
+@pytest.mark.parametrize("shape,nb", [((64, 16), 8), ((32, 8), 8), ((96, 24), 8), ((64, 16), 16), ((32, 8), 13),
+                                      ((64, 16), 100), ((32, 8), 33)])
 def test_bath_form_random_state_matches_oracle(shape, nb):
     """Every field, polarization and bath-mode component nonzero; one tile per plane (32 x 8:
     every halo is the tile's own wrapped column / row) and several; one and two threads per cell."""
@@ -87,7 +89,8 @@ def test_bath_form_random_state_matches_oracle(shape, nb):
         assert rel(tg[:, col], to[:, col]) < TOL[32], col
 
 
-@pytest.mark.parametrize("zchunk,nb", [("16", 8), ("5", 8), ("64", 8), ("16", 16), ("64", 16)])
+@pytest.mark.parametrize("zchunk,nb", [("16", 8), ("5", 8), ("64", 8), ("16", 16), ("64", 16), ("16", 100),
+                                       ("5", 37)])
 def test_bath_form_equals_general_kernel(zchunk, nb):
     """The same run with the bath form and with the general kernel's bath instantiation: fields,
     polarizations and every bath mode to FP32 rounding; the layer cut into chunks of about 5, 16
@@ -135,10 +138,9 @@ def test_bath_form_zero_coupling_is_lorentz():
 
 
 def test_bath_form_not_used_outside_its_range():
-    """FP64, more than 16 modes, x not a multiple of 32, y not of 8, a source plane inside the
-    layer: the general kernel."""
+    """FP64, bf16 bath storage with more than 16 modes, x not a multiple of 32, y not of 8, a
+    source plane inside the layer: the general kernel."""
     cases = [(bath_cavity(steps=1), dict(precision=64)),
-             (bath_cavity(steps=1, nb=17), dict(precision=32)),
              (bath_cavity(steps=1, nb=17), dict(precision=32, bath_storage=1)),
              (bath_cavity(nx=48, steps=1), dict(precision=32)),
              (bath_cavity(ny=12, steps=1), dict(precision=32))]
@@ -150,13 +152,14 @@ def test_bath_form_not_used_outside_its_range():
         g = fb.Simulation(prob, **kw)
         assert not g.bath_plain_kernel(), kw
         g.close()
-    for kw in (dict(precision=32), dict(precision=32, bath_storage=1)):
-        g = fb.Simulation(bath_cavity(steps=1), **kw)
-        assert g.bath_plain_kernel(), kw
+    for nb, kw in ((8, dict(precision=32)), (8, dict(precision=32, bath_storage=1)),
+                   (17, dict(precision=32)), (100, dict(precision=32))):
+        g = fb.Simulation(bath_cavity(steps=1, nb=nb), **kw)
+        assert g.bath_plain_kernel(), (nb, kw)
         g.close()
 
 
-@pytest.mark.parametrize("nb", [8, 16])
+@pytest.mark.parametrize("nb", [8, 16, 100])
 def test_bath_form_snapshot_resume_bitwise(nb):
     """A snapshot taken between steps and restored into a fresh simulation continues bit for bit
     with the bath form (its pending H half-step stays pending across the snapshot)."""
