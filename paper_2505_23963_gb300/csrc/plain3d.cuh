@@ -225,14 +225,16 @@ template <typename T, int VX_, int A, int NB = 0>
 struct Plain3DLayout {
   static constexpr int VX = VX_, TY = plain::TY, TX = 32 * VX;
   static constexpr int NE = A + 1, NH = A;   // E and H_in frame slots
-  // the helper warp (NB = 0); the bath form runs without it, its warps sized for 128 registers.
+  // the helper warp (NB = 0); the bath form in registers runs without it, its warps sized for 128
+  // registers.
   // Above 8 modes (NB = 16) two threads share a cell, each with half of its modes (SPLIT warps
   // per tile row: the first computes the fields, both the bath)
-  static constexpr bool HELPER = NB == 0;
   // Above 16 (NB = 128, STREAM) the modes are streamed: batches of MB modes of one component (both
   // levels) pass through an R-slot shared-memory ring filled by tensor copies, twice per component
-  // (bath sum, then the mode update)
+  // (bath sum, then the mode update); the helper warp returns to issue them (the state held in
+  // registers is small again)
   static constexpr bool STREAM = NB > 16;
+  static constexpr bool HELPER = NB == 0 || STREAM;
   static constexpr int SPLIT = NB > 8 && !STREAM ? 2 : 1, NBH = NB > 0 && !STREAM ? NB / SPLIT : 1;
   static constexpr int MB = kStreamBatchModes, R = 4;
   static constexpr int NMBAR = A + 1 + (STREAM ? 2 * R : 0);   // frame stages, bath state, ring
@@ -434,6 +436,7 @@ plain3d_kernel(const Step3DParams<T> p, const __grid_constant__ PlainMaps maps, 
   // buffer has been read into registers
   unsigned bpar = 0;           // parity of the next bath-state wait
   bool bath_pending = false;   // (issuer) a bath-state copy not yet waited for
+  int bath_issued = 0;         // (issuer) bath-state copies issued
   auto issue_bath = [&](int g) {
     const int mi_ = (sInfo[g] & 0xF) - 1;
     const int i = bm.mat[0] == mi_ ? 0 : 1;
@@ -448,6 +451,7 @@ plain3d_kernel(const Step3DParams<T> p, const __grid_constant__ PlainMaps maps, 
     if (!YB && !L::STREAM) plain::tma_load4(d + L::B_LVL, &bm.y[i][1 - pcur], x0, y0, z, 0, bar);
     plain::tma_load4(d + L::B_LVL + L::B_P, &bm.pp[i][1 - pcur], x0, y0, z, 0, bar);
     bath_pending = true;
+    ++bath_issued;
   };
   // ---- streamed modes (STREAM): batches of MB modes of one component, both levels, in the order
   // of use -- per bath plane of the chunk, per component, the bath-sum pass, then the update pass.
@@ -693,17 +697,39 @@ plain3d_kernel(const Step3DParams<T> p, const __grid_constant__ PlainMaps maps, 
       __syncthreads();   // H^n(k) of the tile and its halo complete; E_in(k), H_in(k) slots free
       if (s_abort) break;
       if (lane == 0 && g + A < np) issue_stage(g + A);
-      if (info & (kMonH | kMonE)) {
+      if constexpr (NB > 0)
+        if (lane == 0 && g + 1 < np && (sInfo[g + 1] & kBath)) issue_bath(g + 1);
+      if (info & kMonH) {
         for (int m = 0; m < p.nmon; ++m) {
           const int zm = p.mon_z[m];
-          if ((info & kMonH) && (k == zm - 1 || k == zm)) {
+          if (k == zm - 1 || k == zm) {
             double v2[2] = {0.0, 0.0};
             block_slot_sums<TY, VX>(v2, red, w, lane);
             __syncthreads();
           }
         }
+      }
+      if constexpr (L::STREAM) {
+        // the ring: as the compute warps release each batch of this plane, the next one in order
+        // of use goes into its slot
+        if (lane == 0 && (info & kBath)) {
+          const int nbat = (p.mat[(info & 0xF) - 1].nb + MB - 1) / MB;
+          for (int t = 0; t < 6 * nbat && !s_abort; ++t) {
+            const int slot = q_landed % R;
+            if (plain::mbar_wait(&rempty[slot], (unsigned)((q_landed / R) & 1))) {
+              ++q_landed;   // released by every compute warp, so landed
+              issue_batch();
+            } else {
+              s_abort = 1;
+              atomicExch(p.err, 1);
+            }
+          }
+        }
+        __syncwarp();
+      }
+      if (info & kMonE) {
         for (int m = 0; m < p.nmon; ++m)
-          if ((info & kMonE) && k == p.mon_z[m]) {
+          if (k == p.mon_z[m]) {
             double v2[2] = {0.0, 0.0};
             block_slot_sums<TY, VX>(v2, red, w, lane);
             __syncthreads();
@@ -1118,8 +1144,8 @@ plain3d_kernel(const Step3DParams<T> p, const __grid_constant__ PlainMaps maps, 
                   }
                 }
               }
-              // the issuer refills the slot once every warp has read it
-              if (issuer && !s_abort) {
+              // without the helper, the issuer refills the slot once every warp has read it
+              if (!HELPER && issuer && !s_abort) {
                 if (plain::mbar_wait(&rempty[slot], par)) {
                   issue_batch();
                 } else {
@@ -1216,7 +1242,8 @@ plain3d_kernel(const Step3DParams<T> p, const __grid_constant__ PlainMaps maps, 
   if (s_abort && issuer) {
     for (int g = wait_ok ? g_last + 1 : g_last; g < np && g < g_last + A; ++g)
       plain::mbar_wait(&mbar[g % A], (unsigned)((g / A) & 1));
-    if (NB > 0 && bath_pending) plain::mbar_wait(&mbar[A], bpar);
+    if (NB > 0 && !HELPER && bath_pending) plain::mbar_wait(&mbar[A], bpar);
+    if (NB > 0 && HELPER && bath_issued > 0) plain::mbar_wait(&mbar[A], (unsigned)((bath_issued - 1) & 1));
     // streamed modes issued whose completion this thread has not seen
     for (int q = q_landed; q < q_issued; ++q) plain::mbar_wait(&rfull[q % R], (unsigned)((q / R) & 1));
   }
