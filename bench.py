@@ -495,8 +495,9 @@ def form_adjoint(fb, torch):
 def profile_form(name: str) -> int:
     """Short runs of one form for profiler captures: the 64-cavity batch for 64 steps in the shape
     the autotuner picks for it (C = 4, 896 threads), 16 steps of the 2048^2 differentiation form forward and
-    reverse (checkpoints every 8 steps: about 2 GB of device memory), or 8 steps of the N_b = 100
-    slab at 128 x 128 (about 1.5 GB)."""
+    reverse (checkpoints every 8 steps: about 2 GB of device memory), 8 steps of the N_b = 100
+    slab at 128 x 128 (about 1.5 GB), or 8 steps of the N_b = 16 precision workload at 128 x 128 x
+    384 (about 1.3 GB)."""
     import torch
     from paper_2505_23963_gb300 import fdtdbath as fb
     torch.cuda.set_device(0)
@@ -505,6 +506,16 @@ def profile_form(name: str) -> int:
         sim.step(8)
         sim.sync()
         print(json.dumps({"form": "manybath", "steps": 8}), flush=True)
+        sim.close()
+        return 0
+    if name == "precision":
+        prob = wl.precision_3d(steps=8)
+        prob = dict(prob, n=(128, 128, prob["n"][2]), name="precision3d_128x128x384_nb16")
+        prob["sources"] = [dict(q, phase=q["phase"][:128, :128]) for q in prob["sources"]]
+        sim = fb.Simulation(prob, precision=32, energy_capacity=16)
+        sim.step(8)
+        sim.sync()
+        print(json.dumps({"form": "precision", "steps": 8, "bath_form": sim.bath_plain_kernel()}), flush=True)
         sim.close()
         return 0
     if name == "batch":
@@ -729,7 +740,7 @@ def main():
     ap.add_argument("--quick", action="store_true",
                     help="FP32 step timing only (for profiler captures)")
     ap.add_argument("--grid", default="", help="override nx,ny of the workload (profiling)")
-    ap.add_argument("--profile-form", default="", choices=["", "batch", "adjoint", "manybath"],
+    ap.add_argument("--profile-form", default="", choices=["", "batch", "adjoint", "manybath", "precision"],
                     help="run a short version of one form only (for profiler captures)")
     args = ap.parse_args()
     if args.warmup < 3:
