@@ -67,6 +67,42 @@ def algorithmic_bytes(prob: dict, esz: int, bath_bytes: float | None = None) -> 
     return float(words.sum()) * nx * ny * esz
 
 
+def algorithmic_bytes_te(prob: dict, esz: int = 4) -> dict:
+    """Bytes per step of the differentiation form's y-invariant TE grid (E_y, H_x, H_z, the y
+    polarization and bath modes), every word once per kernel that touches it:
+      forward: E_y, H_x, H_z read and written (6 words per cell), +2 x 2 CPML memories in the
+      absorber planes, +3 words of P_y (two levels read, one written) in Drude / Lorentz planes,
+      +3 + 3 N_b in Lorentz-Bath planes;
+      record (reverse sweep, recomputed forward steps): the differentiated layer's E_y, P_y of two
+      levels and two levels of its bath modes written, 3 + 2 N_b words per layer cell;
+      adjoint (adjoint_k1 + adjoint_k2): H_bar_x, H_bar_z read and E_bar_y read and written in k1,
+      E_bar_y read and H_bar_x, H_bar_z read and written in k2 (9 words per cell), +5 in the
+      absorber planes (the CPML adjoints), +4 P-adjoint words in Drude / Lorentz planes, in the
+      differentiated Lorentz-Bath layer also 4 N_b bath-adjoint words and the 3 + 2 N_b recorded
+      values read."""
+    nx, ny, nz = prob["n"]
+    pml = prob.get("pml", 0)
+    fwd = np.full(nz, 6.0)
+    adj = np.full(nz, 9.0)
+    fwd[:pml] += 4
+    fwd[nz - pml:] += 4
+    adj[:pml] += 5
+    adj[nz - pml:] += 5
+    rec = 0.0
+    for m in prob["materials"]:
+        lo, hi = m["z"]
+        nb = len(m.get("bath_frequencies", ()))
+        if m["kind"] in ("lorentz", "drude"):
+            fwd[lo:hi] += 3
+            adj[lo:hi] += 4
+        elif m["kind"] == "lorentz_bath":
+            fwd[lo:hi] += 3 + 3 * nb
+            adj[lo:hi] += 4 + 4 * nb + 3 + 2 * nb
+            rec += (3 + 2 * nb) * (hi - lo)
+    w = float(nx * ny * esz)
+    return {"forward": float(fwd.sum()) * w, "record": rec * w, "adjoint": float(adj.sum()) * w}
+
+
 def algorithmic_flops_fp64(prob: dict) -> float:
     """Floating-point operations per step of the FP64 path, which evaluates the literal updates
     (Eq. FDTD-1D with Eq. 1a,b in 3D, Eq. Pz_1D_Lorentz / Pz_update-LB, Eq. Yzj_finite_difference)
@@ -485,8 +521,18 @@ def form_adjoint(fb, torch):
     torch.cuda.synchronize()
     tb = time.perf_counter() - t0
     g = x.grad.numpy()
+    # memory roofline of both sweeps (algorithmic bytes as counted in algorithmic_bytes_te; the
+    # reverse sweep recomputes every forward step with recording, then runs the adjoint kernels)
+    hbm, _ = peaks()
+    bt = algorithmic_bytes_te(prob)
+    fwd_gbs = bt["forward"] * n / tf / 1e9
+    rev_gbs = (bt["forward"] + bt["record"] + bt["adjoint"]) * n / tb / 1e9
+    roof = {"bound": "hbm", "unit": "GB/s", "peak": hbm,
+            "forward": {"bytes_per_step": bt["forward"], "achieved": fwd_gbs, "frac": fwd_gbs / hbm},
+            "reverse": {"bytes_per_step": bt["forward"] + bt["record"] + bt["adjoint"],
+                        "achieved": rev_gbs, "frac": rev_gbs / hbm}}
     return {"workload": prob["name"], "steps": n, "checkpoint_every": 256,
-            "forward_s": tf, "backward_s": tb,
+            "forward_s": tf, "backward_s": tb, "roofline": roof,
             "value": cells * n / (tf + tb), "unit": UNIT + " (forward + reverse sweep)",
             "loss": float(L.detach()), "grad_finite": bool(np.all(np.isfinite(g))),
             "grad": [float(v) for v in g]}
