@@ -4,7 +4,9 @@ Every translation unit is compiled by nvcc for sm_103a only
 (``-gencode arch=compute_103a,code=sm_103a -lineinfo``), in parallel, and linked
 into one shared library with a static CUDA runtime.  The FP64 kernels and the
 FP64 reductions are compiled with ``--fmad=false`` so that each multiply and add
-rounds on its own, the order in which the equations are written.
+rounds on its own, the order in which the equations are written; the bath
+recursion's explicit fused multiply-adds (the same in every kernel) are the
+exception.
 """
 from __future__ import annotations
 

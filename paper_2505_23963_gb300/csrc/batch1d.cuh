@@ -180,7 +180,7 @@ __device__ __forceinline__ void batch_phase_bath(const BatchRun R, const MatK<T>
         if (k < Kc) {
           const int i = i0 + (kb + k) * nt;
           const T y = Yc[j * len + i], ym = Yo[j * len + i];
-          if (!INC) acc[k] = acc[k] + c0 * (c1 * y + c2 * ym);   // k_j (a_j Y^n + b_j Y^{n-1})
+          if (!INC) acc[k] = bath_sum_lit(acc[k], c0, c1, c2, y, ym);   // k_j (a_j Y^n + b_j Y^{n-1})
           else acc[k] = acc[k] + (c0 * y + c1 * (y - ym));       // k_j ((a_j+b_j) Y - b_j V)
         }
       }
@@ -220,14 +220,14 @@ __device__ __forceinline__ void batch_phase_bath(const BatchRun R, const MatK<T>
           const T y = Yc[j * len + i], ym = Yo[j * len + i];
           T Yn, Vy;
           if (!INC) {
-            Yn = c1 * y + c3 * ym + c4 * acc[k];
+            Yn = bath_new_lit(c1, c3, c4, y, ym, acc[k]);
             Vy = Yn - y;
           } else {
             Vy = c2 * y + c3 * (y - ym) + c4 * acc[k];
             Yn = y + Vy;
           }
           Yo[j * len + i] = Yn;
-          if (en) ub += Vy * Vy + c5 * Yn * Yn;
+          if (en) ub = INC ? ub + (Vy * Vy + c5 * Yn * Yn) : bath_energy_lit(ub, Vy, c5, Yn);
         }
       }
     }

@@ -165,7 +165,7 @@ __global__ void __launch_bounds__(kCav1DThreads) cavity1d_kernel(const Cav1DPara
           if (j < nb) {
             const T* cf = cfm + j * kCoefStride;
             if (!INC) {
-              bsum = bsum + cf[0] * (cf[1] * Y[j] + cf[2] * Ym[j]);   // k_j (a_j Y^n + b_j Y^{n-1})
+              bsum = bath_sum_lit(bsum, cf[0], cf[1], cf[2], Y[j], Ym[j]);   // k_j (a_j Y^n + b_j Y^{n-1})
             } else {
               V[j] = Y[j] - Ym[j];
               bsum = bsum + (cf[0] * Y[j] + cf[1] * V[j]);             // k_j ((a_j+b_j) Y - b_j V)
@@ -194,7 +194,7 @@ __global__ void __launch_bounds__(kCav1DThreads) cavity1d_kernel(const Cav1DPara
             const T* cf = cfm + j * kCoefStride;
             T Yn, Vy;
             if (!INC) {
-              Yn = cf[1] * Y[j] + cf[3] * Ym[j] + cf[4] * (Pn - Pb);
+              Yn = bath_new_lit(cf[1], cf[3], cf[4], Y[j], Ym[j], Pn - Pb);
               Vy = Yn - Y[j];
             } else {
               Vy = cf[2] * Y[j] + cf[3] * V[j] + cf[4] * dP;
@@ -202,7 +202,7 @@ __global__ void __launch_bounds__(kCav1DThreads) cavity1d_kernel(const Cav1DPara
             }
             Ym[j] = Y[j];
             Y[j] = Yn;
-            if (en) ub += Vy * Vy + cf[5] * Yn * Yn;
+            if (en) ub = INC ? ub + (Vy * Vy + cf[5] * Yn * Yn) : bath_energy_lit(ub, Vy, cf[5], Yn);
           }
         }
         Pb = Pa;

@@ -31,6 +31,26 @@ constexpr int kMaxChunk = 128;  // planes per z-chunk (the per-plane table in sh
 
 enum Kind { kVacuum = 0, kLorentz = 1, kDrude = 2, kLorentzBath = 3 };
 
+#ifdef __CUDACC__
+// The literal (FP64) form of the bath recursion with fused multiply-adds, the same sequence in
+// every kernel that runs it (one rounding per FMA; the other FP64 arithmetic is uncontracted):
+//   bath sum term   k_j (a_j Y^n + b_j Y^{n-1}),           Eq. Pz_update-LB
+//   new mode        a_j Y^n + (b_j+1) Y^{n-1} + c_j dP,    Eq. Yzj_finite_difference
+//   energy term     (Y^{n+1} - Y^n)^2 + (w_j dt)^2 (Y^{n+1})^2
+template <typename T>
+__device__ __forceinline__ T bath_sum_lit(T bsum, T k, T a, T b, T y, T ym) {
+  return fma(k, fma(a, y, b * ym), bsum);
+}
+template <typename T>
+__device__ __forceinline__ T bath_new_lit(T a, T b1, T c, T y, T ym, T dP) {
+  return fma(c, dP, fma(a, y, b1 * ym));
+}
+template <typename T>
+__device__ __forceinline__ T bath_energy_lit(T ub, T vy, T w2, T yn) {
+  return fma(vy, vy, fma(w2 * yn, yn, ub));
+}
+#endif
+
 template <typename T>
 struct MatK {
   int zlo, zhi, kind, nb;

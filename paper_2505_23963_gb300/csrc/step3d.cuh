@@ -715,7 +715,7 @@ step3d_kernel(const Step3DParams<T> p) {
                     T cf[6];
                     load_coef6(cfm + (j0 + u) * kCoefStride, cf);
                     if (!INC) {
-                      bsum = bsum + cf[0] * (cf[1] * ys[u] + cf[2] * vs[u]);
+                      bsum = bath_sum_lit(bsum, cf[0], cf[1], cf[2], ys[u], vs[u]);
                     } else {
                       const T v = YB ? vs[u] : ys[u] - vs[u];
                       bsum = bsum + (cf[0] * ys[u] + cf[1] * v);
@@ -736,7 +736,7 @@ step3d_kernel(const Step3DParams<T> p) {
                 T cf[6];
                 load_coef6(cfm + jj * kCoefStride, cf);
                 if (!INC) {
-                  bsum = bsum + cf[0] * (cf[1] * Yl[jj] + cf[2] * Vl[jj]);   // k_j (a_j Y^n + b_j Y^{n-1})
+                  bsum = bath_sum_lit(bsum, cf[0], cf[1], cf[2], Yl[jj], Vl[jj]);   // k_j (a_j Y^n + b_j Y^{n-1})
                 } else {
                   if (!YB) Vl[jj] = Yl[jj] - Vl[jj];                         // V_j = Y^n - Y^{n-1}
                   bsum = bsum + (cf[0] * Yl[jj] + cf[1] * Vl[jj]);           // k_j ((a_j+b_j) Y - b_j V)
@@ -784,7 +784,7 @@ step3d_kernel(const Step3DParams<T> p) {
                   load_coef6(cfm + jj * kCoefStride, cf);
                   T Ynew, Vy;
                   if (!INC) {
-                    Ynew = cf[1] * y + cf[3] * v + cf[4] * (Pn - Pb);
+                    Ynew = bath_new_lit(cf[1], cf[3], cf[4], y, v, Pn - Pb);
                     Vy = Ynew - y;
                   } else {
                     Vy = cf[2] * y + cf[3] * v + cf[4] * dP;
@@ -795,7 +795,7 @@ step3d_kernel(const Step3DParams<T> p) {
                   } else {
                     YS::put(yb + yc + jj * mstride, Ynew);
                   }
-                  if (p.eE_on) ub += Vy * Vy + cf[5] * Ynew * Ynew;
+                  if (p.eE_on) ub = INC ? ub + (Vy * Vy + cf[5] * Ynew * Ynew) : bath_energy_lit(ub, Vy, cf[5], Ynew);
                 }
               }
             }
@@ -807,7 +807,7 @@ step3d_kernel(const Step3DParams<T> p) {
                 T Ynew, Vy;
                 if (!INC) {
                   // Eq. Yzj_finite_difference: Y^{n+1} = a Y^n + (b+1) Y^{n-1} + c (P^{n+1} - P^{n-1})
-                  Ynew = cf[1] * Yl[jj] + cf[3] * Vl[jj] + cf[4] * (Pn - Pb);
+                  Ynew = bath_new_lit(cf[1], cf[3], cf[4], Yl[jj], Vl[jj], Pn - Pb);
                   Vy = Ynew - Yl[jj];
                 } else {
                   // V_Y^{n+1} = (a+b) Y^n - (b+1) V_Y^n + c (V_P^{n+1} + V_P^n);  Y^{n+1} = Y^n + V_Y^{n+1}
@@ -819,7 +819,7 @@ step3d_kernel(const Step3DParams<T> p) {
                 } else {
                   YS::put(yb + yc + jj * mstride, Ynew);   // overwrites Y^{n-1}
                 }
-                if (p.eE_on) ub += Vy * Vy + cf[5] * Ynew * Ynew;   // (w_j dt)^2 Y^2
+                if (p.eE_on) ub = INC ? ub + (Vy * Vy + cf[5] * Ynew * Ynew) : bath_energy_lit(ub, Vy, cf[5], Ynew);   // (w_j dt)^2 Y^2
               }
             }
             if (p.eE_on && in_box) {
@@ -844,7 +844,7 @@ step3d_kernel(const Step3DParams<T> p) {
                   if (!liveE(c)) continue;
                   const T y = rY[c][jj];
                   if (!INC) {
-                    bsum[c] = bsum[c] + cf[0] * (cf[1] * y + cf[2] * rV[c][jj]);
+                    bsum[c] = bath_sum_lit(bsum[c], cf[0], cf[1], cf[2], y, rV[c][jj]);
                   } else {
                     if (!YB) rV[c][jj] = y - rV[c][jj];   // V_j = Y^n - Y^{n-1}
                     bsum[c] = bsum[c] + (cf[0] * y + cf[1] * rV[c][jj]);
@@ -887,7 +887,7 @@ step3d_kernel(const Step3DParams<T> p) {
                   const T y = rY[c][jj], v = rV[c][jj];
                   T Ynew, Vy;
                   if (!INC) {
-                    Ynew = cf[1] * y + cf[3] * v + cf[4] * (Pn[c] - rPb[c]);
+                    Ynew = bath_new_lit(cf[1], cf[3], cf[4], y, v, Pn[c] - rPb[c]);
                     Vy = Ynew - y;
                   } else {
                     Vy = cf[2] * y + cf[3] * v + cf[4] * dP[c];
@@ -898,7 +898,7 @@ step3d_kernel(const Step3DParams<T> p) {
                   } else {
                     YS::put(yb + yo, Ynew);
                   }
-                  if (p.eE_on) ub[c] += Vy * Vy + cf[5] * Ynew * Ynew;
+                  if (p.eE_on) ub[c] = INC ? ub[c] + (Vy * Vy + cf[5] * Ynew * Ynew) : bath_energy_lit(ub[c], Vy, cf[5], Ynew);
                 }
               }
             }

@@ -77,11 +77,12 @@ def compare(g, o, prob, precision, check_bath=True):
 
 
 def oracle_sensitivity(prob, steps):
-    """The oracle against itself with the source phase moved by one ulp (same keys as compare)."""
+    """The oracle against itself with the source phase (without a phase table: the pulse delay t0)
+    moved by one ulp (same keys as compare)."""
     a = O.OracleSim(prob)
     p2 = dict(prob)
-    p2["sources"] = [dict(s, phase=None if s.get("phase") is None else np.nextafter(s["phase"], 10.0))
-                     for s in prob["sources"]]
+    p2["sources"] = [dict(s, phase=np.nextafter(s["phase"], 10.0)) if s.get("phase") is not None
+                     else dict(s, t0=float(np.nextafter(s["t0"], 1e9))) for s in prob["sources"]]
     b = O.OracleSim(p2)
     a.step(steps)
     b.step(steps)
