@@ -201,3 +201,42 @@ def test_bath_form_bf16_storage_equals_general_kernel(nb):
     ta, tb = a.trace(), b.trace()
     for col in range(3):
         assert rel(ta[:, col], tb[:, col]) < 1e-4, col
+
+
+def two_layer_cavity(nx=64, ny=16, nbA=8, nbB=5, steps=120):
+    """Two adjacent Lorentz-Bath layers with different baths (A: nbA modes, eps_inf 2; B: nbB
+    modes, sigma 0.02, eps_inf 1.5), a second monitor inside layer A and an energy box that cuts
+    through layer A: bath planes carrying monitor partials, box edges inside a chunk, and both
+    materials' tensor maps."""
+    p = bath_cavity(nx=nx, ny=ny, steps=steps, nb=nbA, layer=20)
+    q = wl.slab_cavity(nx, ny, (8, 14, 3, 20, 3, 12), 20.0, num_bath=nbB, sigma=0.02, bath_seed=9,
+                       phase_seed=3, src_z=12, nfreq=16, steps=steps, name="layer_b")
+    mats = p["materials"]
+    lo, hi = mats[2]["z"]
+    mid = lo + 9
+    lbB = [m for m in q["materials"] if m["kind"] == "lorentz_bath"][0]
+    p["materials"] = [mats[0], mats[1], dict(mats[2], z=(lo, mid)), dict(lbB, z=(mid, hi), eps_inf=1.5),
+                      mats[3]]
+    p["monitors"] = p["monitors"] + [dict(z=lo + 4, freqs=np.linspace(0.5, 1.5, 16))]
+    p["energy_box"] = (lo + 5, hi + 2)
+    return p
+
+
+@pytest.mark.parametrize("nbA,nbB", [(8, 5), (16, 12), (100, 20), (8, 16)])
+def test_bath_form_two_layers_monitor_in_layer_matches_oracle(nbA, nbB):
+    """Both Lorentz-Bath materials through the bath form (per-material maps and coefficient rows;
+    the form set by the larger bath: registers, two threads per cell, or streamed), a monitor
+    inside a layer, an energy box edge inside a layer."""
+    prob = two_layer_cavity(nbA=nbA, nbB=nbB)
+    g = fb.Simulation(prob, precision=32, energy_capacity=200)
+    assert g.bath_plain_kernel()
+    o = O.OracleSim(prob, trace_cap=200)
+    g.step(120)
+    o.step(120)
+    assert_errs(compare(g, o, prob, 32), 32, sens=oracle_sensitivity(prob, 120))
+    for m in range(2):
+        assert rel(g.dft(m), o.dft(m)) < TOL[32], m
+        assert np.max(np.abs(o.dft(m))) > 0, m
+    tg, to = g.trace(), o.trace()
+    for col in range(3):
+        assert rel(tg[:, col], to[:, col]) < TOL[32], col
