@@ -33,6 +33,8 @@
 
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "internal.h"
 
 namespace fdtdbath {
@@ -65,12 +67,19 @@ __device__ __forceinline__ uint32_t adj_div(uint32_t n, FastDiv f) { return (__u
 // they are constants here, and the carried components are bit-identical to the general form's.
 // The TE form carries one component's P / bath adjoints: up to N_b = 8 it fits in 64 registers,
 // so four blocks share an SM (the kernel waits on memory, and more warps hide more of it).
-template <typename T, int NBMAX, bool TE = false>
-__global__ void __launch_bounds__(kAdjThreads, (TE && NBMAX <= 8) ? 4 : 0) adjoint_k1(const AdjParams<T> p) {
+//
+// LIGHT: the launch over the planes outside [ra, rb) (no material there: field and CPML adjoints
+// only), at eight blocks per SM; otherwise the launch over the cells [ra, rb).  The planes without
+// material are most of a cavity's grid and do little work per cell, so at the heavy launch's
+// occupancy they waited on memory latency.
+template <typename T, int NBMAX, bool TE = false, bool LIGHT = false>
+__global__ void __launch_bounds__(kAdjThreads, LIGHT ? 8 : ((TE && NBMAX <= 8) ? 4 : 0))
+adjoint_k1(const AdjParams<T> p) {
   __shared__ double sg[kAdjThreads / 32][kAdjMaxGrad];
   constexpr int NBA = NBMAX > 0 ? NBMAX : 1;
-  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const bool own = q < p.ncell;
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t q = LIGHT ? (idx < p.ra ? idx : idx + (p.rb - p.ra)) : p.ra + idx;
+  const bool own = LIGHT ? q < p.ncell : q < p.rb;
   const int64_t N = p.ncell, plane = p.plane;
   const int nx = p.nx, ny = p.ny, nz = p.nz;
   // gradient terms: summed in the state precision over a thread's components and a warp's cells,
@@ -126,7 +135,7 @@ __global__ void __launch_bounds__(kAdjThreads, (TE && NBMAX <= 8) ? 4 : 0) adjoi
       }
     }
     // F3^T (polarization and bath), with the gradient of material gm
-    const int mi = adj_mat_of(p, k);
+    const int mi = LIGHT ? -1 : adj_mat_of(p, k);
     T inv_eps = T(1);
     T Pold[3], Pmold[3];
     bool haveP = false;
@@ -267,9 +276,9 @@ __global__ void __launch_bounds__(kAdjThreads, (TE && NBMAX <= 8) ? 4 : 0) adjoi
     if (!TE) p.Eb[2 * N + q] = ez;
   }
   // per-block gradient partials of material gm (blocks holding none of its cells skip)
-  if (p.gm >= 0) {
+  if (!LIGHT && p.gm >= 0) {
     const MatK<T>& G = p.mat[p.gm];
-    const int64_t b0 = (int64_t)blockIdx.x * blockDim.x, b1 = b0 + blockDim.x;
+    const int64_t b0 = p.ra + (int64_t)blockIdx.x * blockDim.x, b1 = b0 + blockDim.x;
     const int64_t m0 = (int64_t)G.zlo * plane, m1 = (int64_t)G.zhi * plane;
     if (b1 > m0 && b0 < m1) {
       const int np = 2 + G.nb;
@@ -356,15 +365,29 @@ __global__ void __launch_bounds__(kAdjThreads) adjoint_k2(const AdjParams<T> p) 
 }
 
 template <typename T, bool TE>
-int launch_adjoint_form(const AdjParams<T>& p, int nbmax, void* stream) {
-  const int64_t nblk = (p.ncell + kAdjThreads - 1) / kAdjThreads;
+int launch_adjoint_form(const AdjParams<T>& p0, int nbmax, void* stream) {
+  const int64_t nblk = (p0.ncell + kAdjThreads - 1) / kAdjThreads;
   cudaStream_t st = (cudaStream_t)stream;
-  switch (nbmax) {
-    case 0: adjoint_k1<T, 0, TE><<<(unsigned)nblk, kAdjThreads, 0, st>>>(p); break;
-    case 4: adjoint_k1<T, 4, TE><<<(unsigned)nblk, kAdjThreads, 0, st>>>(p); break;
-    case 8: adjoint_k1<T, 8, TE><<<(unsigned)nblk, kAdjThreads, 0, st>>>(p); break;
-    case 16: adjoint_k1<T, 16, TE><<<(unsigned)nblk, kAdjThreads, 0, st>>>(p); break;
-    default: adjoint_k1<T, 32, TE><<<(unsigned)nblk, kAdjThreads, 0, st>>>(p); break;
+  // adjoint_k1 in two launches: the planes from the first material's to the last's, and the rest
+  AdjParams<T> p = p0;
+  p.ra = p.ncell;
+  p.rb = 0;
+  for (int m = 0; m < p.nmat; ++m) {
+    p.ra = std::min<int64_t>(p.ra, (int64_t)p.mat[m].zlo * p.plane);
+    p.rb = std::max<int64_t>(p.rb, (int64_t)p.mat[m].zhi * p.plane);
+  }
+  if (p.rb <= p.ra) p.ra = p.rb = 0;
+  const int64_t nheavy = (p.rb - p.ra + kAdjThreads - 1) / kAdjThreads;
+  const int64_t nlight = (p.ncell - (p.rb - p.ra) + kAdjThreads - 1) / kAdjThreads;
+  if (nlight > 0) adjoint_k1<T, 0, TE, true><<<(unsigned)nlight, kAdjThreads, 0, st>>>(p);
+  if (nheavy > 0) {
+    switch (nbmax) {
+      case 0: adjoint_k1<T, 0, TE><<<(unsigned)nheavy, kAdjThreads, 0, st>>>(p); break;
+      case 4: adjoint_k1<T, 4, TE><<<(unsigned)nheavy, kAdjThreads, 0, st>>>(p); break;
+      case 8: adjoint_k1<T, 8, TE><<<(unsigned)nheavy, kAdjThreads, 0, st>>>(p); break;
+      case 16: adjoint_k1<T, 16, TE><<<(unsigned)nheavy, kAdjThreads, 0, st>>>(p); break;
+      default: adjoint_k1<T, 32, TE><<<(unsigned)nheavy, kAdjThreads, 0, st>>>(p); break;
+    }
   }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return (int)e;

@@ -271,6 +271,9 @@ struct AdjParams {
   double* gpart;            // [gridDim][kAdjMaxGrad] per-block running sums (FP64)
   FastDiv fd_plane, fd_nx;  // division by plane = nx ny and by nx (cell index -> i, j, k)
   const signed char* zmat;  // [nz] material index of every plane, -1 for none
+  // cells [ra, rb): the planes from the first material's to the last's (adjoint_k1 runs them and
+  // the rest in two launches; set by the launcher)
+  int64_t ra, rb;
 };
 // te = 1: the TE form (the forward run was the y-invariant TE form and the adjoint sources sit
 // on E_y and H_x only): the adjoints of E_x, E_z, H_y, P_x, P_z and the x / z bath modes are zero
