@@ -140,6 +140,10 @@ struct fdtdbath_sim {
   // registers (FP32 or bf16 bath storage) or up to 128 streamed (FP32 storage), 32 x 8 tiles;
   // chunks of at most 64 planes
   bool bath_plain = false;
+  // the TE form's register-streaming kernel (te2d.cuh) for the chunks without bath planes, while
+  // the simulation runs the TE form: FP32, ny = 1, nx a multiple of kTe2dTileX, no source plane
+  // inside a layer
+  bool te2d_ok = false;
   PlainMaps bmaps{};        // tensor maps of 32-cell-wide boxes
   BathMaps bath_maps{};     // tensor maps of its polarization and bath-mode arrays
   // the bath-free and bath launches of a step one after the other on the simulation's stream (the
@@ -482,8 +486,19 @@ int launch_bath_chunks(fdtdbath_sim* s, Step3DParams<T> p, int id_off, int n, cu
 
 // Chunks without bath planes: the plain-plane kernel when it applies (both half-steps of a step),
 // otherwise the general kernel's bath-free instantiation.
+int launch_te2d_typed(const Step3DParams<float>& p, int n, cudaStream_t st) { return launch_te2d_f32(p, n, st); }
+int launch_te2d_typed(const Step3DParams<double>&, int, cudaStream_t) {
+  return (int)cudaErrorInvalidValue;   // FP64 runs the general kernel (te2d_ok is never set)
+}
+
 template <typename T>
 int launch_plain_chunks(fdtdbath_sim* s, Step3DParams<T> p, int id_off, int n, cudaStream_t st) {
+  if (s->te2d_ok && s->te && s->ty == 1 && p.doH && p.doE) {
+    // the TE form's register-streaming kernel (te2d.cuh)
+    p.chunk_ids = (const int*)s->chunk_ids + id_off;
+    s->launches++;
+    return launch_te2d_typed(p, n, st);
+  }
   if (!(s->plain_ok && p.doH && p.doE)) return launch_chunks<T>(s, p, 0, id_off, n, st);
   p.chunk_ids = (const int*)s->chunk_ids + id_off;
   s->launches++;
@@ -1009,6 +1024,8 @@ int fdtdbath_create(const fdtdbath_grid* grid, double resolution, double courant
     const int tx = plain_tile_x(s->prec);
     const char* e = std::getenv("FDTDBATH_PLAIN");
     s->plain_ok = !(e && std::atoi(e) == 0) && s->ty == 8 && nx % tx == 0 && ny % 8 == 0 && !src_in_layer;
+    const char* et = std::getenv("FDTDBATH_TE2D");
+    s->te2d_ok = !(et && std::atoi(et) == 0) && s->prec == 32 && ny == 1 && nx % kTe2dTileX == 0 && !src_in_layer;
     const char* eb = std::getenv("FDTDBATH_BATHPLAIN");
     int nmodes_all = 0;
     for (auto& m : s->mats) nmodes_all += m.nb;
@@ -1489,6 +1506,7 @@ int64_t fdtdbath_query(const fdtdbath_sim* s, int32_t key) {
     case 7: return s->plain_ok ? 1 : 0;
     case 8: return s->path1d && s->ncomp1d == 1 ? 1 : 0;
     case 9: return s->bath_plain ? 1 : 0;
+    case 10: return s->te2d_ok && s->te && s->ty == 1 ? 1 : 0;
     default: return -1;
   }
 }

@@ -427,6 +427,10 @@ class Simulation:
         """Whether the z-chunks without bath modes run the plain-plane kernel (query key 7)."""
         return query(self.h, 7) == 1
 
+    def te2d_kernel(self) -> bool:
+        """Whether the TE form's bath-free chunks run the register-streaming kernel (query key 10)."""
+        return query(self.h, 10) == 1
+
     def bath_plain_kernel(self) -> bool:
         """Whether the z-chunks with bath modes run the plain-plane kernel's Lorentz-Bath form
         (query key 9)."""
