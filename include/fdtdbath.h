@@ -230,9 +230,9 @@ int fdtdbath_bath_form(int32_t shape, double frequency, double gamma, int32_t nu
  * whether the z-chunks with bath modes run the plain-plane kernel's Lorentz-Bath form (FP32; at
  * most 16 bath modes per material with FP32 or bf16 bath storage, or up to 128 with FP32
  * storage; at most two Lorentz-Bath layers; nx a multiple of 32, ny of 8, no source plane inside a
- * layer).  Key 10: whether the z-chunks without bath modes of a simulation in the TE form run the
- * TE form's register-streaming kernel (FP32, nx a multiple of 256, no source plane inside a
- * layer). */
+ * layer).  Key 10: whether the z-chunks of a simulation in the TE form run the TE form's
+ * register-streaming kernel (FP32, nx a multiple of 256, no source plane inside a layer; the
+ * chunks with bath modes only with FP32 bath storage and at most 8 modes per material). */
 int64_t fdtdbath_query(const fdtdbath_sim *sim, int32_t key);
 
 /* Energy (U_EM, U_P, U_bath) of planes z_lo <= k < z_hi of the current state -- the same

@@ -140,9 +140,9 @@ struct fdtdbath_sim {
   // registers (FP32 or bf16 bath storage) or up to 128 streamed (FP32 storage), 32 x 8 tiles;
   // chunks of at most 64 planes
   bool bath_plain = false;
-  // the TE form's register-streaming kernel (te2d.cuh) for the chunks without bath planes, while
-  // the simulation runs the TE form: FP32, ny = 1, nx a multiple of kTe2dTileX, no source plane
-  // inside a layer
+  // the TE form's register-streaming kernel (te2d.cuh) for the chunks without bath planes and
+  // (FP32 bath storage, at most 8 modes) those with, while the simulation runs the TE form: FP32,
+  // ny = 1, nx a multiple of kTe2dTileX, no source plane inside a layer
   bool te2d_ok = false;
   PlainMaps bmaps{};        // tensor maps of 32-cell-wide boxes
   BathMaps bath_maps{};     // tensor maps of its polarization and bath-mode arrays
@@ -474,10 +474,28 @@ int launch_bath_typed(const Step3DParams<double>&, const fdtdbath_sim*, int, cud
   return (int)cudaErrorInvalidValue;   // FP64 runs the general kernel (bath_plain is never set)
 }
 
+int launch_te2d_typed(const Step3DParams<float>& p, int n, int nb, cudaStream_t st) {
+  return launch_te2d_f32(p, n, nb, st);
+}
+int launch_te2d_typed(const Step3DParams<double>&, int, int, cudaStream_t) {
+  return (int)cudaErrorInvalidValue;   // FP64 runs the general kernel (te2d_ok is never set)
+}
+int launch_te2d_fused_typed(const Step3DParams<float>& p, int nplain, int nbath, int nb, cudaStream_t st) {
+  return launch_te2d_fused_f32(p, nplain, nbath, nb, st);
+}
+int launch_te2d_fused_typed(const Step3DParams<double>&, int, int, int, cudaStream_t) {
+  return (int)cudaErrorInvalidValue;
+}
+
 // Chunks with bath planes: the plain-plane kernel's bath form when it applies (both half-steps of
 // a step), otherwise the general kernel with the simulation's bath-mode bound.
 template <typename T>
 int launch_bath_chunks(fdtdbath_sim* s, Step3DParams<T> p, int id_off, int n, cudaStream_t st) {
+  if (s->te2d_ok && s->te && s->ty == 1 && !s->ybf && s->nbmax <= kTe2dMaxModes && p.doH && p.doE) {
+    p.chunk_ids = (const int*)s->chunk_ids + id_off;
+    s->launches++;
+    return launch_te2d_typed(p, n, s->nbmax, st);
+  }
   if (!(s->bath_plain && p.doH && p.doE)) return launch_chunks<T>(s, p, s->nbmax, id_off, n, st);
   p.chunk_ids = (const int*)s->chunk_ids + id_off;
   s->launches++;
@@ -486,10 +504,6 @@ int launch_bath_chunks(fdtdbath_sim* s, Step3DParams<T> p, int id_off, int n, cu
 
 // Chunks without bath planes: the plain-plane kernel when it applies (both half-steps of a step),
 // otherwise the general kernel's bath-free instantiation.
-int launch_te2d_typed(const Step3DParams<float>& p, int n, cudaStream_t st) { return launch_te2d_f32(p, n, st); }
-int launch_te2d_typed(const Step3DParams<double>&, int, cudaStream_t) {
-  return (int)cudaErrorInvalidValue;   // FP64 runs the general kernel (te2d_ok is never set)
-}
 
 template <typename T>
 int launch_plain_chunks(fdtdbath_sim* s, Step3DParams<T> p, int id_off, int n, cudaStream_t st) {
@@ -497,7 +511,7 @@ int launch_plain_chunks(fdtdbath_sim* s, Step3DParams<T> p, int id_off, int n, c
     // the TE form's register-streaming kernel (te2d.cuh)
     p.chunk_ids = (const int*)s->chunk_ids + id_off;
     s->launches++;
-    return launch_te2d_typed(p, n, st);
+    return launch_te2d_typed(p, n, 0, st);
   }
   if (!(s->plain_ok && p.doH && p.doE)) return launch_chunks<T>(s, p, 0, id_off, n, st);
   p.chunk_ids = (const int*)s->chunk_ids + id_off;
@@ -514,6 +528,13 @@ int launch_all(fdtdbath_sim* s, int doH, int doE) {
   Step3DParams<T> p = make_params<T>(s, doH, doE);
   if (!doE) return launch_chunks<T>(s, p, 0, 0, s->nchunks, s->stream);
   if (s->nbmax == 0) return launch_plain_chunks<T>(s, p, 0, s->nchunks, s->stream);
+  if (sizeof(T) == 4 && s->te2d_ok && s->te && s->ty == 1 && !s->ybf && s->nbmax <= kTe2dMaxModes &&
+      s->nplain > 0 && s->nbath > 0 && doH) {
+    // the TE form: both kinds of chunks in one launch of its register-streaming kernel
+    p.chunk_ids = (const int*)s->chunk_ids + s->nchunks;
+    s->launches++;
+    return launch_te2d_fused_typed(p, s->nplain, s->nbath, s->nbmax, s->stream);
+  }
   if (s->nbath == 0) return launch_chunks<T>(s, p, s->nbmax, 0, s->nchunks, s->stream);
   if (s->nplain == 0) return launch_bath_chunks<T>(s, p, s->nchunks, s->nbath, s->stream);
   if (s->serial_pair) {

@@ -209,10 +209,13 @@ struct BathMaps {
 // over them; at most 16 modes)
 int launch_bath3d_f32(const Step3DParams<float>& p, const PlainMaps& maps, const BathMaps& bmaps, int pcur, int ebuf,
                       int hbuf, int nchunks, int nb, int ybf, void* stream);
-// The y-invariant TE form's z-chunks without bath modes (te2d.cuh): FP32, nx a multiple of
-// kTe2dTileX, both half-steps of a step.
+// The y-invariant TE form's z-chunks (te2d.cuh): FP32, nx a multiple of kTe2dTileX, both
+// half-steps of a step; nb = 0 the chunks without bath modes, nb <= kTe2dMaxModes those with.
 constexpr int kTe2dTileX = 256;
-int launch_te2d_f32(const Step3DParams<float>& p, int nchunks, void* stream);
+constexpr int kTe2dMaxModes = 8;
+int launch_te2d_f32(const Step3DParams<float>& p, int nchunks, int nb, void* stream);
+// both kinds in one launch: p.chunk_ids lists the nplain chunks without bath modes, then nbath
+int launch_te2d_fused_f32(const Step3DParams<float>& p, int nplain, int nbath, int nb, void* stream);
 int launch_plain3d_f64(const Step3DParams<double>& p, const PlainMaps& maps, int ebuf, int hbuf, int nchunks,
                        void* stream);
 

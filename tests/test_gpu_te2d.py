@@ -1,11 +1,11 @@
-"""GPU parity of the TE form's register-streaming kernel (te2d.cuh: FP32, the z-chunks without
-bath modes of y-invariant grids driven through E_y, nx a multiple of 256) against the FP64 CPU
-oracle and against the general kernel's TE form.
+"""GPU parity of the TE form's register-streaming kernel (te2d.cuh: FP32, the z-chunks of
+y-invariant grids driven through E_y, nx a multiple of 256; the Lorentz-Bath chunks with at most 8
+modes) against the FP64 CPU oracle and against the general kernel's TE form.
 
 The cavity: CPML | vacuum with a phased E_y source and a flux monitor | an eps_inf = 2.25 spacer |
-eps_inf = 1.5 Drude mirrors | an eps_inf = 2 Lorentz-Bath layer (run by the general kernel) |
-vacuum | CPML, the energy box over spacer, mirrors and layer.  Tolerances as in test_gpu_parity.py
-(FP32 1e-5 for E, H, spectra and energy traces, 1e-4 for polarizations and bath modes).
+eps_inf = 1.5 Drude mirrors | an eps_inf = 2 Lorentz-Bath layer | vacuum | CPML, the energy box
+over spacer, mirrors and layer.  Tolerances as in test_gpu_parity.py (FP32 1e-5 for E, H, spectra
+and energy traces, 1e-4 for polarizations and bath modes).
 """
 import os
 
@@ -97,14 +97,21 @@ def compare_te(g, o, prob):
             assert rel(a, b) < tol, (name, m["kind"])
 
 
-def test_te2d_from_rest_matches_oracle():
-    prob = te_cavity()
+@pytest.mark.parametrize("nb", [4, 8, 16])
+def test_te2d_from_rest_matches_oracle(nb):
+    """N_b 4 and 8: the layer by the TE kernel too; 16: by the general kernel."""
+    prob = te_cavity(nb=nb)
     g = fb.Simulation(prob, precision=32, energy_capacity=200)
     assert g.te_form() and g.te2d_kernel()
     o = O.OracleSim(prob, trace_cap=200)
     g.step(150)
     o.step(150)
     compare_te(g, o, prob)
+    lo, hi = prob["materials"][2]["z"]
+    for j in sorted({0, nb - 1}):
+        for lvl in (0, 1):
+            assert rel(g.get("Y", comp=1, mode=j, level=lvl)[lo:hi],
+                       o.get("Y", comp=1, mode=j, level=lvl)[lo:hi]) < TOL_Y[32], (j, lvl)
     assert rel(g.dft(0), o.dft(0)) < TOL[32]
     assert np.max(np.abs(o.dft(0))) > 0
     tg, to = g.trace(), o.trace()
@@ -131,10 +138,11 @@ def test_te2d_random_state_matches_oracle(nx):
         assert rel(tg[:, col], to[:, col]) < TOL[32], col
 
 
-def test_te2d_equals_general_te_form():
+@pytest.mark.parametrize("nb", [4, 8])
+def test_te2d_equals_general_te_form(nb):
     """The same run with the TE kernel and with the general kernel's TE form: every component,
-    spectrum and energy trace to FP32 rounding."""
-    prob = te_cavity(steps=120)
+    the layer's bath modes, the spectrum and the energy trace to FP32 rounding."""
+    prob = te_cavity(steps=120, nb=nb)
     sims = []
     for flag in ("1", "0"):
         with env(FDTDBATH_TE2D=flag):
@@ -145,6 +153,11 @@ def test_te2d_equals_general_te_form():
     a, b = sims
     for name, c in TE_KEYS + [("P", 1), ("Pm", 1)]:
         assert rel(a.get(name, comp=c), b.get(name, comp=c)) < 1e-6, (name, c)
+    lo, hi = prob["materials"][2]["z"]
+    for j in range(nb):
+        for lvl in (0, 1):
+            assert rel(a.get("Y", comp=1, mode=j, level=lvl)[lo:hi],
+                       b.get("Y", comp=1, mode=j, level=lvl)[lo:hi]) < 1e-6, (j, lvl)
     assert rel(a.dft(0), b.dft(0)) < 1e-6
     ta, tb = a.trace(), b.trace()
     for col in range(3):
