@@ -34,7 +34,10 @@
  * outside 0 <= k < nz every field is zero.  Yee positions (cell units):
  *   Ex (i+1/2, j, k)   Ey (i, j+1/2, k)   Ez (i, j, k+1/2)
  *   Hx (i, j+1/2, k+1/2)  Hy (i+1/2, j, k+1/2)  Hz (i+1/2, j+1/2, k)
- * A material fills whole z-planes lo <= k < hi for every component.
+ * A material fills whole z-planes lo <= k < hi for every component.  Its oscillator strength may
+ * vary per cell, sigma(r) in Eq. EOM_Lorentz / EOM_LorentzBath-1: one value per cell (i, j, k) of
+ * the layer, shared by the three components of that cell, entering the drive term of the P update
+ * and the mass density rho(r) = 1/(sigma(r) w0^2) of the energy (Eq. H_full).
  */
 #include <math.h>
 #include <stdint.h>
@@ -57,6 +60,7 @@ typedef struct {
   int64_t ncell;        /* cells in the material's planes */
   double *P[3], *Pm[3]; /* P^{n+1/2}, P^{n-1/2} per component */
   double *Y[3], *Ym[3]; /* Y_j^{n+1/2}, Y_j^{n-1/2}: [nb][ncell] per component */
+  double *sig;          /* sigma(r) per cell [ncell] (Eq. EOM_Lorentz), or NULL: sigma everywhere */
 } omat;
 
 typedef struct {
@@ -377,16 +381,17 @@ static void orc_update_P(osim *s) {
       int64_t q = m->zlo * plane + r;
       for (int c = 0; c < 3; ++c) {
         double E = s->E[c][q], P = m->P[c][r], Pm = m->Pm[c][r], Pn;
+        const double sg = m->sig ? m->sig[r] : m->sigma;   /* sigma(r) */
         if (m->kind == ORC_LORENTZ) {
-          Pn = orc_lorentz_update(E, P, Pm, m->w0, m->g0, m->sigma, s->dt);
+          Pn = orc_lorentz_update(E, P, Pm, m->w0, m->g0, sg, s->dt);
         } else if (m->kind == ORC_DRUDE) {
-          Pn = orc_drude_update(E, P, Pm, m->w0, m->g0, m->sigma, s->dt);
+          Pn = orc_drude_update(E, P, Pm, m->w0, m->g0, sg, s->dt);
         } else {
           for (int j = 0; j < m->nb; ++j) {
             Yl[j] = m->Y[c][(int64_t)j * m->ncell + r];
             Yml[j] = m->Ym[c][(int64_t)j * m->ncell + r];
           }
-          Pn = orc_lorentz_bath_update(E, P, Pm, m->w0, m->g0, m->sigma, m->nb, m->wj, m->gj, m->kj,
+          Pn = orc_lorentz_bath_update(E, P, Pm, m->w0, m->g0, sg, m->nb, m->wj, m->gj, m->kj,
                                        Yl, Yml, s->dt);
           for (int j = 0; j < m->nb; ++j) {
             m->Y[c][(int64_t)j * m->ncell + r] = Yl[j];
@@ -465,7 +470,7 @@ static void orc_monitors(osim *s) {
 
 /* Energy per unit transverse area inside the box, from the stored state after a step:
  *   U_EM   = sum dx/(nx ny) * 1/2 (eps_inf E.E + H.H)            (E^{n+1/2}, H^{n+1})
- *   U_P    = sum dx/(nx ny) * rho/2 (((P - Pm)/dt)^2 + w0r^2 P^2)   rho = 1/(sigma w0^2)
+ *   U_P    = sum dx/(nx ny) * rho/2 (((P - Pm)/dt)^2 + w0r^2 P^2)   rho = 1/(sigma(r) w0^2)
  *   U_bath = sum dx/(nx ny) * sum_j rho/2 (((Y_j - Ym_j)/dt)^2 + w_j^2 Y_j^2)
  * (w0r = w0, or 0 for Drude).  This follows the energy density of Eq. (H_full)
  * written with P and the Y_j as coordinates (Pi_P = rho (dP/dt + sum k_j Y_j)).  */
@@ -481,10 +486,12 @@ static void orc_energy_box(const osim *s, double out[3]) {
       for (int c = 0; c < 3; ++c) uem += w * 0.5 * (eps * s->E[c][q] * s->E[c][q] + s->H[c][q] * s->H[c][q]);
       if (mi < 0) continue;
       const omat *m = &s->mat[mi];
-      if (m->kind == ORC_VACUUM || m->sigma == 0.0) continue;
-      double rho = 1.0 / (m->sigma * m->w0 * m->w0);
-      double w0r = (m->kind == ORC_DRUDE) ? 0.0 : m->w0;
+      if (m->kind == ORC_VACUUM) continue;
       int64_t r = (k - m->zlo) * plane + p;
+      const double sg = m->sig ? m->sig[r] : m->sigma;
+      if (sg == 0.0) continue;
+      double rho = 1.0 / (sg * m->w0 * m->w0);
+      double w0r = (m->kind == ORC_DRUDE) ? 0.0 : m->w0;
       for (int c = 0; c < 3; ++c) {
         double v = (m->P[c][r] - m->Pm[c][r]) / s->dt;
         up += w * 0.5 * rho * (v * v + w0r * w0r * m->P[c][r] * m->P[c][r]);
@@ -524,10 +531,12 @@ static double orc_invariant(const osim *s, double hdot) {
       for (int c = 0; c < 3; ++c) I += 0.5 * eps * s->E[c][q] * s->E[c][q];
       if (mi < 0) continue;
       const omat *m = &s->mat[mi];
-      if (m->kind == ORC_VACUUM || m->sigma == 0.0) continue;
-      double rho = 1.0 / (m->sigma * m->w0 * m->w0);
-      double w0r = (m->kind == ORC_DRUDE) ? 0.0 : m->w0;
+      if (m->kind == ORC_VACUUM) continue;
       int64_t r = (k - m->zlo) * plane + p;
+      const double sg = m->sig ? m->sig[r] : m->sigma;
+      if (sg == 0.0) continue;
+      double rho = 1.0 / (sg * m->w0 * m->w0);
+      double w0r = (m->kind == ORC_DRUDE) ? 0.0 : m->w0;
       for (int c = 0; c < 3; ++c) {
         double p1 = m->P[c][r], p0 = m->Pm[c][r];
         I += -0.5 * s->E[c][q] * (p1 - p0);
@@ -567,7 +576,9 @@ void orc_step(osim *s, int64_t nsteps) {
 /* ---- state access ------------------------------------------------------------------
  * field ids: 0..2 E, 3..5 H, 6..8 D, 9..11 P^{n+1/2}, 12..14 P^{n-1/2} (full grid, zero
  * outside materials); bath mode j of component c, level l (0: Y^{n+1/2}, 1: Y^{n-1/2}):
- * 64 + (c*2 + l)*128 + j.  CPML memories: 32..33 psiE (x,y), 34..35 psiH (x,y).      */
+ * 64 + (c*2 + l)*128 + j.  CPML memories: 32..33 psiE (x,y), 34..35 psiH (x,y).
+ * 16: sigma(r) (full grid; the material's sigma where no map was written, zero outside the
+ * dispersive layers; a write sets the map of every dispersive layer).                  */
 static double *orc_field_ptr(osim *s, int id, int64_t *is_mat) {
   *is_mat = 0;
   if (id >= 0 && id < 3) return s->E[id];
@@ -595,6 +606,9 @@ static int orc_access(osim *s, int id, double *buf, int write) {
   } else if (id >= 12 && id < 15) {
     c = id - 12;
     lvl = 1;
+  } else if (id == 16) {
+    c = 0;
+    lvl = 0;
   } else if (id >= 64) {
     int r = id - 64;
     j = r % 128;
@@ -608,7 +622,17 @@ static int orc_access(osim *s, int id, double *buf, int write) {
   for (int mi = 0; mi < s->nmat; ++mi) {
     omat *m = &s->mat[mi];
     double *src;
-    if (j < 0) src = lvl ? m->Pm[c] : m->P[c];
+    if (id == 16) {
+      if (m->kind == ORC_VACUUM) continue;
+      if (!m->sig) {
+        if (!write) {
+          for (int64_t r = 0; r < m->ncell; ++r) buf[m->zlo * plane + r] = m->sigma;
+          continue;
+        }
+        m->sig = (double *)xcalloc((size_t)m->ncell, sizeof(double));
+      }
+      src = m->sig;
+    } else if (j < 0) src = lvl ? m->Pm[c] : m->P[c];
     else {
       if (j >= m->nb) continue;
       src = (lvl ? m->Ym[c] : m->Y[c]) + (int64_t)j * m->ncell;
@@ -666,6 +690,7 @@ void orc_free(osim *s) {
       free(m->Y[c]);
       free(m->Ym[c]);
     }
+    free(m->sig);
   }
   for (int m = 0; m < s->nsrc; ++m) free(s->src[m].phase);
   for (int m = 0; m < s->nmon; ++m) {

@@ -8,7 +8,7 @@ the benchmark's CPU-baseline leg and reference arm import it.
 Field ids follow the C file: 0..2 E, 3..5 H, 6..8 D, 9..11 P^{n+1/2},
 12..14 P^{n-1/2}; bath mode j of component c at level l (0: Y^{n+1/2},
 1: Y^{n-1/2}) is ``64 + (2c + l) * 128 + j``; 32..33 / 34..35 are the CPML
-memories of the E / H updates.
+memories of the E / H updates; 16 is the per-cell oscillator strength sigma(r).
 """
 from __future__ import annotations
 
@@ -84,6 +84,8 @@ def field_id(name: str, comp: int = 0, mode: int = 0, level: int = 0) -> int:
         return 32 + comp
     if name == "psiH":
         return 34 + comp
+    if name == "S":   # sigma(r), the per-cell oscillator strength
+        return 16
     raise KeyError(name)
 
 
@@ -210,3 +212,31 @@ def lorentz_bath_update(E, P, Pm, w0, g0, sigma, wj, gj, kj, Y, Ym, dt):
 
 def two_pi() -> float:
     return 2.0 * math.pi
+
+
+# -- per-cell sigma(r) with sub-pixel averaging --------------------------------------
+def box_fill(shape, lo, hi) -> np.ndarray:
+    """Fraction of each cell covered by the box [lo, hi) (cell units, x, y, z order).
+
+    Cell (i, j, k) is the unit cube [i, i+1) x [j, j+1) x [k, k+1); its covered fraction is the
+    product over the axes of the overlap length max(0, min(hi, i+1) - max(lo, i)).  Returned as a
+    [nz][ny][nx] array (``shape`` = (nz, ny, nx)).
+    """
+    out = np.ones(shape)
+    for ax, n in zip((2, 1, 0), shape[::-1]):   # x, y, z
+        a, b = float(lo[2 - ax]), float(hi[2 - ax])
+        i = np.arange(n, dtype=np.float64)
+        f = np.clip(np.minimum(b, i + 1.0) - np.maximum(a, i), 0.0, 1.0)
+        sh = [1, 1, 1]
+        sh[ax] = n
+        out = out * f.reshape(sh)
+    return out
+
+
+def paint_sigma(sim: "OracleSim", lo, hi, sigma: float) -> None:
+    """sigma(r) <- f sigma + (1 - f) sigma_old in every cell of the dispersive layers that the box
+    covers by the fraction f (the cell average of the coupling strength: the susceptibility of
+    Eq. chi_L is linear in sigma)."""
+    old = sim.get("S")
+    f = box_fill(sim.shape, lo, hi)
+    sim.set("S", f * float(sigma) + (1.0 - f) * old)
