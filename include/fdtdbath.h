@@ -71,6 +71,17 @@ enum fdtdbath_bath_shape { FDTDBATH_BATH_UNIFORM = 0, FDTDBATH_BATH_LORENTZIAN =
 #define FDTDBATH_FIELD_P(c) (6 + (c))
 #define FDTDBATH_FIELD_PM(c) (9 + (c))
 #define FDTDBATH_FIELD_Y(c, j, l) (1024 + ((c) * 2 + (l)) * 256 + (j))
+/* The per-cell oscillator strength sigma(r) of Eq. EOM_Lorentz and EOM_LorentzBath-1 (the paper
+ * lets sigma depend on position; rho(r) = 1/(sigma(r) w0^2) weighs the energy of Eq. H_full).  One
+ * value per cell (i, j, k), shared by the three components of that cell.  Reading it returns the
+ * map where one is set, each dispersive layer's own sigma otherwise, and zero outside the Lorentz,
+ * Drude and Lorentz-Bath layers.  Writing it sets the map of every such layer (values elsewhere
+ * are ignored): FDTDBATH_ERR_ARG for a negative or non-finite value, FDTDBATH_ERR_CFL (nothing
+ * changed) when a layer would be unstable at its largest sigma(r) (the bound of fdtdbath_create
+ * with that sigma).  The map takes 4 (FP32) or 8 (FP64) bytes per layer cell; while it is set
+ * every chunk runs on the general step kernel (or the 1D kernel), the adjoint and
+ * fdtdbath_box_energy_noalloc answer FDTDBATH_ERR_UNSUPPORTED, and a snapshot carries the map. */
+#define FDTDBATH_FIELD_SIGMA 12
 
 typedef struct fdtdbath_sim fdtdbath_sim; /* opaque, owned by the library */
 
@@ -167,6 +178,18 @@ int fdtdbath_read_fields(fdtdbath_sim *sim, int32_t field, void *dst, size_t dst
 int fdtdbath_write_fields(fdtdbath_sim *sim, int32_t field, const void *src, size_t src_bytes,
                           int32_t src_on_device);
 
+/* Paint an axis-aligned box of oscillator strength sigma into the sigma(r) map (see
+ * FDTDBATH_FIELD_SIGMA) with sub-pixel averaging.  lo, hi: host arrays (x, y, z) in cell units,
+ * 0 <= lo < hi <= n on every axis (FDTDBATH_ERR_ARG otherwise); cell (i, j, k) is the unit cube
+ * [i, i+1) x [j, j+1) x [k, k+1).  A dispersive-layer cell that the box covers by the fraction f
+ * (the product of its overlap lengths along the three axes) takes
+ *     sigma(r) <- f sigma + (1 - f) sigma(r),
+ * the cell average of the coupling strength (the susceptibility of Eq. chi_L is linear in sigma,
+ * so this is the average susceptibility of the cell's two parts).  Cells outside the dispersive
+ * layers are left alone; eps_inf is not averaged.  Validation and errors as for writing
+ * FDTDBATH_FIELD_SIGMA; synchronizes the simulation's stream. */
+int fdtdbath_sigma_box(fdtdbath_sim *sim, const double lo[3], const double hi[3], double sigma);
+
 /* Spectra of monitor `monitor`: host out[nfreq][4][2] = (re, im) of (Ex, Ey, Hx, Hy).
  * FDTDBATH_ERR_NONFINITE (out filled all the same) when a value is NaN or Inf. */
 int fdtdbath_dft(fdtdbath_sim *sim, int32_t monitor, double *out);
@@ -174,7 +197,7 @@ int fdtdbath_dft(fdtdbath_sim *sim, int32_t monitor, double *out);
 /* Energy trace per step (per unit transverse area, inside the energy box), host
  * trace[len][4] = (U_EM, U_P, U_bath, 0):
  *   U_EM = sum dx/(nx ny) 1/2 (eps_inf E.E + H.H) with E^{n+1/2}, H^{n+1};
- *   U_P = sum dx/(nx ny) rho/2 (((P - PM)/dt)^2 + w0^2 P^2), rho = 1/(sigma w0^2), w0 -> 0 in
+ *   U_P = sum dx/(nx ny) rho/2 (((P - PM)/dt)^2 + w0^2 P^2), rho = 1/(sigma(r) w0^2), w0 -> 0 in
  *   the potential for Drude;  U_bath = sum dx/(nx ny) sum_j rho/2 (((Y_j - Y_j')/dt)^2 + w_j^2 Y_j^2)
  * (the energy density of Eq. H_full with P and Y_j as coordinates).  *len = steps written.
  * FDTDBATH_ERR_NONFINITE (trace and *len filled all the same) when a record is NaN or Inf. */
@@ -195,7 +218,8 @@ int64_t fdtdbath_steps_done(const fdtdbath_sim *sim);
  * device state), written to dst in host or device memory.  fdtdbath_restore checks that the
  * snapshot comes from a simulation of the same layout (grid, CPML, precision, bath storage,
  * material cells and modes, monitors, energy capacity; FDTDBATH_ERR_ARG otherwise) and replaces
- * this simulation's state; a recorded adjoint forward run is discarded.  Both synchronize the
+ * this simulation's state, its sigma(r) map included (a snapshot taken without a map returns the
+ * layers to their own sigma); a recorded adjoint forward run is discarded.  Both synchronize the
  * simulation's stream. */
 int fdtdbath_snapshot_size(fdtdbath_sim *sim, size_t *bytes);
 int fdtdbath_snapshot(fdtdbath_sim *sim, void *dst, size_t dst_bytes, int32_t dst_on_device);
@@ -232,7 +256,8 @@ int fdtdbath_bath_form(int32_t shape, double frequency, double gamma, int32_t nu
  * storage; at most two Lorentz-Bath layers; nx a multiple of 32, ny of 8, no source plane inside a
  * layer).  Key 10: whether the z-chunks of a simulation in the TE form run the TE form's
  * register-streaming kernel (FP32, nx a multiple of 256, no source plane inside a layer; the
- * chunks with bath modes only with FP32 bath storage and at most 8 modes per material). */
+ * chunks with bath modes only with FP32 bath storage and at most 8 modes per material).  Key 11:
+ * whether a per-cell sigma(r) map is set (FDTDBATH_FIELD_SIGMA). */
 int64_t fdtdbath_query(const fdtdbath_sim *sim, int32_t key);
 
 /* Energy (U_EM, U_P, U_bath) of planes z_lo <= k < z_hi of the current state -- the same
@@ -274,8 +299,8 @@ int fdtdbath_measure_fma_rate(int32_t precision, int32_t device, int32_t reps, d
  * --------------------------------------------------------------------------------------------- */
 
 /* Advance nsteps steps (as fdtdbath_step), saving the checkpoints of the run; the spectra and
- * energy traces accumulate as usual.  Not available with bf16 bath storage or with more than 32
- * bath modes in a material (FDTDBATH_ERR_UNSUPPORTED).  A later fdtdbath_step invalidates the recording. */
+ * energy traces accumulate as usual.  Not available with bf16 bath storage, with more than 32
+ * bath modes in a material or with a sigma(r) map (FDTDBATH_ERR_UNSUPPORTED).  A later fdtdbath_step invalidates the recording. */
 int fdtdbath_adjoint_forward(fdtdbath_sim *sim, int64_t nsteps, int32_t checkpoint_every);
 
 /* Reverse sweep of the recorded run.  dL_dF: host array nfreq x 4 x 2 with dL/dRe and dL/dIm of

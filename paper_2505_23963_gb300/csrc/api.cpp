@@ -144,6 +144,11 @@ struct fdtdbath_sim {
   // (FP32 bath storage, at most 8 modes) those with, while the simulation runs the TE form: FP32,
   // ny = 1, nx a multiple of kTe2dTileX, no source plane inside a layer
   bool te2d_ok = false;
+  // per-cell oscillator strength sigma(r) (Eq. EOM_Lorentz), pooled like P, allocated by the first
+  // write of the map; while a map is set the general kernel (or the 1D kernel) runs every chunk
+  void* sig = nullptr;
+  bool sigmap = false;
+  bool plain_ok0 = false, bath_plain0 = false, te2d_ok0 = false, serial_pair0 = false;   // at create
   PlainMaps bmaps{};        // tensor maps of 32-cell-wide boxes
   BathMaps bath_maps{};     // tensor maps of its polarization and bath-mode arrays
   // the bath-free and bath launches of a step one after the other on the simulation's stream (the
@@ -405,6 +410,7 @@ Step3DParams<T> make_params(fdtdbath_sim* s, int doH, int doE) {
   p.nmodes = off;
   p.D = (T*)s->D;
   p.nmatcell = s->nmatcell;
+  p.sig = s->sigmap ? (const T*)s->sig : nullptr;
   p.Pa = (T*)s->Pslot[s->pcur];
   p.Pb = (T*)s->Pslot[1 - s->pcur];
   p.Ya = (T*)s->Yslot[s->ybf ? 0 : s->pcur];
@@ -569,6 +575,7 @@ Cav1DParams<T> make_params1d(fdtdbath_sim* s, int64_t nsteps) {
   p.Yslot[0] = (T*)s->Yslot[0];
   p.Yslot[1] = (T*)s->Yslot[1];
   p.pcur0 = s->pcur;
+  p.sig = s->sigmap ? (const T*)s->sig : nullptr;
   p.coef = (const T*)s->coef;
   p.nmat = (int)s->mats.size();
   int off = 0;
@@ -745,7 +752,7 @@ int switch_to_3d(fdtdbath_sim* s) {
 
 // ---- field access ------------------------------------------------------------------
 struct FieldRef {
-  int kind;  // 0 full grid, 1 material P / PM, 2 bath mode
+  int kind;  // 0 full grid, 1 material P / PM, 2 bath mode, 3 sigma(r)
   int comp, mode, level;
 };
 
@@ -756,6 +763,10 @@ bool parse_field(int32_t f, FieldRef* r) {
   }
   if (f >= 6 && f < 12) {
     *r = {1, (f - 6) % 3, 0, f >= 9 ? 1 : 0};
+    return true;
+  }
+  if (f == FDTDBATH_FIELD_SIGMA) {
+    *r = {3, 0, 0, 0};
     return true;
   }
   if (f >= 1024 && f < 1024 + 6 * 256) {
@@ -785,6 +796,70 @@ int store(fdtdbath_sim* s, void* dptr, const std::vector<double>& in) {
 }
 
 char* elem_ptr(void* base, int64_t idx, size_t esz) { return (char*)base + idx * (int64_t)esz; }
+
+// ---- per-cell oscillator strength sigma(r) (Eq. EOM_Lorentz / EOM_LorentzBath-1) ------------
+// The full-grid sigma(r): the map where one is set, else every dispersive layer's own sigma; zero
+// outside the dispersive layers.
+int sigma_full(fdtdbath_sim* s, std::vector<double>& full) {
+  full.assign((size_t)s->ncell, 0.0);
+  for (auto& m : s->mats) {
+    if (m.kind == FDTDBATH_VACUUM) continue;
+    double* o = full.data() + m.zlo * s->plane;
+    if (!s->sigmap) {
+      std::fill(o, o + m.ncell, m.sigma);
+      continue;
+    }
+    std::vector<double> a;
+    const int rc = fetch(s, elem_ptr(s->sig, m.base, s->esz), m.ncell, a);
+    if (rc) return rc;
+    std::copy(a.begin(), a.end(), o);
+  }
+  return 0;
+}
+
+// The plain-plane and TE register-streaming kernels read each layer's own sigma only: while a map
+// is set every chunk goes to the general kernel (or the 1D kernel); without one the choice made
+// at creation returns.
+void sigma_mode(fdtdbath_sim* s, bool on) {
+  s->sigmap = on;
+  s->plain_ok = on ? false : s->plain_ok0;
+  s->bath_plain = on ? false : s->bath_plain0;
+  s->te2d_ok = on ? false : s->te2d_ok0;
+  s->serial_pair = on ? false : s->serial_pair0;
+}
+
+// Validate a full-grid sigma(r) (finite, >= 0 in the dispersive layers, each layer stable at its
+// largest value; values elsewhere ignored) and make it the simulation's map.
+int set_sigma_map(fdtdbath_sim* s, const std::vector<double>& full) {
+  const int dims = (s->nx > 1) + (s->ny > 1) + (s->nz > 1);
+  for (auto& m : s->mats) {
+    if (m.kind == FDTDBATH_VACUUM) continue;
+    const double* v = full.data() + m.zlo * s->plane;
+    double mx = 0.0;
+    for (int64_t r = 0; r < m.ncell; ++r) {
+      if (!(v[r] >= 0.0) || !std::isfinite(v[r]))
+        return fail(s, FDTDBATH_ERR_ARG, "sigma(r) must be finite and non-negative");
+      mx = std::max(mx, v[r]);
+    }
+    if (!oscillator_stable(m, mx, s->dt, s->courant, dims))
+      return fail(s, FDTDBATH_ERR_CFL, "field-oscillator update unstable at the largest sigma(r) of a layer");
+  }
+  if (!s->sig) {
+    s->sig = dalloc(s, (size_t)s->nmatcell * s->esz);
+    if (!s->sig) return fail(s, FDTDBATH_ERR_OOM, "device allocation failed");
+  }
+  for (auto& m : s->mats) {
+    std::vector<double> v((size_t)m.ncell, 0.0);
+    if (m.kind != FDTDBATH_VACUUM) {
+      const double* src = full.data() + m.zlo * s->plane;
+      std::copy(src, src + m.ncell, v.begin());
+    }
+    const int rc = store(s, elem_ptr(s->sig, m.base, s->esz), v);
+    if (rc) return rc;
+  }
+  sigma_mode(s, true);
+  return 0;
+}
 
 // bf16 <-> float on the host (round to nearest even; no NaN payloads are produced by the kernels)
 float bf16_to_float(uint16_t h) {
@@ -868,6 +943,7 @@ int fdtdbath_internal_view(fdtdbath_sim* s, SimView* v) {
   v->Pa = s->Pslot[s->pcur];
   v->Pb = s->Pslot[1 - s->pcur];
   if (s->ybf) return fail(s, FDTDBATH_ERR_UNSUPPORTED, "this entry point does not read bf16 bath storage");
+  if (s->sigmap) return fail(s, FDTDBATH_ERR_UNSUPPORTED, "this entry point uses each layer's own sigma, not a sigma(r) map");
   v->Ya = s->Yslot[s->pcur];
   v->Yb = s->Yslot[1 - s->pcur];
   v->nmat = (int)s->mats.size();
@@ -1253,6 +1329,10 @@ int fdtdbath_create(const fdtdbath_grid* grid, double resolution, double courant
   }
   ce = cudaStreamSynchronize(s->stream);
   if (ce != cudaSuccess) return bail(FDTDBATH_ERR_CUDA, std::string("create: ") + cudaGetErrorString(ce));
+  s->plain_ok0 = s->plain_ok;
+  s->bath_plain0 = s->bath_plain;
+  s->te2d_ok0 = s->te2d_ok;
+  s->serial_pair0 = s->serial_pair;
   *out = s;
   return FDTDBATH_OK;
 }
@@ -1316,6 +1396,9 @@ int fdtdbath_read_fields(fdtdbath_sim* s, int32_t field, void* dst, size_t dst_b
                                  : elem_ptr(s->H[s->hcur], (f.comp - 3) * s->ncell, s->esz);
     rc = fetch(s, src, s->ncell, full);
     if (rc) return rc;
+  } else if (f.kind == 3) {
+    rc = sigma_full(s, full);
+    if (rc) return rc;
   } else {
     for (auto& m : s->mats) {
       std::vector<double> a;
@@ -1361,8 +1444,9 @@ int fdtdbath_write_fields(fdtdbath_sim* s, int32_t field, const void* src, size_
   if (!parse_field(field, &f)) return fail(s, FDTDBATH_ERR_ARG, "unknown field id");
   if (src_bytes < (size_t)s->ncell * s->esz) return fail(s, FDTDBATH_ERR_ARG, "source too small");
   // the TE form carries only E_y, H_x, H_z and the y polarization / bath modes
-  if ((f.kind == 0 && f.comp != 1 && f.comp != 3 && f.comp != 5) || (f.kind != 0 && f.comp != 1)) s->te = false;
-  {
+  if ((f.kind == 0 && f.comp != 1 && f.comp != 3 && f.comp != 5) || ((f.kind == 1 || f.kind == 2) && f.comp != 1))
+    s->te = false;
+  if (f.kind != 3) {
     // the 1D kernel skips the y/z polarization while it provably stays zero
     const bool xpol = (f.kind == 0 && (f.comp == 0 || f.comp == 4)) || (f.kind != 0 && f.comp == 0);
     cudaSetDevice(s->device);
@@ -1386,6 +1470,7 @@ int fdtdbath_write_fields(fdtdbath_sim* s, int32_t field, const void* src, size_
     for (int64_t i = 0; i < s->ncell; ++i)
       in[(size_t)i] = s->prec == 64 ? ((const double*)raw.data())[i] : (double)((const float*)raw.data())[i];
   }
+  if (f.kind == 3) return set_sigma_map(s, in);
   auto refresh_D = [&](void) -> int {
     // FP64 path: D = eps_inf E + P^{n-1/2} in material cells (the relation E = (D - P)/eps_inf
     // holds between D^{n-1/2}, E^{n-1/2} and P^{n-1/2})
@@ -1439,6 +1524,39 @@ int fdtdbath_write_fields(fdtdbath_sim* s, int32_t field, const void* src, size_
   }
   if (f.kind == 1 && f.level == 1) rc = refresh_D();
   return rc;
+}
+
+int fdtdbath_sigma_box(fdtdbath_sim* s, const double lo[3], const double hi[3], double sigma) {
+  if (!s || !lo || !hi) return fail(s, FDTDBATH_ERR_ARG, "NULL argument");
+  if (!std::isfinite(sigma) || sigma < 0) return fail(s, FDTDBATH_ERR_ARG, "sigma must be finite and non-negative");
+  const int64_t n[3] = {s->nx, s->ny, s->nz};
+  for (int a = 0; a < 3; ++a)
+    if (!(lo[a] >= 0.0 && lo[a] < hi[a] && hi[a] <= (double)n[a]))
+      return fail(s, FDTDBATH_ERR_ARG, "the box must satisfy 0 <= lo < hi <= n on every axis");
+  cudaSetDevice(s->device);
+  int rc = flush_all(s);
+  if (rc) return rc;
+  std::vector<double> full;
+  rc = sigma_full(s, full);
+  if (rc) return rc;
+  // covered fraction of cell (i, j, k) = [i, i+1) x [j, j+1) x [k, k+1): the product of the
+  // overlap lengths of the box with the cell along the three axes
+  std::vector<double> ov[3];
+  for (int a = 0; a < 3; ++a) {
+    ov[a].resize((size_t)n[a]);
+    for (int64_t i = 0; i < n[a]; ++i) {
+      const double t = std::min(hi[a], (double)(i + 1)) - std::max(lo[a], (double)i);
+      ov[a][(size_t)i] = t > 0.0 ? t : 0.0;
+    }
+  }
+  for (int64_t k = (int64_t)lo[2]; k < n[2] && (double)k < hi[2]; ++k)
+    for (int64_t j = (int64_t)lo[1]; j < n[1] && (double)j < hi[1]; ++j)
+      for (int64_t i = (int64_t)lo[0]; i < n[0] && (double)i < hi[0]; ++i) {
+        const double f = ov[0][(size_t)i] * ov[1][(size_t)j] * ov[2][(size_t)k];
+        double& v = full[(size_t)((k * n[1] + j) * n[0] + i)];
+        v = f * sigma + (1.0 - f) * v;
+      }
+  return set_sigma_map(s, full);
 }
 
 int fdtdbath_dft(fdtdbath_sim* s, int32_t monitor, double* out) {
@@ -1528,6 +1646,7 @@ int64_t fdtdbath_query(const fdtdbath_sim* s, int32_t key) {
     case 8: return s->path1d && s->ncomp1d == 1 ? 1 : 0;
     case 9: return s->bath_plain ? 1 : 0;
     case 10: return s->te2d_ok && s->te && s->ty == 1 ? 1 : 0;
+    case 11: return s->sigmap ? 1 : 0;
     default: return -1;
   }
 }
@@ -1848,6 +1967,7 @@ int adjoint_sweep(fdtdbath_sim* s, const HostMon& mon, const std::vector<double>
 int fdtdbath_adjoint_forward(fdtdbath_sim* s, int64_t nsteps, int32_t checkpoint_every) {
   if (!s || nsteps < 1 || checkpoint_every < 1) return fail(s, FDTDBATH_ERR_ARG, "bad arguments to fdtdbath_adjoint_forward");
   if (s->ybf) return fail(s, FDTDBATH_ERR_UNSUPPORTED, "the adjoint does not run on bf16 bath storage");
+  if (s->sigmap) return fail(s, FDTDBATH_ERR_UNSUPPORTED, "the adjoint does not run with a per-cell sigma(r) map");
   if (s->nbmax > kMaxBath) return fail(s, FDTDBATH_ERR_UNSUPPORTED, "the adjoint handles at most 32 bath modes per material");
   cudaSetDevice(s->device);
   AdjState& a = s->adj;
@@ -1916,6 +2036,7 @@ struct SnapHeader {
   int64_t n;
   int32_t pcur, te, ncomp1d, hpend;
   int64_t state_bytes, dft_bytes, trace_bytes, ring_bytes;
+  int32_t sigmap;   // a per-cell sigma(r) map follows the pending step's partial sums
 };
 constexpr char kSnapMagic[8] = {'F', 'D', 'T', 'D', 'B', 'S', 'N', '1'};
 constexpr size_t kSnapHead = 256;
@@ -1924,7 +2045,7 @@ static_assert(sizeof(SnapHeader) <= kSnapHead, "snapshot header");
 SnapHeader snap_header(const fdtdbath_sim* s) {
   SnapHeader h{};
   std::memcpy(h.magic, kSnapMagic, 8);
-  h.version = 1;
+  h.version = 2;
   h.prec = s->prec;
   h.ybf = s->ybf ? 1 : 0;
   h.nmon = (int32_t)s->mons.size();
@@ -1945,13 +2066,14 @@ SnapHeader snap_header(const fdtdbath_sim* s) {
   h.trace_bytes = h.e_cap * 4 * 8;
   h.hpend = s->h_pending ? 1 : 0;
   h.ring_bytes = s->ring_stride * 8;
+  h.sigmap = s->sigmap ? 1 : 0;
   return h;
 }
 
 // Copy every piece of a snapshot between the simulation and buf (host or device), in order:
 // header, device state (the checkpoint layout), DFT accumulators, energy trace, and -- while the
 // H half-step of the last step is pending -- the partial sums of that step (its E half).
-int snap_io(fdtdbath_sim* s, char* buf, bool save, bool on_device, bool hpend) {
+int snap_io(fdtdbath_sim* s, char* buf, bool save, bool on_device, bool hpend, bool smap) {
   const cudaMemcpyKind to_buf = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
   const cudaMemcpyKind from_buf = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
   size_t off = kSnapHead;
@@ -1980,6 +2102,12 @@ int snap_io(fdtdbath_sim* s, char* buf, bool save, bool on_device, bool hpend) {
     const int64_t slot = (s->n - 1) % s->ring_cap;
     const int rc = piece((double*)s->partial + slot * s->ring_stride, (size_t)s->ring_stride * 8);
     if (rc) return rc;
+  } else {
+    off += ((size_t)s->ring_stride * 8 + 255) & ~size_t(255);
+  }
+  if (smap) {
+    const int rc = piece(s->sig, (size_t)s->nmatcell * s->esz);
+    if (rc) return rc;
   }
   const cudaError_t e = cudaStreamSynchronize(s->stream);
   if (e != cudaSuccess) return cuda_fail(s, e, "snapshot stream");
@@ -1992,6 +2120,7 @@ size_t snap_bytes(fdtdbath_sim* s) {
   for (auto& mo : s->mons) n += ((size_t)mo.nfreq * 64 + 255) & ~size_t(255);
   if (s->energy_on) n += ((size_t)s->e_cap * 32 + 255) & ~size_t(255);
   n += ((size_t)s->ring_stride * 8 + 255) & ~size_t(255);
+  n += ((size_t)s->nmatcell * s->esz + 255) & ~size_t(255);   // a sigma(r) map, whether set or not
   return n;
 }
 
@@ -2020,7 +2149,7 @@ int fdtdbath_snapshot(fdtdbath_sim* s, void* dst, size_t dst_bytes, int32_t dst_
   } else {
     std::memcpy(dst, &h, sizeof(h));
   }
-  return snap_io(s, (char*)dst, true, dst_on_device != 0, h.hpend != 0);
+  return snap_io(s, (char*)dst, true, dst_on_device != 0, h.hpend != 0, h.sigmap != 0);
 }
 
 int fdtdbath_restore(fdtdbath_sim* s, const void* src, size_t src_bytes, int32_t src_on_device) {
@@ -2035,13 +2164,14 @@ int fdtdbath_restore(fdtdbath_sim* s, const void* src, size_t src_bytes, int32_t
     std::memcpy(&h, src, sizeof(h));
   }
   SnapHeader mine = snap_header(s);
-  const bool same = std::memcmp(h.magic, kSnapMagic, 8) == 0 && h.version == 1 && h.prec == mine.prec &&
+  const bool same = std::memcmp(h.magic, kSnapMagic, 8) == 0 && h.version == 2 && h.prec == mine.prec &&
                     h.ybf == mine.ybf && h.nmon == mine.nmon && h.nx == mine.nx && h.ny == mine.ny &&
                     h.nz == mine.nz && h.npml == mine.npml && h.nmatcell == mine.nmatcell &&
                     h.nybath == mine.nybath && h.e_cap == mine.e_cap &&
                     std::memcmp(h.nfreq, mine.nfreq, sizeof(h.nfreq)) == 0 && h.state_bytes == mine.state_bytes &&
                     h.ring_bytes == mine.ring_bytes && h.n >= 0 && (h.pcur == 0 || h.pcur == 1) &&
-                    (h.ncomp1d == 1 || h.ncomp1d == 3) && (h.hpend == 0 || (h.hpend == 1 && h.n > 0));
+                    (h.ncomp1d == 1 || h.ncomp1d == 3) && (h.hpend == 0 || (h.hpend == 1 && h.n > 0)) &&
+                    (h.sigmap == 0 || h.sigmap == 1);
   if (!same) return fail(s, FDTDBATH_ERR_ARG, "the snapshot was taken from a simulation of another layout");
   int rc = flush_all(s);   // nothing of this simulation's own queue may land after the restore
   if (rc) return rc;
@@ -2050,8 +2180,13 @@ int fdtdbath_restore(fdtdbath_sim* s, const void* src, size_t src_bytes, int32_t
     if (rc) return rc;
   }
   s->n = h.n;   // the ring slot of a pending step is addressed through n
-  rc = snap_io(s, (char*)const_cast<void*>(src), false, src_on_device != 0, h.hpend != 0);
+  if (h.sigmap && !s->sig) {
+    s->sig = dalloc(s, (size_t)s->nmatcell * s->esz);
+    if (!s->sig) return fail(s, FDTDBATH_ERR_OOM, "device allocation failed");
+  }
+  rc = snap_io(s, (char*)const_cast<void*>(src), false, src_on_device != 0, h.hpend != 0, h.sigmap != 0);
   if (rc) return rc;
+  sigma_mode(s, h.sigmap != 0);   // the snapshot's sigma(r) map, or the layers' own sigma
   s->h_pending = h.hpend != 0;
   s->reduced = s->h_pending ? h.n - 1 : h.n;
   s->pcur = h.pcur;

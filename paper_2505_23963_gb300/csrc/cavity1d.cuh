@@ -111,6 +111,12 @@ __global__ void __launch_bounds__(kCav1DThreads) cavity1d_kernel(const Cav1DPara
     rho_idt2 = M.rho_idt2;
     w0r2dt2 = M.w0r2dt2;
     eps = M.eps;
+    if (p.sig) {
+      // per-cell oscillator strength sigma(r) (Eq. EOM_Lorentz): drive and energy weight
+      const T sg = p.sig[r];
+      cEm = M.dcE * sg;
+      rho_idt2 = sg > T(0) ? M.rho_s / sg : T(0);
+    }
   }
   const T* cfm = mat ? p.coef + p.mat[mi].coef_off * kCoefStride : p.coef;
   const bool in_box = own && z >= p.ebox_lo && z < p.ebox_hi;

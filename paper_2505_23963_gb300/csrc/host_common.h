@@ -21,6 +21,7 @@ struct HostMat {
   std::vector<double> wj, gj, kj;
   // derived (double)
   double cE, c1m, W, c2, A, rho, w0r2;
+  double dcE, rho_s;   // per unit sigma(r): cE = dcE sigma(r), rho = rho_s / sigma(r)
   std::vector<double> rowsLit, rowsInc;  // [nb][kCoefStride]
   int user_index = -1;                    // position in the caller's material list
 };
@@ -95,11 +96,29 @@ inline void expand_material(HostMat& m, double dt) {
     m.A = 1.0 + 0.5 * g0 * dt;
   }
   m.rho = (m.sigma > 0.0 && w0 > 0.0) ? 1.0 / (m.sigma * w0 * w0) : 0.0;
+  m.dcE = w0 * w0 * dt * dt;
+  m.rho_s = w0 > 0.0 ? 1.0 / (w0 * w0) : 0.0;
   if (m.kind == FDTDBATH_VACUUM) {
     m.cE = m.c1m = m.W = m.c2 = 0.0;
     m.A = 1.0;
     m.rho = 0.0;
+    m.dcE = m.rho_s = 0.0;
   }
+}
+
+// Coupled field + oscillator stability of a layer at oscillator strength sigma: a plane wave of
+// the scheme obeys Omega^2 (eps_inf + chi_d) = K^2 with Omega = 2 sin(w dt/2)/dt and
+// K^2 <= 4 dims/dx^2, and its largest Omega^2 is below w_max^2 + K^2/eps_inf (w_max^2 =
+// w0^2 (1 + sigma) + sum k_j^2, or w0^2 sigma for Drude); every root stays on the unit circle
+// while that is <= 4/dt^2.  With a per-cell sigma(r) the bound holds cell by cell, so the largest
+// sigma(r) of the layer decides.
+inline bool oscillator_stable(const HostMat& h, double sigma, double dt, double courant, int dims) {
+  double wmax2 = 0.0;
+  if (h.kind == FDTDBATH_DRUDE) wmax2 = h.w0 * h.w0 * sigma;
+  else if (h.kind != FDTDBATH_VACUUM) wmax2 = h.w0 * h.w0 * (1.0 + sigma);
+  for (double k : h.kj) wmax2 += k * k;
+  const double lhs = wmax2 * dt * dt + 4.0 * courant * courant * dims / h.eps;
+  return !(lhs > 4.0 * (1.0 + 1e-12));
 }
 
 // Validate one layer and fill h (nu-units scaled by 2 pi, coefficients expanded).  `plane` is the
@@ -137,19 +156,9 @@ inline int build_material(const fdtdbath_material& M, int64_t plane, double dt, 
     return why = "w0 dt >= 2: oscillator update unstable", FDTDBATH_ERR_CFL;
   for (double w : h.wj)
     if (w * dt >= 2.0) return why = "w_j dt >= 2: bath update unstable", FDTDBATH_ERR_CFL;
-  // coupled field + oscillator stability: a plane wave of the scheme obeys
-  // Omega^2 (eps_inf + chi_d) = K^2 with Omega = 2 sin(w dt/2)/dt and K^2 <= 4 dims/dx^2, and
-  // its largest Omega^2 is below w_max^2 + K^2/eps_inf (w_max^2 = w0^2 (1 + sigma) + sum k_j^2,
-  // or w0^2 sigma for Drude); every root stays on the unit circle while that is <= 4/dt^2.
-  {
-    double wmax2 = 0.0;
-    if (M.kind == FDTDBATH_DRUDE) wmax2 = h.w0 * h.w0 * h.sigma;
-    else if (M.kind != FDTDBATH_VACUUM) wmax2 = h.w0 * h.w0 * (1.0 + h.sigma);
-    for (double k : h.kj) wmax2 += k * k;
-    const double lhs = wmax2 * dt * dt + 4.0 * courant * courant * dims / h.eps;
-    if (lhs > 4.0 * (1.0 + 1e-12))
-      return why = "field-oscillator update unstable: w_max^2 dt^2 + 4 S^2 dims/eps_inf > 4", FDTDBATH_ERR_CFL;
-  }
+  // coupled field + oscillator stability (oscillator_stable)
+  if (!oscillator_stable(h, h.sigma, dt, courant, dims))
+    return why = "field-oscillator update unstable: w_max^2 dt^2 + 4 S^2 dims/eps_inf > 4", FDTDBATH_ERR_CFL;
   expand_material(h, dt);
   return 0;
 }
@@ -175,6 +184,8 @@ MatK<T> mat_k(const HostMat& m, int coef_off, double dt) {
   k.inv_eps = (T)(1.0 / m.eps);
   k.rho_idt2 = (T)(m.rho / (dt * dt));
   k.w0r2dt2 = (T)(m.w0r2 * dt * dt);
+  k.dcE = (T)m.dcE;
+  k.rho_s = (T)(m.rho_s / (dt * dt));
   return k;
 }
 

@@ -68,6 +68,10 @@ struct MatK {
   T inv_eps;      // 1/eps_inf
   T rho_idt2;     // rho/dt^2, rho = 1/(sigma w0^2) (0 when sigma = 0), energy density
   T w0r2dt2;      // (w0 dt)^2 in the potential term (Drude: 0)
+  // with a per-cell oscillator strength sigma(r) (Eq. EOM_Lorentz): cE = dcE sigma(r),
+  // rho/dt^2 = rho_s / sigma(r) (0 where sigma(r) = 0)
+  T dcE;          // w0^2 dt^2 (0 for a vacuum layer)
+  T rho_s;        // 1/(w0^2 dt^2)
 };
 
 // Per bath mode j (coefficient row of kCoefStride values):
@@ -102,6 +106,7 @@ struct Step3DParams {
   T* Ya;
   T* Yb;
   int64_t nmatcell;
+  const T* sig;   // sigma(r) per material cell (pooled like P), or null: every layer's own sigma
   // sources: J(x, y) = src_a * cos(phase) + src_b * sin(phase)   (src_b unused without phase)
   int nsrc;
   int src_comp[kMaxSrc];
@@ -145,6 +150,7 @@ struct Cav1DParams {
   T* Pslot[2];
   T* Yslot[2];
   int pcur0;                          // slot holding P^{n+1/2} at the first step of the launch
+  const T* sig;                       // sigma(r) per material cell, or null (the layer's sigma)
   const T* coef;
   int nmat;
   MatK<T> mat[kMaxMat];

@@ -519,6 +519,7 @@ step3d_kernel(const Step3DParams<T> p) {
     const bool mat_here = p.doE && own && mi >= 0 && p.mat[mi].kind != kVacuum;
     T rPa[3], rPb[3], rD[3];
     T rY[3][NBP > 0 ? NBP : 1], rV[3][NBP > 0 ? NBP : 1];
+    T rS = T(0);   // sigma(r) of the cell when the simulation has a per-cell map
     int r = 0, rl = 0, mstride = 0, yb0 = 0;
     const int nmc = (int)p.nmatcell;
     if (p.doE && own && mi >= 0) {
@@ -527,6 +528,7 @@ step3d_kernel(const Step3DParams<T> p) {
       r = (int)M.base + rl;
       mstride = (int)M.ncell;
       yb0 = (int)M.ybase + rl;
+      if (p.sig) rS = p.sig[r];
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
         if (!liveE(c)) {
@@ -667,6 +669,10 @@ step3d_kernel(const Step3DParams<T> p) {
           const MatK<T>& M = p.mat[mi];
           const bool bath = (M.kind == kLorentzBath) && (NBMAX > 0);
           const T* cfm = sCoef + M.coef_off * kCoefStride;
+          // the drive coefficient eps0 w0^2 dt^2 sigma(r) and the energy weight rho(r)/dt^2 of
+          // this cell (Eq. EOM_Lorentz's sigma(r); rho = 1/(sigma w0^2))
+          const T cEr = p.sig ? M.dcE * rS : M.cE;
+          const T rhor = p.sig ? (rS > T(0) ? M.rho_s / rS : T(0)) : M.rho_idt2;
           YT* const ya = reinterpret_cast<YT*>(p.Ya) + yb0;
           YT* const yb = reinterpret_cast<YT*>(p.Yb) + yb0;
 #pragma unroll
@@ -747,7 +753,7 @@ step3d_kernel(const Step3DParams<T> p) {
             if (!INC) {
               // Eq. Pz_update-LB (Eq. Pz_1D_Lorentz when there is no bath):
               // P^{n+1} = (1/A) [cE E - (w0^2 dt^2 - 2) P^n - c2 P^{n-1} - dt/2 sum_j k_j(a_j Y^n + b_j Y^{n-1})]
-              T num = M.cE * E - M.c1m * Pa - M.c2 * Pb;
+              T num = cEr * E - M.c1m * Pa - M.c2 * Pb;
               if (bath) num = num - T(0.5) * dt * bsum;
               Pn = M.inv_A * num;
               p.Pb[c * nmc + r] = Pn;   // overwrites P^{n-1}
@@ -756,7 +762,7 @@ step3d_kernel(const Step3DParams<T> p) {
             } else {
               // increment form: V^{n+1} = [cE E - w0^2 dt^2 P^n + c2 V^n - dt/2 sum(...)] / A
               V0 = Pa - Pb;
-              T num = M.cE * E - M.W * Pa + M.c2 * V0;
+              T num = cEr * E - M.W * Pa + M.c2 * V0;
               if (bath) num = num - T(0.5) * dt * bsum;
               Vn = num * M.inv_A;
               Pn = Pa + Vn;
@@ -824,8 +830,8 @@ step3d_kernel(const Step3DParams<T> p) {
             }
             if (p.eE_on && in_box) {
               // rho/dt^2 (V^2 + (w0 dt)^2 P^2) = rho (V/dt)^2 + rho w0^2 P^2, likewise per mode
-              uP += M.rho_idt2 * (Vn * Vn + M.w0r2dt2 * Pn * Pn);
-              uB += M.rho_idt2 * ub;
+              uP += rhor * (Vn * Vn + M.w0r2dt2 * Pn * Pn);
+              uB += rhor * ub;
             }
           }
           if (NBP > 0 && bath && mat_here) {
@@ -859,14 +865,14 @@ step3d_kernel(const Step3DParams<T> p) {
               const T Pa = rPa[c], Pb = rPb[c];
               T V0;
               if (!INC) {
-                T num = M.cE * Ev[c] - M.c1m * Pa - M.c2 * Pb;
+                T num = cEr * Ev[c] - M.c1m * Pa - M.c2 * Pb;
                 num = num - T(0.5) * dt * bsum[c];
                 Pn[c] = M.inv_A * num;
                 Vn[c] = Pn[c] - Pa;
                 V0 = Pa - Pb;
               } else {
                 V0 = Pa - Pb;
-                T num = M.cE * Ev[c] - M.W * Pa + M.c2 * V0;
+                T num = cEr * Ev[c] - M.W * Pa + M.c2 * V0;
                 num = num - T(0.5) * dt * bsum[c];
                 Vn[c] = num * M.inv_A;
                 Pn[c] = Pa + Vn[c];
@@ -906,8 +912,8 @@ step3d_kernel(const Step3DParams<T> p) {
 #pragma unroll
               for (int c = 0; c < 3; ++c) {
                 if (!liveE(c)) continue;
-                uP += M.rho_idt2 * (Vn[c] * Vn[c] + M.w0r2dt2 * Pn[c] * Pn[c]);
-                uB += M.rho_idt2 * ub[c];
+                uP += rhor * (Vn[c] * Vn[c] + M.w0r2dt2 * Pn[c] * Pn[c]);
+                uB += rhor * ub[c];
               }
             }
           }

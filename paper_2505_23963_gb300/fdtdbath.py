@@ -30,7 +30,7 @@ EXPORTED = ["fdtdbath_create", "fdtdbath_step", "fdtdbath_sync", "fdtdbath_read_
             "fdtdbath_batch_step", "fdtdbath_batch_sync", "fdtdbath_batch_read_field",
             "fdtdbath_batch_energy", "fdtdbath_batch_query", "fdtdbath_batch_last_error",
             "fdtdbath_batch_destroy", "fdtdbath_batch_plan", "fdtdbath_adjoint_forward",
-            "fdtdbath_adjoint_backward"]
+            "fdtdbath_adjoint_backward", "fdtdbath_sigma_box"]
 
 
 def field_E(c): return 0 + c
@@ -38,6 +38,7 @@ def field_H(c): return 3 + c
 def field_P(c): return 6 + c
 def field_PM(c): return 9 + c
 def field_Y(c, j, level): return 1024 + (c * 2 + level) * 256 + j
+FIELD_SIGMA = 12   # the per-cell oscillator strength sigma(r)
 
 
 class Grid(C.Structure):
@@ -142,6 +143,8 @@ def lib(build_if_missing: bool = True):
         L.fdtdbath_adjoint_forward.argtypes = [vp, i64, i32]
         L.fdtdbath_adjoint_backward.restype = i32
         L.fdtdbath_adjoint_backward.argtypes = [vp, i32, dp, i32, dp]
+        L.fdtdbath_sigma_box.restype = i32
+        L.fdtdbath_sigma_box.argtypes = [vp, dp, dp, C.c_double]
         i32p, i64p = C.POINTER(i32), C.POINTER(i64)
         L.fdtdbath_batch_create.restype = i32
         L.fdtdbath_batch_create.argtypes = [C.POINTER(Cavity), i32, C.c_double, C.c_double,
@@ -379,15 +382,36 @@ class Simulation:
     def steps_done(self) -> int:
         return steps_done(self.h)
 
-    def get(self, name: str, comp: int = 0, mode: int = 0, level: int = 0) -> np.ndarray:
+    @staticmethod
+    def _field(name: str, comp: int, mode: int, level: int) -> int:
+        if name == "S":   # sigma(r)
+            return FIELD_SIGMA
         fid = {"E": field_E, "H": field_H, "P": field_P, "Pm": field_PM}.get(name)
-        f = fid(comp) if fid else field_Y(comp, mode, level)
-        return read_fields(self.h, f, self.shape, self.dtype)
+        if fid:
+            return fid(comp)
+        if name != "Y":
+            raise KeyError(name)
+        return field_Y(comp, mode, level)
+
+    def get(self, name: str, comp: int = 0, mode: int = 0, level: int = 0) -> np.ndarray:
+        """Read a field: E, H, P, Pm, Y (bath mode `mode` at `level`) or S (sigma(r))."""
+        return read_fields(self.h, self._field(name, comp, mode, level), self.shape, self.dtype)
 
     def set(self, name: str, arr, comp: int = 0, mode: int = 0, level: int = 0):
-        fid = {"E": field_E, "H": field_H, "P": field_P, "Pm": field_PM}.get(name)
-        f = fid(comp) if fid else field_Y(comp, mode, level)
-        write_fields(self.h, f, np.asarray(arr, dtype=self.dtype).reshape(self.shape))
+        """Overwrite a field (names as for get)."""
+        write_fields(self.h, self._field(name, comp, mode, level),
+                     np.asarray(arr, dtype=self.dtype).reshape(self.shape))
+
+    def sigma_box(self, lo, hi, sigma: float):
+        """fdtdbath_sigma_box: paint a box [lo, hi) (x, y, z in cell units) of oscillator strength
+        sigma into the sigma(r) map, each cell weighted by the fraction the box covers."""
+        lo_a = np.ascontiguousarray(lo, dtype=np.float64)
+        hi_a = np.ascontiguousarray(hi, dtype=np.float64)
+        _check(lib().fdtdbath_sigma_box(self.h, _dptr(lo_a), _dptr(hi_a), float(sigma)), self.h)
+
+    def sigma_map(self) -> bool:
+        """Whether a per-cell sigma(r) map is set (query key 11)."""
+        return query(self.h, 11) == 1
 
     def dft(self, mon: int = 0) -> np.ndarray:
         return dft(self.h, mon, self.nfreq[mon])

@@ -256,6 +256,22 @@ def adjoint_target_params(params: np.ndarray, seed: int = 0) -> np.ndarray:
 
 
 # ----------------------------------------------------------------- random states
+def random_sigma_map(prob: dict, seed: int, lo: float = 0.3, hi: float = 1.0) -> np.ndarray:
+    """Seeded per-cell oscillator strengths sigma(r): every cell of a Lorentz, Drude or
+    Lorentz-Bath layer gets its layer's sigma times a factor drawn uniformly from [lo, hi) by
+    default_rng(seed) (factors below 1 keep each layer inside its stability limit); zero elsewhere.
+    float64, shape (nz, ny, nx)."""
+    nx, ny, nz = prob["n"]
+    rng = np.random.default_rng(seed)
+    out = np.zeros((nz, ny, nx))
+    for m in prob["materials"]:
+        if m["kind"] == "vacuum":
+            continue
+        a, b = m["z"]
+        out[a:b] = float(m["sigma"]) * rng.uniform(lo, hi, (b - a, ny, nx))
+    return out
+
+
 def random_state(prob: dict, seed: int, scale: float = 1e-2, with_bath: bool = True) -> dict:
     """Seeded random E, H, P (two levels) and Y (two levels) for every cell of a polarizable
     layer (a vacuum-kind layer, a plain dielectric, has no polarization).
