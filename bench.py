@@ -45,13 +45,15 @@ def peaks():
         return 6800.0, "fallback"
 
 
-def algorithmic_bytes(prob: dict, esz: int, bath_bytes: float | None = None) -> float:
+def algorithmic_bytes(prob: dict, esz: int, bath_bytes: float | None = None,
+                      sigma_map: bool = False) -> float:
     """Bytes per launch with every state word read once and written once: E, H (6 words
     per cell), +4 CPML memories in the absorber planes, +3 x (2 reads + 1 write) of P in
     Drude/Lorentz planes and additionally +3 x 3 N_b words for the bath modes (two levels
     read, one written) in Lorentz-Bath planes.  Coefficient tables are not counted.
     bath_bytes overrides the bytes per bath mode and component (bf16 value/increment pairs
-    read and written: 8)."""
+    read and written: 8); sigma_map adds the read of a per-cell sigma(r) in every Drude,
+    Lorentz and Lorentz-Bath cell."""
     nx, ny, nz = prob["n"]
     pml = prob.get("pml", 0)
     words = np.full(nz, 12.0)
@@ -64,6 +66,8 @@ def algorithmic_bytes(prob: dict, esz: int, bath_bytes: float | None = None) -> 
         elif m["kind"] == "lorentz_bath":
             nb = len(m["bath_frequencies"])
             words[lo:hi] += 9 + (9 * nb if bath_bytes is None else 3 * nb * bath_bytes / esz)
+        if sigma_map and m["kind"] != "vacuum":
+            words[lo:hi] += 1
     return float(words.sum()) * nx * ny * esz
 
 
@@ -384,6 +388,40 @@ def form_many_bath(fb, stream, torch):
     byts = algorithmic_bytes(prob, 4)
     return {"workload": prob["name"], "value": cells / (ms * 1e-3), "unit": UNIT,
             "ms_per_step": ms, "bytes_per_cell": byts / cells,
+            "achieved_GBs": byts / (ms * 1e-3) / 1e9, "frac_hbm": byts / (ms * 1e-3) / 1e9 / hbm,
+            "finite": finite}
+
+
+def form_sigma_map(fb, stream, torch):
+    """Per-cell oscillator strength sigma(r) on the 256^3 slab cavity (N_b = 8, FP32): the
+    Lorentz-Bath layer patterned by fdtdbath_sigma_box -- a 128 x 128-cell square of twice the
+    layer's sigma whose edges cut cells in half (sub-pixel averaged) -- so every cell of the
+    dispersive layers reads its own sigma (one more word per such cell), on the same plain-plane
+    kernels as the headline step."""
+    hbm, _ = peaks()
+    prob = wl.slab_3d(steps=0)
+    cells = float(np.prod(prob["n"]))
+    lb = next(m for m in prob["materials"] if m["kind"] == "lorentz_bath")
+    with torch.cuda.stream(stream):
+        sim = fb.Simulation(prob, precision=32, stream=stream, energy_capacity=64)
+    sim.sigma_box((63.5, 63.5, lb["z"][0]), (191.5, 191.5, lb["z"][1]), 2.0 * lb["sigma"])
+    assert sim.sigma_map()
+    sim_plain = sim.plain_kernel() and sim.bath_plain_kernel()
+    sim.step(3)
+    sim.sync()
+    k = 20
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    ev[0].record(stream)
+    sim.step(k)
+    ev[1].record(stream)
+    torch.cuda.synchronize()
+    ms = ev[0].elapsed_time(ev[1]) / k
+    finite = spectrum_is_finite(fb, sim)
+    sim.close()
+    byts = algorithmic_bytes(prob, 4, sigma_map=True)
+    return {"workload": prob["name"] + "_sigma_box", "value": cells / (ms * 1e-3), "unit": UNIT,
+            "ms_per_step": ms, "bytes_per_cell": byts / cells,
+            "kernel": "plain3d_kernel (bath-free and Lorentz-Bath forms)" if sim_plain else "step3d_kernel",
             "achieved_GBs": byts / (ms * 1e-3) / 1e9, "frac_hbm": byts / (ms * 1e-3) / 1e9 / hbm,
             "finite": finite}
 
@@ -763,6 +801,7 @@ def run_ours(args):
         forms = {}
         for name, fn in (("precision", lambda: form_precision(fb, stream, torch)),
                          ("many_bath", lambda: form_many_bath(fb, stream, torch)),
+                         ("sigma_map", lambda: form_sigma_map(fb, stream, torch)),
                          ("batch", lambda: form_batch(fb, torch)),
                          ("adjoint", lambda: form_adjoint(fb, torch)),
                          ("cavity_1d", lambda: form_cavity_1d(fb, stream, torch))):

@@ -78,9 +78,10 @@ enum fdtdbath_bath_shape { FDTDBATH_BATH_UNIFORM = 0, FDTDBATH_BATH_LORENTZIAN =
  * Drude and Lorentz-Bath layers.  Writing it sets the map of every such layer (values elsewhere
  * are ignored): FDTDBATH_ERR_ARG for a negative or non-finite value, FDTDBATH_ERR_CFL (nothing
  * changed) when a layer would be unstable at its largest sigma(r) (the bound of fdtdbath_create
- * with that sigma).  The map takes 4 (FP32) or 8 (FP64) bytes per layer cell; while it is set
- * every chunk runs on the general step kernel (or the 1D kernel), the adjoint and
- * fdtdbath_box_energy_noalloc answer FDTDBATH_ERR_UNSUPPORTED, and a snapshot carries the map. */
+ * with that sigma).  The map takes 4 (FP32) or 8 (FP64) bytes per layer cell, read once per step
+ * by the step kernels (the TE form's register-streaming kernel leaves its chunks to the general
+ * kernel while a map is set); the adjoint and fdtdbath_box_energy_noalloc answer
+ * FDTDBATH_ERR_UNSUPPORTED, and a snapshot carries the map. */
 #define FDTDBATH_FIELD_SIGMA 12
 
 typedef struct fdtdbath_sim fdtdbath_sim; /* opaque, owned by the library */

@@ -145,10 +145,10 @@ struct fdtdbath_sim {
   // ny = 1, nx a multiple of kTe2dTileX, no source plane inside a layer
   bool te2d_ok = false;
   // per-cell oscillator strength sigma(r) (Eq. EOM_Lorentz), pooled like P, allocated by the first
-  // write of the map; while a map is set the general kernel (or the 1D kernel) runs every chunk
+  // write of the map
   void* sig = nullptr;
   bool sigmap = false;
-  bool plain_ok0 = false, bath_plain0 = false, te2d_ok0 = false, serial_pair0 = false;   // at create
+  bool te2d_ok0 = false;   // the TE kernel's availability at creation
   PlainMaps bmaps{};        // tensor maps of 32-cell-wide boxes
   BathMaps bath_maps{};     // tensor maps of its polarization and bath-mode arrays
   // the bath-free and bath launches of a step one after the other on the simulation's stream (the
@@ -817,15 +817,12 @@ int sigma_full(fdtdbath_sim* s, std::vector<double>& full) {
   return 0;
 }
 
-// The plain-plane and TE register-streaming kernels read each layer's own sigma only: while a map
-// is set every chunk goes to the general kernel (or the 1D kernel); without one the choice made
-// at creation returns.
+// The TE form's register-streaming kernel reads each layer's own sigma only: while a map is set
+// its chunks go to the general kernel; without one the choice made at creation returns.  (The
+// general, plain-plane and 1D kernels read the map.)
 void sigma_mode(fdtdbath_sim* s, bool on) {
   s->sigmap = on;
-  s->plain_ok = on ? false : s->plain_ok0;
-  s->bath_plain = on ? false : s->bath_plain0;
   s->te2d_ok = on ? false : s->te2d_ok0;
-  s->serial_pair = on ? false : s->serial_pair0;
 }
 
 // Validate a full-grid sigma(r) (finite, >= 0 in the dispersive layers, each layer stable at its
@@ -1329,10 +1326,7 @@ int fdtdbath_create(const fdtdbath_grid* grid, double resolution, double courant
   }
   ce = cudaStreamSynchronize(s->stream);
   if (ce != cudaSuccess) return bail(FDTDBATH_ERR_CUDA, std::string("create: ") + cudaGetErrorString(ce));
-  s->plain_ok0 = s->plain_ok;
-  s->bath_plain0 = s->bath_plain;
   s->te2d_ok0 = s->te2d_ok;
-  s->serial_pair0 = s->serial_pair;
   *out = s;
   return FDTDBATH_OK;
 }

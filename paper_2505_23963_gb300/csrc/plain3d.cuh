@@ -624,13 +624,19 @@ plain3d_kernel(const Step3DParams<T> p, const __grid_constant__ PlainMaps maps, 
       }
     }
   };
+  // a cell's eps0 w0^2 dt^2 sigma(r) and rho(r)/dt^2 (Eq. EOM_Lorentz's per-cell sigma; the
+  // layer's own values without a map)
+  auto drive_of = [&](const MatK<T>& M, T sg) -> T { return p.sig ? M.dcE * sg : M.cE; };
+  auto weight_of = [&](const MatK<T>& M, T sg) -> T {
+    return p.sig ? (sg > T(0) ? M.rho_s / sg : T(0)) : M.rho_idt2;
+  };
   // Eq. Pz_update-LB (increment form): P^{n+3/2}, its increment, and P^{n+3/2} - P^{n-1/2}
-  auto p_update = [&](const MatK<T>& M, const T (&bPa)[3], const T (&bPb)[3], const T (&Ev)[3],
+  auto p_update = [&](const MatK<T>& M, T cEr, const T (&bPa)[3], const T (&bPb)[3], const T (&Ev)[3],
                       const T (&bsum)[3], T (&Pn)[3], T (&Vn)[3], T (&dP)[3]) {
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       const T V0 = bPa[c] - bPb[c];
-      T num = M.cE * Ev[c] - M.W * bPa[c] + M.c2 * V0;
+      T num = cEr * Ev[c] - M.W * bPa[c] + M.c2 * V0;
       num = num - T(0.5) * dt * bsum[c];
       Vn[c] = num * M.inv_A;
       Pn[c] = bPa[c] + Vn[c];
@@ -747,11 +753,13 @@ plain3d_kernel(const Step3DParams<T> p, const __grid_constant__ PlainMaps maps, 
       T bPa[3], bPb[3], bY[3][NBH], bV[3][NBH];
       const int mi2 = (info & 0xF) - 1;
       int nbm = 0, yB = 0, mstr = 0;
+      T sg = T(0);
       if (bathp) {
         const MatK<T>& M = p.mat[mi2];
         nbm = M.nb;
         yB = (int)M.ybase + (k - M.zlo) * plane + qxy;
         mstr = (int)M.ncell;
+        if (p.sig) sg = p.sig[(int)M.base + (k - M.zlo) * plane + qxy];
         if (!plain::mbar_wait(&mbar[A], bpar)) {
           s_abort = 1;
           atomicExch(p.err, 1);
@@ -785,12 +793,13 @@ plain3d_kernel(const Step3DParams<T> p, const __grid_constant__ PlainMaps maps, 
           bsum[c] = sX[(3 + c) * XT + cellx] + bsum[c];   // the first half's sum first, as there
         }
         T Pn[3], Vn[3], dP[3];
-        p_update(M, bPa, bPb, Ev, bsum, Pn, Vn, dP);
+        p_update(M, drive_of(M, sg), bPa, bPb, Ev, bsum, Pn, Vn, dP);
         T ub[3] = {T(0), T(0), T(0)};
         bath_modes(cfm, NBH, nbm, yB, mstr, bY, bV, dP, ub);
         if (p.eE_on && (info & kBox)) {
+          const T wr = weight_of(M, sg);
 #pragma unroll
-          for (int c = 0; c < 3; ++c) uB += M.rho_idt2 * ub[c];
+          for (int c = 0; c < 3; ++c) uB += wr * ub[c];
         }
       }
       if (info & kMonE) {
@@ -835,6 +844,7 @@ plain3d_kernel(const Step3DParams<T> p, const __grid_constant__ PlainMaps maps, 
       // V = Y^n - Y^{n-1} below)
       T bPa[3], bPb[3], bY[3][NBH], bV[3][NBH];
       int rB = 0, yB = 0, mstr = 0, nbm = 0;
+      [[maybe_unused]] T sgB = T(0);   // sigma(r) of the cell (with a map)
       if constexpr (BATH) {
         const MatK<T>& M = p.mat[mi];
         const int rl = (k - M.zlo) * plane + qxy;
@@ -842,6 +852,7 @@ plain3d_kernel(const Step3DParams<T> p, const __grid_constant__ PlainMaps maps, 
         yB = (int)M.ybase + rl;
         mstr = (int)M.ncell;
         nbm = M.nb;
+        if (p.sig) sgB = p.sig[rB];
       }
       // without the helper: warp 0 also computes the halo row y0-1 (its CPML memories loaded here)
       [[maybe_unused]] T hpsx[VX], hpsy[VX];
@@ -1057,21 +1068,25 @@ plain3d_kernel(const Step3DParams<T> p, const __grid_constant__ PlainMaps maps, 
             if (M->kind != kVacuum) {
               // Eq. Pz_1D_Lorentz (Drude: w0^2 dropped from the restoring term); the new level
               // overwrites P^{n-1}
-              T Pn[VX];
+              T Pn[VX], Sg[VX];
+#pragma unroll
+              for (int v = 0; v < VX; ++v) Sg[v] = T(0);
+              if (p.sig) VV::ld(p.sig + r, Sg);
 #pragma unroll
               for (int v = 0; v < VX; ++v) {
                 T Vn;
+                const T cEr = drive_of(*M, Sg[v]);
                 if (!INC) {
-                  const T num = M->cE * Ec[v] - M->c1m * Pa[v] - M->c2 * Pb[v];
+                  const T num = cEr * Ec[v] - M->c1m * Pa[v] - M->c2 * Pb[v];
                   Pn[v] = M->inv_A * num;
                   Vn = Pn[v] - Pa[v];
                 } else {
                   const T V0 = Pa[v] - Pb[v];
-                  const T num = M->cE * Ec[v] - M->W * Pa[v] + M->c2 * V0;
+                  const T num = cEr * Ec[v] - M->W * Pa[v] + M->c2 * V0;
                   Vn = num * M->inv_A;
                   Pn[v] = Pa[v] + Vn;
                 }
-                if (p.eE_on && in_box) uP += M->rho_idt2 * (Vn * Vn + M->w0r2dt2 * Pn[v] * Pn[v]);
+                if (p.eE_on && in_box) uP += weight_of(*M, Sg[v]) * (Vn * Vn + M->w0r2dt2 * Pn[v] * Pn[v]);
               }
               VV::st(p.Pb + c * nmc + r, Pn);
             }
@@ -1157,7 +1172,7 @@ plain3d_kernel(const Step3DParams<T> p, const __grid_constant__ PlainMaps maps, 
             }
             if (pass == 0) {
               const T V0 = bPa[c] - bPb[c];
-              T num = M.cE * Ev[c] - M.W * bPa[c] + M.c2 * V0;
+              T num = drive_of(M, sgB) * Ev[c] - M.W * bPa[c] + M.c2 * V0;
               num = num - T(0.5) * dt * bsum;
               Vn = num * M.inv_A;
               Pn = bPa[c] + Vn;
@@ -1166,8 +1181,9 @@ plain3d_kernel(const Step3DParams<T> p, const __grid_constant__ PlainMaps maps, 
             }
           }
           if (p.eE_on && in_box) {
-            uP += M.rho_idt2 * (Vn * Vn + M.w0r2dt2 * Pn * Pn);
-            uB += M.rho_idt2 * ub;
+            const T wr = weight_of(M, sgB);
+            uP += wr * (Vn * Vn + M.w0r2dt2 * Pn * Pn);
+            uB += wr * ub;
           }
         }
       } else if constexpr (BATH) {
@@ -1189,16 +1205,17 @@ plain3d_kernel(const Step3DParams<T> p, const __grid_constant__ PlainMaps maps, 
           for (int c = 0; c < 3; ++c) bsum[c] = bsum[c] + sX[(6 + c) * XT + cellx];
         }
         T Pn[3], Vn[3], dP[3];
-        p_update(M, bPa, bPb, Ev, bsum, Pn, Vn, dP);
+        p_update(M, drive_of(M, sgB), bPa, bPb, Ev, bsum, Pn, Vn, dP);
 #pragma unroll
         for (int c = 0; c < 3; ++c) p.Pb[c * nmc + rB] = Pn[c];   // overwrites P^{n-1/2}
         T ub[3] = {T(0), T(0), T(0)};
         bath_modes(cfm, 0, nbm, yB, mstr, bY, bV, dP, ub);
         if (p.eE_on && in_box) {
+          const T wr = weight_of(M, sgB);
 #pragma unroll
           for (int c = 0; c < 3; ++c) {
-            uP += M.rho_idt2 * (Vn[c] * Vn[c] + M.w0r2dt2 * Pn[c] * Pn[c]);
-            uB += M.rho_idt2 * ub[c];
+            uP += wr * (Vn[c] * Vn[c] + M.w0r2dt2 * Pn[c] * Pn[c]);
+            uB += wr * ub[c];
           }
         }
       }
