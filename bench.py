@@ -583,8 +583,9 @@ def profile_form(name: str) -> int:
     """Short runs of one form for profiler captures: the 64-cavity batch for 64 steps in the shape
     the autotuner picks for it (C = 4, 896 threads), 16 steps of the 2048^2 differentiation form forward and
     reverse (checkpoints every 8 steps: about 2 GB of device memory), 8 steps of the N_b = 100
-    slab at 128 x 128 (about 1.5 GB), or 8 steps of the N_b = 16 precision workload at 128 x 128 x
-    384 (about 1.3 GB)."""
+    slab at 128 x 128 (about 1.5 GB), 8 steps of the N_b = 16 precision workload at 128 x 128 x
+    384 (about 1.3 GB), or 8 steps of the 256^3 slab with the sigma box of the sigma_map form
+    (about 1.7 GB)."""
     import torch
     from paper_2505_23963_gb300 import fdtdbath as fb
     torch.cuda.set_device(0)
@@ -603,6 +604,17 @@ def profile_form(name: str) -> int:
         sim.step(8)
         sim.sync()
         print(json.dumps({"form": "precision", "steps": 8, "bath_form": sim.bath_plain_kernel()}), flush=True)
+        sim.close()
+        return 0
+    if name == "sigma":
+        prob = wl.slab_3d(steps=8)
+        lb = next(m for m in prob["materials"] if m["kind"] == "lorentz_bath")
+        sim = fb.Simulation(prob, precision=32, energy_capacity=16)
+        sim.sigma_box((63.5, 63.5, lb["z"][0]), (191.5, 191.5, lb["z"][1]), 2.0 * lb["sigma"])
+        sim.step(8)
+        sim.sync()
+        print(json.dumps({"form": "sigma", "steps": 8, "plain": sim.plain_kernel(),
+                          "bath_form": sim.bath_plain_kernel()}), flush=True)
         sim.close()
         return 0
     if name == "batch":
@@ -831,7 +843,7 @@ def main():
     ap.add_argument("--quick", action="store_true",
                     help="FP32 step timing only (for profiler captures)")
     ap.add_argument("--grid", default="", help="override nx,ny of the workload (profiling)")
-    ap.add_argument("--profile-form", default="", choices=["", "batch", "adjoint", "manybath", "precision"],
+    ap.add_argument("--profile-form", default="", choices=["", "batch", "adjoint", "manybath", "precision", "sigma"],
                     help="run a short version of one form only (for profiler captures)")
     args = ap.parse_args()
     if args.warmup < 3:
