@@ -65,15 +65,15 @@ __device__ __forceinline__ uint32_t adj_div(uint32_t n, FastDiv f) { return (__u
 // of the adjoint sit on E_y and H_x only.  Then the adjoints of E_x, E_z, H_y and of the x / z
 // polarization and bath modes stay exactly zero (their y-differences vanish on the single row);
 // they are constants here, and the carried components are bit-identical to the general form's.
-// The TE form carries one component's P / bath adjoints: up to N_b = 8 it fits in 64 registers,
-// so four blocks share an SM (the kernel waits on memory, and more warps hide more of it).
+// The TE form carries one component's P / bath adjoints: up to N_b = 8 it runs three blocks per
+// SM (80 registers; at four blocks' 64 registers it spilled and its reverse sweep took 2% longer).
 //
 // LIGHT: the launch over the planes outside [ra, rb) (no material there: field and CPML adjoints
 // only), at eight blocks per SM; otherwise the launch over the cells [ra, rb).  The planes without
 // material are most of a cavity's grid and do little work per cell, so at the heavy launch's
 // occupancy they waited on memory latency.
 template <typename T, int NBMAX, bool TE = false, bool LIGHT = false>
-__global__ void __launch_bounds__(kAdjThreads, LIGHT ? 8 : ((TE && NBMAX <= 8) ? 4 : 0))
+__global__ void __launch_bounds__(kAdjThreads, LIGHT ? 8 : ((TE && NBMAX <= 8) ? 3 : 0))
 adjoint_k1(const AdjParams<T> p) {
   __shared__ double sg[kAdjThreads / 32][kAdjMaxGrad];
   constexpr int NBA = NBMAX > 0 ? NBMAX : 1;
