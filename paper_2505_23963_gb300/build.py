@@ -29,6 +29,7 @@ UNITS = [
     ("step3d_f32.cu", []),
     ("step3d_f64.cu", ["--fmad=false"]),
     ("plain3d_f32.cu", []),
+    ("plain3d_sig_f32.cu", []),
     ("plain3d_f64.cu", ["--fmad=false"]),
     ("te2d_f32.cu", []),
     ("reduce.cu", ["--fmad=false"]),

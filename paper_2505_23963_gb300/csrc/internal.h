@@ -215,6 +215,11 @@ struct BathMaps {
 // over them; at most 16 modes)
 int launch_bath3d_f32(const Step3DParams<float>& p, const PlainMaps& maps, const BathMaps& bmaps, int pcur, int ebuf,
                       int hbuf, int nchunks, int nb, int ybf, void* stream);
+// the same two launches with a per-cell sigma(r) map (p.sig), from their own translation unit
+int launch_plain3d_sig_f32(const Step3DParams<float>& p, const PlainMaps& maps, int ebuf, int hbuf, int nchunks,
+                           void* stream);
+int launch_bath3d_sig_f32(const Step3DParams<float>& p, const PlainMaps& maps, const BathMaps& bmaps, int pcur,
+                          int ebuf, int hbuf, int nchunks, int nb, int ybf, void* stream);
 // The y-invariant TE form's z-chunks (te2d.cuh): FP32, nx a multiple of kTe2dTileX, both
 // half-steps of a step; nb = 0 the chunks without bath modes, nb <= kTe2dMaxModes those with.
 constexpr int kTe2dTileX = 256;

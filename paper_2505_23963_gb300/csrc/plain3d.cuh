@@ -296,7 +296,11 @@ struct Plain3DLayout {
 // YB: bf16 bath storage -- one 32-bit word per mode, component and cell holding the value Y^n and
 // the increment V = Y^n - Y^{n-1} as a bf16 pair, updated in place (the general kernel's layout);
 // one level of words is staged instead of two.
-template <typename T, bool INC, int VX, int A, int NB = 0, bool YB = false>
+//
+// SIG: the simulation has a per-cell sigma(r) map (p.sig): each dispersive cell reads its sigma
+// for the drive term and the energy weight (the Lorentz-Bath forms one plane ahead).  A separate
+// instantiation, so that the kernels without a map carry none of it.
+template <typename T, bool INC, int VX, int A, int NB = 0, bool YB = false, bool SIG = false>
 __global__ void __launch_bounds__(Plain3DLayout<T, VX, A, NB>::threads, Plain3DLayout<T, VX, A, NB>::min_blocks)
 plain3d_kernel(const Step3DParams<T> p, const __grid_constant__ PlainMaps maps, const __grid_constant__ BathMaps bm,
                int pcur, int ebuf, int hbuf) {
@@ -626,9 +630,13 @@ plain3d_kernel(const Step3DParams<T> p, const __grid_constant__ PlainMaps maps, 
   };
   // a cell's eps0 w0^2 dt^2 sigma(r) and rho(r)/dt^2 (Eq. EOM_Lorentz's per-cell sigma; the
   // layer's own values without a map)
-  auto drive_of = [&](const MatK<T>& M, T sg) -> T { return p.sig ? M.dcE * sg : M.cE; };
+  auto drive_of = [&](const MatK<T>& M, T sg) -> T {
+    if constexpr (SIG) return M.dcE * sg;
+    else return M.cE;
+  };
   auto weight_of = [&](const MatK<T>& M, T sg) -> T {
-    return p.sig ? (sg > T(0) ? M.rho_s / sg : T(0)) : M.rho_idt2;
+    if constexpr (SIG) return sg > T(0) ? M.rho_s / sg : T(0);
+    else return M.rho_idt2;
   };
   // Eq. Pz_update-LB (increment form): P^{n+3/2}, its increment, and P^{n+3/2} - P^{n-1/2}
   auto p_update = [&](const MatK<T>& M, T cEr, const T (&bPa)[3], const T (&bPb)[3], const T (&Ev)[3],
@@ -745,6 +753,8 @@ plain3d_kernel(const Step3DParams<T> p, const __grid_constant__ PlainMaps maps, 
   } else if (secondary) {
     // ======== the bath form's second thread of each cell (SPLIT = 2): modes NBH.. of the cells of
     // tile row wrow; the same barriers as the first threads' planes ========
+    T sg_ahead = T(0);   // sigma(r) one bath plane ahead, as the first threads load it
+    int sg_ahead_k = -1;
     for (int g = 0; g < np; ++g) {
       const int k = zb + g;
       const int info = sInfo[g];
@@ -759,7 +769,14 @@ plain3d_kernel(const Step3DParams<T> p, const __grid_constant__ PlainMaps maps, 
         nbm = M.nb;
         yB = (int)M.ybase + (k - M.zlo) * plane + qxy;
         mstr = (int)M.ncell;
-        if (p.sig) sg = p.sig[(int)M.base + (k - M.zlo) * plane + qxy];
+        if constexpr (SIG) {
+          const int rS = (int)M.base + (k - M.zlo) * plane + qxy;
+          sg = sg_ahead_k == k ? sg_ahead : p.sig[rS];
+          if (k + 1 < M.zhi) {
+            sg_ahead = p.sig[rS + plane];
+            sg_ahead_k = k + 1;
+          }
+        }
         if (!plain::mbar_wait(&mbar[A], bpar)) {
           s_abort = 1;
           atomicExch(p.err, 1);
@@ -819,6 +836,10 @@ plain3d_kernel(const Step3DParams<T> p, const __grid_constant__ PlainMaps maps, 
     const unsigned oLJ = w + 1 < TY ? L::E_PL8 + (unsigned)((w + 1) * 4 + 3) * SZ : L::E_PLB + 3u * SZ;
     const unsigned cLJ = w + 1 < TY ? CP8 : CP1;
     const unsigned oLH = L::H_PL8 + (unsigned)(w * 4 + 3) * SZ;
+    // sigma(r) of the cell one bath plane ahead (with a map): loaded at the start of a plane, used
+    // by the next, so the load's latency is covered by a plane of work
+    [[maybe_unused]] T sg_ahead = T(0);
+    [[maybe_unused]] int sg_ahead_k = -1;
     auto body = [&](auto gen_t, auto bath_t, int g, int info) -> bool {
       constexpr bool GEN = decltype(gen_t)::value;
       constexpr bool BATH = NB > 0 && decltype(bath_t)::value;   // a Lorentz-Bath plane with modes
@@ -852,7 +873,13 @@ plain3d_kernel(const Step3DParams<T> p, const __grid_constant__ PlainMaps maps, 
         yB = (int)M.ybase + rl;
         mstr = (int)M.ncell;
         nbm = M.nb;
-        if (p.sig) sgB = p.sig[rB];
+        if constexpr (SIG) {
+          sgB = sg_ahead_k == k ? sg_ahead : p.sig[rB];
+          if (k + 1 < M.zhi) {
+            sg_ahead = p.sig[rB + plane];
+            sg_ahead_k = k + 1;
+          }
+        }
       }
       // without the helper: warp 0 also computes the halo row y0-1 (its CPML memories loaded here)
       [[maybe_unused]] T hpsx[VX], hpsy[VX];
@@ -1071,7 +1098,7 @@ plain3d_kernel(const Step3DParams<T> p, const __grid_constant__ PlainMaps maps, 
               T Pn[VX], Sg[VX];
 #pragma unroll
               for (int v = 0; v < VX; ++v) Sg[v] = T(0);
-              if (p.sig) VV::ld(p.sig + r, Sg);
+              if constexpr (SIG) VV::ld(p.sig + r, Sg);
 #pragma unroll
               for (int v = 0; v < VX; ++v) {
                 T Vn;
