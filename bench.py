@@ -426,6 +426,70 @@ def form_sigma_map(fb, stream, torch):
             "finite": finite}
 
 
+def form_temporal_blocking(fb, stream, torch):
+    """Two steps per pass (temporal blocking) on the 256^3 slab cavity's flux normalization run
+    (its layers removed: 16-cell CPML at both ends, vacuum, the phased plane source, the flux
+    monitor and the energy box; FP32): the two-steps-per-pass kernel against single steps of the
+    plain-plane kernel on the same grid.  The algorithmic bytes count every state word once per
+    step, as for the other forms, so a kernel that moves the state once per two steps can exceed
+    the copy bandwidth (frac_hbm above 1); the DRAM traffic of one two-step launch is recorded
+    beside it when a capture of the current source exists."""
+    import hashlib
+    hbm, _ = peaks()
+    prob = wl.vacuum_of(wl.slab_3d(steps=0))
+    cells = float(np.prod(prob["n"]))
+    byts = algorithmic_bytes(prob, 4)
+    out = {"workload": prob["name"], "unit": UNIT, "bytes_per_cell": byts / cells}
+    k = 40
+    for label, flag in (("two_step", "1"), ("single_step", "0")):
+        old = os.environ.get("FDTDBATH_TB")
+        if flag is None:
+            os.environ.pop("FDTDBATH_TB", None)
+        else:
+            os.environ["FDTDBATH_TB"] = flag
+        try:
+            with torch.cuda.stream(stream):
+                sim = fb.Simulation(prob, precision=32, stream=stream, energy_capacity=64)
+        finally:
+            if old is None:
+                os.environ.pop("FDTDBATH_TB", None)
+            else:
+                os.environ["FDTDBATH_TB"] = old
+        active = sim.tb2_kernel()
+        sim.step(5)   # odd: the H half-step stays pending, so the timed steps run in pairs
+        sim.sync()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        ev[0].record(stream)
+        sim.step(k)
+        ev[1].record(stream)
+        torch.cuda.synchronize()
+        ms = ev[0].elapsed_time(ev[1]) / k
+        finite = spectrum_is_finite(fb, sim)
+        sim.close()
+        out[label] = {"kernel": ("tb2_kernel<float> (one launch per two steps)" if active else
+                                 "plain3d_kernel<float> (one launch per step)"),
+                      "value": cells / (ms * 1e-3), "ms_per_step": ms,
+                      "achieved_GBs": byts / (ms * 1e-3) / 1e9,
+                      "frac_hbm": byts / (ms * 1e-3) / 1e9 / hbm, "finite": finite}
+    out["value"] = out["two_step"]["value"]
+    out["speedup"] = out["single_step"]["ms_per_step"] / out["two_step"]["ms_per_step"]
+    traffic = None
+    prof = os.path.join(ROOT, "profiles", "tb2_f32_vacuum256_traffic.json")
+    if os.path.exists(prof):
+        try:
+            with open(prof) as f:
+                rec = json.load(f)
+            with open(os.path.join(ROOT, "paper_2505_23963_gb300", "csrc", "tb2.cuh"), "rb") as f:
+                cur = hashlib.sha256(f.read()).hexdigest()[:16]
+            if rec.get("source_sha256_16") == cur:
+                traffic = rec.get("dram_bytes_per_launch")
+        except Exception:
+            traffic = None
+    out["dram_bytes_per_two_step_launch"] = traffic
+    out["algorithmic_bytes_per_two_steps"] = 2 * byts
+    return out
+
+
 def form_cavity_1d(fb, stream, torch):
     """The plain method on the 1D Fabry-Perot cavity (Nz = 2000, N_b = 16, 500 DFT frequencies,
     energy every step), 20000 steps on the persistent 1D kernel in FP64 and FP32: steps/s and
@@ -585,7 +649,8 @@ def profile_form(name: str) -> int:
     reverse (checkpoints every 8 steps: about 2 GB of device memory), 8 steps of the N_b = 100
     slab at 128 x 128 (about 1.5 GB), 8 steps of the N_b = 16 precision workload at 128 x 128 x
     384 (about 1.3 GB), or 8 steps of the 256^3 slab with the sigma box of the sigma_map form
-    (about 1.7 GB)."""
+    (about 1.7 GB), 9 steps of the 256^3 flux normalization run (about 1 GB; the two-step
+    kernel), or the temporal-blocking form itself."""
     import torch
     from paper_2505_23963_gb300 import fdtdbath as fb
     torch.cuda.set_device(0)
@@ -616,6 +681,20 @@ def profile_form(name: str) -> int:
         print(json.dumps({"form": "sigma", "steps": 8, "plain": sim.plain_kernel(),
                           "bath_form": sim.bath_plain_kernel()}), flush=True)
         sim.close()
+        return 0
+    if name == "tb2":
+        # the 256^3 flux normalization run: one single step, then four two-step launches
+        os.environ["FDTDBATH_TB"] = "1"
+        sim = fb.Simulation(wl.vacuum_of(wl.slab_3d(steps=9)), precision=32, energy_capacity=16)
+        sim.step(9)
+        sim.sync()
+        print(json.dumps({"form": "tb2", "steps": 9, "two_step": sim.tb2_kernel()}), flush=True)
+        sim.close()
+        return 0
+    if name == "tb2_form":
+        stream = torch.cuda.Stream()
+        print(json.dumps({"form": "temporal_blocking",
+                          **form_temporal_blocking(fb, stream, torch)}), flush=True)
         return 0
     if name == "batch":
         b = fb.Batch(wl.batch_sweep(steps=64), precision=32, energy_every=10, cluster_ctas=4,
@@ -814,6 +893,7 @@ def run_ours(args):
         for name, fn in (("precision", lambda: form_precision(fb, stream, torch)),
                          ("many_bath", lambda: form_many_bath(fb, stream, torch)),
                          ("sigma_map", lambda: form_sigma_map(fb, stream, torch)),
+                         ("temporal_blocking", lambda: form_temporal_blocking(fb, stream, torch)),
                          ("batch", lambda: form_batch(fb, torch)),
                          ("adjoint", lambda: form_adjoint(fb, torch)),
                          ("cavity_1d", lambda: form_cavity_1d(fb, stream, torch))):
@@ -843,7 +923,7 @@ def main():
     ap.add_argument("--quick", action="store_true",
                     help="FP32 step timing only (for profiler captures)")
     ap.add_argument("--grid", default="", help="override nx,ny of the workload (profiling)")
-    ap.add_argument("--profile-form", default="", choices=["", "batch", "adjoint", "manybath", "precision", "sigma"],
+    ap.add_argument("--profile-form", default="", choices=["", "batch", "adjoint", "manybath", "precision", "sigma", "tb2", "tb2_form"],
                     help="run a short version of one form only (for profiler captures)")
     args = ap.parse_args()
     if args.warmup < 3:

@@ -32,6 +32,8 @@ UNITS = [
     ("plain3d_sig_f32.cu", []),
     ("plain3d_f64.cu", ["--fmad=false"]),
     ("te2d_f32.cu", []),
+    ("tb2_f32.cu", []),
+    ("tb2_f64.cu", ["--fmad=false"]),
     ("reduce.cu", ["--fmad=false"]),
     ("noalloc.cu", ["--fmad=false"]),
     ("peak.cu", []),

@@ -3,7 +3,8 @@
 // State layout in HBM (one simulation):
 //   E, H        : two buffers each (ping-pong), [3][nz][ny][nx]; one launch reads the
 //                 "in" buffer (halo neighbours included) and writes the "out" buffer.
-//   psiE        : CPML memories of the E update, [2][2*npml][ny][nx], updated in place.
+//   psiE        : CPML memories of the E update, [2][2*npml][ny][nx], updated in place by the
+//                 single-step kernels; a second buffer for the two-steps-per-pass kernel.
 //   psiH        : CPML memories of the H update, two buffers, [2][2*npml+1][ny][nx].
 //   D           : FP64 path only, [3][material cells] (material planes only).
 //   Pa / Pb     : P^{n+1/2} and P^{n-1/2} slots; the new P^{n+3/2} overwrites the older
@@ -229,6 +230,25 @@ int launch_te2d_f32(const Step3DParams<float>& p, int nchunks, int nb, void* str
 int launch_te2d_fused_f32(const Step3DParams<float>& p, int nplain, int nbath, int nb, void* stream);
 int launch_plain3d_f64(const Step3DParams<double>& p, const PlainMaps& maps, int ebuf, int hbuf, int nchunks,
                        void* stream);
+
+// Two steps per pass (tb2.cuh) over grids without polarizable material: 32 x 8 tiles, grids tiled
+// exactly by them.  p describes step n (fields and CPML memories in / out, its sources and partial
+// rows); the rest, step n+1.  Every output goes to the other buffer: E, H, psiH as p.Eout / p.Hout /
+// p.psiHout, the E-side memories to psiEout.
+constexpr int kTbTX = 32, kTbTY = 8;
+template <typename T>
+struct Tb2Params {
+  Step3DParams<T> p;
+  T* psiEout;
+  T src_a2[kMaxSrc], src_b2[kMaxSrc];    // source amplitudes of step n+1
+  double* mon_partial_E2;                // partial rows of step n+1
+  double* mon_partial_H2;
+  double* en_partial_E2;
+  double* en_partial_H2;
+  int eE_on2, eH_on2;
+};
+int launch_tb2_f32(const Tb2Params<float>& q, int nchunks, void* stream);
+int launch_tb2_f64(const Tb2Params<double>& q, int nchunks, void* stream);
 
 // ---- discrete adjoint (adjoint.cu) ----
 // One reverse step of the exact transpose of the forward step (D-free form), applied to the

@@ -455,6 +455,11 @@ class Simulation:
         """Whether the TE form's bath-free chunks run the register-streaming kernel (query key 10)."""
         return query(self.h, 10) == 1
 
+    def tb2_kernel(self) -> bool:
+        """Whether pairs of steps run in one launch of the two-steps-per-pass kernel (query key 12:
+        grids without polarizable material tiled exactly by 32 x 8 tiles)."""
+        return query(self.h, 12) == 1
+
     def bath_plain_kernel(self) -> bool:
         """Whether the z-chunks with bath modes run the plain-plane kernel's Lorentz-Bath form
         (query key 9)."""
