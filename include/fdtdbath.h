@@ -258,7 +258,12 @@ int fdtdbath_bath_form(int32_t shape, double frequency, double gamma, int32_t nu
  * layer).  Key 10: whether the z-chunks of a simulation in the TE form run the TE form's
  * register-streaming kernel (FP32, nx a multiple of 256, no source plane inside a layer; the
  * chunks with bath modes only with FP32 bath storage and at most 8 modes per material).  Key 11:
- * whether a per-cell sigma(r) map is set (FDTDBATH_FIELD_SIGMA). */
+ * whether a per-cell sigma(r) map is set (FDTDBATH_FIELD_SIGMA).  Key 12: whether pairs of steps
+ * run as one launch of the two-steps-per-pass kernel (temporal blocking; taken when the
+ * environment variable FDTDBATH_TB=1 is set at creation, on grids without materials, of at least
+ * 8 rows, nx a multiple of 32 and ny of 8): fdtdbath_step then advances the state two steps per
+ * launch (a single step where one is left over or no H half-step is pending), with the same
+ * results -- FP64 state bit for bit -- as single steps. */
 int64_t fdtdbath_query(const fdtdbath_sim *sim, int32_t key);
 
 /* Energy (U_EM, U_P, U_bath) of planes z_lo <= k < z_hi of the current state -- the same

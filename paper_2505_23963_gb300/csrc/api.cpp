@@ -285,6 +285,30 @@ int plan_chunks(fdtdbath_sim* s, int zc, bool balanced, int plain_zc, int bath_z
   return (int)starts.size() - 1;
 }
 
+// Chunk length for the two-steps-per-pass kernel on a grid without polarizable material (one z
+// range): the number of chunks n whose CTAs (tiles x n) fill the last wave of resident CTAs best,
+// weighed against the three ghost planes each chunk recomputes: maximise
+// (waves / ceil(waves)) * (L / (L + 3)), L = nz / n, n = 1 .. 16, chunks of at most 64 planes.
+int tb_chunk_planes(const fdtdbath_sim* s) {
+  int sms = 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s->device) != cudaSuccess || sms <= 0) return 32;
+  const double slots = (double)sms * (s->prec == 64 ? 1 : 3);   // resident CTAs (shared memory)
+  const double tiles = (double)(s->nx / kTbTX) * (double)(s->ny / kTbTY);
+  int best = 32;
+  double best_eff = -1.0;
+  for (int n = 1; n <= 16; ++n) {
+    const double L = (double)s->nz / n;
+    if (L > 64.0 || L < 4.0) continue;
+    const double waves = tiles * n / slots;
+    const double eff = waves / std::ceil(waves) * (L / (L + 3.0));
+    if (eff > best_eff + 1e-12) {
+      best_eff = eff;
+      best = (int)std::ceil(L);
+    }
+  }
+  return best;
+}
+
 // Source amplitude at t_n: A exp(-u^2/(2 tau^2)) sin(2 pi nu u), u = t_n - t0 (no phase), or
 // the pair (A g sin(theta), A g cos(theta)) combined with cos/sin of the phase table.
 void source_amp(const HostSrc& q, double t, double* a, double* b) {
@@ -1183,7 +1207,7 @@ int fdtdbath_create(const fdtdbath_grid* grid, double resolution, double courant
   }
   int plain_zc = 0, bath_zc = 0, bath_nmin = 1;
   if (s->plain_ok) {
-    plain_zc = s->tb_ok ? 32 : 16;
+    plain_zc = s->tb_ok ? tb_chunk_planes(s) : 16;
     if (const char* e = std::getenv("FDTDBATH_PLAIN_ZCHUNK")) plain_zc = std::min(64, std::max(1, std::atoi(e)));
   }
   if (s->bath_plain) {

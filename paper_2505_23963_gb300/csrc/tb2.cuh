@@ -36,9 +36,10 @@
 namespace fdtdbath {
 
 constexpr int kTbThreads = kTbTX * kTbTY;   // Tb2Params, kTbTX, kTbTY: internal.h
-constexpr int kTbAhead = 2;                   // frames requested this many planes ahead
-constexpr int kTbRingE = kTbAhead + 2;        // E^{n-1/2} frames: planes k .. k+1+kTbAhead
-constexpr int kTbRingH = kTbAhead + 1;        // H^{n-1} frames: planes k .. k+kTbAhead
+constexpr int kTbRingE = 3;    // E^{n-1/2} frames: planes k, k+1 (read), k+2 (landing)
+constexpr int kTbRingH = 2;    // H^{n-1} frames: plane k (read), k+1 (landing)
+constexpr int kTbRingH1 = 3;   // H^n and the H-side memories after step n: planes k-2 .. k
+constexpr int kTbRingE1 = 2;   // E^{n+1/2}: planes k-1, k
 constexpr int kTbFX = kTbTX + 8, kTbFY = kTbTY + 4, kTbFE = kTbFX * kTbFY, kTbFH = kTbFX * (kTbFY - 1);
 // halo cells (box minus tile) of the three boxes, in frame columns [c0, c1) and rows [r0, r1)
 constexpr int kTbH1c0 = 2, kTbH1c1 = kTbTX + 5, kTbH1r0 = 0, kTbH1r1 = kTbTY + 3;
@@ -49,10 +50,11 @@ static_assert(tb_halo(kTbH1c0, kTbH1c1, kTbH1r0, kTbH1r1) <= kTbThreads, "one H1
 static_assert(tb_halo(kTbE1c0, kTbE1c1, kTbE1r0, kTbE1r1) <= kTbThreads, "one E1 halo cell per thread");
 static_assert(tb_halo(kTbH2c0, kTbH2c1, kTbH2r0, kTbH2r1) <= kTbThreads, "one H2 halo cell per thread");
 
-// shared-memory elements: E^{n-1/2} and H^{n-1} rings, H^n and E^{n+1/2} of two planes, H^{n+1} of
-// one plane (three components each), the H-side memories after step n of two planes (two
-// components); then eight doubles of block-sum scratch
-constexpr int kTbSmemElems = kTbRingE * 3 * kTbFE + kTbRingH * 3 * kTbFH + 2 * 3 * kTbFH * 2 + 3 * kTbFH + 2 * 2 * kTbFH;
+// shared-memory elements: the E^{n-1/2}, H^{n-1}, H^n and E^{n+1/2} rings and H^{n+1} of one plane
+// (three components each), the ring of the H-side memories after step n (two components); then
+// eight doubles of block-sum scratch
+constexpr int kTbSmemElems = kTbRingE * 3 * kTbFE + (kTbRingH + kTbRingH1 + kTbRingE1) * 3 * kTbFH + 3 * kTbFH +
+                             kTbRingH1 * 2 * kTbFH;
 template <typename T>
 constexpr size_t tb2_smem_bytes() {
   return (size_t)kTbSmemElems * sizeof(T) + 8 * sizeof(double);
@@ -83,13 +85,13 @@ __global__ void __launch_bounds__(kTbThreads, sizeof(T) == 4 ? 3 : 1) tb2_kernel
   constexpr int NPH = (kTbFY - 1) * CPR;             // H frame: rows 0 .. kTbFY-2
   constexpr int CE = (NPE + kTbThreads - 1) / kTbThreads, CH = (NPH + kTbThreads - 1) / kTbThreads;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* sE0 = reinterpret_cast<T*>(smem_raw);           // [kTbRingE][3][FE]
-  T* sH0 = sE0 + kTbRingE * 3 * FE;                  // [kTbRingH][3][F]
-  T* sH1 = sH0 + kTbRingH * 3 * F;                   // [2][3][F]   H^n
-  T* sE1 = sH1 + 2 * 3 * F;                          // [2][3][F]   E^{n+1/2}
-  T* sH2 = sE1 + 2 * 3 * F;                          // [3][F]      H^{n+1}
-  T* sPH = sH2 + 3 * F;                              // [2][2][F]   H-side memories after step n
-  double* sred = reinterpret_cast<double*>(sPH + 2 * 2 * F);
+  T* sE0 = reinterpret_cast<T*>(smem_raw);           // [kTbRingE][3][FE]  E^{n-1/2}
+  T* sH0 = sE0 + kTbRingE * 3 * FE;                  // [kTbRingH][3][F]   H^{n-1}
+  T* sH1 = sH0 + kTbRingH * 3 * F;                   // [kTbRingH1][3][F]  H^n
+  T* sE1 = sH1 + kTbRingH1 * 3 * F;                  // [kTbRingE1][3][F]  E^{n+1/2}
+  T* sH2 = sE1 + kTbRingE1 * 3 * F;                  // [3][F]             H^{n+1}
+  T* sPH = sH2 + 3 * F;                              // [kTbRingH1][2][F]  H-side memories after step n
+  double* sred = reinterpret_cast<double*>(sPH + kTbRingH1 * 2 * F);
 
   const int tx = threadIdx.x, ty = threadIdx.y;
   const int tid = ty * kTbTX + tx;
@@ -114,9 +116,13 @@ __global__ void __launch_bounds__(kTbThreads, sizeof(T) == 4 ? 3 : 1) tb2_kernel
   constexpr int NH1 = tb_halo(kTbH1c0, kTbH1c1, kTbH1r0, kTbH1r1);
   constexpr int NE1 = tb_halo(kTbE1c0, kTbE1c1, kTbE1r0, kTbE1r1);
   constexpr int NH2 = tb_halo(kTbH2c0, kTbH2c1, kTbH2r0, kTbH2r1);
+  // the two boxes of each phase on different warps: H^n halo cells on threads 0.., H^{n+1} halo
+  // cells on threads 160.. (phase 1), E^{n+1/2} halo cells on the last threads (phase 2)
+  constexpr int H2T0 = 160, E1T0 = kTbThreads - NE1;
+  static_assert(NH1 <= H2T0 && H2T0 + NH2 <= kTbThreads, "halo threads");
   const int h1_f = tid < NH1 ? tb_halo_cell(tid, kTbH1c0, kTbH1c1, kTbH1r0, kTbH1r1) : -1;
-  const int e1_f = tid < NE1 ? tb_halo_cell(tid, kTbE1c0, kTbE1c1, kTbE1r0, kTbE1r1) : -1;
-  const int h2_f = tid < NH2 ? tb_halo_cell(tid, kTbH2c0, kTbH2c1, kTbH2r0, kTbH2r1) : -1;
+  const int e1_f = tid >= E1T0 ? tb_halo_cell(tid - E1T0, kTbE1c0, kTbE1c1, kTbE1r0, kTbE1r1) : -1;
+  const int h2_f = (tid >= H2T0 && tid < H2T0 + NH2) ? tb_halo_cell(tid - H2T0, kTbH2c0, kTbH2c1, kTbH2r0, kTbH2r1) : -1;
   const int h1_g = h1_f >= 0 ? gcol(h1_f) : 0;
   const int e1_g = e1_f >= 0 ? gcol(e1_f) : 0;
   const int h2_g = h2_f >= 0 ? gcol(h2_f) : 0;
@@ -175,8 +181,10 @@ __global__ void __launch_bounds__(kTbThreads, sizeof(T) == 4 ? 3 : 1) tb2_kernel
     }
   };
 
-  // planes: H^n from kA (two planes below the chunk; none below the grid), E^{n+1/2} from a1,
-  // H^{n+1} from a1 and E^{n+3/2} on the chunk; the march ends at plane ze (level 1) / ze-1
+  // planes: H^n from kA (two planes below the chunk; none below the grid) to ze, E^{n+1/2} from a1
+  // to ze, H^{n+1} from a1 and E^{n+3/2} on the chunk.  Iteration k computes, in two phases with
+  // one barrier between them, {H^n(k), H^{n+1}(k-2)} and then {E^{n+1/2}(k), E^{n+3/2}(k-2)}: the
+  // second step lags two planes behind the first, so no phase waits for its own results.
   const int kA = zb >= 2 ? zb - 2 : 0;
   const int a1 = zb >= 1 ? zb - 1 : 0;
   const int kE_last = ze + 1;                        // last E^{n-1/2} plane read
@@ -209,44 +217,68 @@ __global__ void __launch_bounds__(kTbThreads, sizeof(T) == 4 ? 3 : 1) tb2_kernel
     return false;
   };
   auto in_box = [&](int k) { return k >= p.ebox_lo && k < p.ebox_hi; };
+  // H-side monitor partials of a plane from the own cells' values (rows of one step)
+  auto mon_H = [&](int k, T vx, T vy, double* rows) {
+    for (int mm = 0; mm < p.nmon; ++mm) {
+      const int zm = p.mon_z[mm];
+      if (k == zm - 1 || k == zm) {
+        const int off = (k == zm) ? 1 : 0;
+        const double sx = block_sum((double)vx, sred);
+        const double sy = block_sum((double)vy, sred);
+        if (tid == 0 && rows) {
+          rows[(int64_t)(4 * mm + off) * nbxy + bxy] = sx;
+          rows[(int64_t)(4 * mm + 2 + off) * nbxy + bxy] = sy;
+        }
+      }
+    }
+  };
+  auto mon_E = [&](int k, T vx, T vy, double* rows) {
+    for (int mm = 0; mm < p.nmon; ++mm) {
+      if (k == p.mon_z[mm]) {
+        const double sx = block_sum((double)vx, sred);
+        const double sy = block_sum((double)vy, sred);
+        if (tid == 0 && rows) {
+          rows[(int64_t)(2 * mm) * nbxy + bxy] = sx;
+          rows[(int64_t)(2 * mm + 1) * nbxy + bxy] = sy;
+        }
+      }
+    }
+  };
 
   // per-thread energy sums of both steps (state precision, block-reduced in FP64 at the end)
   T uE1 = T(0), uH1 = T(0), uE2 = T(0), uH2 = T(0);
-  T hxm2 = T(0), hym2 = T(0);        // H^{n+1} of the plane below at the own cell
-  T pe_prev[2] = {T(0), T(0)};       // E-side memories after step n at the own cell, plane k-1
-  T pe_new[2] = {T(0), T(0)};
+  // own-cell values carried between planes: H^{n+1} of the plane below E^{n+3/2}'s plane, and
+  // E^{n+1/2} with the E-side memories after step n of the two planes before the current one
+  T hm[2] = {T(0), T(0)};
+  T q0[3] = {T(0), T(0), T(0)}, q1[3] = {T(0), T(0), T(0)};
+  T pq0[2] = {T(0), T(0)}, pq1[2] = {T(0), T(0)};
 
-  // prologue: group g carries E(kA+1+g) and H(kA+g); group 0 also E(kA)
   issueE(kA);
   issueE(kA + 1);
   issueH(kA);
   cp_async_commit();
-#pragma unroll
-  for (int g = 1; g < kTbAhead; ++g) {
-    if (kA + 1 + g <= kE_last) issueE(kA + 1 + g);
-    if (kA + g <= kH_last) issueH(kA + g);
+
+  for (int k = kA; k <= ze + 1; ++k) {
+    cp_async_wait<0>();   // E(k+1) and H(k), requested one plane ago
+    __syncthreads();      // ... and every read of the previous plane's phases is done
+    if (k + 2 <= kE_last) issueE(k + 2);   // into the slot of E(k-1)
+    if (k + 1 <= kH_last) issueH(k + 1);   // into the slot of H(k-1)
     cp_async_commit();
-  }
 
-  for (int k = kA; k <= ze; ++k) {
-    {
-      const int ke = k + 1 + kTbAhead, kh = k + kTbAhead;
-      if (ke <= kE_last) issueE(ke);
-      if (kh <= kH_last) issueH(kh);
-    }
-    cp_async_commit();
-    cp_async_wait<kTbAhead>();   // group k - kA: E(k+1) and H(k) have landed
-    __syncthreads();
+    const int m = k - 2;                                   // plane of the second step
+    const bool doH1 = k <= ze && k < nz;
+    const bool doE1 = k >= a1 && k <= ze && k < nz;
+    const bool own1 = k >= zb && k < ze;                   // plane k belongs to the chunk
+    const bool doL2 = m >= a1 && m < ze;                   // H^{n+1}(m)
+    const bool out2 = m >= zb && m < ze;                   // E^{n+3/2}(m), stored outputs
+    T* h1 = sH1 + (k % kTbRingH1) * 3 * F;                 // H^n(k)
+    const T* h1m = sH1 + ((k + 2) % kTbRingH1) * 3 * F;    // H^n(k-1)
+    T* ph1 = sPH + (k % kTbRingH1) * 2 * F;
+    T* e1 = sE1 + (k & 1) * 3 * F;                         // E^{n+1/2}(k)
 
-    const bool l1 = k < nz;                         // level 1 (step n) at plane k
-    const bool own1 = k >= zb && k < ze;            // plane k belongs to the chunk
-    T* h1 = sH1 + (k & 1) * 3 * F;                  // H^n(k)
-    const T* h1m = sH1 + ((k - 1) & 1) * 3 * F;     // H^n(k-1)
-    T* e1 = sE1 + (k & 1) * 3 * F;                  // E^{n+1/2}(k)
-    T* ph1 = sPH + (k & 1) * 2 * F;                 // H-side memories after step n, plane k
-
-    // ---------------- H^n(k) on the H1 box ----------------
-    if (l1) {
+    // ---------------- phase 1: H^n(k) on the H1 box, H^{n+1}(m) on the H2 box ----------------
+    T h1own[3] = {T(0), T(0), T(0)}, h2own[3] = {T(0), T(0), T(0)};
+    if (doH1) {
       const T* e0 = sE0 + (k % kTbRingE) * 3 * FE;
       const T* e0n = sE0 + ((k + 1) % kTbRingE) * 3 * FE;
       const T* hin = sH0 + (k % kTbRingH) * 3 * F;
@@ -256,7 +288,7 @@ __global__ void __launch_bounds__(kTbThreads, sizeof(T) == 4 ? 3 : 1) tb2_kernel
         b = p.pmlH[2 * k];
         c = p.pmlH[2 * k + 1];
       }
-      auto cell = [&](int f, int g) {
+      auto cell = [&](int f, int g, T* o) {
         HIn<T> e;
         e.ex0 = e0[f];
         e.ex_k1 = e0n[f];
@@ -281,33 +313,127 @@ __global__ void __launch_bounds__(kTbThreads, sizeof(T) == 4 ? 3 : 1) tb2_kernel
           ph1[f] = psx;
           ph1[F + f] = psy;
         }
+        o[0] = hx;
+        o[1] = hy;
+        o[2] = hz;
       };
-      cell(own_f, own_g);
-      if (h1_f >= 0) cell(h1_f, h1_g);
+      cell(own_f, own_g, h1own);
+      if (h1_f >= 0) {
+        T d[3];
+        cell(h1_f, h1_g, d);
+      }
     }
-    __syncthreads();
-    // H-side monitor and energy partials of step n (H^n of the chunk's planes)
-    if (l1 && own1) {
-      for (int m = 0; m < p.nmon; ++m) {
-        const int zm = p.mon_z[m];
-        if (k == zm - 1 || k == zm) {
-          const int off = (k == zm) ? 1 : 0;
-          const double sx = block_sum((double)h1[own_f], sred);
-          const double sy = block_sum((double)h1[F + own_f], sred);
-          if (tid == 0 && p.mon_partial_H) {
-            p.mon_partial_H[(int64_t)(4 * m + off) * nbxy + bxy] = sx;
-            p.mon_partial_H[(int64_t)(4 * m + 2 + off) * nbxy + bxy] = sy;
+    if (doL2) {
+      const T* ea = sE1 + (m & 1) * 3 * F;                 // E^{n+1/2}(m)
+      const T* eb = sE1 + ((m + 1) & 1) * 3 * F;           // E^{n+1/2}(m+1)
+      const T* ha = sH1 + ((k + 1) % kTbRingH1) * 3 * F;   // H^n(m)
+      const T* pa = sPH + ((k + 1) % kTbRingH1) * 2 * F;
+      const int ip = psiH_plane(m, nz, p.npml);
+      T b = T(1), c = T(0);
+      if (ip >= 0) {
+        b = p.pmlH[2 * m];
+        c = p.pmlH[2 * m + 1];
+      }
+      auto cell = [&](int f, int g, bool write_out, T* o) {
+        HIn<T> e;
+        e.ex0 = ea[f];
+        e.ex_k1 = eb[f];
+        e.ex_j1 = ea[f + FX];
+        e.ey0 = ea[F + f];
+        e.ey_k1 = eb[F + f];
+        e.ey_i1 = ea[F + f + 1];
+        e.ez0 = ea[2 * F + f];
+        e.ez_j1 = ea[2 * F + f + FX];
+        e.ez_i1 = ea[2 * F + f + 1];
+        T hx = ha[f], hy = ha[F + f], hz = ha[2 * F + f];
+        T psx = T(0), psy = T(0);
+        if (ip >= 0) {
+          psx = pa[f];
+          psy = pa[F + f];
+        }
+        h_update<T>(e, hx, hy, hz, &psx, &psy, b, c, ip >= 0, S);
+        sH2[f] = hx;
+        sH2[F + f] = hy;
+        sH2[2 * F + f] = hz;
+        if (write_out) {
+          const int qo = m * plane + g;
+          p.Hout[qo] = hx;
+          p.Hout[ncell + qo] = hy;
+          p.Hout[2 * ncell + qo] = hz;
+          if (ip >= 0) {
+            p.psiHout[ip * plane + g] = psx;
+            p.psiHout[pstrH + ip * plane + g] = psy;
           }
         }
-      }
-      if (p.eH_on && in_box(k)) {
-        const T a = h1[own_f], b = h1[F + own_f], c = h1[2 * F + own_f];
-        uH1 += a * a + b * b + c * c;
+        o[0] = hx;
+        o[1] = hy;
+        o[2] = hz;
+      };
+      cell(own_f, own_g, out2, h2own);
+      if (h2_f >= 0) {
+        T d[3];
+        cell(h2_f, h2_g, false, d);
       }
     }
+    // H-side monitor and energy partials: step n (H^n of the chunk's planes), step n+1 (H^{n+1})
+    if (doH1 && own1) {
+      mon_H(k, h1own[0], h1own[1], p.mon_partial_H);
+      if (p.eH_on && in_box(k)) uH1 += h1own[0] * h1own[0] + h1own[1] * h1own[1] + h1own[2] * h1own[2];
+    }
+    if (out2) {
+      mon_H(m, h2own[0], h2own[1], q.mon_partial_H2);
+      if (q.eH_on2 && in_box(m)) uH2 += h2own[0] * h2own[0] + h2own[1] * h2own[1] + h2own[2] * h2own[2];
+    }
+    __syncthreads();
 
-    // ---------------- E^{n+1/2}(k) on the E1 box ----------------
-    if (l1 && k >= a1) {
+    // ---------------- phase 2: E^{n+3/2}(m) on the tile, E^{n+1/2}(k) on the E1 box ----------------
+    if (out2) {
+      const int f = own_f;
+      const T Hx = sH2[f], Hy = sH2[F + f], Hz = sH2[2 * F + f];
+      const T dyHz = Hz - sH2[2 * F + f - FX];
+      const T dzHy = Hy - hm[1];
+      const T dzHx = Hx - hm[0];
+      const T dxHz = Hz - sH2[2 * F + f - 1];
+      const T dxHy = Hy - sH2[F + f - 1];
+      const T dyHx = Hx - sH2[f - FX];
+      T curl[3];
+      const int ip = psiE_plane(m, nz, p.npml);
+      if (ip >= 0) {
+        const T b = p.pmlE[2 * m], c = p.pmlE[2 * m + 1];
+        const int pq = ip * plane + own_g;
+        const T px = b * pq0[0] + c * dzHy;
+        const T py = b * pq0[1] + c * dzHx;
+        q.psiEout[pq] = px;
+        q.psiEout[pstrE + pq] = py;
+        curl[0] = dyHz - (dzHy + px);
+        curl[1] = (dzHx + py) - dxHz;
+      } else {
+        curl[0] = dyHz - dzHy;
+        curl[1] = dzHx - dxHz;
+      }
+      curl[2] = dxHy - dyHx;
+      T J[3];
+      bool has[3];
+      if (src_plane(m)) {
+        source(m, own_g, q.src_a2, q.src_b2, J, has);
+      } else {
+        J[0] = J[1] = J[2] = T(0);
+        has[0] = has[1] = has[2] = false;
+      }
+      T Ev[3];
+      const int qo = m * plane + own_g;
+#pragma unroll
+      for (int cc = 0; cc < 3; ++cc) {
+        T e = q0[cc] + S * curl[cc];
+        if (has[cc]) e = e + dt * J[cc];
+        Ev[cc] = e;
+        p.Eout[cc * ncell + qo] = e;
+      }
+      if (q.eE_on2 && in_box(m)) uE2 += T(1) * (Ev[0] * Ev[0] + Ev[1] * Ev[1] + Ev[2] * Ev[2]);
+      mon_E(m, Ev[0], Ev[1], q.mon_partial_E2);
+    }
+    T e1own[3] = {T(0), T(0), T(0)}, pe1own[2] = {T(0), T(0)};
+    if (doE1) {
       const T* e0 = sE0 + (k % kTbRingE) * 3 * FE;
       const bool below0 = k == 0;                   // no H below the grid
       const int ip = psiE_plane(k, nz, p.npml);
@@ -357,160 +483,34 @@ __global__ void __launch_bounds__(kTbThreads, sizeof(T) == 4 ? 3 : 1) tb2_kernel
           e1[cc * F + f] = e;
         }
       };
-      T Ev[3], dummy_pe[2];
-      cell(own_f, own_g, Ev, pe_new);
+      cell(own_f, own_g, e1own, pe1own);
       if (e1_f >= 0) {
-        T Eh[3];
-        cell(e1_f, e1_g, Eh, dummy_pe);
+        T d[3], dp[2];
+        cell(e1_f, e1_g, d, dp);
       }
       if (own1) {
-        if (p.eE_on && in_box(k)) uE1 += T(1) * (Ev[0] * Ev[0] + Ev[1] * Ev[1] + Ev[2] * Ev[2]);
-        for (int m = 0; m < p.nmon; ++m) {
-          if (k == p.mon_z[m]) {
-            const double sx = block_sum((double)Ev[0], sred);
-            const double sy = block_sum((double)Ev[1], sred);
-            if (tid == 0 && p.mon_partial_E) {
-              p.mon_partial_E[(int64_t)(2 * m) * nbxy + bxy] = sx;
-              p.mon_partial_E[(int64_t)(2 * m + 1) * nbxy + bxy] = sy;
-            }
-          }
-        }
+        if (p.eE_on && in_box(k)) uE1 += T(1) * (e1own[0] * e1own[0] + e1own[1] * e1own[1] + e1own[2] * e1own[2]);
+        mon_E(k, e1own[0], e1own[1], p.mon_partial_E);
       }
-    } else if (!l1) {
-      // plane nz: no E above the grid
+    } else if (k == nz) {
+      // plane nz: no E above the grid (read by H^{n+1}(nz-1) on the next plane)
       for (int t = tid; t < 3 * F; t += kTbThreads) e1[t] = T(0);
     }
-    __syncthreads();
-
-    // ---------------- H^{n+1}(k-1) on the H2 box ----------------
-    const int km = k - 1;
-    if (km >= a1) {
-      const T* ea = sE1 + (km & 1) * 3 * F;         // E^{n+1/2}(k-1)
-      const T* eb = sE1 + (k & 1) * 3 * F;          // E^{n+1/2}(k)
-      const T* ha = sH1 + (km & 1) * 3 * F;         // H^n(k-1)
-      const T* pa = sPH + (km & 1) * 2 * F;
-      const int ip = psiH_plane(km, nz, p.npml);
-      T b = T(1), c = T(0);
-      if (ip >= 0) {
-        b = p.pmlH[2 * km];
-        c = p.pmlH[2 * km + 1];
-      }
-      auto cell = [&](int f, int g, bool write_out) {
-        HIn<T> e;
-        e.ex0 = ea[f];
-        e.ex_k1 = eb[f];
-        e.ex_j1 = ea[f + FX];
-        e.ey0 = ea[F + f];
-        e.ey_k1 = eb[F + f];
-        e.ey_i1 = ea[F + f + 1];
-        e.ez0 = ea[2 * F + f];
-        e.ez_j1 = ea[2 * F + f + FX];
-        e.ez_i1 = ea[2 * F + f + 1];
-        T hx = ha[f], hy = ha[F + f], hz = ha[2 * F + f];
-        T psx = T(0), psy = T(0);
-        if (ip >= 0) {
-          psx = pa[f];
-          psy = pa[F + f];
-        }
-        h_update<T>(e, hx, hy, hz, &psx, &psy, b, c, ip >= 0, S);
-        sH2[f] = hx;
-        sH2[F + f] = hy;
-        sH2[2 * F + f] = hz;
-        if (write_out) {
-          const int qo = km * plane + g;
-          p.Hout[qo] = hx;
-          p.Hout[ncell + qo] = hy;
-          p.Hout[2 * ncell + qo] = hz;
-          if (ip >= 0) {
-            p.psiHout[ip * plane + g] = psx;
-            p.psiHout[pstrH + ip * plane + g] = psy;
-          }
-        }
-      };
-      cell(own_f, own_g, km >= zb);
-      if (h2_f >= 0) cell(h2_f, h2_g, false);
-    }
-    __syncthreads();
-
-    // ---------------- E^{n+3/2}(k-1) on the tile ----------------
-    if (km >= zb) {
-      // H-side monitor and energy partials of step n+1 (H^{n+1} of the chunk's planes)
-      for (int m = 0; m < p.nmon; ++m) {
-        const int zm = p.mon_z[m];
-        if (km == zm - 1 || km == zm) {
-          const int off = (km == zm) ? 1 : 0;
-          const double sx = block_sum((double)sH2[own_f], sred);
-          const double sy = block_sum((double)sH2[F + own_f], sred);
-          if (tid == 0 && q.mon_partial_H2) {
-            q.mon_partial_H2[(int64_t)(4 * m + off) * nbxy + bxy] = sx;
-            q.mon_partial_H2[(int64_t)(4 * m + 2 + off) * nbxy + bxy] = sy;
-          }
-        }
-      }
-      if (q.eH_on2 && in_box(km)) {
-        const T a = sH2[own_f], b = sH2[F + own_f], c = sH2[2 * F + own_f];
-        uH2 += a * a + b * b + c * c;
-      }
-      const int f = own_f;
-      const T* ea = sE1 + (km & 1) * 3 * F;
-      const T Hx = sH2[f], Hy = sH2[F + f], Hz = sH2[2 * F + f];
-      const T dyHz = Hz - sH2[2 * F + f - FX];
-      const T dzHy = Hy - hym2;
-      const T dzHx = Hx - hxm2;
-      const T dxHz = Hz - sH2[2 * F + f - 1];
-      const T dxHy = Hy - sH2[F + f - 1];
-      const T dyHx = Hx - sH2[f - FX];
-      T curl[3];
-      const int ip = psiE_plane(km, nz, p.npml);
-      if (ip >= 0) {
-        const T b = p.pmlE[2 * km], c = p.pmlE[2 * km + 1];
-        const int pq = ip * plane + own_g;
-        const T px = b * pe_prev[0] + c * dzHy;
-        const T py = b * pe_prev[1] + c * dzHx;
-        q.psiEout[pq] = px;
-        q.psiEout[pstrE + pq] = py;
-        curl[0] = dyHz - (dzHy + px);
-        curl[1] = (dzHx + py) - dxHz;
-      } else {
-        curl[0] = dyHz - dzHy;
-        curl[1] = dzHx - dxHz;
-      }
-      curl[2] = dxHy - dyHx;
-      T J[3];
-      bool has[3];
-      if (src_plane(km)) {
-        source(km, own_g, q.src_a2, q.src_b2, J, has);
-      } else {
-        J[0] = J[1] = J[2] = T(0);
-        has[0] = has[1] = has[2] = false;
-      }
-      T Ev[3];
-      const int qo = km * plane + own_g;
+    if (k >= a1) {   // the carried own values move one plane on
 #pragma unroll
       for (int cc = 0; cc < 3; ++cc) {
-        T e = ea[cc * F + f] + S * curl[cc];
-        if (has[cc]) e = e + dt * J[cc];
-        Ev[cc] = e;
-        p.Eout[cc * ncell + qo] = e;
+        q0[cc] = q1[cc];
+        q1[cc] = e1own[cc];
       }
-      if (q.eE_on2 && in_box(km)) uE2 += T(1) * (Ev[0] * Ev[0] + Ev[1] * Ev[1] + Ev[2] * Ev[2]);
-      for (int m = 0; m < p.nmon; ++m) {
-        if (km == p.mon_z[m]) {
-          const double sx = block_sum((double)Ev[0], sred);
-          const double sy = block_sum((double)Ev[1], sred);
-          if (tid == 0 && q.mon_partial_E2) {
-            q.mon_partial_E2[(int64_t)(2 * m) * nbxy + bxy] = sx;
-            q.mon_partial_E2[(int64_t)(2 * m + 1) * nbxy + bxy] = sy;
-          }
-        }
-      }
+      pq0[0] = pq1[0];
+      pq0[1] = pq1[1];
+      pq1[0] = pe1own[0];
+      pq1[1] = pe1own[1];
     }
-    if (km >= a1) {
-      hxm2 = sH2[own_f];
-      hym2 = sH2[F + own_f];
+    if (doL2) {
+      hm[0] = h2own[0];
+      hm[1] = h2own[1];
     }
-    pe_prev[0] = pe_new[0];
-    pe_prev[1] = pe_new[1];
   }
   cp_async_wait<0>();
 
